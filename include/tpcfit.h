@@ -1,0 +1,152 @@
+/*
+ * tpcfit -- batched Kalman fit of TPC track candidates on one GB300 GPU.
+ *
+ * The operation: every track candidate of a time frame (its clusters, at most
+ * one per pad row, ordered by row) is fitted as a helix in a uniform Bz field.
+ * The track state is propagated from pad row to pad row in the local frame of
+ * its TPC sector, rotated into the next sector's frame when the candidate
+ * crosses a sector boundary, and updated with each 2D cluster (y, z) while
+ * chi2 accumulates.  The fit consists of an outward pass from the seed and an
+ * inward refit.  Source: the paper names track propagation through the
+ * magnetic field as the shared component of TPC tracking (Sec. 4) and the time
+ * frame as the processing unit (Sec. 1).  The deterministic mode follows the
+ * rules of Sec. 2; per-time-frame constants live in GPU constant memory as in
+ * Sec. 4.1.
+ *
+ * Conventions (all calls):
+ *   - Units cm, GeV/c, T.  Track state p = (y, z, sin phi, tan lambda, q/pt)
+ *     at local x = X_row, in the frame of a sector; the covariance is packed
+ *     lower-triangular: (00, 10, 11, 20, 21, 22, 30, 31, 32, 33, 40, .., 44).
+ *   - Sectors 0-17 are the A side (z >= 0), 18-35 the C side, sector s centred
+ *     at azimuth ((s mod 18) + 0.5) * sector_width.  rowsec = row << 6 | sector.
+ *   - Arrays are structure-of-arrays: params_out[5][n_tracks] means component
+ *     c of track i at params_out[c * n_tracks + i].
+ *   - "device" pointers must be CUDA device memory of the current device;
+ *     "host" pointers ordinary host memory.  The library never frees caller
+ *     memory and keeps no pointer to it after a call returns, except where a
+ *     call says otherwise.
+ *   - stream is a cudaStream_t (NULL = the legacy default stream).  Every call
+ *     that takes a stream only enqueues work on it and returns; argument
+ *     errors are returned synchronously before anything is enqueued.
+ *   - A handle is not thread-safe; use one handle per host thread.
+ */
+#ifndef TPCFIT_H_
+#define TPCFIT_H_
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  TPCFIT_OK = 0,
+  TPCFIT_EINVAL = 1,   /* bad argument (null pointer, negative or inconsistent size) */
+  TPCFIT_ECUDA = 2,    /* a CUDA runtime call failed */
+  TPCFIT_ENOMEM = 3,   /* device allocation failed */
+  TPCFIT_EDEVICE = 4,  /* a kernel found invalid input (see tpcfit_get_status) */
+  TPCFIT_ETIMEOUT = 5, /* a bounded device-side wait ran out */
+  TPCFIT_ESTATE = 6    /* call not allowed in the handle's current state */
+} tpcfit_status;
+
+/* Detector geometry (copied at tpcfit_create; row_x is a host array). */
+typedef struct {
+  int32_t n_sectors;       /* must be 36 */
+  int32_t n_rows;          /* 1..152 */
+  const double* row_x;     /* host [n_rows]: local x of each pad-row plane, cm, ascending */
+  double sector_width_deg; /* 20 */
+  double z_max;            /* 250 cm (informational) */
+} tpcfit_geometry;
+
+/* Clusters of a time frame, device SoA, track-major (a track's clusters are
+ * contiguous and ordered by increasing row). */
+typedef struct {
+  const float* y;          /* device [n_hits] local y, cm */
+  const float* z;          /* device [n_hits] z, cm */
+  const uint16_t* rowsec;  /* device [n_hits] row << 6 | sector */
+  int64_t n_hits;
+} tpcfit_hits;
+
+typedef struct tpcfit_handle tpcfit_handle;
+
+/* Create a fitter on the current CUDA device for the given geometry and field.
+ * Builds the geometry tables (pad-row x, sector rotation cos/sin) on the host in
+ * FP64, rounds them to FP32 and uploads them to every kernel module's constant
+ * memory.  Returns EINVAL for a bad geometry, ECUDA/ENOMEM on CUDA failure. */
+tpcfit_status tpcfit_create(const tpcfit_geometry* geometry, double bz_tesla, tpcfit_handle** out);
+
+/* Release the handle and its device scratch.  Synchronises the device first.
+ * NULL is ignored. */
+void tpcfit_destroy(tpcfit_handle* h);
+
+/* Run-time switch between the fast FP32 mode (0, default: FMA contraction,
+ * approximate division and square root) and the deterministic mode (1: IEEE
+ * FP32 without contraction, fixed operation order, results bit-identical to the
+ * strict-FP32 host reference and independent of launch configuration), as the
+ * run-time part of the deterministic mode of Sec. 2. */
+tpcfit_status tpcfit_set_mode(tpcfit_handle* h, int deterministic);
+
+/* Launch configuration of the fit: lanes_per_track (1 = one track per lane)
+ * and rows_per_stage (hits per track staged into shared memory per refill:
+ * 4, 8 or 16).  sort_by_length != 0 orders tracks by length before the fit so
+ * that a warp's tracks finish together.  In deterministic mode the results do
+ * not depend on these choices.  EINVAL for unsupported values. */
+tpcfit_status tpcfit_set_config(tpcfit_handle* h, int lanes_per_track, int rows_per_stage, int sort_by_length);
+
+/* Alignment offsets d[36][152][2] (dy, dz per sector and row, cm) subtracted
+ * from every cluster before the fit.  d is a device pointer; its contents are
+ * copied into the handle on `stream` (so the caller may overwrite d after the
+ * copy has run).  d = NULL sets all offsets to zero.  Offsets are constant per
+ * time frame, like the calibration constants of Sec. 4.1. */
+tpcfit_status tpcfit_set_alignment(tpcfit_handle* h, const float* d, void* stream);
+
+/* Pre-size the handle's device scratch for up to max_tracks tracks (the length
+ * permutation) so that later fits allocate nothing, e.g. during CUDA-graph
+ * capture.  Synchronous. */
+tpcfit_status tpcfit_reserve(tpcfit_handle* h, int64_t max_tracks, int64_t max_hits);
+
+/* Fit n_tracks tracks.
+ *   track_offsets: device int32 [n_tracks + 1], non-decreasing, offsets into the
+ *                  hit arrays; track i owns hits [off[i], off[i+1]).
+ *   seeds:         device float [5][n_tracks], state at the track's first hit.
+ *   params_out:    device float [5][n_tracks]  inward-refit state at the first hit
+ *                  (x = X of that hit's row, frame of that hit's sector);
+ *   cov_out:       device float [15][n_tracks] its covariance (packed);
+ *   chi2_out:      device float [n_tracks]     chi2 of the inward refit;
+ *   ndf_out:       device int32 [n_tracks]     2 * clusters used - 5.
+ * A track whose fit fails numerically (|sin phi| >= 0.999, a backward step
+ * through a sector rotation, fewer than 3 clusters) is not an error: it gets
+ * ndf = -1 and NaN parameters, covariance and chi2.  A track with invalid input
+ * (offsets out of order or beyond n_hits, row >= n_rows, sector >= 36) gets
+ * ndf = -2 and NaNs, and the handle's error word records it (tpcfit_get_status).
+ * n_tracks = 0 is a no-op.  May allocate scratch (see tpcfit_reserve). */
+tpcfit_status tpcfit_fit(tpcfit_handle* h, const tpcfit_hits* hits, const int32_t* track_offsets, int32_t n_tracks,
+                         const float* seeds, float* params_out, float* cov_out, float* chi2_out, int32_t* ndf_out,
+                         void* stream);
+
+/* Fit with HOST buffers: copies hits, offsets and seeds to the device, fits and
+ * copies the outputs back, all on `stream`, then synchronises the stream.
+ * Same argument meaning as tpcfit_fit with every array in host memory
+ * (pinned memory gives asynchronous copies).  Device staging buffers are owned
+ * by the handle and grown as needed. */
+tpcfit_status tpcfit_fit_host(tpcfit_handle* h, const float* y, const float* z, const uint16_t* rowsec,
+                              int64_t n_hits, const int32_t* track_offsets, int32_t n_tracks, const float* seeds,
+                              float* params_out, float* cov_out, float* chi2_out, int32_t* ndf_out, void* stream);
+
+/* Read (and clear) the handle's device error word: the first invalid-input code
+ * a kernel recorded (0 = none; 1 = bad offsets, 2 = row or sector out of range)
+ * and the track it was found on (-1 if none).  Synchronises `stream`.  Returns
+ * EDEVICE if an error was recorded, OK otherwise. */
+tpcfit_status tpcfit_get_status(tpcfit_handle* h, void* stream, int32_t* err_code, int64_t* err_track);
+
+/* Static description of a status code. */
+const char* tpcfit_status_string(tpcfit_status s);
+
+/* Library version as MAJOR*10000 + MINOR*100 + PATCH. */
+int32_t tpcfit_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* TPCFIT_H_ */

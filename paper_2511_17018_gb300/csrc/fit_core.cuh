@@ -1,0 +1,488 @@
+// Device code of the batched TPC track fit.  Included by exactly one kernel
+// module per mode; the module's compile flags select the arithmetic:
+//   fit_fast.cu : FMA contraction, approximate division / square root, FTZ;
+//   fit_det.cu  : -fmad=false -prec-div=true -prec-sqrt=true -ftz=false, i.e.
+//                 the deterministic-mode rules of Sec. 2 (no FMA, IEEE
+//                 operations, fixed order, functions without a deterministic
+//                 FP32 result evaluated in FP64 by a fixed routine).
+// The module defines TPCFIT_DET (0/1) and TPCFIT_NS before including this.
+//
+// The fit (per track): extended Kalman filter in the local frame of a TPC
+// sector, state p = (y, z, sin phi, tan lambda, q/pt), covariance kept as a
+// square-root factor C = L L^T (Potter form).  Outward pass from the seed with
+// C0 = 100 I, updating at the first cluster first; inward refit from the
+// outward result with C reset to C0 and chi2 reset; the output is the inward
+// state at the first cluster, ndf = 2 n_used - 5.  Each step: rotation into the
+// next cluster's sector frame if needed, analytic helix propagation to that pad
+// row with its Jacobian, L <- J L, two scalar Potter updates (y then z).
+//
+// Work mapping: one track per lane; a warp stages the next `RPS` clusters of
+// its 32 tracks into shared memory with coalesced loads (alignment offsets
+// subtracted on the way), then each lane runs its steps from shared memory.
+// Tracks are processed in an order that puts tracks of equal length into the
+// same warp (see length_order.cu) so that a warp's lanes finish together.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "internal.h"
+
+#ifndef TPCFIT_DET
+#error "define TPCFIT_DET before including fit_core.cuh"
+#endif
+
+namespace tpcfit {
+namespace TPCFIT_NS {
+
+__constant__ GeoConst c_geo;
+
+struct Jac {
+  bool rot;
+  float yy, ys, yq, zy, zs, zt, zq, sy, ss, sq;
+};
+
+// ---------------------------------------------------------------- arcsin pieces
+// FP64 arcsin: Maclaurin series for |u| <= 1/2, asin u = pi/2 - 2 asin(sqrt((1-u)/2))
+// above (Abramowitz & Stegun 4.4.40-4.4.41); coefficients from the constant bank.
+__device__ __forceinline__ double asin_series_f64(double u) {
+  const double q = u * u;
+  double acc = c_geo.asin_a[29];
+#pragma unroll 1
+  for (int n = 28; n >= 0; --n) acc = acc * q + c_geo.asin_a[n];
+  return acc * u;
+}
+
+__device__ __noinline__ double asin_f64(double u) {
+  const double au = u < 0.0 ? -u : u;
+  double r;
+  if (au <= 0.5) {
+    r = asin_series_f64(au);
+  } else {
+    const double h = sqrt((1.0 - au) * 0.5);
+    r = 1.5707963267948966 - 2.0 * asin_series_f64(h);
+  }
+  return u < 0.0 ? -r : r;
+}
+
+// asin(u)/u: Horner in u^2 over the Maclaurin coefficients (c0..c6) for
+// |u| <= 1/4, else the FP64 island (deterministic) or asinf (fast).
+__device__ __forceinline__ float asinc_f(float u) {
+  const float au = u < 0.0f ? -u : u;
+  if (au <= 0.25f) {
+    const float c0 = 1.0f;
+    const float c1 = static_cast<float>(1.0 / 6.0);
+    const float c2 = static_cast<float>(3.0 / 40.0);
+    const float c3 = static_cast<float>(5.0 / 112.0);
+    const float c4 = static_cast<float>(35.0 / 1152.0);
+    const float c5 = static_cast<float>(63.0 / 2816.0);
+    const float c6 = static_cast<float>(231.0 / 13312.0);
+    const float q = u * u;
+    float acc = c6;
+    acc = acc * q + c5;
+    acc = acc * q + c4;
+    acc = acc * q + c3;
+    acc = acc * q + c2;
+    acc = acc * q + c1;
+    acc = acc * q + c0;
+    return acc;
+  }
+#if TPCFIT_DET
+  const double ud = (double)u;
+  return (float)(asin_f64(ud) / ud);
+#else
+  return asinf(u) / u;
+#endif
+}
+
+// ---------------------------------------------------------------- geometry in smem
+struct SmemTables {
+  float row_x[kMaxRows];
+  float rot_c[kNSide * kNSide];
+  float rot_s[kNSide * kNSide];
+};
+
+__device__ __forceinline__ void load_tables(SmemTables& t) {
+  for (int i = threadIdx.x; i < kMaxRows; i += blockDim.x) t.row_x[i] = c_geo.row_x[i];
+  for (int i = threadIdx.x; i < kNSide * kNSide; i += blockDim.x) {
+    t.rot_c[i] = c_geo.rot_c[i];
+    t.rot_s[i] = c_geo.rot_s[i];
+  }
+}
+
+// ---------------------------------------------------------------- one prediction step
+// From state (p, x) in sector-frame a (mod 18) to pad row X in frame b: optional
+// rotation at the current point, then helix propagation at fixed Bz.  Returns
+// false, leaving nothing changed, if the step is impossible.
+__device__ __forceinline__ bool predict(const SmemTables& T, const float pin[5], float xin, int a, int b, float X,
+                                        float pout[5], Jac& J) {
+  const float kappa = c_geo.kappa;
+  const float maxsnp = c_geo.max_snp;
+  float x1 = xin, y1 = pin[0], s1 = pin[2];
+  const float t = pin[3];
+  const float q = pin[4];
+  J.rot = (a != b);
+  float cprev = 0.0f, crot = 0.0f, ca = 1.0f, sa = 0.0f;
+  if (J.rot) {
+    ca = T.rot_c[a * kNSide + b];
+    sa = T.rot_s[a * kNSide + b];
+    const float s = pin[2];
+    const float c = sqrtf((1.0f - s) * (1.0f + s));
+    const float xr = xin * ca + pin[0] * sa;
+    const float yr = pin[0] * ca - xin * sa;
+    const float sr = s * ca - c * sa;
+    const float cr = c * ca + s * sa;
+    if (!(cr > 0.0f)) return false;
+    if (!(fabsf(sr) < maxsnp)) return false;
+    x1 = xr;
+    y1 = yr;
+    s1 = sr;
+    cprev = c;
+    crot = cr;
+  }
+  const float dx = X - x1;
+  const float k = q * kappa;
+  const float kdx = k * dx;
+  const float s2 = s1 + kdx;
+  if (!(fabsf(s2) < maxsnp)) return false;
+  const float c1 = sqrtf((1.0f - s1) * (1.0f + s1));
+  const float c2 = sqrtf((1.0f - s2) * (1.0f + s2));
+  const float Tm = (s1 + s2) / (c1 + c2);
+  const float w = c1 + s1 * Tm;
+  const float sig = kdx * w;
+  const float dl = (dx * w) * asinc_f(sig);
+  pout[0] = y1 + dx * Tm;
+  pout[1] = pin[1] + t * dl;
+  pout[2] = s2;
+  pout[3] = t;
+  pout[4] = q;
+  const float ic1 = 1.0f / c1;
+  const float ic2 = 1.0f / c2;
+  const float tt = 1.0f + Tm * Tm;
+  J.ys = (dx * tt) * ((ic1 + ic2) * 0.5f);
+  J.yq = ((dx * kappa) * dx) * (tt * (ic2 * 0.5f));
+  J.zs = (t * dx) * (Tm * (ic1 * ic2));
+  J.zt = dl;
+  float Lk;  // d(path)/dk
+  if (fabsf(kdx) < 0.01f) {
+    const float i2 = ic1 * ic1;
+    const float i3 = i2 * ic1;
+    const float i5 = i3 * i2;
+    const float i7 = i5 * i2;
+    const float s1s = s1 * s1;
+    const float a1 = (s1 * i3) * 0.5f;
+    const float a2 = ((1.0f + 2.0f * s1s) * i5) * static_cast<float>(1.0 / 3.0);
+    const float a3 = ((s1 * (3.0f + 2.0f * s1s)) * i7) * 0.125f;
+    Lk = (dx * dx) * (a1 + kdx * (a2 + kdx * a3));
+  } else {
+    Lk = (dx * ic2 - dl) / k;
+  }
+  J.zq = (t * kappa) * Lk;
+  J.sq = dx * kappa;
+  if (J.rot) {
+    const float rr = crot / cprev;
+    J.yy = ca - sa * (s2 * ic2);
+    J.zy = -(sa * (t * ic2));
+    J.sy = -(sa * k);
+    J.ss = rr;
+    J.ys = J.ys * rr;
+    J.zs = J.zs * rr;
+  } else {
+    J.yy = 1.0f;
+    J.zy = 0.0f;
+    J.sy = 0.0f;
+    J.ss = 1.0f;
+  }
+  return true;
+}
+
+// L <- J L (rows t, q of J are identity).
+__device__ __forceinline__ void transport(float L[5][5], const Jac& J) {
+  if (!J.rot) {
+#pragma unroll
+    for (int c = 0; c < 5; ++c) {
+      const float ny = (L[0][c] + J.ys * L[2][c]) + J.yq * L[4][c];
+      const float nz = ((L[1][c] + J.zs * L[2][c]) + J.zt * L[3][c]) + J.zq * L[4][c];
+      const float ns = L[2][c] + J.sq * L[4][c];
+      L[0][c] = ny;
+      L[1][c] = nz;
+      L[2][c] = ns;
+    }
+  } else {
+#pragma unroll
+    for (int c = 0; c < 5; ++c) {
+      const float ny = (J.yy * L[0][c] + J.ys * L[2][c]) + J.yq * L[4][c];
+      const float nz = (((J.zy * L[0][c] + L[1][c]) + J.zs * L[2][c]) + J.zt * L[3][c]) + J.zq * L[4][c];
+      const float ns = (J.sy * L[0][c] + J.ss * L[2][c]) + J.sq * L[4][c];
+      L[0][c] = ny;
+      L[1][c] = nz;
+      L[2][c] = ns;
+    }
+  }
+}
+
+// Potter scalar update of component H (0 = y, 1 = z) with measured value mv.
+template <int H>
+__device__ __forceinline__ void scalar_update(float p[5], float L[5][5], float& chi2, float mv) {
+  const float v = c_geo.v_meas;
+  float a[5];
+#pragma unroll
+  for (int c = 0; c < 5; ++c) a[c] = L[H][c];
+  float s2 = v + a[0] * a[0];
+#pragma unroll
+  for (int c = 1; c < 5; ++c) s2 = s2 + a[c] * a[c];
+  const float alpha = 1.0f / s2;
+  const float r = mv - p[H];
+  float K[5];
+#pragma unroll
+  for (int i = 0; i < 5; ++i) {
+    float la = L[i][0] * a[0];
+#pragma unroll
+    for (int c = 1; c < 5; ++c) la = la + L[i][c] * a[c];
+    K[i] = la * alpha;
+  }
+#pragma unroll
+  for (int i = 0; i < 5; ++i) p[i] = p[i] + K[i] * r;
+  chi2 = chi2 + (r * r) * alpha;
+  const float beta = sqrtf(alpha * v);
+  const float gamma = 1.0f / (1.0f + beta);
+#pragma unroll
+  for (int i = 0; i < 5; ++i) {
+    if (i == H) continue;
+    const float gk = gamma * K[i];
+#pragma unroll
+    for (int c = 0; c < 5; ++c) L[i][c] = L[i][c] - gk * a[c];
+  }
+#pragma unroll
+  for (int c = 0; c < 5; ++c) L[H][c] = a[c] * beta;
+}
+
+__device__ __forceinline__ void reset_factor(float L[5][5]) {
+#pragma unroll
+  for (int i = 0; i < 5; ++i)
+#pragma unroll
+    for (int c = 0; c < 5; ++c) L[i][c] = (i == c) ? c_geo.l0 : 0.0f;
+}
+
+__device__ __forceinline__ void record_error(unsigned long long* err, unsigned long long code, int64_t track) {
+  const unsigned long long v = (code << 56) | ((unsigned long long)track & 0x00FFFFFFFFFFFFFFull);
+  atomicCAS(err, 0ull, v);
+}
+
+// ---------------------------------------------------------------- the fit kernel
+// Lane state across the two passes.
+struct TrackState {
+  float p[5];
+  float L[5][5];
+  float x;
+  float chi2;
+  int sec;      // sector (mod 18) of the current frame
+  int used;
+};
+
+// Shared staging of RPS clusters for each of a warp's 32 tracks; row pitch
+// RPS + 1 keeps both the loader's and the consumer's accesses conflict-free.
+template <int RPS>
+struct WarpStage {
+  float m0[kWarp][RPS + 1];
+  float m1[kWarp][RPS + 1];
+  int rs[kWarp][RPS + 1];
+};
+
+// Stage local steps [c0, c0 + RPS) of every lane's pass: lane t's step i is hit
+// base_t + start_t + dir * i (valid for i < count_t).  Loads are coalesced per
+// track; the alignment offsets are subtracted here.  Invalid (row, sector)
+// values are passed on as rs = -1.
+template <int RPS>
+__device__ __forceinline__ void stage(WarpStage<RPS>& st, const FitArgs& a, int64_t my_first, int my_count, int dir,
+                                      int c0, int lane) {
+#pragma unroll
+  for (int it = 0; it < RPS; ++it) {
+    const int e = it * kWarp + lane;
+    const int t = e / RPS;   // owner lane
+    const int k = e % RPS;   // step within the chunk
+    const int64_t first_t = __shfl_sync(0xffffffffu, my_first, t);
+    const int count_t = __shfl_sync(0xffffffffu, my_count, t);
+    const int i = c0 + k;
+    if (i < count_t) {
+      const int64_t h = first_t + (int64_t)dir * i;
+      const int rsv = (int)__ldg(a.rowsec + h);
+      const int row = rsv >> 6;
+      const int sec = rsv & 63;
+      float m0 = __ldg(a.y + h);
+      float m1 = __ldg(a.z + h);
+      int out = -1;
+      if (row < c_geo.n_rows && sec < kNSectors) {
+        const int key = (sec * kMaxRows + row) * 2;
+        m0 = m0 - __ldg(a.align + key);
+        m1 = m1 - __ldg(a.align + key + 1);
+        out = rsv;
+      }
+      st.m0[t][k] = m0;
+      st.m1[t][k] = m1;
+      st.rs[t][k] = out;
+    }
+  }
+}
+
+template <int RPS>
+__global__ void __launch_bounds__(256, 2) fit_kernel(FitArgs a) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  SmemTables& T = *reinterpret_cast<SmemTables*>(smem_raw);
+  WarpStage<RPS>* stages = reinterpret_cast<WarpStage<RPS>*>(smem_raw + sizeof(SmemTables));
+  load_tables(T);
+  __syncthreads();
+
+  const int lane = threadIdx.x & 31;
+  WarpStage<RPS>& st = stages[threadIdx.x >> 5];
+  const int64_t slot = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const bool have = slot < a.n_tracks;
+  const int32_t trk = have ? (a.perm ? a.perm[slot] : (int32_t)slot) : 0;
+
+  // ---- per-track input checks
+  int status = have ? 0 : 1;  // 0 fitting, 1 idle, 2 numerical failure, 3 invalid input
+  int64_t begin = 0;
+  int n = 0;
+  if (have) {
+    const int64_t b = a.off[trk];
+    const int64_t e = a.off[trk + 1];
+    if (b < 0 || e < b || e > a.n_hits) {
+      status = 3;
+      record_error(a.err, kErrOffsets, trk);
+    } else {
+      begin = b;
+      n = (int)(e - b);
+      if (n < 1) status = 2;
+    }
+  }
+  TrackState S;
+  int last = 0;
+  if (status == 0) {
+#pragma unroll
+    for (int c = 0; c < 5; ++c) S.p[c] = __ldg(a.seeds + (int64_t)c * a.n_tracks + trk);
+    if (!(fabsf(S.p[2]) < c_geo.max_snp)) status = 2;
+  }
+
+  // ---- two passes: outward (dir +1 from hit 0) and inward (dir -1 from `last`)
+#pragma unroll 1
+  for (int pass = 0; pass < 2; ++pass) {
+    const int dir = pass == 0 ? 1 : -1;
+    const int64_t my_first = begin + (pass == 0 ? 0 : last);
+    const int my_count = (status == 0) ? (pass == 0 ? n : last + 1) : 0;
+    bool go = status == 0;
+    if (go) {
+      reset_factor(S.L);
+      S.chi2 = 0.0f;
+      S.used = 0;
+    }
+    int count_max = my_count;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) count_max = max(count_max, __shfl_xor_sync(0xffffffffu, count_max, o));
+#pragma unroll 1
+    for (int c0 = 0; c0 < count_max; c0 += RPS) {
+      __syncwarp();
+      stage<RPS>(st, a, my_first, my_count, dir, c0, lane);
+      __syncwarp();
+#pragma unroll 1
+      for (int k = 0; k < RPS; ++k) {
+        const int i = c0 + k;
+        if (!go || i >= my_count) continue;
+        const int rsv = st.rs[lane][k];
+        if (rsv < 0) {
+          status = 3;
+          go = false;
+          record_error(a.err, kErrRowSector, trk);
+          continue;
+        }
+        const float m0 = st.m0[lane][k];
+        const float m1 = st.m1[lane][k];
+        const int row = rsv >> 6;
+        const int sec18 = (rsv & 63) % kNSide;
+        if (i == 0) {
+          // first cluster of the pass: the state sits on its row already
+          S.x = T.row_x[row];
+          S.sec = sec18;
+        } else {
+          float pn[5];
+          Jac J;
+          if (!predict(T, S.p, S.x, S.sec, sec18, T.row_x[row], pn, J)) {
+            go = false;
+            if (pass == 1) status = 2;  // the inward pass must reach the first cluster
+            continue;
+          }
+#pragma unroll
+          for (int c = 0; c < 5; ++c) S.p[c] = pn[c];
+          S.x = T.row_x[row];
+          S.sec = sec18;
+          transport(S.L, J);
+        }
+        scalar_update<0>(S.p, S.L, S.chi2, m0);
+        scalar_update<1>(S.p, S.L, S.chi2, m1);
+        S.used += 1;
+        if (pass == 0) last = i;
+      }
+    }
+  }
+
+  // ---- outputs at the track's slot
+  if (!have) return;
+  const int64_t N = a.n_tracks;
+  if (status == 0 && S.used >= 3) {
+#pragma unroll
+    for (int c = 0; c < 5; ++c) a.params[(int64_t)c * N + trk] = S.p[c];
+    int e = 0;
+#pragma unroll
+    for (int i = 0; i < 5; ++i)
+#pragma unroll
+      for (int j = 0; j <= i; ++j) {
+        float acc = S.L[i][0] * S.L[j][0];
+#pragma unroll
+        for (int c = 1; c < 5; ++c) acc = acc + S.L[i][c] * S.L[j][c];
+        a.cov[(int64_t)e * N + trk] = acc;
+        ++e;
+      }
+    a.chi2[trk] = S.chi2;
+    a.ndf[trk] = 2 * S.used - 5;
+  } else {
+    const float qnan = __int_as_float(0x7fc00000);
+#pragma unroll
+    for (int c = 0; c < 5; ++c) a.params[(int64_t)c * N + trk] = qnan;
+#pragma unroll
+    for (int e = 0; e < 15; ++e) a.cov[(int64_t)e * N + trk] = qnan;
+    a.chi2[trk] = qnan;
+    a.ndf[trk] = (status == 3) ? -2 : -1;
+  }
+}
+
+template <int RPS>
+cudaError_t launch_rps(const FitArgs& a, cudaStream_t s) {
+  constexpr int kThreads = 256;
+  const size_t smem = sizeof(SmemTables) + (kThreads / kWarp) * sizeof(WarpStage<RPS>);
+  static bool configured = false;
+  if (!configured) {
+    cudaError_t e = cudaFuncSetAttribute(fit_kernel<RPS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    configured = true;
+  }
+  const int64_t blocks = (a.n_tracks + kThreads - 1) / kThreads;
+  fit_kernel<RPS><<<(unsigned)blocks, kThreads, smem, s>>>(a);
+  return cudaGetLastError();
+}
+
+inline cudaError_t launch(const FitArgs& a, int lanes_per_track, int rps, cudaStream_t s) {
+  if (a.n_tracks <= 0) return cudaSuccess;
+  if (lanes_per_track != 1) return cudaErrorInvalidValue;
+  switch (rps) {
+    case 4: return launch_rps<4>(a, s);
+    case 8: return launch_rps<8>(a, s);
+    case 16: return launch_rps<16>(a, s);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+cudaError_t upload(const GeoConst& g, cudaStream_t s) {
+  return cudaMemcpyToSymbolAsync(c_geo, &g, sizeof(GeoConst), 0, cudaMemcpyHostToDevice, s);
+}
+
+}  // namespace TPCFIT_NS
+}  // namespace tpcfit

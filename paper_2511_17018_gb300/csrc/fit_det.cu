@@ -1,0 +1,14 @@
+// Deterministic fit module: compiled as its own unit with -fmad=false
+// -prec-div=true -prec-sqrt=true -ftz=false (the compile-time part of the
+// deterministic mode, Sec. 2), so that its operation sequence equals the
+// strict-FP32 host reference bit for bit.
+#define TPCFIT_DET 1
+#define TPCFIT_NS det
+#include "fit_core.cuh"
+
+namespace tpcfit {
+static ConstRegistration reg_det("fit_det", &det::upload);
+cudaError_t launch_fit_det(const FitArgs& a, int lanes_per_track, int rows_per_stage, cudaStream_t s) {
+  return det::launch(a, lanes_per_track, rows_per_stage, s);
+}
+}  // namespace tpcfit

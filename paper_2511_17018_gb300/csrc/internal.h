@@ -1,0 +1,70 @@
+// Internal declarations shared by the host part of libtpcfit and its kernel
+// modules.  Not part of the public C ABI (include/tpcfit.h).
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace tpcfit {
+
+constexpr int kNSectors = 36;
+constexpr int kNSide = 18;
+constexpr int kMaxRows = 152;
+constexpr int kAlignFloats = kNSectors * kMaxRows * 2;
+constexpr int kWarp = 32;
+
+// Per-time-frame constants of the fit, uploaded to the __constant__ bank of
+// every kernel module (each compilation unit has its own copy, Sec. 4.1).
+struct GeoConst {
+  float row_x[kMaxRows];      // local x of each pad-row plane (FP64 -> FP32)
+  float rot_c[kNSide * kNSide];  // cos / sin of the rotation from sector a to b
+  float rot_s[kNSide * kNSide];  //   (index a * 18 + b), FP64 -> FP32
+  double asin_a[30];          // Maclaurin coefficients of arcsin (FP64 island)
+  float kappa;                // -0.00299792458 * Bz  [1/cm per (c/GeV)]
+  float v_meas;               // cluster variance (0.1 cm)^2
+  float l0;                   // sqrt of the initial covariance diagonal (10)
+  float max_snp;              // |sin phi| limit (0.999)
+  int32_t n_rows;
+};
+
+// Arguments of one fit launch.
+struct FitArgs {
+  const float* y;
+  const float* z;
+  const uint16_t* rowsec;
+  int64_t n_hits;
+  const int32_t* off;
+  int32_t n_tracks;
+  const float* seeds;
+  const float* align;          // [36][152][2], always valid (zeros when unset)
+  const int32_t* perm;         // [n_tracks] processing order, or null
+  float* params;
+  float* cov;
+  float* chi2;
+  int32_t* ndf;
+  unsigned long long* err;     // error word: code << 56 | track
+};
+
+// Error codes recorded in the device error word.
+constexpr unsigned long long kErrOffsets = 1;
+constexpr unsigned long long kErrRowSector = 2;
+
+// ---- constant-memory registry (Sec. 4.1): every kernel module registers an
+// uploader for its own __constant__ copy; the host updates all of them.
+using ConstUploader = cudaError_t (*)(const GeoConst&, cudaStream_t);
+struct ConstRegistration {
+  ConstRegistration(const char* module, ConstUploader up);
+};
+cudaError_t upload_constants_all(const GeoConst& g, cudaStream_t s);
+int registered_constant_modules();
+
+// ---- kernel launchers, one per module
+cudaError_t launch_fit_fast(const FitArgs& a, int lanes_per_track, int rows_per_stage, cudaStream_t s);
+cudaError_t launch_fit_det(const FitArgs& a, int lanes_per_track, int rows_per_stage, cudaStream_t s);
+
+// Length-ordering permutation: perm[k] = track processed k-th, longest first.
+// scratch: int32[2 * 256] (zeroed by the launcher).
+cudaError_t launch_length_order(const int32_t* off, int32_t n_tracks, int32_t* perm, int32_t* scratch,
+                                cudaStream_t s);
+
+}  // namespace tpcfit

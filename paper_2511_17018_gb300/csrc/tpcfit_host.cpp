@@ -1,0 +1,333 @@
+// Host side of libtpcfit: the C ABI of include/tpcfit.h.  Validates arguments,
+// owns the handle's device scratch, builds the geometry tables and keeps every
+// kernel module's constant bank up to date (Sec. 4.1), and enqueues the kernels.
+#include "tpcfit.h"
+
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdint>
+#include <cstring>
+#include <mutex>
+#include <new>
+#include <utility>
+#include <vector>
+
+#include "internal.h"
+
+namespace tpcfit {
+
+// ---------------------------------------------------------------- constant registry
+namespace {
+struct Registry {
+  std::mutex mu;
+  std::vector<std::pair<const char*, ConstUploader>> modules;
+  const void* last_owner = nullptr;  // handle whose constants are resident
+  int last_device = -1;
+};
+Registry& registry() {
+  static Registry r;
+  return r;
+}
+}  // namespace
+
+ConstRegistration::ConstRegistration(const char* module, ConstUploader up) {
+  Registry& r = registry();
+  std::lock_guard<std::mutex> lk(r.mu);
+  r.modules.emplace_back(module, up);
+}
+
+cudaError_t upload_constants_all(const GeoConst& g, cudaStream_t s) {
+  Registry& r = registry();
+  for (auto& m : r.modules) {
+    cudaError_t e = m.second(g, s);
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
+}
+
+int registered_constant_modules() { return (int)registry().modules.size(); }
+
+}  // namespace tpcfit
+
+using namespace tpcfit;
+
+struct tpcfit_handle {
+  int device = 0;
+  GeoConst geo{};
+  int deterministic = 0;
+  int lanes_per_track = 1;
+  int rows_per_stage = 16;
+  int sort_by_length = 1;
+  float* d_align = nullptr;
+  unsigned long long* d_err = nullptr;
+  int32_t* d_sort_scratch = nullptr;
+  int32_t* d_perm = nullptr;
+  int64_t perm_cap = 0;
+  // staging for tpcfit_fit_host
+  unsigned char* d_stage = nullptr;
+  size_t stage_cap = 0;
+};
+
+namespace {
+
+tpcfit_status from_cuda(cudaError_t e) {
+  if (e == cudaSuccess) return TPCFIT_OK;
+  if (e == cudaErrorMemoryAllocation) return TPCFIT_ENOMEM;
+  return TPCFIT_ECUDA;
+}
+
+bool aligned(const void* p, size_t a) { return ((uintptr_t)p % a) == 0; }
+
+// Build the per-time-frame constants on the host in FP64, rounded to FP32.
+bool build_geo(const tpcfit_geometry* g, double bz, GeoConst& out) {
+  if (!g || !g->row_x || g->n_sectors != kNSectors || g->n_rows < 1 || g->n_rows > kMaxRows) return false;
+  if (!(g->sector_width_deg > 0.0) || !(g->sector_width_deg <= 90.0) || !std::isfinite(bz)) return false;
+  std::memset(&out, 0, sizeof(out));
+  for (int r = 0; r < g->n_rows; ++r) {
+    if (!std::isfinite(g->row_x[r]) || !(g->row_x[r] > 0.0)) return false;
+    if (r > 0 && !(g->row_x[r] > g->row_x[r - 1])) return false;
+    out.row_x[r] = (float)g->row_x[r];
+  }
+  // rotation from sector a to b: m = (b - a) mod 18 in [-8, 9], angle m * width
+  const double w_rad = g->sector_width_deg * 3.14159265358979323846 / 180.0;
+  for (int a = 0; a < kNSide; ++a)
+    for (int b = 0; b < kNSide; ++b) {
+      int m = ((b - a) % kNSide + kNSide) % kNSide;
+      if (m > 9) m -= kNSide;
+      const double da = (double)m * w_rad;
+      out.rot_c[a * kNSide + b] = (float)std::cos(da);
+      out.rot_s[a * kNSide + b] = (float)std::sin(da);
+    }
+  // arcsin Maclaurin coefficients: a_n = a_{n-1} (2n-1)^2 / ((2n)(2n+1))
+  out.asin_a[0] = 1.0;
+  for (int n = 1; n < 30; ++n) {
+    const double num = (double)(2 * n - 1) * (double)(2 * n - 1);
+    const double den = (double)(2 * n) * (double)(2 * n + 1);
+    out.asin_a[n] = out.asin_a[n - 1] * num / den;
+  }
+  out.kappa = (float)(-0.00299792458 * bz);
+  out.v_meas = (float)0.01;
+  out.l0 = (float)std::sqrt((double)(float)100.0);
+  out.max_snp = (float)0.999;
+  out.n_rows = g->n_rows;
+  return true;
+}
+
+// Make the handle's constants resident in every module (shared per device).
+tpcfit_status make_resident(tpcfit_handle* h, cudaStream_t s) {
+  Registry& r = registry();
+  std::lock_guard<std::mutex> lk(r.mu);
+  if (r.last_owner == h && r.last_device == h->device) return TPCFIT_OK;
+  cudaError_t e = upload_constants_all(h->geo, s);
+  if (e != cudaSuccess) return from_cuda(e);
+  r.last_owner = h;
+  r.last_device = h->device;
+  return TPCFIT_OK;
+}
+
+tpcfit_status ensure_perm(tpcfit_handle* h, int64_t n) {
+  if (n <= h->perm_cap) return TPCFIT_OK;
+  if (h->d_perm) cudaFree(h->d_perm);
+  h->d_perm = nullptr;
+  h->perm_cap = 0;
+  cudaError_t e = cudaMalloc(&h->d_perm, sizeof(int32_t) * (size_t)n);
+  if (e != cudaSuccess) return from_cuda(e);
+  h->perm_cap = n;
+  return TPCFIT_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int32_t tpcfit_version(void) { return 1 * 10000 + 0 * 100 + 0; }
+
+const char* tpcfit_status_string(tpcfit_status s) {
+  switch (s) {
+    case TPCFIT_OK: return "ok";
+    case TPCFIT_EINVAL: return "invalid argument";
+    case TPCFIT_ECUDA: return "CUDA runtime error";
+    case TPCFIT_ENOMEM: return "device allocation failed";
+    case TPCFIT_EDEVICE: return "a kernel found invalid input";
+    case TPCFIT_ETIMEOUT: return "a bounded device-side wait ran out";
+    case TPCFIT_ESTATE: return "call not allowed in the current state";
+  }
+  return "unknown status";
+}
+
+tpcfit_status tpcfit_create(const tpcfit_geometry* geometry, double bz_tesla, tpcfit_handle** out) {
+  if (!out) return TPCFIT_EINVAL;
+  *out = nullptr;
+  tpcfit_handle* h = new (std::nothrow) tpcfit_handle();
+  if (!h) return TPCFIT_ENOMEM;
+  if (!build_geo(geometry, bz_tesla, h->geo)) {
+    delete h;
+    return TPCFIT_EINVAL;
+  }
+  cudaError_t e = cudaGetDevice(&h->device);
+  if (e == cudaSuccess) e = cudaMalloc(&h->d_align, sizeof(float) * kAlignFloats);
+  if (e == cudaSuccess) e = cudaMalloc(&h->d_err, sizeof(unsigned long long));
+  if (e == cudaSuccess) e = cudaMalloc(&h->d_sort_scratch, sizeof(int32_t) * 512);
+  if (e == cudaSuccess) e = cudaMemset(h->d_align, 0, sizeof(float) * kAlignFloats);
+  if (e == cudaSuccess) e = cudaMemset(h->d_err, 0, sizeof(unsigned long long));
+  if (e == cudaSuccess) {
+    tpcfit_status st = make_resident(h, nullptr);
+    if (st == TPCFIT_OK) e = cudaDeviceSynchronize();
+    else e = cudaErrorUnknown;
+  }
+  if (e != cudaSuccess) {
+    tpcfit_destroy(h);
+    return from_cuda(e);
+  }
+  *out = h;
+  return TPCFIT_OK;
+}
+
+void tpcfit_destroy(tpcfit_handle* h) {
+  if (!h) return;
+  cudaDeviceSynchronize();
+  if (h->d_align) cudaFree(h->d_align);
+  if (h->d_err) cudaFree(h->d_err);
+  if (h->d_sort_scratch) cudaFree(h->d_sort_scratch);
+  if (h->d_perm) cudaFree(h->d_perm);
+  if (h->d_stage) cudaFree(h->d_stage);
+  {
+    Registry& r = registry();
+    std::lock_guard<std::mutex> lk(r.mu);
+    if (r.last_owner == h) r.last_owner = nullptr;
+  }
+  delete h;
+}
+
+tpcfit_status tpcfit_set_mode(tpcfit_handle* h, int deterministic) {
+  if (!h || (deterministic != 0 && deterministic != 1)) return TPCFIT_EINVAL;
+  h->deterministic = deterministic;
+  return TPCFIT_OK;
+}
+
+tpcfit_status tpcfit_set_config(tpcfit_handle* h, int lanes_per_track, int rows_per_stage, int sort_by_length) {
+  if (!h) return TPCFIT_EINVAL;
+  if (lanes_per_track != 1) return TPCFIT_EINVAL;
+  if (rows_per_stage != 4 && rows_per_stage != 8 && rows_per_stage != 16) return TPCFIT_EINVAL;
+  h->lanes_per_track = lanes_per_track;
+  h->rows_per_stage = rows_per_stage;
+  h->sort_by_length = sort_by_length ? 1 : 0;
+  return TPCFIT_OK;
+}
+
+tpcfit_status tpcfit_set_alignment(tpcfit_handle* h, const float* d, void* stream) {
+  if (!h) return TPCFIT_EINVAL;
+  if (d && !aligned(d, 4)) return TPCFIT_EINVAL;
+  cudaStream_t s = (cudaStream_t)stream;
+  cudaError_t e = d ? cudaMemcpyAsync(h->d_align, d, sizeof(float) * kAlignFloats, cudaMemcpyDeviceToDevice, s)
+                    : cudaMemsetAsync(h->d_align, 0, sizeof(float) * kAlignFloats, s);
+  return from_cuda(e);
+}
+
+tpcfit_status tpcfit_reserve(tpcfit_handle* h, int64_t max_tracks, int64_t max_hits) {
+  if (!h || max_tracks < 0 || max_hits < 0 || max_tracks > INT32_MAX) return TPCFIT_EINVAL;
+  return ensure_perm(h, max_tracks);
+}
+
+tpcfit_status tpcfit_fit(tpcfit_handle* h, const tpcfit_hits* hits, const int32_t* track_offsets, int32_t n_tracks,
+                         const float* seeds, float* params_out, float* cov_out, float* chi2_out, int32_t* ndf_out,
+                         void* stream) {
+  if (!h || !hits || n_tracks < 0 || hits->n_hits < 0) return TPCFIT_EINVAL;
+  if (n_tracks == 0) return TPCFIT_OK;
+  if (!track_offsets || !seeds || !params_out || !cov_out || !chi2_out || !ndf_out) return TPCFIT_EINVAL;
+  if (hits->n_hits > 0 && (!hits->y || !hits->z || !hits->rowsec)) return TPCFIT_EINVAL;
+  if (!aligned(hits->y, 4) || !aligned(hits->z, 4) || !aligned(hits->rowsec, 2) || !aligned(track_offsets, 4) ||
+      !aligned(seeds, 4) || !aligned(params_out, 4) || !aligned(cov_out, 4) || !aligned(chi2_out, 4) ||
+      !aligned(ndf_out, 4))
+    return TPCFIT_EINVAL;
+  if (hits->n_hits > INT32_MAX) return TPCFIT_EINVAL;  // int32 track offsets
+  cudaStream_t s = (cudaStream_t)stream;
+  tpcfit_status st = make_resident(h, s);
+  if (st != TPCFIT_OK) return st;
+  FitArgs a{};
+  a.y = hits->y;
+  a.z = hits->z;
+  a.rowsec = hits->rowsec;
+  a.n_hits = hits->n_hits;
+  a.off = track_offsets;
+  a.n_tracks = n_tracks;
+  a.seeds = seeds;
+  a.align = h->d_align;
+  a.perm = nullptr;
+  a.params = params_out;
+  a.cov = cov_out;
+  a.chi2 = chi2_out;
+  a.ndf = ndf_out;
+  a.err = h->d_err;
+  if (h->sort_by_length) {
+    st = ensure_perm(h, n_tracks);
+    if (st != TPCFIT_OK) return st;
+    cudaError_t e = launch_length_order(track_offsets, n_tracks, h->d_perm, h->d_sort_scratch, s);
+    if (e != cudaSuccess) return from_cuda(e);
+    a.perm = h->d_perm;
+  }
+  cudaError_t e = h->deterministic ? launch_fit_det(a, h->lanes_per_track, h->rows_per_stage, s)
+                                   : launch_fit_fast(a, h->lanes_per_track, h->rows_per_stage, s);
+  return from_cuda(e);
+}
+
+tpcfit_status tpcfit_fit_host(tpcfit_handle* h, const float* y, const float* z, const uint16_t* rowsec,
+                              int64_t n_hits, const int32_t* track_offsets, int32_t n_tracks, const float* seeds,
+                              float* params_out, float* cov_out, float* chi2_out, int32_t* ndf_out, void* stream) {
+  if (!h || n_tracks < 0 || n_hits < 0 || n_hits > INT32_MAX) return TPCFIT_EINVAL;
+  if (n_tracks == 0) return TPCFIT_OK;
+  if (!track_offsets || !seeds || !params_out || !cov_out || !chi2_out || !ndf_out) return TPCFIT_EINVAL;
+  if (n_hits > 0 && (!y || !z || !rowsec)) return TPCFIT_EINVAL;
+  cudaStream_t s = (cudaStream_t)stream;
+  const size_t N = (size_t)n_tracks, H = (size_t)n_hits;
+  auto up = [](size_t b) { return (b + 255) & ~(size_t)255; };
+  const size_t o_y = 0, o_z = o_y + up(4 * H), o_rs = o_z + up(4 * H), o_off = o_rs + up(2 * H),
+               o_seed = o_off + up(4 * (N + 1)), o_par = o_seed + up(20 * N), o_cov = o_par + up(20 * N),
+               o_chi = o_cov + up(60 * N), o_ndf = o_chi + up(4 * N), total = o_ndf + up(4 * N);
+  if (total > h->stage_cap) {
+    if (h->d_stage) cudaFree(h->d_stage);
+    h->d_stage = nullptr;
+    h->stage_cap = 0;
+    cudaError_t e = cudaMalloc(&h->d_stage, total);
+    if (e != cudaSuccess) return from_cuda(e);
+    h->stage_cap = total;
+  }
+  unsigned char* b = h->d_stage;
+  cudaError_t e = cudaSuccess;
+  if (H) {
+    e = cudaMemcpyAsync(b + o_y, y, 4 * H, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(b + o_z, z, 4 * H, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(b + o_rs, rowsec, 2 * H, cudaMemcpyHostToDevice, s);
+  }
+  if (e == cudaSuccess) e = cudaMemcpyAsync(b + o_off, track_offsets, 4 * (N + 1), cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(b + o_seed, seeds, 20 * N, cudaMemcpyHostToDevice, s);
+  if (e != cudaSuccess) return from_cuda(e);
+  tpcfit_hits hh{(const float*)(b + o_y), (const float*)(b + o_z), (const uint16_t*)(b + o_rs), n_hits};
+  tpcfit_status st = tpcfit_fit(h, &hh, (const int32_t*)(b + o_off), n_tracks, (const float*)(b + o_seed),
+                                (float*)(b + o_par), (float*)(b + o_cov), (float*)(b + o_chi), (int32_t*)(b + o_ndf),
+                                stream);
+  if (st != TPCFIT_OK) return st;
+  e = cudaMemcpyAsync(params_out, b + o_par, 20 * N, cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(cov_out, b + o_cov, 60 * N, cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(chi2_out, b + o_chi, 4 * N, cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(ndf_out, b + o_ndf, 4 * N, cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  return from_cuda(e);
+}
+
+tpcfit_status tpcfit_get_status(tpcfit_handle* h, void* stream, int32_t* err_code, int64_t* err_track) {
+  if (!h) return TPCFIT_EINVAL;
+  cudaStream_t s = (cudaStream_t)stream;
+  unsigned long long w = 0;
+  cudaError_t e = cudaMemcpyAsync(&w, h->d_err, sizeof(w), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(h->d_err, 0, sizeof(w), s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return from_cuda(e);
+  const int32_t code = (int32_t)(w >> 56);
+  if (err_code) *err_code = code;
+  if (err_track) *err_track = code ? (int64_t)(w & 0x00FFFFFFFFFFFFFFull) : -1;
+  return code ? TPCFIT_EDEVICE : TPCFIT_OK;
+}
+
+}  // extern "C"

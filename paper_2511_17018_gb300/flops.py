@@ -1,0 +1,35 @@
+"""Algorithmic FP32 operation counts of the fit (for roofline accounting).
+
+Counted from the formula list of one step as the kernels evaluate it: every
+add, subtract and multiply is one operation (a fused multiply-add counts as
+two), every division and square root one.  A step = rotation-free prediction
+(79, with the d(path)/dk series that single-row steps use) + square-root
+transport L <- J L (60) + two Potter scalar updates (2 x 128) + the alignment
+subtraction (2).  The first cluster of a pass has no prediction or transport.
+The output covariance C = L L^T costs 135 per track.
+"""
+from __future__ import annotations
+
+import numpy as np
+
+PREDICT = 79
+TRANSPORT = 60
+SCALAR_UPDATE = 128
+MEAS = 2
+STEP = PREDICT + TRANSPORT + 2 * SCALAR_UPDATE + MEAS          # 397
+FIRST = 2 * SCALAR_UPDATE + MEAS                               # 258
+OUTPUT = 135
+
+
+def fit_flops(lengths) -> float:
+    """Algorithmic flops of fitting tracks with the given cluster counts (both passes)."""
+    n = np.asarray(lengths, dtype=np.int64)
+    n = n[n >= 1]
+    return float(np.sum(2 * ((n - 1) * STEP + FIRST) + OUTPUT))
+
+
+def fit_bytes(lengths) -> float:
+    """Algorithmic DRAM bytes: clusters read once (10 B), per track offsets (4),
+    seeds (20), outputs (5 + 15 + 1 + 1 words = 88)."""
+    n = np.asarray(lengths, dtype=np.int64)
+    return float(10 * n.sum() + (4 + 20 + 88) * n.shape[0])

@@ -1,0 +1,244 @@
+"""Python binding of libtpcfit (include/tpcfit.h): argument marshalling only.
+
+Every function has the name of the C entry point it calls.  Device arrays are
+torch CUDA tensors (torch provides device memory and streams); every step of
+the fit runs in the library's kernels.  There is no CPU fallback: if the
+shared library is missing or fails to load, the functions raise.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libtpcfit.so")
+
+OK, EINVAL, ECUDA, ENOMEM, EDEVICE, ETIMEOUT, ESTATE = range(7)
+
+
+class TpcfitError(RuntimeError):
+    def __init__(self, status: int, where: str):
+        self.status = status
+        super().__init__(f"{where}: {status_string(status)} (status {status})")
+
+
+class _Geometry(C.Structure):
+    _fields_ = [("n_sectors", C.c_int32), ("n_rows", C.c_int32), ("row_x", C.POINTER(C.c_double)),
+                ("sector_width_deg", C.c_double), ("z_max", C.c_double)]
+
+
+class _Hits(C.Structure):
+    _fields_ = [("y", C.c_void_p), ("z", C.c_void_p), ("rowsec", C.c_void_p), ("n_hits", C.c_int64)]
+
+
+_lib = None
+
+
+def load():
+    """Load libtpcfit.so (built by paper_2511_17018_gb300.build); raise if absent."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError(f"libtpcfit.so not built ({LIB_PATH}); run paper_2511_17018_gb300.build.build()")
+    L = C.CDLL(LIB_PATH)
+    vp, i32, i64 = C.c_void_p, C.c_int32, C.c_int64
+    sig = {
+        "tpcfit_create": (C.c_int, [C.POINTER(_Geometry), C.c_double, C.POINTER(vp)]),
+        "tpcfit_destroy": (None, [vp]),
+        "tpcfit_set_mode": (C.c_int, [vp, C.c_int]),
+        "tpcfit_set_config": (C.c_int, [vp, C.c_int, C.c_int, C.c_int]),
+        "tpcfit_set_alignment": (C.c_int, [vp, vp, vp]),
+        "tpcfit_reserve": (C.c_int, [vp, i64, i64]),
+        "tpcfit_fit": (C.c_int, [vp, C.POINTER(_Hits), vp, i32, vp, vp, vp, vp, vp, vp]),
+        "tpcfit_fit_host": (C.c_int, [vp, vp, vp, vp, i64, vp, i32, vp, vp, vp, vp, vp, vp]),
+        "tpcfit_get_status": (C.c_int, [vp, vp, C.POINTER(i32), C.POINTER(i64)]),
+        "tpcfit_status_string": (C.c_char_p, [C.c_int]),
+        "tpcfit_version": (i32, []),
+    }
+    for name, (res, args) in sig.items():
+        f = getattr(L, name)
+        f.restype = res
+        f.argtypes = args
+    _lib = L
+    return L
+
+
+def _check(st: int, where: str):
+    if st != OK:
+        raise TpcfitError(st, where)
+
+
+def _stream(stream):
+    if stream is None:
+        import torch
+        return torch.cuda.current_stream().cuda_stream
+    return getattr(stream, "cuda_stream", stream)
+
+
+def _dev(t, dtype, name):
+    import torch
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise TypeError(f"{name} must be a CUDA tensor")
+    if t.dtype != dtype or not t.is_contiguous():
+        raise TypeError(f"{name} must be a contiguous {dtype} tensor")
+    return t.data_ptr()
+
+
+def status_string(st: int) -> str:
+    return load().tpcfit_status_string(int(st)).decode()
+
+
+def tpcfit_version() -> int:
+    return int(load().tpcfit_version())
+
+
+def tpcfit_create(geometry, bz: float):
+    """geometry: object with row_x (float64 array), n_sectors, sector_width_deg, z_max."""
+    L = load()
+    rx = np.ascontiguousarray(geometry.row_x, dtype=np.float64)
+    g = _Geometry(int(geometry.n_sectors), int(rx.shape[0]), rx.ctypes.data_as(C.POINTER(C.c_double)),
+                  float(geometry.sector_width_deg), float(getattr(geometry, "z_max", 250.0)))
+    h = C.c_void_p()
+    _check(L.tpcfit_create(C.byref(g), float(bz), C.byref(h)), "tpcfit_create")
+    return h
+
+
+def tpcfit_destroy(h) -> None:
+    load().tpcfit_destroy(h)
+
+
+def tpcfit_set_mode(h, deterministic: bool) -> None:
+    _check(load().tpcfit_set_mode(h, int(bool(deterministic))), "tpcfit_set_mode")
+
+
+def tpcfit_set_config(h, lanes_per_track: int = 1, rows_per_stage: int = 16, sort_by_length: bool = True) -> None:
+    _check(load().tpcfit_set_config(h, int(lanes_per_track), int(rows_per_stage), int(bool(sort_by_length))),
+           "tpcfit_set_config")
+
+
+def tpcfit_set_alignment(h, d=None, stream=None) -> None:
+    import torch
+    ptr = None
+    if d is not None:
+        if d.numel() != 36 * 152 * 2:
+            raise ValueError("alignment must have 36*152*2 elements")
+        ptr = _dev(d, torch.float32, "alignment")
+    _check(load().tpcfit_set_alignment(h, ptr, _stream(stream)), "tpcfit_set_alignment")
+
+
+def tpcfit_reserve(h, max_tracks: int, max_hits: int = 0) -> None:
+    _check(load().tpcfit_reserve(h, int(max_tracks), int(max_hits)), "tpcfit_reserve")
+
+
+def tpcfit_fit(h, y, z, rowsec, offsets, seeds, params, cov, chi2, ndf, stream=None) -> None:
+    """Enqueue the fit of all tracks (device tensors; see include/tpcfit.h).
+
+    rowsec is an int16 tensor holding the uint16 bits row << 6 | sector."""
+    import torch
+    n = int(offsets.numel()) - 1
+    hits = _Hits(_dev(y, torch.float32, "y"), _dev(z, torch.float32, "z"), _dev(rowsec, torch.int16, "rowsec"),
+                 int(y.numel()))
+    if z.numel() != y.numel() or rowsec.numel() != y.numel():
+        raise ValueError("y, z and rowsec must have the same length")
+    if seeds.numel() != 5 * n or params.numel() != 5 * n or cov.numel() != 15 * n or chi2.numel() != n \
+            or ndf.numel() != n:
+        raise ValueError("seed / output sizes do not match the number of tracks")
+    st = load().tpcfit_fit(h, C.byref(hits), _dev(offsets, torch.int32, "offsets"), n, _dev(seeds, torch.float32, "seeds"),
+                           _dev(params, torch.float32, "params"), _dev(cov, torch.float32, "cov"),
+                           _dev(chi2, torch.float32, "chi2"), _dev(ndf, torch.int32, "ndf"), _stream(stream))
+    _check(st, "tpcfit_fit")
+
+
+def tpcfit_fit_host(h, y, z, rowsec, offsets, seeds, stream=None, out=None):
+    """Fit from host arrays (numpy or pinned CPU tensors); returns host outputs."""
+    def arr(a, dt):
+        if hasattr(a, "numpy"):
+            a = a.numpy()
+        a = np.asarray(a)
+        if a.dtype != dt or not a.flags["C_CONTIGUOUS"]:
+            raise TypeError(f"host array must be contiguous {dt}")
+        return a
+    y = arr(y, np.float32); z = arr(z, np.float32); rowsec = arr(rowsec, np.uint16)
+    offsets = arr(offsets, np.int32); seeds = arr(seeds, np.float32)
+    n = offsets.shape[0] - 1
+    if out is None:
+        out = dict(params=np.empty((5, n), np.float32), cov=np.empty((15, n), np.float32),
+                   chi2=np.empty(n, np.float32), ndf=np.empty(n, np.int32))
+    st = load().tpcfit_fit_host(h, y.ctypes.data, z.ctypes.data, rowsec.ctypes.data, y.shape[0], offsets.ctypes.data,
+                                n, seeds.ctypes.data, out["params"].ctypes.data, out["cov"].ctypes.data,
+                                out["chi2"].ctypes.data, out["ndf"].ctypes.data, _stream(stream))
+    _check(st, "tpcfit_fit_host")
+    return out
+
+
+def tpcfit_get_status(h, stream=None):
+    """Returns (status, err_code, err_track) and clears the device error word."""
+    code = C.c_int32(0)
+    trk = C.c_int64(-1)
+    st = load().tpcfit_get_status(h, _stream(stream), C.byref(code), C.byref(trk))
+    if st not in (OK, EDEVICE):
+        _check(st, "tpcfit_get_status")
+    return st, int(code.value), int(trk.value)
+
+
+# ------------------------------------------------------------------ conveniences
+def frame_to_device(frame, device="cuda"):
+    """Copy a synth.Frame's inputs to device tensors (one H2D copy per array)."""
+    import torch
+    return dict(
+        y=torch.from_numpy(frame.y).to(device), z=torch.from_numpy(frame.z).to(device),
+        rowsec=torch.from_numpy(frame.rowsec.view(np.int16)).to(device),
+        offsets=torch.from_numpy(frame.offsets).to(device),
+        seeds=torch.from_numpy(np.ascontiguousarray(frame.seeds)).to(device),
+    )
+
+
+def empty_outputs(n: int, device="cuda"):
+    import torch
+    return dict(params=torch.empty((5, n), dtype=torch.float32, device=device),
+                cov=torch.empty((15, n), dtype=torch.float32, device=device),
+                chi2=torch.empty(n, dtype=torch.float32, device=device),
+                ndf=torch.empty(n, dtype=torch.int32, device=device))
+
+
+class Fitter:
+    """Owns a tpcfit handle."""
+
+    def __init__(self, geometry, bz: float, deterministic: bool = False, rows_per_stage: int = 16,
+                 sort_by_length: bool = True):
+        self.h = tpcfit_create(geometry, bz)
+        tpcfit_set_mode(self.h, deterministic)
+        tpcfit_set_config(self.h, 1, rows_per_stage, sort_by_length)
+
+    def close(self):
+        if self.h is not None:
+            tpcfit_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_mode(self, deterministic: bool):
+        tpcfit_set_mode(self.h, deterministic)
+
+    def set_config(self, lanes_per_track=1, rows_per_stage=16, sort_by_length=True):
+        tpcfit_set_config(self.h, lanes_per_track, rows_per_stage, sort_by_length)
+
+    def set_alignment(self, d=None, stream=None):
+        tpcfit_set_alignment(self.h, d, stream)
+
+    def fit(self, dev: dict, out: dict | None = None, stream=None) -> dict:
+        n = int(dev["offsets"].numel()) - 1
+        out = out or empty_outputs(n, dev["y"].device)
+        tpcfit_fit(self.h, dev["y"], dev["z"], dev["rowsec"], dev["offsets"], dev["seeds"], out["params"],
+                   out["cov"], out["chi2"], out["ndf"], stream)
+        return out
+
+    def status(self, stream=None):
+        return tpcfit_get_status(self.h, stream)

@@ -1,0 +1,69 @@
+"""The C-ABI library builds, loads and exports every entry point its header
+declares; argument checks that return before any CUDA call work without a GPU."""
+import ctypes as C
+import os
+import re
+import subprocess
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_entry_points():
+    src = open(os.path.join(ROOT, "include", "tpcfit.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(tpcfit_[a-z_0-9]+)\s*\(", src)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2511_17018_gb300 import build, tpcfit
+    build.build()
+    return tpcfit.load()
+
+
+def test_header_declares_entry_points():
+    names = declared_entry_points()
+    for n in ("tpcfit_create", "tpcfit_fit", "tpcfit_destroy", "tpcfit_set_mode", "tpcfit_get_status"):
+        assert n in names
+
+
+def test_library_exports_every_declared_symbol(lib):
+    from paper_2511_17018_gb300 import tpcfit
+    out = subprocess.run(["nm", "-D", "--defined-only", tpcfit.LIB_PATH], capture_output=True, text=True,
+                         check=True).stdout
+    exported = set(re.findall(r"\bT (tpcfit_\w+)", out))
+    declared = set(declared_entry_points())
+    assert declared <= exported, declared - exported
+    assert exported <= declared, exported - declared   # nothing undocumented
+    for n in declared:
+        assert hasattr(lib, n)
+
+
+def test_status_strings_and_version(lib):
+    from paper_2511_17018_gb300 import tpcfit
+    assert tpcfit.status_string(0) == "ok"
+    assert "invalid" in tpcfit.status_string(1)
+    assert tpcfit.tpcfit_version() >= 10000
+
+
+def test_argument_errors_before_any_cuda_call(lib):
+    from paper_2511_17018_gb300 import tpcfit
+    h = C.c_void_p()
+    # null geometry / null output handle
+    assert lib.tpcfit_create(None, 0.5, C.byref(h)) == tpcfit.EINVAL
+    assert lib.tpcfit_create(None, 0.5, None) == tpcfit.EINVAL
+    # bad geometry: wrong sector count, non-ascending rows
+    rx = (C.c_double * 3)(85.0, 84.0, 86.0)
+    g = tpcfit._Geometry(36, 3, C.cast(rx, C.POINTER(C.c_double)), 20.0, 250.0)
+    assert lib.tpcfit_create(C.byref(g), 0.5, C.byref(h)) == tpcfit.EINVAL
+    g = tpcfit._Geometry(35, 3, C.cast(rx, C.POINTER(C.c_double)), 20.0, 250.0)
+    assert lib.tpcfit_create(C.byref(g), 0.5, C.byref(h)) == tpcfit.EINVAL
+    # null handle everywhere
+    assert lib.tpcfit_set_mode(None, 1) == tpcfit.EINVAL
+    assert lib.tpcfit_set_config(None, 1, 16, 1) == tpcfit.EINVAL
+    assert lib.tpcfit_reserve(None, 10, 10) == tpcfit.EINVAL
+    assert lib.tpcfit_fit(None, None, None, 0, None, None, None, None, None, None) == tpcfit.EINVAL
+    assert lib.tpcfit_get_status(None, None, None, None) == tpcfit.EINVAL
+    lib.tpcfit_destroy(None)

@@ -1,0 +1,177 @@
+"""Parity of the CUDA fit with the CPU oracle (run on a GB300 with -m gpu).
+
+Fast mode: within the FP32-vs-FP64 tolerance of paper_2511_17018_gb300.tolerance.
+Deterministic mode: bit-exact against the strict-FP32 oracle, run to run and
+for every launch configuration."""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+import oracle  # noqa: E402
+from paper_2511_17018_gb300 import synth, tolerance  # noqa: E402
+from paper_2511_17018_gb300 import tpcfit as tf  # noqa: E402
+
+
+def _host(out):
+    torch.cuda.synchronize()
+    return {k: v.cpu().numpy() for k, v in out.items()}
+
+
+def _bits_equal(a, b):
+    for k in ("params", "cov", "chi2", "ndf"):
+        x = np.ascontiguousarray(a[k]).view(np.int32)
+        y = np.ascontiguousarray(b[k]).view(np.int32)
+        if not np.array_equal(x, y):
+            bad = np.nonzero(x != y)
+            return f"{k}: {len(bad[0])} words differ, first at {tuple(i[0] for i in bad)}"
+    return None
+
+
+@pytest.fixture(scope="module")
+def fitter():
+    tf.load()
+    f = tf.Fitter(synth.default_geometry(), 0.5)
+    yield f
+    f.close()
+
+
+@pytest.fixture(scope="module")
+def frames():
+    return {
+        "plain1000": synth.config1(),
+        "drop20k": synth.generate(20000, 2, drop_p=0.05, cap_lengths=True),
+        "align5k": synth.generate(5000, 3, drop_p=0.05, cap_lengths=True, d_true=synth.alignment_offsets(3)),
+    }
+
+
+@pytest.mark.parametrize("name", ["plain1000", "drop20k"])
+def test_fast_mode_matches_fp64_oracle(fitter, frames, name):
+    fr = frames[name]
+    fitter.set_mode(False)
+    fitter.set_config(1, 16, True)
+    got = _host(fitter.fit(tf.frame_to_device(fr)))
+    ref = oracle.fit(fr, "f64")
+    rep = tolerance.compare_to_fp64(got, ref)
+    assert rep["ok"], rep
+    assert np.array_equal(got["ndf"], ref["ndf"])
+
+
+@pytest.mark.parametrize("name", ["plain1000", "drop20k"])
+def test_deterministic_mode_bit_exact_vs_strict_fp32(fitter, frames, name):
+    fr = frames[name]
+    fitter.set_mode(True)
+    fitter.set_config(1, 16, True)
+    got = _host(fitter.fit(tf.frame_to_device(fr)))
+    ref = oracle.fit(fr, "f32")
+    assert _bits_equal(got, ref) is None, _bits_equal(got, ref)
+
+
+def test_deterministic_mode_independent_of_launch_config_and_runs(fitter, frames):
+    fr = frames["drop20k"]
+    dev = tf.frame_to_device(fr)
+    fitter.set_mode(True)
+    base = None
+    for rps in (4, 8, 16):
+        for srt in (True, False):
+            fitter.set_config(1, rps, srt)
+            for _ in range(2):
+                got = _host(fitter.fit(dev))
+                if base is None:
+                    base = got
+                assert _bits_equal(got, base) is None, (rps, srt)
+    fitter.set_config(1, 16, True)
+
+
+def test_alignment_offsets_are_subtracted(fitter, frames):
+    fr = frames["align5k"]
+    d = torch.from_numpy(fr.d_true).cuda()
+    fitter.set_alignment(d)
+    try:
+        fitter.set_mode(True)
+        got = _host(fitter.fit(tf.frame_to_device(fr)))
+        ref = oracle.fit(fr, "f32", align=fr.d_true)
+        assert _bits_equal(got, ref) is None
+        fitter.set_mode(False)
+        got = _host(fitter.fit(tf.frame_to_device(fr)))
+        rep = tolerance.compare_to_fp64(got, oracle.fit(fr, "f64", align=fr.d_true))
+        assert rep["ok"], rep
+    finally:
+        fitter.set_alignment(None)
+
+
+def test_edge_cases(fitter):
+    fr = synth.generate(64, 31, drop_p=0.05, cap_lengths=True)
+    lens = fr.lengths().copy()
+    lens[0] = 0   # empty track
+    lens[1] = 1   # one cluster
+    lens[2] = 2   # two clusters
+    lens[3] = 3   # minimal fit
+    idx = np.concatenate([np.arange(o, o + l) for o, l in zip(fr.offsets[:-1], lens)])
+    fr.y, fr.z, fr.rowsec = fr.y[idx], fr.z[idx], fr.rowsec[idx]
+    fr.offsets = np.concatenate([[0], np.cumsum(lens)]).astype(np.int32)
+    fr.seeds[2, 5] = 0.9995   # unusable seed
+    fitter.set_mode(True)
+    got = _host(fitter.fit(tf.frame_to_device(fr)))
+    ref = oracle.fit(fr, "f32")
+    assert list(got["ndf"][:4]) == [-1, -1, -1, 1]
+    assert got["ndf"][5] == -1
+    assert _bits_equal(got, ref) is None
+    # empty frame
+    empty = fr.subset(np.arange(0))
+    dev = tf.frame_to_device(empty)
+    out = tf.empty_outputs(0)
+    tf.tpcfit_fit(fitter.h, dev["y"], dev["z"], dev["rowsec"], dev["offsets"], dev["seeds"], out["params"],
+                  out["cov"], out["chi2"], out["ndf"])
+    assert fitter.status()[0] == tf.OK
+
+
+def test_invalid_input_is_flagged_not_fatal(fitter):
+    fr = synth.generate(100, 32)
+    rs = fr.rowsec.copy()
+    bad_track = 7
+    rs[fr.offsets[bad_track] + 3] = (200 << 6) | 5   # row 200 does not exist
+    fr.rowsec = rs
+    fitter.set_mode(False)
+    got = _host(fitter.fit(tf.frame_to_device(fr)))
+    assert got["ndf"][bad_track] == -2
+    assert np.all(got["ndf"][np.arange(100) != bad_track] > 0)
+    st, code, trk = fitter.status()
+    assert st == tf.EDEVICE and code == 2 and trk == bad_track
+    assert fitter.status()[0] == tf.OK   # the word was cleared
+    # offsets past the end of the hit arrays
+    dev = tf.frame_to_device(fr)
+    dev["offsets"][-1] = int(fr.n_hits) + 5
+    _host(fitter.fit(dev))
+    st, code, trk = fitter.status()
+    assert st == tf.EDEVICE and code == 1 and trk == fr.n_tracks - 1
+
+
+def test_host_buffer_entry_point_equals_device_entry_point(fitter, frames):
+    fr = frames["drop20k"]
+    fitter.set_mode(True)
+    dev = _host(fitter.fit(tf.frame_to_device(fr)))
+    host = tf.tpcfit_fit_host(fitter.h, fr.y, fr.z, fr.rowsec, fr.offsets, np.ascontiguousarray(fr.seeds))
+    assert _bits_equal(dev, host) is None
+
+
+def test_full_size_time_frame_sampled(fitter):
+    # 400,000 tracks in one launch (the time-frame-sized batch); the oracle checks
+    # a seeded sample of 3,000 tracks one by one
+    fr = synth.config2()
+    dev = tf.frame_to_device(fr)
+    rng = np.random.default_rng(77)
+    sample = np.sort(rng.choice(fr.n_tracks, 3000, replace=False))
+    sub = fr.subset(sample)
+    fitter.set_mode(False)
+    got = _host(fitter.fit(dev))
+    gs = {k: (v[:, sample] if v.ndim == 2 else v[sample]) for k, v in got.items()}
+    rep = tolerance.compare_to_fp64(gs, oracle.fit(sub, "f64"))
+    assert rep["ok"], rep
+    assert np.all(got["ndf"] >= -1)
+    fitter.set_mode(True)
+    got = _host(fitter.fit(dev))
+    gs = {k: (v[:, sample] if v.ndim == 2 else v[sample]) for k, v in got.items()}
+    assert _bits_equal(gs, oracle.fit(sub, "f32")) is None
+    assert fitter.status()[0] == tf.OK
