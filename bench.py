@@ -176,14 +176,37 @@ def run_reference(args, rank: int, world: int):
     print(json.dumps(line), flush=True)
 
 
+def e2e_run(fitter, fr, out, steps, tf, torch):
+    """Tracks/s through tpcfit_fit_host with pinned host buffers: every step
+    copies the batch to the device, fits and copies the results back."""
+    pin = {k: torch.from_numpy(np.ascontiguousarray(v)).pin_memory() for k, v in
+           (("y", fr.y), ("z", fr.z), ("rowsec", fr.rowsec.view(np.int16)), ("offsets", fr.offsets),
+            ("seeds", fr.seeds))}
+    hout = {k: torch.empty(tuple(v.shape), dtype=v.dtype).pin_memory() for k, v in out.items()}
+    hnp = {k: v.numpy() for k, v in hout.items()}
+    args_np = (pin["y"].numpy(), pin["z"].numpy(), pin["rowsec"].numpy().view(np.uint16), pin["offsets"].numpy(),
+               pin["seeds"].numpy())
+    for _ in range(2):
+        tf.tpcfit_fit_host(fitter.h, *args_np, out=hnp)
+    n = max(3, min(50, steps // 10))
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(n):
+        tf.tpcfit_fit_host(fitter.h, *args_np, out=hnp)
+    return fr.n_tracks / ((time.perf_counter() - t0) / n)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--steps", type=int, default=1000)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--mode", choices=["fast", "det"], default="fast")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--tracks", type=int, default=N_TRACKS,
+                    help="batch size override (profiling of smaller cases only; the bench value uses the default)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -204,7 +227,7 @@ def main():
     from paper_2511_17018_gb300 import flops, synth
     from paper_2511_17018_gb300 import tpcfit as tf
 
-    fr = synth.generate(N_TRACKS, 2 + 1000 * rank, drop_p=0.05, cap_lengths=True)
+    fr = synth.generate(args.tracks, 2 + 1000 * rank, drop_p=0.05, cap_lengths=True)
     lengths = fr.lengths()
     dev = tf.frame_to_device(fr)
     fitter = tf.Fitter(fr.geometry, fr.bz, deterministic=(args.mode == "det"))
@@ -245,23 +268,12 @@ def main():
     ndf = out["ndf"].cpu().numpy()
 
     # end to end through the host-buffer entry point (pinned host memory)
-    pin = {k: torch.from_numpy(np.ascontiguousarray(v)).pin_memory() for k, v in
-           (("y", fr.y), ("z", fr.z), ("rowsec", fr.rowsec.view(np.int16)), ("offsets", fr.offsets),
-            ("seeds", fr.seeds))}
-    hout = {k: torch.empty(v.shape, dtype=v.dtype).pin_memory() for k, v in out.items()}
-    hnp = {k: v.numpy() for k, v in hout.items()}
-    args_np = (pin["y"].numpy(), pin["z"].numpy(), pin["rowsec"].numpy().view(np.uint16), pin["offsets"].numpy(),
-               pin["seeds"].numpy())
-    for _ in range(2):
-        tf.tpcfit_fit_host(fitter.h, *args_np, out=hnp)
-    e2e_steps = max(3, args.steps // 2)
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    for _ in range(e2e_steps):
-        tf.tpcfit_fit_host(fitter.h, *args_np, out=hnp)
-    e2e_s = (time.perf_counter() - t0) / e2e_steps
     h2d = 10 * fr.n_hits + 4 * (fr.n_tracks + 1) + 20 * fr.n_tracks
     d2h = 88 * fr.n_tracks
+    e2e = None
+    if not args.no_e2e:
+        e2e = {"value": e2e_run(fitter, fr, out, args.steps, tf, torch), "unit": UNIT,
+               "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h}
 
     if rank != 0:
         fitter.close()
@@ -287,13 +299,13 @@ def main():
         "hits_per_s": value * float(lengths.mean()),
         "roofline": {"bound": "alu", "achieved": achieved_tf, "peak": peak_tf, "unit": "TFLOP/s",
                      "frac": achieved_tf / peak_tf, "traffic": _traffic("fit_fast" if args.mode == "fast" else "fit_det"),
-                     "kernel": "fit_kernel<16> (+ length ordering) per tpcfit_fit call",
+                     "kernel": "fit_kernel (+ length ordering) per tpcfit_fit call",
                      "algorithmic_flops_per_launch": alg_flops,
                      "peak_source": f"152 SMs x 128 FP32 lanes x 2 x {peaks.get('sm_max_mhz', 2070.0)} MHz "
                                     f"(sm_max_mhz, {peak_src} peaks file)",
                      "frac_at_sampled_clock": (achieved_tf / fp32_peak_tflops(clocks["sm_mhz"]))
                      if clocks.get("sm_mhz") else None},
-        "e2e": {"value": fr.n_tracks / e2e_s, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+        "e2e": e2e,
         "gpu_launches": 3 * args.steps,
         "clocks": clocks,
     }

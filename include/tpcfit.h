@@ -86,12 +86,15 @@ void tpcfit_destroy(tpcfit_handle* h);
  * run-time part of the deterministic mode of Sec. 2. */
 tpcfit_status tpcfit_set_mode(tpcfit_handle* h, int deterministic);
 
-/* Launch configuration of the fit: lanes_per_track (1 = one track per lane)
- * and rows_per_stage (hits per track staged into shared memory per refill:
- * 4, 8 or 16).  sort_by_length != 0 orders tracks by length before the fit so
- * that a warp's tracks finish together.  In deterministic mode the results do
- * not depend on these choices.  EINVAL for unsupported values. */
-tpcfit_status tpcfit_set_config(tpcfit_handle* h, int lanes_per_track, int rows_per_stage, int sort_by_length);
+/* Launch configuration of the fit: lanes_per_track (1 = one track per lane),
+ * rows_per_stage (clusters per track staged into shared memory per refill) and
+ * warps_per_block.  Supported (rows_per_stage, warps_per_block) shapes:
+ * (4, 8), (4, 12), (4, 24), (8, 8), (8, 16), (16, 8); default (4, 24).
+ * sort_by_length != 0 (default) orders tracks by length before the fit so that
+ * a warp's tracks finish together.  In deterministic mode the results do not
+ * depend on these choices.  EINVAL for unsupported values. */
+tpcfit_status tpcfit_set_config(tpcfit_handle* h, int lanes_per_track, int rows_per_stage, int warps_per_block,
+                                int sort_by_length);
 
 /* Alignment offsets d[36][152][2] (dy, dz per sector and row, cm) subtracted
  * from every cluster before the fit.  d is a device pointer; its contents are

@@ -16,11 +16,13 @@
 // next cluster's sector frame if needed, analytic helix propagation to that pad
 // row with its Jacobian, L <- J L, two scalar Potter updates (y then z).
 //
-// Work mapping: one track per lane; a warp stages the next `RPS` clusters of
-// its 32 tracks into shared memory with coalesced loads (alignment offsets
-// subtracted on the way), then each lane runs its steps from shared memory.
-// Tracks are processed in an order that puts tracks of equal length into the
-// same warp (see length_order.cu) so that a warp's lanes finish together.
+// Work mapping: a persistent grid; each warp takes 32-track work items from a
+// global counter and fits one track per lane.  While a lane computes the steps
+// of the current chunk, the warp's asynchronous copies (cp.async) bring the
+// next `RPS` clusters of all 32 tracks into the other half of a shared-memory
+// double buffer.  The alignment table and the geometry live in shared memory.
+// Tracks are taken in an order that puts tracks of equal length into the same
+// warp (length_order.cu) so that a warp's lanes finish together.
 #pragma once
 
 #include <cuda_runtime.h>
@@ -95,6 +97,37 @@ __device__ __forceinline__ float asinc_f(float u) {
 #endif
 }
 
+// c = sqrt(u) and 1/c.  Deterministic: IEEE square root and division, in the
+// canonical order; fast: one reciprocal square root.
+__device__ __forceinline__ void sqrt_and_inv(float u, float& c, float& ic) {
+#if TPCFIT_DET
+  c = sqrtf(u);
+  ic = 1.0f / c;
+#else
+  ic = rsqrtf(u);
+  c = u * ic;
+#endif
+}
+
+// Potter coefficients for innovation variance s2 and cluster variance v:
+// alpha = 1/s2, beta = sqrt(alpha v), gamma = 1/(1 + beta).  Fast mode derives
+// alpha and beta from one reciprocal square root (beta = sqrt(v) rsqrt(s2)).
+__device__ __forceinline__ void potter_coeffs(float s2, float v, float sqrt_v, float& alpha, float& beta,
+                                              float& gamma) {
+#if TPCFIT_DET
+  (void)sqrt_v;
+  alpha = 1.0f / s2;
+  beta = sqrtf(alpha * v);
+  gamma = 1.0f / (1.0f + beta);
+#else
+  (void)v;
+  const float r = rsqrtf(s2);
+  alpha = r * r;
+  beta = sqrt_v * r;
+  gamma = __fdividef(1.0f, 1.0f + beta);
+#endif
+}
+
 // ---------------------------------------------------------------- geometry in smem
 struct SmemTables {
   float row_x[kMaxRows];
@@ -145,8 +178,9 @@ __device__ __forceinline__ bool predict(const SmemTables& T, const float pin[5],
   const float kdx = k * dx;
   const float s2 = s1 + kdx;
   if (!(fabsf(s2) < maxsnp)) return false;
-  const float c1 = sqrtf((1.0f - s1) * (1.0f + s1));
-  const float c2 = sqrtf((1.0f - s2) * (1.0f + s2));
+  float c1, ic1, c2, ic2;
+  sqrt_and_inv((1.0f - s1) * (1.0f + s1), c1, ic1);
+  sqrt_and_inv((1.0f - s2) * (1.0f + s2), c2, ic2);
   const float Tm = (s1 + s2) / (c1 + c2);
   const float w = c1 + s1 * Tm;
   const float sig = kdx * w;
@@ -156,8 +190,6 @@ __device__ __forceinline__ bool predict(const SmemTables& T, const float pin[5],
   pout[2] = s2;
   pout[3] = t;
   pout[4] = q;
-  const float ic1 = 1.0f / c1;
-  const float ic2 = 1.0f / c2;
   const float tt = 1.0f + Tm * Tm;
   J.ys = (dx * tt) * ((ic1 + ic2) * 0.5f);
   J.yq = ((dx * kappa) * dx) * (tt * (ic2 * 0.5f));
@@ -231,7 +263,8 @@ __device__ __forceinline__ void scalar_update(float p[5], float L[5][5], float& 
   float s2 = v + a[0] * a[0];
 #pragma unroll
   for (int c = 1; c < 5; ++c) s2 = s2 + a[c] * a[c];
-  const float alpha = 1.0f / s2;
+  float alpha, beta, gamma;
+  potter_coeffs(s2, v, c_geo.sqrt_v, alpha, beta, gamma);
   const float r = mv - p[H];
   float K[5];
 #pragma unroll
@@ -244,8 +277,6 @@ __device__ __forceinline__ void scalar_update(float p[5], float L[5][5], float& 
 #pragma unroll
   for (int i = 0; i < 5; ++i) p[i] = p[i] + K[i] * r;
   chi2 = chi2 + (r * r) * alpha;
-  const float beta = sqrtf(alpha * v);
-  const float gamma = 1.0f / (1.0f + beta);
 #pragma unroll
   for (int i = 0; i < 5; ++i) {
     if (i == H) continue;
@@ -280,204 +311,258 @@ struct TrackState {
   int used;
 };
 
-// Shared staging of RPS clusters for each of a warp's 32 tracks; row pitch
-// RPS + 1 keeps both the loader's and the consumer's accesses conflict-free.
+// Asynchronous 4-byte global -> shared copies (no register staging).
+__device__ __forceinline__ void cp_async4(void* smem_dst, const void* gmem_src) {
+  const unsigned s = (unsigned)__cvta_generic_to_shared(smem_dst);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(s), "l"(gmem_src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
+
+// Double-buffered staging of RPS clusters for each of a warp's 32 tracks.  Row
+// pitch RPS + 1 keeps the consumer's reads (lane t reads row t) conflict-free.
+// rowsec travels as the aligned 32-bit word that contains it.
 template <int RPS>
 struct WarpStage {
-  float m0[kWarp][RPS + 1];
-  float m1[kWarp][RPS + 1];
-  int rs[kWarp][RPS + 1];
+  float y[2][kWarp][RPS + 1];
+  float z[2][kWarp][RPS + 1];
+  uint32_t rs[2][kWarp][RPS + 1];
 };
 
-// Stage local steps [c0, c0 + RPS) of every lane's pass: lane t's step i is hit
-// base_t + start_t + dir * i (valid for i < count_t).  Loads are coalesced per
-// track; the alignment offsets are subtracted here.  Invalid (row, sector)
-// values are passed on as rs = -1.
+// Issue the copies of local steps [c0, c0 + RPS) of every lane's pass into
+// buffer b: lane t's step i is hit first_t + dir * i (valid for i < count_t).
+// Each group of RPS lanes copies RPS consecutive clusters of one track.
 template <int RPS>
-__device__ __forceinline__ void stage(WarpStage<RPS>& st, const FitArgs& a, int64_t my_first, int my_count, int dir,
-                                      int c0, int lane) {
+__device__ __forceinline__ void stage_issue(WarpStage<RPS>& st, int b, const FitArgs& a, int my_first,
+                                            int my_count, int dir, int c0, int lane) {
+  const uintptr_t rs_begin = (uintptr_t)a.rowsec;
+  const uintptr_t rs_end = (uintptr_t)(a.rowsec + a.n_hits);
 #pragma unroll
   for (int it = 0; it < RPS; ++it) {
     const int e = it * kWarp + lane;
-    const int t = e / RPS;   // owner lane
-    const int k = e % RPS;   // step within the chunk
-    const int64_t first_t = __shfl_sync(0xffffffffu, my_first, t);
+    const int t = e / RPS;
+    const int k = e % RPS;
+    const int first_t = __shfl_sync(0xffffffffu, my_first, t);
     const int count_t = __shfl_sync(0xffffffffu, my_count, t);
     const int i = c0 + k;
     if (i < count_t) {
-      const int64_t h = first_t + (int64_t)dir * i;
-      const int rsv = (int)__ldg(a.rowsec + h);
-      const int row = rsv >> 6;
-      const int sec = rsv & 63;
-      float m0 = __ldg(a.y + h);
-      float m1 = __ldg(a.z + h);
-      int out = -1;
-      if (row < c_geo.n_rows && sec < kNSectors) {
-        const int key = (sec * kMaxRows + row) * 2;
-        m0 = m0 - __ldg(a.align + key);
-        m1 = m1 - __ldg(a.align + key + 1);
-        out = rsv;
+      const int h = first_t + dir * i;
+      cp_async4(&st.y[b][t][k], a.y + h);
+      cp_async4(&st.z[b][t][k], a.z + h);
+      const uint16_t* rp = a.rowsec + h;
+      const uintptr_t wa = (uintptr_t)rp & ~(uintptr_t)3;
+      if (wa >= rs_begin && wa + 4 <= rs_end) {
+        cp_async4(&st.rs[b][t][k], (const void*)wa);
+      } else {  // a cluster whose 32-bit word reaches outside the array
+        st.rs[b][t][k] = (uint32_t)__ldg(rp) << (16u * (unsigned)(((uintptr_t)rp >> 1) & 1u));
       }
-      st.m0[t][k] = m0;
-      st.m1[t][k] = m1;
-      st.rs[t][k] = out;
     }
   }
+  cp_async_commit();
 }
 
-template <int RPS>
-__global__ void __launch_bounds__(256, 2) fit_kernel(FitArgs a) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  SmemTables& T = *reinterpret_cast<SmemTables*>(smem_raw);
-  WarpStage<RPS>* stages = reinterpret_cast<WarpStage<RPS>*>(smem_raw + sizeof(SmemTables));
-  load_tables(T);
-  __syncthreads();
+struct BlockSmem {
+  SmemTables T;
+  float align[kAlignFloats];
+};
 
+template <int RPS, int WARPS, int MINB>
+__global__ void __launch_bounds__(WARPS * 32, MINB) fit_kernel(FitArgs a) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  BlockSmem& B = *reinterpret_cast<BlockSmem*>(smem_raw);
+  WarpStage<RPS>* stages = reinterpret_cast<WarpStage<RPS>*>(smem_raw + sizeof(BlockSmem));
+  load_tables(B.T);
+  for (int i = threadIdx.x; i < kAlignFloats; i += blockDim.x) B.align[i] = __ldg(a.align + i);
+  __syncthreads();
+  const SmemTables& T = B.T;
   const int lane = threadIdx.x & 31;
   WarpStage<RPS>& st = stages[threadIdx.x >> 5];
-  const int64_t slot = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  const bool have = slot < a.n_tracks;
-  const int32_t trk = have ? (a.perm ? a.perm[slot] : (int32_t)slot) : 0;
+  const unsigned rs_par0 = (unsigned)(((uintptr_t)a.rowsec >> 1) & 1u);
+  const int64_t n_chunks = ((int64_t)a.n_tracks + kWarp - 1) / kWarp;
 
-  // ---- per-track input checks
-  int status = have ? 0 : 1;  // 0 fitting, 1 idle, 2 numerical failure, 3 invalid input
-  int64_t begin = 0;
-  int n = 0;
-  if (have) {
-    const int64_t b = a.off[trk];
-    const int64_t e = a.off[trk + 1];
-    if (b < 0 || e < b || e > a.n_hits) {
-      status = 3;
-      record_error(a.err, kErrOffsets, trk);
-    } else {
-      begin = b;
-      n = (int)(e - b);
-      if (n < 1) status = 2;
-    }
-  }
-  TrackState S;
-  int last = 0;
-  if (status == 0) {
-#pragma unroll
-    for (int c = 0; c < 5; ++c) S.p[c] = __ldg(a.seeds + (int64_t)c * a.n_tracks + trk);
-    if (!(fabsf(S.p[2]) < c_geo.max_snp)) status = 2;
-  }
+#pragma unroll 1
+  for (;;) {
+    // ---- take the next 32-track work item
+    int64_t chunk = 0;
+    if (lane == 0) chunk = (int64_t)atomicAdd(a.work, 1u);
+    chunk = __shfl_sync(0xffffffffu, chunk, 0);
+    if (chunk >= n_chunks) break;
+    const int64_t slot = chunk * kWarp + lane;
+    const bool have = slot < a.n_tracks;
+    const int32_t trk = have ? (a.perm ? a.perm[slot] : (int32_t)slot) : 0;
 
-  // ---- two passes: outward (dir +1 from hit 0) and inward (dir -1 from `last`)
-#pragma unroll 1
-  for (int pass = 0; pass < 2; ++pass) {
-    const int dir = pass == 0 ? 1 : -1;
-    const int64_t my_first = begin + (pass == 0 ? 0 : last);
-    const int my_count = (status == 0) ? (pass == 0 ? n : last + 1) : 0;
-    bool go = status == 0;
-    if (go) {
-      reset_factor(S.L);
-      S.chi2 = 0.0f;
-      S.used = 0;
+    // ---- per-track input checks
+    // hit indices fit in int32: the host rejects n_hits > INT32_MAX
+    int status = have ? 0 : 1;  // 0 fitting, 1 idle, 2 numerical failure, 3 invalid input
+    int begin = 0;
+    int n = 0;
+    if (have) {
+      const int b = a.off[trk];
+      const int e = a.off[trk + 1];
+      if (b < 0 || e < b || (int64_t)e > a.n_hits) {
+        status = 3;
+        record_error(a.err, kErrOffsets, trk);
+      } else {
+        begin = b;
+        n = e - b;
+        if (n < 1) status = 2;
+      }
     }
-    int count_max = my_count;
+    TrackState S;
+    int last = 0;
+    if (status == 0) {
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) count_max = max(count_max, __shfl_xor_sync(0xffffffffu, count_max, o));
+      for (int c = 0; c < 5; ++c) S.p[c] = __ldg(a.seeds + (int64_t)c * a.n_tracks + trk);
+      if (!(fabsf(S.p[2]) < c_geo.max_snp)) status = 2;
+    }
+
+    // ---- two passes: outward (dir +1 from hit 0) and inward (dir -1 from `last`)
 #pragma unroll 1
-    for (int c0 = 0; c0 < count_max; c0 += RPS) {
+    for (int pass = 0; pass < 2; ++pass) {
+      const int dir = pass == 0 ? 1 : -1;
+      const int my_first = begin + (pass == 0 ? 0 : last);
+      const int my_count = (status == 0) ? (pass == 0 ? n : last + 1) : 0;
+      bool go = status == 0;
+      if (go) {
+        reset_factor(S.L);
+        S.chi2 = 0.0f;
+        S.used = 0;
+      }
+      int count_max = my_count;
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) count_max = max(count_max, __shfl_xor_sync(0xffffffffu, count_max, o));
+      if (count_max == 0) continue;
       __syncwarp();
-      stage<RPS>(st, a, my_first, my_count, dir, c0, lane);
-      __syncwarp();
+      stage_issue<RPS>(st, 0, a, my_first, my_count, dir, 0, lane);
+      int buf = 0;
 #pragma unroll 1
-      for (int k = 0; k < RPS; ++k) {
-        const int i = c0 + k;
-        if (!go || i >= my_count) continue;
-        const int rsv = st.rs[lane][k];
-        if (rsv < 0) {
-          status = 3;
-          go = false;
-          record_error(a.err, kErrRowSector, trk);
-          continue;
-        }
-        const float m0 = st.m0[lane][k];
-        const float m1 = st.m1[lane][k];
-        const int row = rsv >> 6;
-        const int sec18 = (rsv & 63) % kNSide;
-        if (i == 0) {
-          // first cluster of the pass: the state sits on its row already
-          S.x = T.row_x[row];
-          S.sec = sec18;
+      for (int c0 = 0; c0 < count_max; c0 += RPS) {
+        const bool more = c0 + RPS < count_max;
+        if (more) {
+          stage_issue<RPS>(st, buf ^ 1, a, my_first, my_count, dir, c0 + RPS, lane);
+          cp_async_wait<1>();
         } else {
-          float pn[5];
-          Jac J;
-          if (!predict(T, S.p, S.x, S.sec, sec18, T.row_x[row], pn, J)) {
+          cp_async_wait<0>();
+        }
+        __syncwarp();
+#pragma unroll 1
+        for (int k = 0; k < RPS; ++k) {
+          const int i = c0 + k;
+          if (!go || i >= my_count) continue;
+          const int h = my_first + dir * i;
+          const unsigned shift = 16u * ((rs_par0 + (unsigned)h) & 1u);
+          const int rsv = (int)((st.rs[buf][lane][k] >> shift) & 0xffffu);
+          const int row = rsv >> 6;
+          const int sec = rsv & 63;
+          if (row >= c_geo.n_rows || sec >= kNSectors) {
+            status = 3;
             go = false;
-            if (pass == 1) status = 2;  // the inward pass must reach the first cluster
+            record_error(a.err, kErrRowSector, trk);
             continue;
           }
+          const float2 d = reinterpret_cast<const float2*>(B.align)[sec * kMaxRows + row];
+          const float m0 = st.y[buf][lane][k] - d.x;
+          const float m1 = st.z[buf][lane][k] - d.y;
+          const int sec18 = sec % kNSide;
+          if (i == 0) {
+            // first cluster of the pass: the state sits on its row already
+            S.x = T.row_x[row];
+            S.sec = sec18;
+          } else {
+            float pn[5];
+            Jac J;
+            if (!predict(T, S.p, S.x, S.sec, sec18, T.row_x[row], pn, J)) {
+              go = false;
+              if (pass == 1) status = 2;  // the inward pass must reach the first cluster
+              continue;
+            }
 #pragma unroll
-          for (int c = 0; c < 5; ++c) S.p[c] = pn[c];
-          S.x = T.row_x[row];
-          S.sec = sec18;
-          transport(S.L, J);
+            for (int c = 0; c < 5; ++c) S.p[c] = pn[c];
+            S.x = T.row_x[row];
+            S.sec = sec18;
+            transport(S.L, J);
+          }
+          scalar_update<0>(S.p, S.L, S.chi2, m0);
+          scalar_update<1>(S.p, S.L, S.chi2, m1);
+          S.used += 1;
+          if (pass == 0) last = i;
         }
-        scalar_update<0>(S.p, S.L, S.chi2, m0);
-        scalar_update<1>(S.p, S.L, S.chi2, m1);
-        S.used += 1;
-        if (pass == 0) last = i;
+        __syncwarp();
+        buf ^= 1;
       }
     }
-  }
 
-  // ---- outputs at the track's slot
-  if (!have) return;
-  const int64_t N = a.n_tracks;
-  if (status == 0 && S.used >= 3) {
+    // ---- outputs at the track's own index
+    if (!have) continue;
+    const int64_t N = a.n_tracks;
+    if (status == 0 && S.used >= 3) {
 #pragma unroll
-    for (int c = 0; c < 5; ++c) a.params[(int64_t)c * N + trk] = S.p[c];
-    int e = 0;
+      for (int c = 0; c < 5; ++c) a.params[(int64_t)c * N + trk] = S.p[c];
+      int e = 0;
 #pragma unroll
-    for (int i = 0; i < 5; ++i)
+      for (int i = 0; i < 5; ++i)
 #pragma unroll
-      for (int j = 0; j <= i; ++j) {
-        float acc = S.L[i][0] * S.L[j][0];
+        for (int j = 0; j <= i; ++j) {
+          float acc = S.L[i][0] * S.L[j][0];
 #pragma unroll
-        for (int c = 1; c < 5; ++c) acc = acc + S.L[i][c] * S.L[j][c];
-        a.cov[(int64_t)e * N + trk] = acc;
-        ++e;
-      }
-    a.chi2[trk] = S.chi2;
-    a.ndf[trk] = 2 * S.used - 5;
-  } else {
-    const float qnan = __int_as_float(0x7fc00000);
+          for (int c = 1; c < 5; ++c) acc = acc + S.L[i][c] * S.L[j][c];
+          a.cov[(int64_t)e * N + trk] = acc;
+          ++e;
+        }
+      a.chi2[trk] = S.chi2;
+      a.ndf[trk] = 2 * S.used - 5;
+    } else {
+      const float qnan = __int_as_float(0x7fc00000);
 #pragma unroll
-    for (int c = 0; c < 5; ++c) a.params[(int64_t)c * N + trk] = qnan;
+      for (int c = 0; c < 5; ++c) a.params[(int64_t)c * N + trk] = qnan;
 #pragma unroll
-    for (int e = 0; e < 15; ++e) a.cov[(int64_t)e * N + trk] = qnan;
-    a.chi2[trk] = qnan;
-    a.ndf[trk] = (status == 3) ? -2 : -1;
+      for (int e = 0; e < 15; ++e) a.cov[(int64_t)e * N + trk] = qnan;
+      a.chi2[trk] = qnan;
+      a.ndf[trk] = (status == 3) ? -2 : -1;
+    }
   }
 }
 
-template <int RPS>
-cudaError_t launch_rps(const FitArgs& a, cudaStream_t s) {
-  constexpr int kThreads = 256;
-  const size_t smem = sizeof(SmemTables) + (kThreads / kWarp) * sizeof(WarpStage<RPS>);
-  static bool configured = false;
-  if (!configured) {
-    cudaError_t e = cudaFuncSetAttribute(fit_kernel<RPS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+template <int RPS, int WARPS, int MINB>
+cudaError_t launch_cfg(const FitArgs& a, cudaStream_t s) {
+  constexpr int kThreads = WARPS * 32;
+  const size_t smem = sizeof(BlockSmem) + WARPS * sizeof(WarpStage<RPS>);
+  static int grid = 0;
+  if (grid == 0) {
+    cudaError_t e =
+        cudaFuncSetAttribute(fit_kernel<RPS, WARPS, MINB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    configured = true;
+    int dev = 0, sms = 0, per_sm = 0;
+    e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e == cudaSuccess)
+      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fit_kernel<RPS, WARPS, MINB>, kThreads, smem);
+    if (e != cudaSuccess) return e;
+    if (per_sm < 1) return cudaErrorInvalidConfiguration;
+    grid = sms * per_sm;
   }
-  const int64_t blocks = (a.n_tracks + kThreads - 1) / kThreads;
-  fit_kernel<RPS><<<(unsigned)blocks, kThreads, smem, s>>>(a);
+  const int64_t chunks = ((int64_t)a.n_tracks + kWarp - 1) / kWarp;
+  const int64_t need = (chunks + WARPS - 1) / WARPS;
+  const int blocks = (int)(need < grid ? need : grid);
+  cudaError_t e = cudaMemsetAsync(a.work, 0, sizeof(unsigned int), s);
+  if (e != cudaSuccess) return e;
+  fit_kernel<RPS, WARPS, MINB><<<blocks, kThreads, smem, s>>>(a);
   return cudaGetLastError();
 }
 
-inline cudaError_t launch(const FitArgs& a, int lanes_per_track, int rps, cudaStream_t s) {
+// Supported (rows per stage, warps per block) shapes; the shared-memory budget
+// (alignment table + double buffer) decides how many blocks fit on an SM.
+inline cudaError_t launch(const FitArgs& a, int lanes_per_track, int rps, int warps, cudaStream_t s) {
   if (a.n_tracks <= 0) return cudaSuccess;
   if (lanes_per_track != 1) return cudaErrorInvalidValue;
-  switch (rps) {
-    case 4: return launch_rps<4>(a, s);
-    case 8: return launch_rps<8>(a, s);
-    case 16: return launch_rps<16>(a, s);
-    default: return cudaErrorInvalidValue;
-  }
+  if (rps == 4 && warps == 8) return launch_cfg<4, 8, 2>(a, s);
+  if (rps == 4 && warps == 12) return launch_cfg<4, 12, 2>(a, s);
+  if (rps == 4 && warps == 24) return launch_cfg<4, 24, 1>(a, s);
+  if (rps == 8 && warps == 8) return launch_cfg<8, 8, 2>(a, s);
+  if (rps == 8 && warps == 16) return launch_cfg<8, 16, 1>(a, s);
+  if (rps == 16 && warps == 8) return launch_cfg<16, 8, 1>(a, s);
+  return cudaErrorInvalidValue;
 }
 
 cudaError_t upload(const GeoConst& g, cudaStream_t s) {

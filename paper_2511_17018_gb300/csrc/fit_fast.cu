@@ -7,7 +7,7 @@
 
 namespace tpcfit {
 static ConstRegistration reg_fast("fit_fast", &fast::upload);
-cudaError_t launch_fit_fast(const FitArgs& a, int lanes_per_track, int rows_per_stage, cudaStream_t s) {
-  return fast::launch(a, lanes_per_track, rows_per_stage, s);
+cudaError_t launch_fit_fast(const FitArgs& a, int lanes_per_track, int rows_per_stage, int warps, cudaStream_t s) {
+  return fast::launch(a, lanes_per_track, rows_per_stage, warps, s);
 }
 }  // namespace tpcfit

@@ -22,6 +22,7 @@ struct GeoConst {
   double asin_a[30];          // Maclaurin coefficients of arcsin (FP64 island)
   float kappa;                // -0.00299792458 * Bz  [1/cm per (c/GeV)]
   float v_meas;               // cluster variance (0.1 cm)^2
+  float sqrt_v;               // its square root (fast-mode Potter coefficients)
   float l0;                   // sqrt of the initial covariance diagonal (10)
   float max_snp;              // |sin phi| limit (0.999)
   int32_t n_rows;
@@ -43,6 +44,7 @@ struct FitArgs {
   float* chi2;
   int32_t* ndf;
   unsigned long long* err;     // error word: code << 56 | track
+  unsigned int* work;          // work-item counter (zeroed by the launcher)
 };
 
 // Error codes recorded in the device error word.
@@ -59,8 +61,10 @@ cudaError_t upload_constants_all(const GeoConst& g, cudaStream_t s);
 int registered_constant_modules();
 
 // ---- kernel launchers, one per module
-cudaError_t launch_fit_fast(const FitArgs& a, int lanes_per_track, int rows_per_stage, cudaStream_t s);
-cudaError_t launch_fit_det(const FitArgs& a, int lanes_per_track, int rows_per_stage, cudaStream_t s);
+cudaError_t launch_fit_fast(const FitArgs& a, int lanes_per_track, int rows_per_stage, int warps, cudaStream_t s);
+cudaError_t launch_fit_det(const FitArgs& a, int lanes_per_track, int rows_per_stage, int warps, cudaStream_t s);
+// true if (lanes_per_track, rows_per_stage, warps) is a compiled launch shape
+bool fit_shape_supported(int lanes_per_track, int rows_per_stage, int warps);
 
 // Length-ordering permutation: perm[k] = track processed k-th, longest first.
 // scratch: int32[2 * 256] (zeroed by the launcher).

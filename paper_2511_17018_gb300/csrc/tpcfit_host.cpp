@@ -17,6 +17,12 @@
 
 namespace tpcfit {
 
+bool fit_shape_supported(int lanes_per_track, int rows_per_stage, int warps) {
+  if (lanes_per_track != 1) return false;
+  return (rows_per_stage == 4 && (warps == 8 || warps == 12 || warps == 24)) ||
+         (rows_per_stage == 8 && (warps == 8 || warps == 16)) || (rows_per_stage == 16 && warps == 8);
+}
+
 // ---------------------------------------------------------------- constant registry
 namespace {
 struct Registry {
@@ -57,10 +63,12 @@ struct tpcfit_handle {
   GeoConst geo{};
   int deterministic = 0;
   int lanes_per_track = 1;
-  int rows_per_stage = 16;
+  int rows_per_stage = 4;
+  int warps_per_block = 24;
   int sort_by_length = 1;
   float* d_align = nullptr;
   unsigned long long* d_err = nullptr;
+  unsigned int* d_work = nullptr;
   int32_t* d_sort_scratch = nullptr;
   int32_t* d_perm = nullptr;
   int64_t perm_cap = 0;
@@ -108,6 +116,7 @@ bool build_geo(const tpcfit_geometry* g, double bz, GeoConst& out) {
   }
   out.kappa = (float)(-0.00299792458 * bz);
   out.v_meas = (float)0.01;
+  out.sqrt_v = (float)0.1;
   out.l0 = (float)std::sqrt((double)(float)100.0);
   out.max_snp = (float)0.999;
   out.n_rows = g->n_rows;
@@ -168,6 +177,7 @@ tpcfit_status tpcfit_create(const tpcfit_geometry* geometry, double bz_tesla, tp
   cudaError_t e = cudaGetDevice(&h->device);
   if (e == cudaSuccess) e = cudaMalloc(&h->d_align, sizeof(float) * kAlignFloats);
   if (e == cudaSuccess) e = cudaMalloc(&h->d_err, sizeof(unsigned long long));
+  if (e == cudaSuccess) e = cudaMalloc(&h->d_work, sizeof(unsigned int) * 64);
   if (e == cudaSuccess) e = cudaMalloc(&h->d_sort_scratch, sizeof(int32_t) * 512);
   if (e == cudaSuccess) e = cudaMemset(h->d_align, 0, sizeof(float) * kAlignFloats);
   if (e == cudaSuccess) e = cudaMemset(h->d_err, 0, sizeof(unsigned long long));
@@ -189,6 +199,7 @@ void tpcfit_destroy(tpcfit_handle* h) {
   cudaDeviceSynchronize();
   if (h->d_align) cudaFree(h->d_align);
   if (h->d_err) cudaFree(h->d_err);
+  if (h->d_work) cudaFree(h->d_work);
   if (h->d_sort_scratch) cudaFree(h->d_sort_scratch);
   if (h->d_perm) cudaFree(h->d_perm);
   if (h->d_stage) cudaFree(h->d_stage);
@@ -206,12 +217,13 @@ tpcfit_status tpcfit_set_mode(tpcfit_handle* h, int deterministic) {
   return TPCFIT_OK;
 }
 
-tpcfit_status tpcfit_set_config(tpcfit_handle* h, int lanes_per_track, int rows_per_stage, int sort_by_length) {
+tpcfit_status tpcfit_set_config(tpcfit_handle* h, int lanes_per_track, int rows_per_stage, int warps_per_block,
+                                int sort_by_length) {
   if (!h) return TPCFIT_EINVAL;
-  if (lanes_per_track != 1) return TPCFIT_EINVAL;
-  if (rows_per_stage != 4 && rows_per_stage != 8 && rows_per_stage != 16) return TPCFIT_EINVAL;
+  if (!fit_shape_supported(lanes_per_track, rows_per_stage, warps_per_block)) return TPCFIT_EINVAL;
   h->lanes_per_track = lanes_per_track;
   h->rows_per_stage = rows_per_stage;
+  h->warps_per_block = warps_per_block;
   h->sort_by_length = sort_by_length ? 1 : 0;
   return TPCFIT_OK;
 }
@@ -260,6 +272,7 @@ tpcfit_status tpcfit_fit(tpcfit_handle* h, const tpcfit_hits* hits, const int32_
   a.chi2 = chi2_out;
   a.ndf = ndf_out;
   a.err = h->d_err;
+  a.work = h->d_work;
   if (h->sort_by_length) {
     st = ensure_perm(h, n_tracks);
     if (st != TPCFIT_OK) return st;
@@ -267,8 +280,8 @@ tpcfit_status tpcfit_fit(tpcfit_handle* h, const tpcfit_hits* hits, const int32_
     if (e != cudaSuccess) return from_cuda(e);
     a.perm = h->d_perm;
   }
-  cudaError_t e = h->deterministic ? launch_fit_det(a, h->lanes_per_track, h->rows_per_stage, s)
-                                   : launch_fit_fast(a, h->lanes_per_track, h->rows_per_stage, s);
+  cudaError_t e = h->deterministic ? launch_fit_det(a, h->lanes_per_track, h->rows_per_stage, h->warps_per_block, s)
+                                   : launch_fit_fast(a, h->lanes_per_track, h->rows_per_stage, h->warps_per_block, s);
   return from_cuda(e);
 }
 

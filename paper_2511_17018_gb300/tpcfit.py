@@ -49,7 +49,7 @@ def load():
         "tpcfit_create": (C.c_int, [C.POINTER(_Geometry), C.c_double, C.POINTER(vp)]),
         "tpcfit_destroy": (None, [vp]),
         "tpcfit_set_mode": (C.c_int, [vp, C.c_int]),
-        "tpcfit_set_config": (C.c_int, [vp, C.c_int, C.c_int, C.c_int]),
+        "tpcfit_set_config": (C.c_int, [vp, C.c_int, C.c_int, C.c_int, C.c_int]),
         "tpcfit_set_alignment": (C.c_int, [vp, vp, vp]),
         "tpcfit_reserve": (C.c_int, [vp, i64, i64]),
         "tpcfit_fit": (C.c_int, [vp, C.POINTER(_Hits), vp, i32, vp, vp, vp, vp, vp, vp]),
@@ -114,9 +114,10 @@ def tpcfit_set_mode(h, deterministic: bool) -> None:
     _check(load().tpcfit_set_mode(h, int(bool(deterministic))), "tpcfit_set_mode")
 
 
-def tpcfit_set_config(h, lanes_per_track: int = 1, rows_per_stage: int = 16, sort_by_length: bool = True) -> None:
-    _check(load().tpcfit_set_config(h, int(lanes_per_track), int(rows_per_stage), int(bool(sort_by_length))),
-           "tpcfit_set_config")
+def tpcfit_set_config(h, lanes_per_track: int = 1, rows_per_stage: int = 4, warps_per_block: int = 24,
+                      sort_by_length: bool = True) -> None:
+    _check(load().tpcfit_set_config(h, int(lanes_per_track), int(rows_per_stage), int(warps_per_block),
+                                    int(bool(sort_by_length))), "tpcfit_set_config")
 
 
 def tpcfit_set_alignment(h, d=None, stream=None) -> None:
@@ -207,11 +208,11 @@ def empty_outputs(n: int, device="cuda"):
 class Fitter:
     """Owns a tpcfit handle."""
 
-    def __init__(self, geometry, bz: float, deterministic: bool = False, rows_per_stage: int = 16,
-                 sort_by_length: bool = True):
+    def __init__(self, geometry, bz: float, deterministic: bool = False, rows_per_stage: int = 4,
+                 warps_per_block: int = 24, sort_by_length: bool = True):
         self.h = tpcfit_create(geometry, bz)
         tpcfit_set_mode(self.h, deterministic)
-        tpcfit_set_config(self.h, 1, rows_per_stage, sort_by_length)
+        tpcfit_set_config(self.h, 1, rows_per_stage, warps_per_block, sort_by_length)
 
     def close(self):
         if self.h is not None:
@@ -227,8 +228,8 @@ class Fitter:
     def set_mode(self, deterministic: bool):
         tpcfit_set_mode(self.h, deterministic)
 
-    def set_config(self, lanes_per_track=1, rows_per_stage=16, sort_by_length=True):
-        tpcfit_set_config(self.h, lanes_per_track, rows_per_stage, sort_by_length)
+    def set_config(self, lanes_per_track=1, rows_per_stage=4, warps_per_block=24, sort_by_length=True):
+        tpcfit_set_config(self.h, lanes_per_track, rows_per_stage, warps_per_block, sort_by_length)
 
     def set_alignment(self, d=None, stream=None):
         tpcfit_set_alignment(self.h, d, stream)

@@ -62,7 +62,7 @@ def test_argument_errors_before_any_cuda_call(lib):
     assert lib.tpcfit_create(C.byref(g), 0.5, C.byref(h)) == tpcfit.EINVAL
     # null handle everywhere
     assert lib.tpcfit_set_mode(None, 1) == tpcfit.EINVAL
-    assert lib.tpcfit_set_config(None, 1, 16, 1) == tpcfit.EINVAL
+    assert lib.tpcfit_set_config(None, 1, 4, 8, 1) == tpcfit.EINVAL
     assert lib.tpcfit_reserve(None, 10, 10) == tpcfit.EINVAL
     assert lib.tpcfit_fit(None, None, None, 0, None, None, None, None, None, None) == tpcfit.EINVAL
     assert lib.tpcfit_get_status(None, None, None, None) == tpcfit.EINVAL

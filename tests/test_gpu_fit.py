@@ -50,7 +50,7 @@ def frames():
 def test_fast_mode_matches_fp64_oracle(fitter, frames, name):
     fr = frames[name]
     fitter.set_mode(False)
-    fitter.set_config(1, 16, True)
+    fitter.set_config(1, 4, 24, True)
     got = _host(fitter.fit(tf.frame_to_device(fr)))
     ref = oracle.fit(fr, "f64")
     rep = tolerance.compare_to_fp64(got, ref)
@@ -62,7 +62,7 @@ def test_fast_mode_matches_fp64_oracle(fitter, frames, name):
 def test_deterministic_mode_bit_exact_vs_strict_fp32(fitter, frames, name):
     fr = frames[name]
     fitter.set_mode(True)
-    fitter.set_config(1, 16, True)
+    fitter.set_config(1, 4, 24, True)
     got = _host(fitter.fit(tf.frame_to_device(fr)))
     ref = oracle.fit(fr, "f32")
     assert _bits_equal(got, ref) is None, _bits_equal(got, ref)
@@ -73,15 +73,15 @@ def test_deterministic_mode_independent_of_launch_config_and_runs(fitter, frames
     dev = tf.frame_to_device(fr)
     fitter.set_mode(True)
     base = None
-    for rps in (4, 8, 16):
+    for rps, warps in ((4, 8), (4, 12), (4, 24), (8, 8), (8, 16), (16, 8)):
         for srt in (True, False):
-            fitter.set_config(1, rps, srt)
+            fitter.set_config(1, rps, warps, srt)
             for _ in range(2):
                 got = _host(fitter.fit(dev))
                 if base is None:
                     base = got
-                assert _bits_equal(got, base) is None, (rps, srt)
-    fitter.set_config(1, 16, True)
+                assert _bits_equal(got, base) is None, (rps, warps, srt)
+    fitter.set_config(1, 4, 24, True)
 
 
 def test_alignment_offsets_are_subtracted(fitter, frames):
