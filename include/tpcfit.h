@@ -136,6 +136,36 @@ tpcfit_status tpcfit_fit_host(tpcfit_handle* h, const float* y, const float* z, 
                               int64_t n_hits, const int32_t* track_offsets, int32_t n_tracks, const float* seeds,
                               float* params_out, float* cov_out, float* chi2_out, int32_t* ndf_out, void* stream);
 
+/* Largest n_tracks that tpcfit_fit_noalloc accepts (2^20). */
+#define TPCFIT_NOALLOC_MAX_TRACKS 1048576
+
+/* Fit without allocating device memory and without a handle.
+ * The paper has no counterpart; this entry point is for callers that cannot
+ * call cudaMalloc or cudaFree: code running inside a stream capture it does
+ * not own, real-time loops that forbid allocator calls (and the device
+ * synchronisation they can imply), or frameworks that only hand out their own
+ * buffers.  It computes exactly what tpcfit_fit computes with the default
+ * launch configuration (length ordering on, 4 rows per stage, 24 warps per
+ * block), in the fast (deterministic = 0) or deterministic (1) mode.
+ *   geometry, bz_tesla: as for tpcfit_create; the constants are rebuilt and
+ *               uploaded to the kernels' constant memory on every call.
+ *   alignment:  device float [36][152][2] offsets, or NULL for none.
+ *   other arguments and outputs: as for tpcfit_fit.
+ * Its scratch is a fixed static device array of about 4.3 MB (room for
+ * TPCFIT_NOALLOC_MAX_TRACKS tracks) that each GPU loading the library holds
+ * until the process exits; n_tracks above TPCFIT_NOALLOC_MAX_TRACKS returns
+ * EINVAL without touching the GPU.  The first call on a device looks up the
+ * array's device address (cudaGetSymbolAddress); make that first call before
+ * any stream capture.  All calls share the one array, so calls whose work
+ * overlaps on the GPU (other streams, other host threads) race: serialise
+ * them.  Invalid input gives ndf = -2 for the track (there is no error word
+ * to read back).  Calls from a handle's functions afterwards re-upload the
+ * handle's constants themselves. */
+tpcfit_status tpcfit_fit_noalloc(const tpcfit_geometry* geometry, double bz_tesla, const float* alignment,
+                                 int deterministic, const tpcfit_hits* hits, const int32_t* track_offsets,
+                                 int32_t n_tracks, const float* seeds, float* params_out, float* cov_out,
+                                 float* chi2_out, int32_t* ndf_out, void* stream);
+
 /* Read (and clear) the handle's device error word: the first invalid-input code
  * a kernel recorded (0 = none; 1 = bad offsets, 2 = row or sector out of range)
  * and the track it was found on (-1 if none).  Synchronises `stream`.  Returns

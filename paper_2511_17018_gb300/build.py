@@ -32,6 +32,7 @@ UNITS = {
     "fit_fast.cu": FAST,
     "fit_det.cu": DET,
     "length_order.cu": [],
+    "tpcfit_noalloc.cu": [],
 }
 
 

@@ -5,6 +5,8 @@
 #include <cstdint>
 #include <cuda_runtime.h>
 
+#include "tpcfit.h"
+
 namespace tpcfit {
 
 constexpr int kNSectors = 36;
@@ -58,7 +60,12 @@ struct ConstRegistration {
   ConstRegistration(const char* module, ConstUploader up);
 };
 cudaError_t upload_constants_all(const GeoConst& g, cudaStream_t s);
+void forget_resident_constants();
 int registered_constant_modules();
+
+// Geometry and field -> per-time-frame constants (host, FP64 rounded to FP32);
+// false for an invalid geometry.
+bool build_geo(const tpcfit_geometry* g, double bz, GeoConst& out);
 
 // ---- kernel launchers, one per module
 cudaError_t launch_fit_fast(const FitArgs& a, int lanes_per_track, int rows_per_stage, int warps, cudaStream_t s);

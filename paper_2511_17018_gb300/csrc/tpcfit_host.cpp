@@ -54,39 +54,6 @@ cudaError_t upload_constants_all(const GeoConst& g, cudaStream_t s) {
 
 int registered_constant_modules() { return (int)registry().modules.size(); }
 
-}  // namespace tpcfit
-
-using namespace tpcfit;
-
-struct tpcfit_handle {
-  int device = 0;
-  GeoConst geo{};
-  int deterministic = 0;
-  int lanes_per_track = 1;
-  int rows_per_stage = 4;
-  int warps_per_block = 24;
-  int sort_by_length = 1;
-  float* d_align = nullptr;
-  unsigned long long* d_err = nullptr;
-  unsigned int* d_work = nullptr;
-  int32_t* d_sort_scratch = nullptr;
-  int32_t* d_perm = nullptr;
-  int64_t perm_cap = 0;
-  // staging for tpcfit_fit_host
-  unsigned char* d_stage = nullptr;
-  size_t stage_cap = 0;
-};
-
-namespace {
-
-tpcfit_status from_cuda(cudaError_t e) {
-  if (e == cudaSuccess) return TPCFIT_OK;
-  if (e == cudaErrorMemoryAllocation) return TPCFIT_ENOMEM;
-  return TPCFIT_ECUDA;
-}
-
-bool aligned(const void* p, size_t a) { return ((uintptr_t)p % a) == 0; }
-
 // Build the per-time-frame constants on the host in FP64, rounded to FP32.
 bool build_geo(const tpcfit_geometry* g, double bz, GeoConst& out) {
   if (!g || !g->row_x || g->n_sectors != kNSectors || g->n_rows < 1 || g->n_rows > kMaxRows) return false;
@@ -122,6 +89,48 @@ bool build_geo(const tpcfit_geometry* g, double bz, GeoConst& out) {
   out.n_rows = g->n_rows;
   return true;
 }
+
+// Forget which handle's constants are resident, so that the next handle call
+// uploads its own (used by callers that upload constants without a handle).
+void forget_resident_constants() {
+  Registry& r = registry();
+  std::lock_guard<std::mutex> lk(r.mu);
+  r.last_owner = nullptr;
+  r.last_device = -1;
+}
+
+}  // namespace tpcfit
+
+using namespace tpcfit;
+
+struct tpcfit_handle {
+  int device = 0;
+  GeoConst geo{};
+  int deterministic = 0;
+  int lanes_per_track = 1;
+  int rows_per_stage = 4;
+  int warps_per_block = 24;
+  int sort_by_length = 1;
+  float* d_align = nullptr;
+  unsigned long long* d_err = nullptr;
+  unsigned int* d_work = nullptr;
+  int32_t* d_sort_scratch = nullptr;
+  int32_t* d_perm = nullptr;
+  int64_t perm_cap = 0;
+  // staging for tpcfit_fit_host
+  unsigned char* d_stage = nullptr;
+  size_t stage_cap = 0;
+};
+
+namespace {
+
+tpcfit_status from_cuda(cudaError_t e) {
+  if (e == cudaSuccess) return TPCFIT_OK;
+  if (e == cudaErrorMemoryAllocation) return TPCFIT_ENOMEM;
+  return TPCFIT_ECUDA;
+}
+
+bool aligned(const void* p, size_t a) { return ((uintptr_t)p % a) == 0; }
 
 // Make the handle's constants resident in every module (shared per device).
 tpcfit_status make_resident(tpcfit_handle* h, cudaStream_t s) {

@@ -55,6 +55,8 @@ def load():
         "tpcfit_fit": (C.c_int, [vp, C.POINTER(_Hits), vp, i32, vp, vp, vp, vp, vp, vp]),
         "tpcfit_fit_host": (C.c_int, [vp, vp, vp, vp, i64, vp, i32, vp, vp, vp, vp, vp, vp]),
         "tpcfit_get_status": (C.c_int, [vp, vp, C.POINTER(i32), C.POINTER(i64)]),
+        "tpcfit_fit_noalloc": (C.c_int, [C.POINTER(_Geometry), C.c_double, vp, C.c_int, C.POINTER(_Hits), vp, i32, vp,
+                                         vp, vp, vp, vp, vp]),
         "tpcfit_status_string": (C.c_char_p, [C.c_int]),
         "tpcfit_version": (i32, []),
     }
@@ -173,6 +175,27 @@ def tpcfit_fit_host(h, y, z, rowsec, offsets, seeds, stream=None, out=None):
                                 out["chi2"].ctypes.data, out["ndf"].ctypes.data, _stream(stream))
     _check(st, "tpcfit_fit_host")
     return out
+
+
+NOALLOC_MAX_TRACKS = 1 << 20
+
+
+def tpcfit_fit_noalloc(geometry, bz, alignment, deterministic, y, z, rowsec, offsets, seeds, params, cov, chi2, ndf,
+                       stream=None) -> None:
+    """Fit without a handle and without device allocation (see include/tpcfit.h)."""
+    import torch
+    n = int(offsets.numel()) - 1
+    rx = np.ascontiguousarray(geometry.row_x, dtype=np.float64)
+    g = _Geometry(int(geometry.n_sectors), int(rx.shape[0]), rx.ctypes.data_as(C.POINTER(C.c_double)),
+                  float(geometry.sector_width_deg), float(getattr(geometry, "z_max", 250.0)))
+    hits = _Hits(_dev(y, torch.float32, "y"), _dev(z, torch.float32, "z"), _dev(rowsec, torch.int16, "rowsec"),
+                 int(y.numel()))
+    al = None if alignment is None else _dev(alignment, torch.float32, "alignment")
+    st = load().tpcfit_fit_noalloc(C.byref(g), float(bz), al, int(bool(deterministic)), C.byref(hits),
+                                   _dev(offsets, torch.int32, "offsets"), n, _dev(seeds, torch.float32, "seeds"),
+                                   _dev(params, torch.float32, "params"), _dev(cov, torch.float32, "cov"),
+                                   _dev(chi2, torch.float32, "chi2"), _dev(ndf, torch.int32, "ndf"), _stream(stream))
+    _check(st, "tpcfit_fit_noalloc")
 
 
 def tpcfit_get_status(h, stream=None):
