@@ -196,10 +196,48 @@ def e2e_run(fitter, fr, out, steps, tf, torch):
     return fr.n_tracks / ((time.perf_counter() - t0) / n)
 
 
+def e2e_fit_adjoint(fitter, fr, steps, tf, torch):
+    """Tracks/s of fit + adjoint through the public API from pinned host buffers:
+    each step copies the batch and dL/dchi2 to the device, fits with
+    checkpoints, runs the adjoint and copies chi2, ndf and both gradients back."""
+    n = fr.n_tracks
+    pin = {k: torch.from_numpy(np.ascontiguousarray(v)).pin_memory() for k, v in
+           (("y", fr.y), ("z", fr.z), ("rowsec", fr.rowsec.view(np.int16)), ("offsets", fr.offsets),
+            ("seeds", fr.seeds), ("g", np.full(n, 1.0 / n, np.float32)))}
+    d = {k: torch.empty_like(v, device="cuda") for k, v in pin.items()}
+    out = tf.empty_outputs(n)
+    ga = torch.empty(36 * 152 * 2, dtype=torch.float32, device="cuda")
+    gs = torch.empty((5, n), dtype=torch.float32, device="cuda")
+    host_out = {"chi2": torch.empty(n).pin_memory(), "ndf": torch.empty(n, dtype=torch.int32).pin_memory(),
+                "ga": torch.empty(36 * 152 * 2).pin_memory(), "gs": torch.empty((5, n)).pin_memory()}
+
+    def step():
+        for k in d:
+            d[k].copy_(pin[k], non_blocking=True)
+        fitter.fit(d, out)
+        tf.tpcfit_fit_backward(fitter.h, d["y"], d["z"], d["rowsec"], d["offsets"], out["ndf"], d["g"], ga, gs)
+        host_out["chi2"].copy_(out["chi2"], non_blocking=True)
+        host_out["ndf"].copy_(out["ndf"], non_blocking=True)
+        host_out["ga"].copy_(ga, non_blocking=True)
+        host_out["gs"].copy_(gs, non_blocking=True)
+        torch.cuda.current_stream().synchronize()
+
+    for _ in range(2):
+        step()
+    m = max(3, min(30, steps // 10))
+    t0 = time.perf_counter()
+    for _ in range(m):
+        step()
+    dt = (time.perf_counter() - t0) / m
+    h2d = sum(v.numel() * v.element_size() for v in pin.values())
+    d2h = sum(v.numel() * v.element_size() for v in host_out.values())
+    return n / dt, h2d, d2h
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=1000)
+    ap.add_argument("--steps", type=int, default=200)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--mode", choices=["fast", "det"], default="fast")
@@ -233,31 +271,53 @@ def main():
     fitter = tf.Fitter(fr.geometry, fr.bz, deterministic=(args.mode == "det"))
     tf.tpcfit_reserve(fitter.h, fr.n_tracks, fr.n_hits)
     out = tf.empty_outputs(fr.n_tracks)
+    g_chi2 = torch.full((fr.n_tracks,), 1.0 / fr.n_tracks, dtype=torch.float32, device="cuda")
+    g_align = torch.empty(36 * 152 * 2, dtype=torch.float32, device="cuda")
+    g_seeds = torch.empty((5, fr.n_tracks), dtype=torch.float32, device="cuda")
     stream = torch.cuda.current_stream()
 
-    for _ in range(args.warmup):
+    def fit_adjoint():
         fitter.fit(dev, out)
-    torch.cuda.synchronize()
-    if world > 1:
-        dist.barrier()
-    torch.cuda.synchronize()
+        tf.tpcfit_fit_backward(fitter.h, dev["y"], dev["z"], dev["rowsec"], dev["offsets"], out["ndf"], g_chi2,
+                               g_align, g_seeds)
 
-    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
-    with ClockSampler(local) as clk:
-        t_start = torch.cuda.Event(enable_timing=True)
-        t_end = torch.cuda.Event(enable_timing=True)
-        t_start.record(stream)
-        for i in range(args.steps):
+    def timed(fn, steps, split=False):
+        """device time of `steps` calls (CUDA events on the launching stream)."""
+        ev = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(steps)]
+        t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        t0.record(stream)
+        for i in range(steps):
             ev[i][0].record(stream)
-            fitter.fit(dev, out)
-            ev[i][1].record(stream)
-        t_end.record(stream)
+            fn(ev[i][1])
+            ev[i][2].record(stream)
+        t1.record(stream)
         torch.cuda.synchronize()
+        per = [(a.elapsed_time(b), b.elapsed_time(c)) for a, b, c in ev]
+        return t0.elapsed_time(t1), per
+
+    def step_fa(mid):
+        fitter.fit(dev, out)
+        mid.record(stream)
+        tf.tpcfit_fit_backward(fitter.h, dev["y"], dev["z"], dev["rowsec"], dev["offsets"], out["ndf"], g_chi2,
+                               g_align, g_seeds)
+
+    def step_fit(mid):
+        fitter.fit(dev, out)
+        mid.record(stream)
+
+    # ---- the step: fit with checkpoints + adjoint
+    fitter.set_record(True)
+    for _ in range(args.warmup):
+        fit_adjoint()
+    torch.cuda.synchronize()
     if world > 1:
         dist.barrier()
     torch.cuda.synchronize()
-    total_ms = t_start.elapsed_time(t_end)
-    step_ms = [a.elapsed_time(b) for a, b in ev]
+    with ClockSampler(local) as clk:
+        total_ms, per = timed(step_fa, args.steps)
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
     if world > 1:
         t = torch.tensor([total_ms], device="cuda")
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
@@ -266,14 +326,32 @@ def main():
     if st != 0:
         raise RuntimeError(f"device reported invalid input: code {code} track {trk}")
     ndf = out["ndf"].cpu().numpy()
+    fit_rec_ms = statistics.mean(p[0] for p in per)
+    bwd_ms = statistics.mean(p[1] for p in per)
 
-    # end to end through the host-buffer entry point (pinned host memory)
+    # ---- the plain fit (no checkpoints)
+    fitter.set_record(False)
+    for _ in range(args.warmup):
+        fitter.fit(dev, out)
+    torch.cuda.synchronize()
+    plain_steps = max(args.steps, 20)
+    plain_total, plain_per = timed(step_fit, plain_steps)
+    plain_ms = statistics.mean(p[0] for p in plain_per)
+
+    # ---- end to end through the public API with host buffers
     h2d = 10 * fr.n_hits + 4 * (fr.n_tracks + 1) + 20 * fr.n_tracks
     d2h = 88 * fr.n_tracks
-    e2e = None
+    e2e = e2e_plain = None
     if not args.no_e2e:
-        e2e = {"value": e2e_run(fitter, fr, out, args.steps, tf, torch), "unit": UNIT,
-               "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h}
+        e2e_plain = {"value": e2e_run(fitter, fr, out, args.steps, tf, torch), "unit": UNIT,
+                     "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h}
+        fitter.set_record(True)
+        v, hb, db = e2e_fit_adjoint(fitter, fr, args.steps, tf, torch)
+        if world > 1:  # whole job: every rank streams its own batch; the slowest rank sets the pace
+            t = torch.tensor([v, e2e_plain["value"]], device="cuda")
+            dist.all_reduce(t, op=dist.ReduceOp.MIN)
+            v, e2e_plain["value"] = float(t[0]) * world, float(t[1]) * world
+        e2e = {"value": v, "unit": UNIT, "h2d_bytes_per_step": hb, "d2h_bytes_per_step": db}
 
     if rank != 0:
         fitter.close()
@@ -282,31 +360,44 @@ def main():
         return
 
     peaks, peak_src = _peaks()
-    mean_step_s = statistics.mean(step_ms) / 1e3
-    alg_flops = flops.fit_flops(lengths)
     peak_tf = fp32_peak_tflops(float(peaks.get("sm_max_mhz", 2070.0)))
-    achieved_tf = alg_flops / mean_step_s / 1e12
     value = world * fr.n_tracks * args.steps / (total_ms / 1e3)
     clocks = clk.summary()
+    bwd_flops = flops.backward_flops(lengths)
+    fit_fl = flops.fit_flops(lengths)
+    bwd_tf = bwd_flops / (bwd_ms / 1e3) / 1e12
+    fit_tf = fit_fl / (plain_ms / 1e3) / 1e12
+    fa_tf = flops.fit_adjoint_flops(lengths) / (total_ms / args.steps / 1e3) / 1e12
+    peak_note = (f"152 SMs x 128 FP32 lanes x 2 x {peaks.get('sm_max_mhz', 2070.0)} MHz "
+                 f"(sm_max_mhz from the {peak_src} peaks file)")
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "mode": args.mode, "tracks": fr.n_tracks, "hits": fr.n_hits,
+        "config": {"workload": WORKLOAD, "step": "fit with checkpoints + adjoint (gradients w.r.t. alignment and seeds)",
+                   "mode": args.mode, "tracks": fr.n_tracks, "hits": fr.n_hits,
                    "mean_hits_per_track": float(lengths.mean()),
                    "l2": "inputs larger than L2 (clusters %.0f MB > 126 MB), no flush" % (10 * fr.n_hits / 1e6),
                    "fitted_fraction": float(np.mean(ndf > 0))},
         "hits_per_s": value * float(lengths.mean()),
-        "roofline": {"bound": "alu", "achieved": achieved_tf, "peak": peak_tf, "unit": "TFLOP/s",
-                     "frac": achieved_tf / peak_tf, "traffic": _traffic("fit_fast" if args.mode == "fast" else "fit_det"),
-                     "kernel": "fit_kernel (+ length ordering) per tpcfit_fit call",
-                     "algorithmic_flops_per_launch": alg_flops,
-                     "peak_source": f"152 SMs x 128 FP32 lanes x 2 x {peaks.get('sm_max_mhz', 2070.0)} MHz "
-                                    f"(sm_max_mhz, {peak_src} peaks file)",
-                     "frac_at_sampled_clock": (achieved_tf / fp32_peak_tflops(clocks["sm_mhz"]))
+        "roofline": {"bound": "alu", "achieved": bwd_tf, "peak": peak_tf, "unit": "TFLOP/s", "frac": bwd_tf / peak_tf,
+                     "traffic": _traffic("backward_" + args.mode),
+                     "kernel": "backward_kernel (adjoint, dominant kernel of the step)",
+                     "algorithmic_flops_per_launch": bwd_flops, "launch_ms": bwd_ms, "peak_source": peak_note,
+                     "frac_at_sampled_clock": (bwd_tf / fp32_peak_tflops(clocks["sm_mhz"]))
                      if clocks.get("sm_mhz") else None},
+        "fit_adjoint": {"tracks_per_s": value, "fit_ms": fit_rec_ms, "backward_ms": bwd_ms,
+                        "achieved_tflops": fa_tf, "frac": fa_tf / peak_tf,
+                        "algorithmic_flops_per_step": flops.fit_adjoint_flops(lengths)},
+        "plain_fit": {"tracks_per_s": fr.n_tracks / (plain_ms / 1e3), "ms": plain_ms,
+                      "hits_per_s": fr.n_tracks / (plain_ms / 1e3) * float(lengths.mean()),
+                      "roofline": {"bound": "alu", "achieved": fit_tf, "peak": peak_tf, "unit": "TFLOP/s",
+                                   "frac": fit_tf / peak_tf, "traffic": _traffic("fit_" + args.mode),
+                                   "kernel": "fit_kernel<4,24> + length ordering",
+                                   "algorithmic_flops_per_launch": fit_fl},
+                      "e2e": e2e_plain},
         "e2e": e2e,
-        "gpu_launches": 3 * args.steps,
+        "gpu_launches": 4 * args.steps,
         "clocks": clocks,
     }
     if not args.no_cpu_baseline:

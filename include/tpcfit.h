@@ -127,6 +127,32 @@ tpcfit_status tpcfit_fit(tpcfit_handle* h, const tpcfit_hits* hits, const int32_
                          const float* seeds, float* params_out, float* cov_out, float* chi2_out, int32_t* ndf_out,
                          void* stream);
 
+/* Record checkpoints for the adjoint (record = 1) or not (0, default).  With
+ * recording on, tpcfit_fit also stores the filter state before every 16th step
+ * of both passes (about 9 floats per cluster, handle-owned, grown as needed) so
+ * that tpcfit_fit_backward can follow.  Any tpcfit_fit call replaces the
+ * recording. */
+tpcfit_status tpcfit_set_record(tpcfit_handle* h, int record);
+
+/* Adjoint of the recorded fit: gradients of L = sum_i grad_chi2[i] * chi2_i.
+ * Inputs must be those of the last tpcfit_fit on this handle, which must have
+ * run with recording on and in the same mode (otherwise ESTATE):
+ *   hits, track_offsets, n_tracks: as for tpcfit_fit;
+ *   ndf:        device int32 [n_tracks], the ndf output of that fit;
+ *   grad_chi2:  device float [n_tracks], dL/dchi2_i.
+ * Outputs (device, overwritten):
+ *   grad_align: float [36][152][2], dL/d(dy, dz) of the alignment offsets;
+ *   grad_seeds: float [5][n_tracks], dL/dseed;
+ *   grad_meas:  float [n_hits][2], dL/d(measured y, z) per cluster, or NULL.
+ * The backward recomputes each 16-step segment from its checkpoint and runs the
+ * hand-written reverse of every step.  Fast mode accumulates grad_align with
+ * atomics; deterministic mode writes per-cluster gradients, sorts the clusters
+ * by (sector, row) with a stable radix sort and sums each key in a fixed order,
+ * so grad_align is bitwise reproducible.  Tracks with ndf <= 0 contribute 0. */
+tpcfit_status tpcfit_fit_backward(tpcfit_handle* h, const tpcfit_hits* hits, const int32_t* track_offsets,
+                                  int32_t n_tracks, const int32_t* ndf, const float* grad_chi2, float* grad_align,
+                                  float* grad_seeds, float* grad_meas, void* stream);
+
 /* Fit with HOST buffers: copies hits, offsets and seeds to the device, fits and
  * copies the outputs back, all on `stream`, then synchronises the stream.
  * Same argument meaning as tpcfit_fit with every array in host memory

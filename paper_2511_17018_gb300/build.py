@@ -33,6 +33,7 @@ UNITS = {
     "fit_det.cu": DET,
     "length_order.cu": [],
     "tpcfit_noalloc.cu": [],
+    "key_reduce.cu": [],
 }
 
 

@@ -1,0 +1,553 @@
+// Adjoint (reverse mode) of the batched track fit.  Included after
+// fit_core.cuh by the same kernel module, so that the forward recomputation
+// uses the module's own arithmetic bit for bit.
+//
+// Objective: L = sum_i g_i chi2_i, chi2_i the inward-refit chi2 of track i.
+// Gradients: dL/dm_h for every cluster measurement m_h = (y - dy, z - dz)
+// (hence dL/d(dy, dz)[sector][row] = -sum over the clusters with that key),
+// and dL/dseed_i.  The outward pass feeds the inward one through its final
+// state (the covariance is reset, the outward chi2 is not part of L).
+//
+// Checkpoints: the forward writes the filter state (p, L, x, sector, chi2)
+// before every 16th step of each pass.  The backward walks the segments of a
+// track in reverse: it recomputes a segment's 16 steps from its checkpoint into
+// a per-thread state array, then reverses the steps one by one (recomputing
+// each step's intermediates from the state before it).
+#pragma once
+
+namespace tpcfit {
+namespace TPCFIT_NS {
+
+constexpr int kCkptEvery = 16;
+constexpr int kCkptFloats = 36;  // p 5, L 25, x, sector (bits), chi2, 3 pad
+
+struct JacBar {
+  float yy, ys, yq, zy, zs, zt, zq, sy, ss, sq;
+};
+
+// d/du of asinc_f(u), consistent with the branch asinc_f takes.
+__device__ __forceinline__ float asinc_deriv(float u) {
+  const float au = u < 0.0f ? -u : u;
+  if (au <= 0.25f) {
+    const float c1 = static_cast<float>(1.0 / 6.0);
+    const float c2 = static_cast<float>(3.0 / 40.0);
+    const float c3 = static_cast<float>(5.0 / 112.0);
+    const float c4 = static_cast<float>(35.0 / 1152.0);
+    const float c5 = static_cast<float>(63.0 / 2816.0);
+    const float c6 = static_cast<float>(231.0 / 13312.0);
+    const float q = u * u;
+    float acc = 6.0f * c6;
+    acc = acc * q + 5.0f * c5;
+    acc = acc * q + 4.0f * c4;
+    acc = acc * q + 3.0f * c3;
+    acc = acc * q + 2.0f * c2;
+    acc = acc * q + c1;
+    return (2.0f * u) * acc;
+  }
+#if TPCFIT_DET
+  const double ud = (double)u;
+  const double sq = sqrt((1.0 - ud) * (1.0 + ud));
+  return (float)((ud / sq - asin_f64(ud)) / (ud * ud));
+#else
+  return (u * rsqrtf((1.0f - u) * (1.0f + u)) - asinf(u)) / (u * u);
+#endif
+}
+
+// Reverse of scalar_update<H>.  p, L: state before the update; b_p, b_L: in =
+// adjoint after the update, out = adjoint before; b_chi: adjoint of chi2 (the
+// same before and after).  b_m receives the adjoint of the measured value.
+template <int H>
+__device__ __forceinline__ void scalar_update_rev(const float p[5], const float L[5][5], float mv, float b_p[5],
+                                                  float b_L[5][5], float b_chi, float& b_m) {
+  const float v = c_geo.v_meas;
+  float a[5];
+#pragma unroll
+  for (int c = 0; c < 5; ++c) a[c] = L[H][c];
+  float s2 = v + a[0] * a[0];
+#pragma unroll
+  for (int c = 1; c < 5; ++c) s2 = s2 + a[c] * a[c];
+  float alpha, beta, gamma;
+  potter_coeffs(s2, v, c_geo.sqrt_v, alpha, beta, gamma);
+  const float r = mv - p[H];
+  float la[5], K[5];
+#pragma unroll
+  for (int i = 0; i < 5; ++i) {
+    float acc = L[i][0] * a[0];
+#pragma unroll
+    for (int c = 1; c < 5; ++c) acc = acc + L[i][c] * a[c];
+    la[i] = acc;
+    K[i] = acc * alpha;
+  }
+  // p' = p + K r ; chi2' = chi2 + r^2 alpha
+  float b_K[5], b_a[5];
+  float b_r = 0.0f, b_alpha = 0.0f, b_gamma = 0.0f, b_beta = 0.0f;
+#pragma unroll
+  for (int i = 0; i < 5; ++i) {
+    b_K[i] = r * b_p[i];
+    b_r += K[i] * b_p[i];
+  }
+  b_r += 2.0f * r * alpha * b_chi;
+  b_alpha += r * r * b_chi;
+#pragma unroll
+  for (int c = 0; c < 5; ++c) b_a[c] = 0.0f;
+  // L'_i = L_i - (gamma K_i) a (i != H)
+#pragma unroll
+  for (int i = 0; i < 5; ++i) {
+    if (i == H) continue;
+    const float gk = gamma * K[i];
+    float b_gk = 0.0f;
+#pragma unroll
+    for (int c = 0; c < 5; ++c) {
+      b_gk -= b_L[i][c] * a[c];
+      b_a[c] -= gk * b_L[i][c];
+    }
+    b_gamma += K[i] * b_gk;
+    b_K[i] += gamma * b_gk;
+  }
+  // L'_H = beta a
+#pragma unroll
+  for (int c = 0; c < 5; ++c) {
+    b_a[c] += beta * b_L[H][c];
+    b_beta += a[c] * b_L[H][c];
+  }
+  // gamma = 1/(1 + beta)
+  b_beta -= gamma * gamma * b_gamma;
+  // K_i = la_i alpha
+  float b_la[5];
+#pragma unroll
+  for (int i = 0; i < 5; ++i) {
+    b_la[i] = alpha * b_K[i];
+    b_alpha += la[i] * b_K[i];
+  }
+  // r = m - p_H
+  b_m = b_r;
+  b_p[H] -= b_r;
+  // alpha = 1/s2, beta = sqrt(v/s2)
+  const float b_s2 = -(alpha * alpha) * b_alpha - 0.5f * (beta * alpha) * b_beta;
+  // la_i = L_i . a (i != H); la_H = a . a
+#pragma unroll
+  for (int i = 0; i < 5; ++i) {
+    if (i == H) continue;
+#pragma unroll
+    for (int c = 0; c < 5; ++c) {
+      b_L[i][c] += a[c] * b_la[i];
+      b_a[c] += L[i][c] * b_la[i];
+    }
+  }
+#pragma unroll
+  for (int c = 0; c < 5; ++c) b_a[c] += 2.0f * a[c] * (b_la[H] + b_s2);
+  // a = L_H: row H enters only through a
+#pragma unroll
+  for (int c = 0; c < 5; ++c) b_L[H][c] = b_a[c];
+}
+
+// Reverse of transport (L' = J L): b_L in = adjoint of L', out = adjoint of L;
+// bJ = adjoint of the Jacobian entries.  L: the factor before the transport.
+__device__ __forceinline__ void transport_rev(const float L[5][5], const Jac& J, float b_L[5][5], JacBar& bJ) {
+  bJ.yy = bJ.ys = bJ.yq = bJ.zy = bJ.zs = bJ.zt = bJ.zq = bJ.sy = bJ.ss = bJ.sq = 0.0f;
+#pragma unroll
+  for (int c = 0; c < 5; ++c) {
+    const float b0 = b_L[0][c], b1 = b_L[1][c], b2 = b_L[2][c];
+    bJ.ys += b0 * L[2][c];
+    bJ.yq += b0 * L[4][c];
+    bJ.zs += b1 * L[2][c];
+    bJ.zt += b1 * L[3][c];
+    bJ.zq += b1 * L[4][c];
+    bJ.sq += b2 * L[4][c];
+    b_L[3][c] += J.zt * b1;
+    b_L[4][c] += J.yq * b0 + J.zq * b1 + J.sq * b2;
+    if (!J.rot) {
+      b_L[2][c] = b2 + J.ys * b0 + J.zs * b1;
+    } else {
+      bJ.yy += b0 * L[0][c];
+      bJ.zy += b1 * L[0][c];
+      bJ.sy += b2 * L[0][c];
+      bJ.ss += b2 * L[2][c];
+      b_L[0][c] = J.yy * b0 + J.zy * b1 + J.sy * b2;
+      b_L[2][c] = J.ys * b0 + J.zs * b1 + J.ss * b2;
+    }
+  }
+}
+
+// Reverse of predict_t: b_po = adjoint of the predicted state, bJ = adjoint of
+// the Jacobian entries; b_pi receives the adjoint of the state before the step.
+__device__ __forceinline__ void predict_rev(const PredTape& tp, const Jac& J, float t, const float b_po[5],
+                                            const JacBar& bJ, float b_pi[5]) {
+  const float kappa = c_geo.kappa;
+  const float dx = tp.dx, s1 = tp.s1, s2 = tp.s2, ic1 = tp.ic1, ic2 = tp.ic2, Tm = tp.Tm, tt = tp.tt;
+  float b_t = b_po[3], b_q = b_po[4], b_s2 = b_po[2];
+  float b_s1 = 0.0f, b_dx = 0.0f, b_k = 0.0f, b_kdx = 0.0f, b_ic1 = 0.0f, b_ic2 = 0.0f, b_c1 = 0.0f, b_c2 = 0.0f;
+  float b_Tm = 0.0f, b_tt = 0.0f, b_dl = 0.0f, b_w = 0.0f, b_rr = 0.0f;
+  float bJys0 = bJ.ys, bJzs0 = bJ.zs;
+  if (J.rot) {
+    const float rr = J.ss;
+    b_rr = bJ.ss + bJ.ys * tp.Jys0 + bJ.zs * tp.Jzs0;
+    bJys0 = bJ.ys * rr;
+    bJzs0 = bJ.zs * rr;
+    b_k -= tp.sa * bJ.sy;
+    b_t -= tp.sa * ic2 * bJ.zy;
+    b_ic2 -= tp.sa * t * bJ.zy;
+    b_s2 -= tp.sa * ic2 * bJ.yy;
+    b_ic2 -= tp.sa * s2 * bJ.yy;
+  }
+  // Jsq = dx kappa ; Jzq = (t kappa) Lk
+  b_dx += kappa * bJ.sq;
+  b_t += kappa * tp.Lk * bJ.zq;
+  const float b_Lk = t * kappa * bJ.zq;
+  if (tp.series) {
+    const float i2 = ic1 * ic1, i3 = i2 * ic1, i5 = i3 * i2, i7 = i5 * i2, s1s = s1 * s1;
+    const float a1 = (s1 * i3) * 0.5f;
+    const float a2 = ((1.0f + 2.0f * s1s) * i5) * static_cast<float>(1.0 / 3.0);
+    const float a3 = ((s1 * (3.0f + 2.0f * s1s)) * i7) * 0.125f;
+    const float kdx = tp.kdx, Q = a2 + kdx * a3, P = a1 + kdx * Q;
+    b_dx += 2.0f * dx * P * b_Lk;
+    const float b_P = dx * dx * b_Lk;
+    const float b_a1 = b_P;
+    b_kdx += Q * b_P;
+    const float b_Q = kdx * b_P;
+    const float b_a2 = b_Q;
+    b_kdx += a3 * b_Q;
+    const float b_a3 = kdx * b_Q;
+    float b_s1s = 0.0f, b_i2 = 0.0f, b_i3 = 0.0f, b_i5 = 0.0f, b_i7 = 0.0f;
+    b_s1 += 0.5f * i3 * b_a1;
+    b_i3 += 0.5f * s1 * b_a1;
+    b_s1s += static_cast<float>(2.0 / 3.0) * i5 * b_a2;
+    b_i5 += (1.0f + 2.0f * s1s) * static_cast<float>(1.0 / 3.0) * b_a2;
+    b_s1 += 0.125f * (3.0f + 2.0f * s1s) * i7 * b_a3;
+    b_s1s += 0.25f * s1 * i7 * b_a3;
+    b_i7 += 0.125f * s1 * (3.0f + 2.0f * s1s) * b_a3;
+    b_s1 += 2.0f * s1 * b_s1s;
+    b_i5 += i2 * b_i7;
+    b_i2 += i5 * b_i7;
+    b_i3 += i2 * b_i5;
+    b_i2 += i3 * b_i5;
+    b_i2 += ic1 * b_i3;
+    b_ic1 += i2 * b_i3;
+    b_ic1 += 2.0f * ic1 * b_i2;
+  } else {
+    const float k = tp.k;
+    const float b_D = b_Lk / k;
+    b_k -= tp.Lk / k * b_Lk;
+    b_dx += ic2 * b_D;
+    b_ic2 += dx * b_D;
+    b_dl -= b_D;
+  }
+  b_dl += bJ.zt;  // Jzt = dl
+  {  // Jzs0 = (t dx) (Tm (ic1 ic2))
+    const float E = ic1 * ic2, F = Tm * E, G = t * dx;
+    const float b_G = F * bJzs0, b_F = G * bJzs0, b_E = Tm * b_F;
+    b_Tm += E * b_F;
+    b_ic1 += ic2 * b_E;
+    b_ic2 += ic1 * b_E;
+    b_t += dx * b_G;
+    b_dx += t * b_G;
+  }
+  {  // Jyq = ((dx kappa) dx) (tt (ic2 / 2))
+    const float M = (dx * kappa) * dx;
+    b_dx += 2.0f * kappa * dx * (tt * (ic2 * 0.5f)) * bJ.yq;
+    b_tt += ic2 * 0.5f * M * bJ.yq;
+    b_ic2 += tt * 0.5f * M * bJ.yq;
+  }
+  {  // Jys0 = (dx tt) ((ic1 + ic2) / 2)
+    const float Hh = (ic1 + ic2) * 0.5f;
+    b_dx += tt * Hh * bJys0;
+    b_tt += dx * Hh * bJys0;
+    b_ic1 += 0.5f * dx * tt * bJys0;
+    b_ic2 += 0.5f * dx * tt * bJys0;
+  }
+  b_Tm += 2.0f * Tm * b_tt;  // tt = 1 + Tm^2
+  // z2 = z1 + t dl ; y2 = y1 + dx Tm
+  b_t += tp.dl * b_po[1];
+  b_dl += t * b_po[1];
+  b_dx += Tm * b_po[0];
+  b_Tm += dx * b_po[0];
+  // dl = (dx w) A ; A = asinc(sig) ; sig = kdx w
+  const float b_A = dx * tp.w * b_dl;
+  b_dx += tp.w * tp.A * b_dl;
+  b_w += dx * tp.A * b_dl;
+  const float b_sig = asinc_deriv(tp.sig) * b_A;
+  b_kdx += tp.w * b_sig;
+  b_w += tp.kdx * b_sig;
+  // w = c1 + s1 Tm
+  b_c1 += b_w;
+  b_s1 += Tm * b_w;
+  b_Tm += s1 * b_w;
+  // Tm = (s1 + s2) / den, den = c1 + c2
+  const float b_num = b_Tm / tp.den;
+  const float b_den = -Tm * b_Tm / tp.den;
+  b_s1 += b_num;
+  b_s2 += b_num;
+  b_c1 += b_den;
+  b_c2 += b_den;
+  // (c, 1/c) = sqrt_and_inv(u), u = (1 - s)(1 + s)
+  const float b_u2 = 0.5f * ic2 * (b_c2 - ic2 * ic2 * b_ic2);
+  const float b_u1 = 0.5f * ic1 * (b_c1 - ic1 * ic1 * b_ic1);
+  b_s2 -= 2.0f * s2 * b_u2;
+  b_s1 -= 2.0f * s1 * b_u1;
+  // s2 = s1 + kdx ; kdx = k dx ; k = q kappa
+  b_s1 += b_s2;
+  b_kdx += b_s2;
+  b_k += dx * b_kdx;
+  b_dx += tp.k * b_kdx;
+  b_q += kappa * b_k;
+  // dx = X - x1
+  const float b_x1 = -b_dx;
+  if (J.rot) {
+    // x1 = x ca + y sa ; y1 = y ca - x sa ; s1 = s ca - c sa ; cr = c ca + s sa ;
+    // rr = cr / c ; c = sqrt((1 - s)(1 + s))
+    const float rr = J.ss;
+    const float b_cr = b_rr / tp.c;
+    float b_c = -rr * b_rr / tp.c;
+    b_pi[0] = tp.sa * b_x1 + tp.ca * b_po[0];
+    float b_s = tp.ca * b_s1;
+    b_c -= tp.sa * b_s1;
+    b_c += tp.ca * b_cr;
+    b_s += tp.sa * b_cr;
+    b_s -= (tp.s / tp.c) * b_c;
+    b_pi[2] = b_s;
+  } else {
+    b_pi[0] = b_po[0];
+    b_pi[2] = b_s1;
+  }
+  b_pi[1] = b_po[1];
+  b_pi[3] = b_t;
+  b_pi[4] = b_q;
+}
+
+// ---------------------------------------------------------------- backward kernel
+struct StepState {
+  float p[5];
+  float L[5][5];
+  float x;
+  int sec;
+};
+
+__device__ __forceinline__ void load_ckpt(const float* src, StepState& S, float& chi2) {
+  const float4* s4 = reinterpret_cast<const float4*>(src);
+  float v[kCkptFloats];
+#pragma unroll
+  for (int j = 0; j < kCkptFloats / 4; ++j) {
+    const float4 f = __ldg(s4 + j);
+    v[4 * j] = f.x;
+    v[4 * j + 1] = f.y;
+    v[4 * j + 2] = f.z;
+    v[4 * j + 3] = f.w;
+  }
+#pragma unroll
+  for (int c = 0; c < 5; ++c) S.p[c] = v[c];
+#pragma unroll
+  for (int i = 0; i < 5; ++i)
+#pragma unroll
+    for (int c = 0; c < 5; ++c) S.L[i][c] = v[5 + 5 * i + c];
+  S.x = v[30];
+  S.sec = __float_as_int(v[31]);
+  chi2 = v[32];
+}
+
+// Cluster h of the pass: measurement (alignment subtracted), row, sector.
+__device__ __forceinline__ bool read_hit(const BwdArgs& a, const float* align_s, int h, float& m0, float& m1,
+                                         int& row, int& sec) {
+  const int rsv = (int)__ldg(a.rowsec + h);
+  row = rsv >> 6;
+  sec = rsv & 63;
+  if (row >= c_geo.n_rows || sec >= kNSectors) return false;
+  const float2 d = reinterpret_cast<const float2*>(align_s)[sec * kMaxRows + row];
+  m0 = __ldg(a.y + h) - d.x;
+  m1 = __ldg(a.z + h) - d.y;
+  return true;
+}
+
+// Forward of one step on a StepState (the same operations as the fit).
+__device__ __forceinline__ void step_fwd(const SmemTables& T, StepState& S, float& chi2, bool first, int row,
+                                         int sec18, float m0, float m1) {
+  if (first) {
+    S.x = T.row_x[row];
+    S.sec = sec18;
+  } else {
+    float pn[5];
+    Jac J;
+    predict(T, S.p, S.x, S.sec, sec18, T.row_x[row], pn, J);
+#pragma unroll
+    for (int c = 0; c < 5; ++c) S.p[c] = pn[c];
+    S.x = T.row_x[row];
+    S.sec = sec18;
+    transport(S.L, J);
+  }
+  scalar_update<0>(S.p, S.L, chi2, m0);
+  scalar_update<1>(S.p, S.L, chi2, m1);
+}
+
+// Reverse of one step from the state before it.  b_p, b_L: in = adjoint after
+// the step, out = adjoint before it.
+__device__ __forceinline__ void step_rev(const SmemTables& T, const StepState& S0, bool first, int row, int sec18,
+                                         float m0, float m1, float b_p[5], float b_L[5][5], float b_chi, float& b_m0,
+                                         float& b_m1) {
+  float p1[5];
+  Jac J;
+  float L[5][5];
+  if (first) {
+#pragma unroll
+    for (int c = 0; c < 5; ++c) p1[c] = S0.p[c];
+  } else {
+    predict(T, S0.p, S0.x, S0.sec, sec18, T.row_x[row], p1, J);
+  }
+  // state before the z update
+  float p2[5];
+  float chi_dummy = 0.0f;
+#pragma unroll
+  for (int c = 0; c < 5; ++c) p2[c] = p1[c];
+#pragma unroll
+  for (int i = 0; i < 5; ++i)
+#pragma unroll
+    for (int c = 0; c < 5; ++c) L[i][c] = S0.L[i][c];
+  if (!first) transport(L, J);
+  scalar_update<0>(p2, L, chi_dummy, m0);
+  scalar_update_rev<1>(p2, L, m1, b_p, b_L, b_chi, b_m1);
+  // state before the y update (recomputed)
+#pragma unroll
+  for (int i = 0; i < 5; ++i)
+#pragma unroll
+    for (int c = 0; c < 5; ++c) L[i][c] = S0.L[i][c];
+  if (!first) transport(L, J);
+  scalar_update_rev<0>(p1, L, m0, b_p, b_L, b_chi, b_m0);
+  if (first) return;
+  JacBar bJ;
+  transport_rev(S0.L, J, b_L, bJ);
+  float pn[5];
+  PredTape tp;
+  predict_t(T, S0.p, S0.x, S0.sec, sec18, T.row_x[row], pn, J, tp);
+  float b_pi[5];
+  predict_rev(tp, J, S0.p[3], b_p, bJ, b_pi);
+#pragma unroll
+  for (int c = 0; c < 5; ++c) b_p[c] = b_pi[c];
+}
+
+template <int WARPS>
+__global__ void __launch_bounds__(WARPS * 32, 1) backward_kernel(BwdArgs a) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  BlockSmem& B = *reinterpret_cast<BlockSmem*>(smem_raw);
+  load_tables(B.T);
+  for (int i = threadIdx.x; i < kAlignFloats; i += blockDim.x) B.align[i] = __ldg(a.align + i);
+  __syncthreads();
+  const SmemTables& T = B.T;
+  const int lane = threadIdx.x & 31;
+  const int64_t n_chunks = ((int64_t)a.n_tracks + kWarp - 1) / kWarp;
+  const int64_t N = a.n_tracks;
+  StepState seg[kCkptEvery];
+
+#pragma unroll 1
+  for (;;) {
+    int64_t chunk = 0;
+    if (lane == 0) chunk = (int64_t)atomicAdd(a.work, 1u);
+    chunk = __shfl_sync(0xffffffffu, chunk, 0);
+    if (chunk >= n_chunks) break;
+    const int64_t slot = chunk * kWarp + lane;
+    if (slot >= N) continue;
+    const int32_t trk = a.perm ? a.perm[slot] : (int32_t)slot;
+    const float g = __ldg(a.grad_chi2 + trk);
+    const bool fitted = a.ndf[trk] > 0;
+    float b_p[5] = {0.0f, 0.0f, 0.0f, 0.0f, 0.0f};
+    if (fitted) {
+      const int begin = a.off[trk];
+      const int last = a.ck_last[trk];
+      float b_L[5][5];
+      // pass 1 (inward) is reversed first, then pass 0 (outward)
+#pragma unroll 1
+      for (int pass = 1; pass >= 0; --pass) {
+#pragma unroll
+        for (int i = 0; i < 5; ++i)
+#pragma unroll
+          for (int c = 0; c < 5; ++c) b_L[i][c] = 0.0f;
+        const float b_chi = pass == 1 ? g : 0.0f;
+        const int steps = last + 1;
+        const int nseg = (steps + kCkptEvery - 1) / kCkptEvery;
+        const float* ckp = a.ck + ((int64_t)pass * a.ck_slots + (begin >> 4) + trk) * kCkptFloats;
+#pragma unroll 1
+        for (int s = nseg - 1; s >= 0; --s) {
+          StepState S;
+          float chi2;
+          load_ckpt(ckp + (int64_t)s * kCkptFloats, S, chi2);
+          const int i0 = s * kCkptEvery;
+          const int cnt = min(kCkptEvery, steps - i0);
+          // recompute the segment, keeping the state before each step
+#pragma unroll 1
+          for (int kk = 0; kk < cnt; ++kk) {
+            const int i = i0 + kk;
+            const int h = pass == 0 ? begin + i : begin + last - i;
+            float m0 = 0.0f, m1 = 0.0f;
+            int row = 0, sec = 0;
+            read_hit(a, B.align, h, m0, m1, row, sec);
+            seg[kk] = S;
+            step_fwd(T, S, chi2, i == 0, row, sec % kNSide, m0, m1);
+          }
+          // reverse the segment
+#pragma unroll 1
+          for (int kk = cnt - 1; kk >= 0; --kk) {
+            const int i = i0 + kk;
+            const int h = pass == 0 ? begin + i : begin + last - i;
+            float m0 = 0.0f, m1 = 0.0f;
+            int row = 0, sec = 0;
+            read_hit(a, B.align, h, m0, m1, row, sec);
+            float b_m0 = 0.0f, b_m1 = 0.0f;
+            step_rev(T, seg[kk], i == 0, row, sec % kNSide, m0, m1, b_p, b_L, b_chi, b_m0, b_m1);
+            if (a.grad_meas) {
+              float2* gm = reinterpret_cast<float2*>(a.grad_meas) + h;
+              if (pass == 1) {
+                *gm = make_float2(b_m0, b_m1);
+              } else {
+                const float2 o = *gm;
+                *gm = make_float2(o.x + b_m0, o.y + b_m1);
+              }
+            }
+            if (a.grad_align_atomic) {
+              float* dst = a.grad_align_atomic + (sec * kMaxRows + row) * 2;
+              atomicAdd(dst, -b_m0);
+              atomicAdd(dst + 1, -b_m1);
+            }
+          }
+        }
+        // the inward pass starts from the outward result with the factor reset:
+        // b_p carries over, b_L does not
+      }
+    } else if (a.grad_meas) {
+      const int begin = a.off[trk];
+      const int end = a.off[trk + 1];
+      for (int h = begin; h < end; ++h) reinterpret_cast<float2*>(a.grad_meas)[h] = make_float2(0.0f, 0.0f);
+    }
+#pragma unroll
+    for (int c = 0; c < 5; ++c) a.grad_seeds[(int64_t)c * N + trk] = b_p[c];
+  }
+}
+
+template <int WARPS>
+cudaError_t launch_backward_cfg(const BwdArgs& a, cudaStream_t s) {
+  constexpr int kThreads = WARPS * 32;
+  const size_t smem = sizeof(BlockSmem);
+  static int grid = 0;
+  if (grid == 0) {
+    cudaError_t e = cudaFuncSetAttribute(backward_kernel<WARPS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    int dev = 0, sms = 0, per_sm = 0;
+    e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, backward_kernel<WARPS>, kThreads, smem);
+    if (e != cudaSuccess) return e;
+    if (per_sm < 1) return cudaErrorInvalidConfiguration;
+    grid = sms * per_sm;
+  }
+  const int64_t chunks = ((int64_t)a.n_tracks + kWarp - 1) / kWarp;
+  const int64_t need = (chunks + WARPS - 1) / WARPS;
+  const int blocks = (int)(need < grid ? need : grid);
+  cudaError_t e = cudaMemsetAsync(a.work, 0, sizeof(unsigned int), s);
+  if (e != cudaSuccess) return e;
+  backward_kernel<WARPS><<<blocks, kThreads, smem, s>>>(a);
+  return cudaGetLastError();
+}
+
+inline cudaError_t launch_backward(const BwdArgs& a, cudaStream_t s) {
+  if (a.n_tracks <= 0) return cudaSuccess;
+  return launch_backward_cfg<8>(a, s);
+}
+
+}  // namespace TPCFIT_NS
+}  // namespace tpcfit

@@ -144,11 +144,22 @@ __device__ __forceinline__ void load_tables(SmemTables& t) {
 }
 
 // ---------------------------------------------------------------- one prediction step
+// Intermediates of one prediction, kept for its adjoint.  The fit ignores
+// them (the compiler drops the dead stores).
+struct PredTape {
+  float x, y, s;                // state before the step (pre-rotation)
+  float c, cr, ca, sa;          // rotation pieces
+  float x1, s1, dx, k, kdx, s2;
+  float c1, ic1, c2, ic2, Tm, den, w, sig, A, dl, tt;
+  float Jys0, Jzs0, Lk;
+  bool series;
+};
+
 // From state (p, x) in sector-frame a (mod 18) to pad row X in frame b: optional
 // rotation at the current point, then helix propagation at fixed Bz.  Returns
 // false, leaving nothing changed, if the step is impossible.
-__device__ __forceinline__ bool predict(const SmemTables& T, const float pin[5], float xin, int a, int b, float X,
-                                        float pout[5], Jac& J) {
+__device__ __forceinline__ bool predict_t(const SmemTables& T, const float pin[5], float xin, int a, int b, float X,
+                                          float pout[5], Jac& J, PredTape& tp) {
   const float kappa = c_geo.kappa;
   const float maxsnp = c_geo.max_snp;
   float x1 = xin, y1 = pin[0], s1 = pin[2];
@@ -156,6 +167,9 @@ __device__ __forceinline__ bool predict(const SmemTables& T, const float pin[5],
   const float q = pin[4];
   J.rot = (a != b);
   float cprev = 0.0f, crot = 0.0f, ca = 1.0f, sa = 0.0f;
+  tp.x = xin;
+  tp.y = pin[0];
+  tp.s = pin[2];
   if (J.rot) {
     ca = T.rot_c[a * kNSide + b];
     sa = T.rot_s[a * kNSide + b];
@@ -173,6 +187,10 @@ __device__ __forceinline__ bool predict(const SmemTables& T, const float pin[5],
     cprev = c;
     crot = cr;
   }
+  tp.c = cprev;
+  tp.cr = crot;
+  tp.ca = ca;
+  tp.sa = sa;
   const float dx = X - x1;
   const float k = q * kappa;
   const float kdx = k * dx;
@@ -181,10 +199,12 @@ __device__ __forceinline__ bool predict(const SmemTables& T, const float pin[5],
   float c1, ic1, c2, ic2;
   sqrt_and_inv((1.0f - s1) * (1.0f + s1), c1, ic1);
   sqrt_and_inv((1.0f - s2) * (1.0f + s2), c2, ic2);
-  const float Tm = (s1 + s2) / (c1 + c2);
+  const float den = c1 + c2;
+  const float Tm = (s1 + s2) / den;
   const float w = c1 + s1 * Tm;
   const float sig = kdx * w;
-  const float dl = (dx * w) * asinc_f(sig);
+  const float A = asinc_f(sig);
+  const float dl = (dx * w) * A;
   pout[0] = y1 + dx * Tm;
   pout[1] = pin[1] + t * dl;
   pout[2] = s2;
@@ -196,7 +216,8 @@ __device__ __forceinline__ bool predict(const SmemTables& T, const float pin[5],
   J.zs = (t * dx) * (Tm * (ic1 * ic2));
   J.zt = dl;
   float Lk;  // d(path)/dk
-  if (fabsf(kdx) < 0.01f) {
+  const bool series = fabsf(kdx) < 0.01f;
+  if (series) {
     const float i2 = ic1 * ic1;
     const float i3 = i2 * ic1;
     const float i5 = i3 * i2;
@@ -211,6 +232,9 @@ __device__ __forceinline__ bool predict(const SmemTables& T, const float pin[5],
   }
   J.zq = (t * kappa) * Lk;
   J.sq = dx * kappa;
+  tp.x1 = x1; tp.s1 = s1; tp.dx = dx; tp.k = k; tp.kdx = kdx; tp.s2 = s2;
+  tp.c1 = c1; tp.ic1 = ic1; tp.c2 = c2; tp.ic2 = ic2; tp.Tm = Tm; tp.den = den; tp.w = w; tp.sig = sig;
+  tp.A = A; tp.dl = dl; tp.tt = tt; tp.Jys0 = J.ys; tp.Jzs0 = J.zs; tp.Lk = Lk; tp.series = series;
   if (J.rot) {
     const float rr = crot / cprev;
     J.yy = ca - sa * (s2 * ic2);
@@ -226,6 +250,12 @@ __device__ __forceinline__ bool predict(const SmemTables& T, const float pin[5],
     J.ss = 1.0f;
   }
   return true;
+}
+
+__device__ __forceinline__ bool predict(const SmemTables& T, const float pin[5], float xin, int a, int b, float X,
+                                        float pout[5], Jac& J) {
+  PredTape tp;
+  return predict_t(T, pin, xin, a, b, X, pout, J, tp);
 }
 
 // L <- J L (rows t, q of J are identity).
@@ -367,7 +397,25 @@ struct BlockSmem {
   float align[kAlignFloats];
 };
 
-template <int RPS, int WARPS, int MINB>
+__device__ __forceinline__ void write_ckpt(const FitArgs& a, int pass, int begin, int trk, int seg,
+                                           const TrackState& S) {
+  float4* dst = reinterpret_cast<float4*>(a.ck + ((int64_t)pass * a.ck_slots + (begin >> 4) + trk + seg) * 36);
+  float v[36];
+#pragma unroll
+  for (int c = 0; c < 5; ++c) v[c] = S.p[c];
+#pragma unroll
+  for (int i = 0; i < 5; ++i)
+#pragma unroll
+    for (int c = 0; c < 5; ++c) v[5 + 5 * i + c] = S.L[i][c];
+  v[30] = S.x;
+  v[31] = __int_as_float(S.sec);
+  v[32] = S.chi2;
+  v[33] = v[34] = v[35] = 0.0f;
+#pragma unroll
+  for (int j = 0; j < 9; ++j) dst[j] = make_float4(v[4 * j], v[4 * j + 1], v[4 * j + 2], v[4 * j + 3]);
+}
+
+template <int RPS, int WARPS, int MINB, bool RECORD>
 __global__ void __launch_bounds__(WARPS * 32, MINB) fit_kernel(FitArgs a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   BlockSmem& B = *reinterpret_cast<BlockSmem*>(smem_raw);
@@ -410,6 +458,8 @@ __global__ void __launch_bounds__(WARPS * 32, MINB) fit_kernel(FitArgs a) {
       }
     }
     TrackState S;
+    S.x = 0.0f;
+    S.sec = 0;
     int last = 0;
     if (status == 0) {
 #pragma unroll
@@ -465,6 +515,7 @@ __global__ void __launch_bounds__(WARPS * 32, MINB) fit_kernel(FitArgs a) {
           const float m0 = st.y[buf][lane][k] - d.x;
           const float m1 = st.z[buf][lane][k] - d.y;
           const int sec18 = sec % kNSide;
+          if (RECORD && (i & 15) == 0) write_ckpt(a, pass, begin, trk, i >> 4, S);
           if (i == 0) {
             // first cluster of the pass: the state sits on its row already
             S.x = T.row_x[row];
@@ -495,6 +546,7 @@ __global__ void __launch_bounds__(WARPS * 32, MINB) fit_kernel(FitArgs a) {
 
     // ---- outputs at the track's own index
     if (!have) continue;
+    if (RECORD) a.ck_last[trk] = last;
     const int64_t N = a.n_tracks;
     if (status == 0 && S.used >= 3) {
 #pragma unroll
@@ -524,20 +576,20 @@ __global__ void __launch_bounds__(WARPS * 32, MINB) fit_kernel(FitArgs a) {
   }
 }
 
-template <int RPS, int WARPS, int MINB>
+template <int RPS, int WARPS, int MINB, bool RECORD>
 cudaError_t launch_cfg(const FitArgs& a, cudaStream_t s) {
   constexpr int kThreads = WARPS * 32;
   const size_t smem = sizeof(BlockSmem) + WARPS * sizeof(WarpStage<RPS>);
   static int grid = 0;
   if (grid == 0) {
     cudaError_t e =
-        cudaFuncSetAttribute(fit_kernel<RPS, WARPS, MINB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        cudaFuncSetAttribute(fit_kernel<RPS, WARPS, MINB, RECORD>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     int dev = 0, sms = 0, per_sm = 0;
     e = cudaGetDevice(&dev);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     if (e == cudaSuccess)
-      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fit_kernel<RPS, WARPS, MINB>, kThreads, smem);
+      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fit_kernel<RPS, WARPS, MINB, RECORD>, kThreads, smem);
     if (e != cudaSuccess) return e;
     if (per_sm < 1) return cudaErrorInvalidConfiguration;
     grid = sms * per_sm;
@@ -547,22 +599,27 @@ cudaError_t launch_cfg(const FitArgs& a, cudaStream_t s) {
   const int blocks = (int)(need < grid ? need : grid);
   cudaError_t e = cudaMemsetAsync(a.work, 0, sizeof(unsigned int), s);
   if (e != cudaSuccess) return e;
-  fit_kernel<RPS, WARPS, MINB><<<blocks, kThreads, smem, s>>>(a);
+  fit_kernel<RPS, WARPS, MINB, RECORD><<<blocks, kThreads, smem, s>>>(a);
   return cudaGetLastError();
 }
 
 // Supported (rows per stage, warps per block) shapes; the shared-memory budget
 // (alignment table + double buffer) decides how many blocks fit on an SM.
+template <bool RECORD>
+inline cudaError_t launch_rec(const FitArgs& a, int rps, int warps, cudaStream_t s) {
+  if (rps == 4 && warps == 8) return launch_cfg<4, 8, 2, RECORD>(a, s);
+  if (rps == 4 && warps == 12) return launch_cfg<4, 12, 2, RECORD>(a, s);
+  if (rps == 4 && warps == 24) return launch_cfg<4, 24, 1, RECORD>(a, s);
+  if (rps == 8 && warps == 8) return launch_cfg<8, 8, 2, RECORD>(a, s);
+  if (rps == 8 && warps == 16) return launch_cfg<8, 16, 1, RECORD>(a, s);
+  if (rps == 16 && warps == 8) return launch_cfg<16, 8, 1, RECORD>(a, s);
+  return cudaErrorInvalidValue;
+}
+
 inline cudaError_t launch(const FitArgs& a, int lanes_per_track, int rps, int warps, cudaStream_t s) {
   if (a.n_tracks <= 0) return cudaSuccess;
   if (lanes_per_track != 1) return cudaErrorInvalidValue;
-  if (rps == 4 && warps == 8) return launch_cfg<4, 8, 2>(a, s);
-  if (rps == 4 && warps == 12) return launch_cfg<4, 12, 2>(a, s);
-  if (rps == 4 && warps == 24) return launch_cfg<4, 24, 1>(a, s);
-  if (rps == 8 && warps == 8) return launch_cfg<8, 8, 2>(a, s);
-  if (rps == 8 && warps == 16) return launch_cfg<8, 16, 1>(a, s);
-  if (rps == 16 && warps == 8) return launch_cfg<16, 8, 1>(a, s);
-  return cudaErrorInvalidValue;
+  return a.ck ? launch_rec<true>(a, rps, warps, s) : launch_rec<false>(a, rps, warps, s);
 }
 
 cudaError_t upload(const GeoConst& g, cudaStream_t s) {

@@ -5,10 +5,12 @@
 #define TPCFIT_DET 1
 #define TPCFIT_NS det
 #include "fit_core.cuh"
+#include "adjoint_core.cuh"
 
 namespace tpcfit {
 static ConstRegistration reg_det("fit_det", &det::upload);
 cudaError_t launch_fit_det(const FitArgs& a, int lanes_per_track, int rows_per_stage, int warps, cudaStream_t s) {
   return det::launch(a, lanes_per_track, rows_per_stage, warps, s);
 }
+cudaError_t launch_backward_det(const BwdArgs& a, cudaStream_t s) { return det::launch_backward(a, s); }
 }  // namespace tpcfit

@@ -4,10 +4,12 @@
 #define TPCFIT_DET 0
 #define TPCFIT_NS fast
 #include "fit_core.cuh"
+#include "adjoint_core.cuh"
 
 namespace tpcfit {
 static ConstRegistration reg_fast("fit_fast", &fast::upload);
 cudaError_t launch_fit_fast(const FitArgs& a, int lanes_per_track, int rows_per_stage, int warps, cudaStream_t s) {
   return fast::launch(a, lanes_per_track, rows_per_stage, warps, s);
 }
+cudaError_t launch_backward_fast(const BwdArgs& a, cudaStream_t s) { return fast::launch_backward(a, s); }
 }  // namespace tpcfit

@@ -47,6 +47,31 @@ struct FitArgs {
   int32_t* ndf;
   unsigned long long* err;     // error word: code << 56 | track
   unsigned int* work;          // work-item counter (zeroed by the launcher)
+  // checkpoint recording for the adjoint (null = off)
+  float* ck;                   // [2][ck_slots][36] filter state before every 16th step of each pass
+  int32_t* ck_last;            // [n_tracks] index of the last cluster of the outward pass
+  int64_t ck_slots;            // slots per pass: n_hits / 16 + n_tracks + 1
+};
+
+// Arguments of one backward launch (same frame as the recorded fit).
+struct BwdArgs {
+  const float* y;
+  const float* z;
+  const uint16_t* rowsec;
+  int64_t n_hits;
+  const int32_t* off;
+  int32_t n_tracks;
+  const float* align;
+  const int32_t* perm;
+  const int32_t* ndf;          // outputs of the recorded fit
+  const float* ck;
+  const int32_t* ck_last;
+  int64_t ck_slots;
+  const float* grad_chi2;      // [n_tracks] dL/dchi2_i
+  float* grad_seeds;           // [5][n_tracks]
+  float* grad_meas;            // [n_hits][2] dL/dm per cluster, or null
+  float* grad_align_atomic;    // [36][152][2] accumulated with atomics, or null
+  unsigned int* work;
 };
 
 // Error codes recorded in the device error word.
@@ -70,6 +95,15 @@ bool build_geo(const tpcfit_geometry* g, double bz, GeoConst& out);
 // ---- kernel launchers, one per module
 cudaError_t launch_fit_fast(const FitArgs& a, int lanes_per_track, int rows_per_stage, int warps, cudaStream_t s);
 cudaError_t launch_fit_det(const FitArgs& a, int lanes_per_track, int rows_per_stage, int warps, cudaStream_t s);
+cudaError_t launch_backward_fast(const BwdArgs& a, cudaStream_t s);
+cudaError_t launch_backward_det(const BwdArgs& a, cudaStream_t s);
+
+// Deterministic per-key reduction of cluster gradients (key_reduce.cu).
+size_t key_sort_scratch_bytes(int64_t n_hits);
+cudaError_t launch_key_sort(const uint16_t* rowsec, int64_t n_hits, int n_rows, void* scratch, int** sorted_out,
+                            int** key_start_out, cudaStream_t s);
+cudaError_t launch_key_reduce(const float* grad_meas, const int* sorted, const int* key_start, float* grad_align,
+                              cudaStream_t s);
 // true if (lanes_per_track, rows_per_stage, warps) is a compiled launch shape
 bool fit_shape_supported(int lanes_per_track, int rows_per_stage, int warps);
 

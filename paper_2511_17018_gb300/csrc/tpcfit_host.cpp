@@ -120,6 +120,21 @@ struct tpcfit_handle {
   // staging for tpcfit_fit_host
   unsigned char* d_stage = nullptr;
   size_t stage_cap = 0;
+  // adjoint: checkpoints of the last recorded fit
+  int record = 0;
+  float* d_ck = nullptr;
+  int64_t ck_cap = 0;          // floats
+  int32_t* d_ck_last = nullptr;
+  int64_t ck_last_cap = 0;
+  int64_t ck_slots = 0;
+  bool rec_valid = false;
+  int64_t rec_tracks = 0, rec_hits = 0;
+  int rec_det = 0;
+  // adjoint scratch: per-cluster gradients and the key sort
+  float* d_gm = nullptr;
+  int64_t gm_cap = 0;          // floats
+  unsigned char* d_keys = nullptr;
+  size_t keys_cap = 0;
 };
 
 namespace {
@@ -141,6 +156,18 @@ tpcfit_status make_resident(tpcfit_handle* h, cudaStream_t s) {
   if (e != cudaSuccess) return from_cuda(e);
   r.last_owner = h;
   r.last_device = h->device;
+  return TPCFIT_OK;
+}
+
+template <class T>
+tpcfit_status grow(T*& ptr, int64_t& cap, int64_t need) {
+  if (need <= cap) return TPCFIT_OK;
+  if (ptr) cudaFree(ptr);
+  ptr = nullptr;
+  cap = 0;
+  cudaError_t e = cudaMalloc(&ptr, sizeof(T) * (size_t)need);
+  if (e != cudaSuccess) return from_cuda(e);
+  cap = need;
   return TPCFIT_OK;
 }
 
@@ -212,6 +239,10 @@ void tpcfit_destroy(tpcfit_handle* h) {
   if (h->d_sort_scratch) cudaFree(h->d_sort_scratch);
   if (h->d_perm) cudaFree(h->d_perm);
   if (h->d_stage) cudaFree(h->d_stage);
+  if (h->d_ck) cudaFree(h->d_ck);
+  if (h->d_ck_last) cudaFree(h->d_ck_last);
+  if (h->d_gm) cudaFree(h->d_gm);
+  if (h->d_keys) cudaFree(h->d_keys);
   {
     Registry& r = registry();
     std::lock_guard<std::mutex> lk(r.mu);
@@ -282,6 +313,17 @@ tpcfit_status tpcfit_fit(tpcfit_handle* h, const tpcfit_hits* hits, const int32_
   a.ndf = ndf_out;
   a.err = h->d_err;
   a.work = h->d_work;
+  h->rec_valid = false;
+  if (h->record) {
+    const int64_t slots = hits->n_hits / 16 + (int64_t)n_tracks + 1;
+    st = grow(h->d_ck, h->ck_cap, 2 * slots * 36);
+    if (st == TPCFIT_OK) st = grow(h->d_ck_last, h->ck_last_cap, (int64_t)n_tracks);
+    if (st != TPCFIT_OK) return st;
+    a.ck = h->d_ck;
+    a.ck_last = h->d_ck_last;
+    a.ck_slots = slots;
+    h->ck_slots = slots;
+  }
   if (h->sort_by_length) {
     st = ensure_perm(h, n_tracks);
     if (st != TPCFIT_OK) return st;
@@ -291,6 +333,87 @@ tpcfit_status tpcfit_fit(tpcfit_handle* h, const tpcfit_hits* hits, const int32_
   }
   cudaError_t e = h->deterministic ? launch_fit_det(a, h->lanes_per_track, h->rows_per_stage, h->warps_per_block, s)
                                    : launch_fit_fast(a, h->lanes_per_track, h->rows_per_stage, h->warps_per_block, s);
+  if (e == cudaSuccess && h->record) {
+    h->rec_valid = true;
+    h->rec_tracks = n_tracks;
+    h->rec_hits = hits->n_hits;
+    h->rec_det = h->deterministic;
+  }
+  return from_cuda(e);
+}
+
+tpcfit_status tpcfit_set_record(tpcfit_handle* h, int record) {
+  if (!h || (record != 0 && record != 1)) return TPCFIT_EINVAL;
+  h->record = record;
+  if (!record) h->rec_valid = false;
+  return TPCFIT_OK;
+}
+
+tpcfit_status tpcfit_fit_backward(tpcfit_handle* h, const tpcfit_hits* hits, const int32_t* track_offsets,
+                                  int32_t n_tracks, const int32_t* ndf, const float* grad_chi2, float* grad_align,
+                                  float* grad_seeds, float* grad_meas, void* stream) {
+  if (!h || !hits || n_tracks < 0 || hits->n_hits < 0) return TPCFIT_EINVAL;
+  if (!grad_align || !aligned(grad_align, 4)) return TPCFIT_EINVAL;
+  cudaStream_t s = (cudaStream_t)stream;
+  if (n_tracks == 0) return from_cuda(cudaMemsetAsync(grad_align, 0, sizeof(float) * kAlignFloats, s));
+  if (!track_offsets || !ndf || !grad_chi2 || !grad_seeds) return TPCFIT_EINVAL;
+  if (hits->n_hits > 0 && (!hits->y || !hits->z || !hits->rowsec)) return TPCFIT_EINVAL;
+  if (!aligned(grad_chi2, 4) || !aligned(grad_seeds, 4) || !aligned(ndf, 4) || (grad_meas && !aligned(grad_meas, 8)))
+    return TPCFIT_EINVAL;
+  if (!h->rec_valid || h->rec_tracks != n_tracks || h->rec_hits != hits->n_hits ||
+      h->rec_det != h->deterministic)
+    return TPCFIT_ESTATE;
+  tpcfit_status st = make_resident(h, s);
+  if (st != TPCFIT_OK) return st;
+  BwdArgs b{};
+  b.y = hits->y;
+  b.z = hits->z;
+  b.rowsec = hits->rowsec;
+  b.n_hits = hits->n_hits;
+  b.off = track_offsets;
+  b.n_tracks = n_tracks;
+  b.align = h->d_align;
+  b.perm = h->sort_by_length ? h->d_perm : nullptr;
+  b.ndf = ndf;
+  b.ck = h->d_ck;
+  b.ck_last = h->d_ck_last;
+  b.ck_slots = h->ck_slots;
+  b.grad_chi2 = grad_chi2;
+  b.grad_seeds = grad_seeds;
+  b.work = h->d_work;
+  cudaError_t e = cudaSuccess;
+  if (!h->deterministic) {
+    // fast: atomics straight into the alignment gradient
+    b.grad_meas = grad_meas;
+    b.grad_align_atomic = grad_align;
+    e = cudaMemsetAsync(grad_align, 0, sizeof(float) * kAlignFloats, s);
+    if (e == cudaSuccess) e = launch_backward_fast(b, s);
+    return from_cuda(e);
+  }
+  // deterministic: per-cluster gradients, then a stable key sort and
+  // fixed-order sums per key
+  float* gm = grad_meas;
+  if (!gm) {
+    st = grow(h->d_gm, h->gm_cap, 2 * hits->n_hits);
+    if (st != TPCFIT_OK) return st;
+    gm = h->d_gm;
+  }
+  const size_t kb = key_sort_scratch_bytes(hits->n_hits);
+  if (kb > h->keys_cap) {
+    if (h->d_keys) cudaFree(h->d_keys);
+    h->d_keys = nullptr;
+    h->keys_cap = 0;
+    e = cudaMalloc(&h->d_keys, kb);
+    if (e != cudaSuccess) return from_cuda(e);
+    h->keys_cap = kb;
+  }
+  b.grad_meas = gm;
+  b.grad_align_atomic = nullptr;
+  e = launch_backward_det(b, s);
+  int* sorted = nullptr;
+  int* key_start = nullptr;
+  if (e == cudaSuccess) e = launch_key_sort(hits->rowsec, hits->n_hits, h->geo.n_rows, h->d_keys, &sorted, &key_start, s);
+  if (e == cudaSuccess) e = launch_key_reduce(gm, sorted, key_start, grad_align, s);
   return from_cuda(e);
 }
 

@@ -1,4 +1,4 @@
-"""Algorithmic FP32 operation counts of the fit (for roofline accounting).
+"""Algorithmic FP32 operation counts of the fit and its adjoint (roofline accounting).
 
 Counted from the formula list of one step as the kernels evaluate it: every
 add, subtract and multiply is one operation (a fused multiply-add counts as
@@ -33,3 +33,26 @@ def fit_bytes(lengths) -> float:
     seeds (20), outputs (5 + 15 + 1 + 1 words = 88)."""
     n = np.asarray(lengths, dtype=np.int64)
     return float(10 * n.sum() + (4 + 20 + 88) * n.shape[0])
+
+
+# Reverse sweep (adjoint), counted from the formula list of the hand-written
+# reverse of each forward piece: a Potter scalar update (268), the transport
+# L <- J L (120) and the prediction with its Jacobian (150).  Recomputation of
+# forward values (checkpoint segments, per-step intermediates) is overhead and
+# is not counted.
+REV_SCALAR_UPDATE = 268
+REV_TRANSPORT = 120
+REV_PREDICT = 150
+REV_STEP = REV_PREDICT + REV_TRANSPORT + 2 * REV_SCALAR_UPDATE   # 806
+REV_FIRST = 2 * REV_SCALAR_UPDATE                                 # 536
+
+
+def backward_flops(lengths) -> float:
+    """Algorithmic flops of the reverse sweep over both passes."""
+    n = np.asarray(lengths, dtype=np.int64)
+    n = n[n >= 1]
+    return float(np.sum(2 * ((n - 1) * REV_STEP + REV_FIRST)))
+
+
+def fit_adjoint_flops(lengths) -> float:
+    return fit_flops(lengths) + backward_flops(lengths)

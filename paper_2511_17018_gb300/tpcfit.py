@@ -57,6 +57,8 @@ def load():
         "tpcfit_get_status": (C.c_int, [vp, vp, C.POINTER(i32), C.POINTER(i64)]),
         "tpcfit_fit_noalloc": (C.c_int, [C.POINTER(_Geometry), C.c_double, vp, C.c_int, C.POINTER(_Hits), vp, i32, vp,
                                          vp, vp, vp, vp, vp]),
+        "tpcfit_set_record": (C.c_int, [vp, C.c_int]),
+        "tpcfit_fit_backward": (C.c_int, [vp, C.POINTER(_Hits), vp, i32, vp, vp, vp, vp, vp, vp]),
         "tpcfit_status_string": (C.c_char_p, [C.c_int]),
         "tpcfit_version": (i32, []),
     }
@@ -153,6 +155,27 @@ def tpcfit_fit(h, y, z, rowsec, offsets, seeds, params, cov, chi2, ndf, stream=N
                            _dev(params, torch.float32, "params"), _dev(cov, torch.float32, "cov"),
                            _dev(chi2, torch.float32, "chi2"), _dev(ndf, torch.int32, "ndf"), _stream(stream))
     _check(st, "tpcfit_fit")
+
+
+def tpcfit_set_record(h, record: bool) -> None:
+    _check(load().tpcfit_set_record(h, int(bool(record))), "tpcfit_set_record")
+
+
+def tpcfit_fit_backward(h, y, z, rowsec, offsets, ndf, grad_chi2, grad_align, grad_seeds, grad_meas=None,
+                        stream=None) -> None:
+    """Enqueue the adjoint of the last recorded fit (device tensors; see include/tpcfit.h)."""
+    import torch
+    n = int(offsets.numel()) - 1
+    hits = _Hits(_dev(y, torch.float32, "y"), _dev(z, torch.float32, "z"), _dev(rowsec, torch.int16, "rowsec"),
+                 int(y.numel()))
+    if grad_align.numel() != 36 * 152 * 2 or grad_seeds.numel() != 5 * n or grad_chi2.numel() != n:
+        raise ValueError("gradient sizes do not match")
+    gm = None if grad_meas is None else _dev(grad_meas, torch.float32, "grad_meas")
+    st = load().tpcfit_fit_backward(h, C.byref(hits), _dev(offsets, torch.int32, "offsets"), n,
+                                    _dev(ndf, torch.int32, "ndf"), _dev(grad_chi2, torch.float32, "grad_chi2"),
+                                    _dev(grad_align, torch.float32, "grad_align"),
+                                    _dev(grad_seeds, torch.float32, "grad_seeds"), gm, _stream(stream))
+    _check(st, "tpcfit_fit_backward")
 
 
 def tpcfit_fit_host(h, y, z, rowsec, offsets, seeds, stream=None, out=None):
@@ -266,3 +289,16 @@ class Fitter:
 
     def status(self, stream=None):
         return tpcfit_get_status(self.h, stream)
+
+    def set_record(self, record: bool):
+        tpcfit_set_record(self.h, record)
+
+    def backward(self, dev: dict, out: dict, grad_chi2, grad_meas=None, stream=None):
+        """Gradients of sum_i grad_chi2[i] chi2_i for the last recorded fit."""
+        import torch
+        n = int(dev["offsets"].numel()) - 1
+        ga = torch.empty(36 * 152 * 2, dtype=torch.float32, device=dev["y"].device)
+        gs = torch.empty((5, n), dtype=torch.float32, device=dev["y"].device)
+        tpcfit_fit_backward(self.h, dev["y"], dev["z"], dev["rowsec"], dev["offsets"], out["ndf"], grad_chi2, ga, gs,
+                            grad_meas, stream)
+        return ga.view(36, 152, 2), gs

@@ -1,0 +1,149 @@
+"""The hand-written adjoint against the oracle's FP64 forward-mode gradient and
+FP64 central finite differences (run on a GB300 with -m gpu).
+
+The FP32 gradient cannot be closer to the FP64 one than the FP32 forward is to
+the FP64 forward: cluster positions up to ~40 cm carry ~4e-6 cm of rounding
+against residuals of ~0.1 cm, i.e. ~5e-5 of the gradient per step.  The bounds
+below (5e-4 in relative norm) are a few times that floor."""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+import oracle  # noqa: E402
+from paper_2511_17018_gb300 import synth  # noqa: E402
+from paper_2511_17018_gb300 import tpcfit as tf  # noqa: E402
+from paper_2511_17018_gb300.autograd import fit_chi2  # noqa: E402
+
+REL = 5e-4
+
+
+def rel(a, b):
+    return float(np.linalg.norm(np.asarray(a, np.float64) - b) / np.linalg.norm(b))
+
+
+@pytest.fixture(scope="module")
+def case():
+    d_true = synth.alignment_offsets(3)
+    fr = synth.generate(3000, 3, drop_p=0.05, cap_lengths=True, d_true=d_true)
+    w = np.random.default_rng(5).uniform(0.5, 2.0, fr.n_tracks).astype(np.float32)
+    ref = oracle.grad(fr, weights=w.astype(np.float64), align=d_true)
+    return fr, d_true, w, ref
+
+
+def _gpu_grad(fr, d_true, w, det, rps=4, warps=24, srt=True):
+    dev = tf.frame_to_device(fr)
+    f = tf.Fitter(fr.geometry, fr.bz, deterministic=det, rows_per_stage=rps, warps_per_block=warps,
+                  sort_by_length=srt)
+    try:
+        f.set_alignment(torch.from_numpy(d_true).cuda())
+        f.set_record(True)
+        out = f.fit(dev)
+        gm = torch.empty((fr.n_hits, 2), device="cuda")
+        ga, gs = f.backward(dev, out, torch.from_numpy(w).cuda(), gm)
+        torch.cuda.synchronize()
+        return gm.cpu().numpy(), ga.cpu().numpy(), gs.cpu().numpy(), out["ndf"].cpu().numpy()
+    finally:
+        f.close()
+
+
+@pytest.mark.parametrize("det", [False, True])
+def test_adjoint_matches_forward_mode_oracle(case, det):
+    fr, d_true, w, ref = case
+    gm, ga, gs, ndf = _gpu_grad(fr, d_true, w, det)
+    assert np.array_equal(ndf, ref["ndf"])
+    assert rel(gm, ref["grad_meas"]) < REL
+    assert rel(ga, oracle.align_grad_from_meas(fr, ref["grad_meas"])) < REL
+    assert rel(gs, ref["grad_seed"]) < 10 * REL   # the seed gradient is ~1e-5 of the cluster gradient
+    assert np.abs(gs - ref["grad_seed"]).max() < 1e-5 * np.abs(ref["grad_meas"]).max()
+
+
+def test_deterministic_adjoint_is_bitwise_reproducible(case):
+    fr, d_true, w, _ = case
+    base = _gpu_grad(fr, d_true, w, True)
+    for rps, warps, srt in ((4, 24, True), (8, 8, False), (16, 8, True)):
+        got = _gpu_grad(fr, d_true, w, True, rps, warps, srt)
+        for a, b in zip(got[:3], base[:3]):
+            assert np.array_equal(a.view(np.int32), b.view(np.int32)), (rps, warps, srt)
+
+
+def test_alignment_gradient_matches_fp64_finite_differences():
+    # central differences of the FP64 oracle's weighted chi2 sum, step 1e-4 cm,
+    # on a 200-track subset, for 40 (sector, row, component) keys the subset uses
+    d_true = synth.alignment_offsets(3)
+    fr = synth.generate(200, 33, drop_p=0.05, cap_lengths=True, d_true=d_true)
+    w = np.ones(fr.n_tracks, np.float32)
+    _, ga, _, ndf = _gpu_grad(fr, d_true, w, False)
+    assert np.all(ndf > 0)
+    rs = fr.rowsec.astype(np.int64)
+    keys = np.unique((rs & 63) * 152 + (rs >> 6))
+    pick = np.random.default_rng(6).choice(keys, 40, replace=False)
+    h = 1e-4
+    fd, got = [], []
+    for k in pick:
+        for c in (0, 1):
+            dp = d_true.astype(np.float64).copy().reshape(-1, 2)
+            dm = dp.copy()
+            dp[k, c] += h
+            dm[k, c] -= h
+            lp = np.nansum(oracle.fit(fr, "f64", align=dp.reshape(36, 152, 2))["chi2"])
+            lm = np.nansum(oracle.fit(fr, "f64", align=dm.reshape(36, 152, 2))["chi2"])
+            fd.append((lp - lm) / (2 * h))
+            got.append(ga.reshape(-1, 2)[k, c])
+    assert rel(got, np.array(fd)) < REL
+
+
+def test_autograd_function_and_masking(case):
+    fr, d_true, w, ref = case
+    dev = tf.frame_to_device(fr)
+    f = tf.Fitter(fr.geometry, fr.bz)
+    try:
+        align = torch.from_numpy(d_true).cuda().requires_grad_(True)
+        seeds = dev["seeds"].clone().requires_grad_(True)
+        chi2, params, ndf = fit_chi2(align, seeds, f, dev)
+        ok = ndf > 0
+        loss = (chi2[ok] * torch.from_numpy(w).cuda()[ok]).sum()
+        loss.backward()
+        assert rel(align.grad.cpu().numpy(), oracle.align_grad_from_meas(fr, ref["grad_meas"])) < REL
+        assert rel(seeds.grad.cpu().numpy(), ref["grad_seed"]) < 10 * REL
+    finally:
+        f.close()
+
+
+def test_backward_requires_a_recorded_fit():
+    fr = synth.generate(50, 34)
+    dev = tf.frame_to_device(fr)
+    f = tf.Fitter(fr.geometry, fr.bz)
+    try:
+        out = f.fit(dev)  # recording is off
+        with pytest.raises(tf.TpcfitError) as e:
+            f.backward(dev, out, torch.ones(fr.n_tracks, device="cuda"))
+        assert e.value.status == tf.ESTATE
+        f.set_record(True)
+        out = f.fit(dev)
+        f.set_mode(True)   # mode changed since the recording
+        with pytest.raises(tf.TpcfitError):
+            f.backward(dev, out, torch.ones(fr.n_tracks, device="cuda"))
+    finally:
+        f.close()
+
+
+def test_failed_tracks_contribute_nothing():
+    fr = synth.generate(64, 35)
+    fr.seeds[2, :8] = 0.9995  # unusable seeds: these tracks fail
+    dev = tf.frame_to_device(fr)
+    f = tf.Fitter(fr.geometry, fr.bz)
+    try:
+        f.set_record(True)
+        out = f.fit(dev)
+        gm = torch.full((fr.n_hits, 2), 9.0, device="cuda")
+        ga, gs = f.backward(dev, out, torch.ones(fr.n_tracks, device="cuda"), gm)
+        torch.cuda.synchronize()
+        assert np.all(out["ndf"].cpu().numpy()[:8] == -1)
+        gm = gm.cpu().numpy()
+        assert np.all(gm[: fr.offsets[8]] == 0)
+        assert np.all(gs.cpu().numpy()[:, :8] == 0)
+        assert np.all(np.isfinite(ga.cpu().numpy()))
+    finally:
+        f.close()
