@@ -127,6 +127,33 @@ tpcfit_status tpcfit_fit(tpcfit_handle* h, const tpcfit_hits* hits, const int32_
                          const float* seeds, float* params_out, float* cov_out, float* chi2_out, int32_t* ndf_out,
                          void* stream);
 
+/* Fit many time frames in one persistent launch.  The clusters, offsets,
+ * seeds and outputs of all frames are concatenated (track-major, as for
+ * tpcfit_fit with n_tracks tracks in total); frame f owns tracks
+ * [frame_track_base[f], frame_track_base[f + 1]) (device int64 [n_frames + 1],
+ * frame_track_base[0] = 0, frame_track_base[n_frames] = n_tracks).
+ *   frame_alignment: device float [n_frames][36][152][2], the per-frame offsets
+ *                    (constants that change between time frames, Sec. 4.1), or
+ *                    NULL to use the handle's alignment for every frame.
+ *   frame_ready:     device int32 [n_frames] flags, or NULL.  With flags, warps
+ *                    wait (acquire load, polled) until the flag of each of their
+ *                    tracks' frames is nonzero before reading its clusters, so the
+ *                    caller may copy frames in on another stream and set each flag
+ *                    after its frame's copy.  A wait gives up after
+ *                    wait_timeout_ns of device time (0 = 1 s): the frame's tracks
+ *                    get ndf = -3 and tpcfit_get_status returns ETIMEOUT.  With
+ *                    flags, `stream` must not be the legacy default stream (NULL),
+ *                    whose implicit ordering would hold the copies back (EINVAL).
+ * Work is ordered by frame, then by decreasing track length.  Recording for
+ * the adjoint does not apply (tpcfit_fit_backward returns ESTATE after this).
+ * Capturable in a CUDA graph after one call with the same sizes has run
+ * outside the capture (scratch and constants are then in place). */
+tpcfit_status tpcfit_fit_frames(tpcfit_handle* h, const tpcfit_hits* hits, const int32_t* track_offsets,
+                                int32_t n_tracks, const int64_t* frame_track_base, int32_t n_frames,
+                                const float* frame_alignment, const int32_t* frame_ready, int64_t wait_timeout_ns,
+                                const float* seeds, float* params_out, float* cov_out, float* chi2_out,
+                                int32_t* ndf_out, void* stream);
+
 /* Record checkpoints for the adjoint (record = 1) or not (0, default).  With
  * recording on, tpcfit_fit also stores the filter state before every 16th step
  * of both passes (about 9 floats per cluster, handle-owned, grown as needed) so
@@ -192,10 +219,11 @@ tpcfit_status tpcfit_fit_noalloc(const tpcfit_geometry* geometry, double bz_tesl
                                  int32_t n_tracks, const float* seeds, float* params_out, float* cov_out,
                                  float* chi2_out, int32_t* ndf_out, void* stream);
 
-/* Read (and clear) the handle's device error word: the first invalid-input code
- * a kernel recorded (0 = none; 1 = bad offsets, 2 = row or sector out of range)
- * and the track it was found on (-1 if none).  Synchronises `stream`.  Returns
- * EDEVICE if an error was recorded, OK otherwise. */
+/* Read (and clear) the handle's device error word: the first code a kernel
+ * recorded (0 = none; 1 = bad offsets or frame table, 2 = row or sector out of
+ * range, 3 = a frame-ready wait ran out) and the track it was found on (-1 if
+ * none).  Synchronises `stream`.  Returns ETIMEOUT for code 3, EDEVICE for the
+ * others, OK if nothing was recorded. */
 tpcfit_status tpcfit_get_status(tpcfit_handle* h, void* stream, int32_t* err_code, int64_t* err_track);
 
 /* Static description of a status code. */

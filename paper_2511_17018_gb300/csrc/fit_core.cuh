@@ -29,6 +29,7 @@
 #include <stdint.h>
 
 #include "internal.h"
+#include "device_util.cuh"
 
 #ifndef TPCFIT_DET
 #error "define TPCFIT_DET before including fit_core.cuh"
@@ -415,7 +416,7 @@ __device__ __forceinline__ void write_ckpt(const FitArgs& a, int pass, int begin
   for (int j = 0; j < 9; ++j) dst[j] = make_float4(v[4 * j], v[4 * j + 1], v[4 * j + 2], v[4 * j + 3]);
 }
 
-template <int RPS, int WARPS, int MINB, bool RECORD>
+template <int RPS, int WARPS, int MINB, bool RECORD, bool FRAMES>
 __global__ void __launch_bounds__(WARPS * 32, MINB) fit_kernel(FitArgs a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   BlockSmem& B = *reinterpret_cast<BlockSmem*>(smem_raw);
@@ -442,10 +443,26 @@ __global__ void __launch_bounds__(WARPS * 32, MINB) fit_kernel(FitArgs a) {
 
     // ---- per-track input checks
     // hit indices fit in int32: the host rejects n_hits > INT32_MAX
-    int status = have ? 0 : 1;  // 0 fitting, 1 idle, 2 numerical failure, 3 invalid input
+    int status = have ? 0 : 1;  // 0 fitting, 1 idle, 2 numerical failure, 3 invalid input, 4 timeout
     int begin = 0;
     int n = 0;
-    if (have) {
+    const float* lane_align = B.align;
+    if (FRAMES && have) {
+      // the track's time frame: its alignment table and, when streaming, its ready flag
+      const int f = frame_of(a.frame_base, a.n_frames, trk);
+      if (f < 0) {
+        status = 3;
+        record_error(a.err, kErrOffsets, trk);
+      } else {
+        if (a.frame_ready && !wait_flag(a.frame_ready + f, a.wait_ns)) {
+          status = 4;
+          record_error(a.err, kErrTimeout, trk);
+        }
+        if (a.frame_align) lane_align = a.frame_align + (int64_t)f * kAlignFloats;
+      }
+    }
+    if (FRAMES) __syncwarp();  // every lane's frame is in place before the warp stages clusters
+    if (have && status == 0) {
       const int b = a.off[trk];
       const int e = a.off[trk + 1];
       if (b < 0 || e < b || (int64_t)e > a.n_hits) {
@@ -511,7 +528,8 @@ __global__ void __launch_bounds__(WARPS * 32, MINB) fit_kernel(FitArgs a) {
             record_error(a.err, kErrRowSector, trk);
             continue;
           }
-          const float2 d = reinterpret_cast<const float2*>(B.align)[sec * kMaxRows + row];
+          const float2 d = FRAMES ? reinterpret_cast<const float2*>(lane_align)[sec * kMaxRows + row]
+                                  : reinterpret_cast<const float2*>(B.align)[sec * kMaxRows + row];
           const float m0 = st.y[buf][lane][k] - d.x;
           const float m1 = st.z[buf][lane][k] - d.y;
           const int sec18 = sec % kNSide;
@@ -571,25 +589,25 @@ __global__ void __launch_bounds__(WARPS * 32, MINB) fit_kernel(FitArgs a) {
 #pragma unroll
       for (int e = 0; e < 15; ++e) a.cov[(int64_t)e * N + trk] = qnan;
       a.chi2[trk] = qnan;
-      a.ndf[trk] = (status == 3) ? -2 : -1;
+      a.ndf[trk] = (status == 3) ? -2 : (status == 4 ? -3 : -1);
     }
   }
 }
 
-template <int RPS, int WARPS, int MINB, bool RECORD>
+template <int RPS, int WARPS, int MINB, bool RECORD, bool FRAMES>
 cudaError_t launch_cfg(const FitArgs& a, cudaStream_t s) {
   constexpr int kThreads = WARPS * 32;
   const size_t smem = sizeof(BlockSmem) + WARPS * sizeof(WarpStage<RPS>);
   static int grid = 0;
   if (grid == 0) {
     cudaError_t e =
-        cudaFuncSetAttribute(fit_kernel<RPS, WARPS, MINB, RECORD>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        cudaFuncSetAttribute(fit_kernel<RPS, WARPS, MINB, RECORD, FRAMES>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     int dev = 0, sms = 0, per_sm = 0;
     e = cudaGetDevice(&dev);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     if (e == cudaSuccess)
-      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fit_kernel<RPS, WARPS, MINB, RECORD>, kThreads, smem);
+      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fit_kernel<RPS, WARPS, MINB, RECORD, FRAMES>, kThreads, smem);
     if (e != cudaSuccess) return e;
     if (per_sm < 1) return cudaErrorInvalidConfiguration;
     grid = sms * per_sm;
@@ -599,27 +617,28 @@ cudaError_t launch_cfg(const FitArgs& a, cudaStream_t s) {
   const int blocks = (int)(need < grid ? need : grid);
   cudaError_t e = cudaMemsetAsync(a.work, 0, sizeof(unsigned int), s);
   if (e != cudaSuccess) return e;
-  fit_kernel<RPS, WARPS, MINB, RECORD><<<blocks, kThreads, smem, s>>>(a);
+  fit_kernel<RPS, WARPS, MINB, RECORD, FRAMES><<<blocks, kThreads, smem, s>>>(a);
   return cudaGetLastError();
 }
 
 // Supported (rows per stage, warps per block) shapes; the shared-memory budget
 // (alignment table + double buffer) decides how many blocks fit on an SM.
-template <bool RECORD>
+template <bool RECORD, bool FRAMES>
 inline cudaError_t launch_rec(const FitArgs& a, int rps, int warps, cudaStream_t s) {
-  if (rps == 4 && warps == 8) return launch_cfg<4, 8, 2, RECORD>(a, s);
-  if (rps == 4 && warps == 12) return launch_cfg<4, 12, 2, RECORD>(a, s);
-  if (rps == 4 && warps == 24) return launch_cfg<4, 24, 1, RECORD>(a, s);
-  if (rps == 8 && warps == 8) return launch_cfg<8, 8, 2, RECORD>(a, s);
-  if (rps == 8 && warps == 16) return launch_cfg<8, 16, 1, RECORD>(a, s);
-  if (rps == 16 && warps == 8) return launch_cfg<16, 8, 1, RECORD>(a, s);
+  if (rps == 4 && warps == 8) return launch_cfg<4, 8, 2, RECORD, FRAMES>(a, s);
+  if (rps == 4 && warps == 12) return launch_cfg<4, 12, 2, RECORD, FRAMES>(a, s);
+  if (rps == 4 && warps == 24) return launch_cfg<4, 24, 1, RECORD, FRAMES>(a, s);
+  if (rps == 8 && warps == 8) return launch_cfg<8, 8, 2, RECORD, FRAMES>(a, s);
+  if (rps == 8 && warps == 16) return launch_cfg<8, 16, 1, RECORD, FRAMES>(a, s);
+  if (rps == 16 && warps == 8) return launch_cfg<16, 8, 1, RECORD, FRAMES>(a, s);
   return cudaErrorInvalidValue;
 }
 
 inline cudaError_t launch(const FitArgs& a, int lanes_per_track, int rps, int warps, cudaStream_t s) {
   if (a.n_tracks <= 0) return cudaSuccess;
   if (lanes_per_track != 1) return cudaErrorInvalidValue;
-  return a.ck ? launch_rec<true>(a, rps, warps, s) : launch_rec<false>(a, rps, warps, s);
+  if (a.frame_base) return a.ck ? launch_rec<true, true>(a, rps, warps, s) : launch_rec<false, true>(a, rps, warps, s);
+  return a.ck ? launch_rec<true, false>(a, rps, warps, s) : launch_rec<false, false>(a, rps, warps, s);
 }
 
 cudaError_t upload(const GeoConst& g, cudaStream_t s) {

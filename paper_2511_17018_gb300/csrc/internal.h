@@ -51,6 +51,12 @@ struct FitArgs {
   float* ck;                   // [2][ck_slots][36] filter state before every 16th step of each pass
   int32_t* ck_last;            // [n_tracks] index of the last cluster of the outward pass
   int64_t ck_slots;            // slots per pass: n_hits / 16 + n_tracks + 1
+  // several time frames in one launch (frame_base = null: one frame)
+  const int64_t* frame_base;   // [n_frames + 1] first track of each frame
+  int32_t n_frames;
+  const float* frame_align;    // [n_frames][36][152][2] per-frame offsets, or null (handle's table)
+  const int32_t* frame_ready;  // [n_frames] ready flags (!= 0 when the frame's clusters are in place), or null
+  int64_t wait_ns;             // bound of a ready-flag wait
 };
 
 // Arguments of one backward launch (same frame as the recorded fit).
@@ -77,6 +83,7 @@ struct BwdArgs {
 // Error codes recorded in the device error word.
 constexpr unsigned long long kErrOffsets = 1;
 constexpr unsigned long long kErrRowSector = 2;
+constexpr unsigned long long kErrTimeout = 3;
 
 // ---- constant-memory registry (Sec. 4.1): every kernel module registers an
 // uploader for its own __constant__ copy; the host updates all of them.
@@ -106,6 +113,15 @@ cudaError_t launch_key_reduce(const float* grad_meas, const int* sorted, const i
                               cudaStream_t s);
 // true if (lanes_per_track, rows_per_stage, warps) is a compiled launch shape
 bool fit_shape_supported(int lanes_per_track, int rows_per_stage, int warps);
+
+// Ordering by (frame ascending, length descending) for batched frames.
+// scratch: int32 [2 * n_frames * 256 + scan_tmp_ints(n_frames * 256)].
+int64_t frame_order_scratch_ints(int32_t n_frames);
+cudaError_t launch_frame_length_order(const int32_t* off, int32_t n_tracks, const int64_t* frame_base,
+                                      int32_t n_frames, int32_t* perm, int32_t* scratch, cudaStream_t s);
+// Exclusive prefix sum of n ints in place (key_reduce.cu); tmp: scan_tmp_ints(n) ints.
+int64_t scan_tmp_ints(int64_t n);
+cudaError_t launch_scan_exclusive(int* v, int n, int* tmp, cudaStream_t s);
 
 // Length-ordering permutation: perm[k] = track processed k-th, longest first.
 // scratch: int32[2 * 256] (zeroed by the launcher).

@@ -216,6 +216,17 @@ cudaError_t launch_key_sort(const uint16_t* rowsec, int64_t n_hits, int n_rows, 
   return cudaGetLastError();
 }
 
+int64_t scan_tmp_ints(int64_t n) { return (n + kScanTile - 1) / kScanTile + 1; }
+
+cudaError_t launch_scan_exclusive(int* v, int n, int* tmp, cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  const int n_tiles = (n + kScanTile - 1) / kScanTile;
+  scan_tiles<<<n_tiles, 1024, 0, s>>>(v, n, tmp);
+  scan_totals<<<1, 1024, 0, s>>>(tmp, n_tiles);
+  scan_add<<<n_tiles, 1024, 0, s>>>(v, n, tmp);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_key_reduce(const float* grad_meas, const int* sorted, const int* key_start, float* grad_align,
                               cudaStream_t s) {
   key_sum<<<(kKeys + 7) / 8, 256, 0, s>>>(grad_meas, sorted, key_start, grad_align);

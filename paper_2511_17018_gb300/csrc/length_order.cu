@@ -7,6 +7,7 @@
 #include <stdint.h>
 
 #include "internal.h"
+#include "device_util.cuh"
 
 namespace tpcfit {
 namespace {
@@ -73,7 +74,50 @@ __global__ void __launch_bounds__(kThreads) length_scatter(const int32_t* off, i
   }
 }
 
+// Batched frames: key = frame * 256 + (255 - length) orders by frame, then by
+// decreasing length.  Histogram with global atomics, exclusive scan, scatter.
+__device__ __forceinline__ int frame_key(const int32_t* off, const int64_t* fb, int n_frames, int64_t i) {
+  int f = frame_of(fb, n_frames, i);
+  if (f < 0) f = n_frames - 1;  // out-of-table tracks are rejected by the fit; keep them in range here
+  return f * kBins + (kBins - 1 - length_bin(off, i));
+}
+
+__global__ void frame_hist(const int32_t* off, int32_t n, const int64_t* fb, int n_frames, int32_t* hist) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) atomicAdd(&hist[frame_key(off, fb, n_frames, i)], 1);
+}
+
+__global__ void frame_scatter(const int32_t* off, int32_t n, const int64_t* fb, int n_frames, const int32_t* start,
+                              int32_t* cursor, int32_t* perm) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const int k = frame_key(off, fb, n_frames, i);
+  perm[start[k] + atomicAdd(&cursor[k], 1)] = (int32_t)i;
+}
+
 }  // namespace
+
+int64_t frame_order_scratch_ints(int32_t n_frames) {
+  const int64_t bins = (int64_t)n_frames * kBins;
+  return 2 * bins + scan_tmp_ints(bins);
+}
+
+cudaError_t launch_frame_length_order(const int32_t* off, int32_t n_tracks, const int64_t* frame_base,
+                                      int32_t n_frames, int32_t* perm, int32_t* scratch, cudaStream_t s) {
+  if (n_tracks <= 0) return cudaSuccess;
+  const int64_t bins = (int64_t)n_frames * kBins;
+  int32_t* start = scratch;
+  int32_t* cursor = scratch + bins;
+  int32_t* tmp = scratch + 2 * bins;
+  cudaError_t e = cudaMemsetAsync(scratch, 0, sizeof(int32_t) * 2 * bins, s);
+  if (e != cudaSuccess) return e;
+  const int64_t blocks = ((int64_t)n_tracks + 255) / 256;
+  frame_hist<<<(unsigned)blocks, 256, 0, s>>>(off, n_tracks, frame_base, n_frames, start);
+  e = launch_scan_exclusive(start, (int)bins, tmp, s);
+  if (e != cudaSuccess) return e;
+  frame_scatter<<<(unsigned)blocks, 256, 0, s>>>(off, n_tracks, frame_base, n_frames, start, cursor, perm);
+  return cudaGetLastError();
+}
 
 cudaError_t launch_length_order(const int32_t* off, int32_t n_tracks, int32_t* perm, int32_t* scratch,
                                 cudaStream_t s) {

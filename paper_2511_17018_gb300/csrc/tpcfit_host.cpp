@@ -135,6 +135,9 @@ struct tpcfit_handle {
   int64_t gm_cap = 0;          // floats
   unsigned char* d_keys = nullptr;
   size_t keys_cap = 0;
+  // batched frames: ordering scratch
+  int32_t* d_frame_scratch = nullptr;
+  int64_t frame_scratch_cap = 0;
 };
 
 namespace {
@@ -243,6 +246,7 @@ void tpcfit_destroy(tpcfit_handle* h) {
   if (h->d_ck_last) cudaFree(h->d_ck_last);
   if (h->d_gm) cudaFree(h->d_gm);
   if (h->d_keys) cudaFree(h->d_keys);
+  if (h->d_frame_scratch) cudaFree(h->d_frame_scratch);
   {
     Registry& r = registry();
     std::lock_guard<std::mutex> lk(r.mu);
@@ -339,6 +343,61 @@ tpcfit_status tpcfit_fit(tpcfit_handle* h, const tpcfit_hits* hits, const int32_
     h->rec_hits = hits->n_hits;
     h->rec_det = h->deterministic;
   }
+  return from_cuda(e);
+}
+
+tpcfit_status tpcfit_fit_frames(tpcfit_handle* h, const tpcfit_hits* hits, const int32_t* track_offsets,
+                                int32_t n_tracks, const int64_t* frame_track_base, int32_t n_frames,
+                                const float* frame_alignment, const int32_t* frame_ready, int64_t wait_timeout_ns,
+                                const float* seeds, float* params_out, float* cov_out, float* chi2_out,
+                                int32_t* ndf_out, void* stream) {
+  if (!h || !hits || n_tracks < 0 || hits->n_hits < 0 || n_frames < 1 || !frame_track_base) return TPCFIT_EINVAL;
+  if (wait_timeout_ns < 0) return TPCFIT_EINVAL;
+  if (n_tracks == 0) return TPCFIT_OK;
+  if (!track_offsets || !seeds || !params_out || !cov_out || !chi2_out || !ndf_out) return TPCFIT_EINVAL;
+  if (hits->n_hits > 0 && (!hits->y || !hits->z || !hits->rowsec)) return TPCFIT_EINVAL;
+  if (!aligned(hits->y, 4) || !aligned(hits->z, 4) || !aligned(hits->rowsec, 2) || !aligned(track_offsets, 4) ||
+      !aligned(seeds, 4) || !aligned(params_out, 4) || !aligned(cov_out, 4) || !aligned(chi2_out, 4) ||
+      !aligned(ndf_out, 4) || !aligned(frame_track_base, 8) || (frame_alignment && !aligned(frame_alignment, 8)) ||
+      (frame_ready && !aligned(frame_ready, 4)))
+    return TPCFIT_EINVAL;
+  if (hits->n_hits > INT32_MAX) return TPCFIT_EINVAL;
+  cudaStream_t s = (cudaStream_t)stream;
+  // ready flags are set by work on other streams; on the legacy default stream
+  // that work would wait for the fit itself
+  if (frame_ready && (s == nullptr || s == cudaStreamLegacy)) return TPCFIT_EINVAL;
+  tpcfit_status st = make_resident(h, s);
+  if (st != TPCFIT_OK) return st;
+  st = ensure_perm(h, n_tracks);
+  if (st == TPCFIT_OK) st = grow(h->d_frame_scratch, h->frame_scratch_cap, frame_order_scratch_ints(n_frames));
+  if (st != TPCFIT_OK) return st;
+  FitArgs a{};
+  a.y = hits->y;
+  a.z = hits->z;
+  a.rowsec = hits->rowsec;
+  a.n_hits = hits->n_hits;
+  a.off = track_offsets;
+  a.n_tracks = n_tracks;
+  a.seeds = seeds;
+  a.align = h->d_align;
+  a.perm = h->d_perm;
+  a.params = params_out;
+  a.cov = cov_out;
+  a.chi2 = chi2_out;
+  a.ndf = ndf_out;
+  a.err = h->d_err;
+  a.work = h->d_work;
+  a.frame_base = frame_track_base;
+  a.n_frames = n_frames;
+  a.frame_align = frame_alignment;
+  a.frame_ready = frame_ready;
+  a.wait_ns = wait_timeout_ns > 0 ? wait_timeout_ns : 1000000000LL;
+  h->rec_valid = false;  // the adjoint follows single-frame fits only
+  cudaError_t e =
+      launch_frame_length_order(track_offsets, n_tracks, frame_track_base, n_frames, h->d_perm, h->d_frame_scratch, s);
+  if (e == cudaSuccess)
+    e = h->deterministic ? launch_fit_det(a, h->lanes_per_track, h->rows_per_stage, h->warps_per_block, s)
+                         : launch_fit_fast(a, h->lanes_per_track, h->rows_per_stage, h->warps_per_block, s);
   return from_cuda(e);
 }
 
@@ -472,6 +531,7 @@ tpcfit_status tpcfit_get_status(tpcfit_handle* h, void* stream, int32_t* err_cod
   const int32_t code = (int32_t)(w >> 56);
   if (err_code) *err_code = code;
   if (err_track) *err_track = code ? (int64_t)(w & 0x00FFFFFFFFFFFFFFull) : -1;
+  if (code == (int32_t)kErrTimeout) return TPCFIT_ETIMEOUT;
   return code ? TPCFIT_EDEVICE : TPCFIT_OK;
 }
 

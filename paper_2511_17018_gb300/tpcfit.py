@@ -58,6 +58,8 @@ def load():
         "tpcfit_fit_noalloc": (C.c_int, [C.POINTER(_Geometry), C.c_double, vp, C.c_int, C.POINTER(_Hits), vp, i32, vp,
                                          vp, vp, vp, vp, vp]),
         "tpcfit_set_record": (C.c_int, [vp, C.c_int]),
+        "tpcfit_fit_frames": (C.c_int, [vp, C.POINTER(_Hits), vp, i32, vp, i32, vp, vp, i64, vp, vp, vp, vp, vp,
+                                        vp]),
         "tpcfit_fit_backward": (C.c_int, [vp, C.POINTER(_Hits), vp, i32, vp, vp, vp, vp, vp, vp]),
         "tpcfit_status_string": (C.c_char_p, [C.c_int]),
         "tpcfit_version": (i32, []),
@@ -157,6 +159,26 @@ def tpcfit_fit(h, y, z, rowsec, offsets, seeds, params, cov, chi2, ndf, stream=N
     _check(st, "tpcfit_fit")
 
 
+def tpcfit_fit_frames(h, y, z, rowsec, offsets, frame_base, seeds, params, cov, chi2, ndf, frame_alignment=None,
+                      frame_ready=None, wait_timeout_ns: int = 0, stream=None) -> None:
+    """Enqueue the fit of several concatenated time frames (see include/tpcfit.h)."""
+    import torch
+    n = int(offsets.numel()) - 1
+    nf = int(frame_base.numel()) - 1
+    hits = _Hits(_dev(y, torch.float32, "y"), _dev(z, torch.float32, "z"), _dev(rowsec, torch.int16, "rowsec"),
+                 int(y.numel()))
+    fa = None if frame_alignment is None else _dev(frame_alignment, torch.float32, "frame_alignment")
+    fr = None if frame_ready is None else _dev(frame_ready, torch.int32, "frame_ready")
+    if fa is not None and frame_alignment.numel() != nf * 36 * 152 * 2:
+        raise ValueError("frame_alignment must be [n_frames, 36, 152, 2]")
+    st = load().tpcfit_fit_frames(h, C.byref(hits), _dev(offsets, torch.int32, "offsets"), n,
+                                  _dev(frame_base, torch.int64, "frame_base"), nf, fa, fr, int(wait_timeout_ns),
+                                  _dev(seeds, torch.float32, "seeds"), _dev(params, torch.float32, "params"),
+                                  _dev(cov, torch.float32, "cov"), _dev(chi2, torch.float32, "chi2"),
+                                  _dev(ndf, torch.int32, "ndf"), _stream(stream))
+    _check(st, "tpcfit_fit_frames")
+
+
 def tpcfit_set_record(h, record: bool) -> None:
     _check(load().tpcfit_set_record(h, int(bool(record))), "tpcfit_set_record")
 
@@ -226,7 +248,7 @@ def tpcfit_get_status(h, stream=None):
     code = C.c_int32(0)
     trk = C.c_int64(-1)
     st = load().tpcfit_get_status(h, _stream(stream), C.byref(code), C.byref(trk))
-    if st not in (OK, EDEVICE):
+    if st not in (OK, EDEVICE, ETIMEOUT):
         _check(st, "tpcfit_get_status")
     return st, int(code.value), int(trk.value)
 
