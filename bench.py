@@ -234,6 +234,75 @@ def e2e_fit_adjoint(fitter, fr, steps, tf, torch):
     return n / dt, h2d, d2h
 
 
+def run_batched_frames(args, tf, torch, synth, flops, peak_tf):
+    """256 frames, track counts log-uniform on [1e3, 2e5] (about 15M tracks), one
+    persistent launch replayed from a CUDA graph; launch shape from the autotuner."""
+    from paper_2511_17018_gb300 import autotune
+    from paper_2511_17018_gb300.frames import FrameBatch, GraphedFrameFit, fit_frames
+    pool, picks = synth.config4(pool_tracks=args.pool_tracks)
+    batch = FrameBatch.from_pool(pool, picks)
+    lengths = np.diff(batch.offsets.cpu().numpy().astype(np.int64))
+    res = {"workload": "256 frames, tracks per frame log-uniform on [1e3, 2e5], drawn from a simulated pool of "
+                       f"{pool.n_tracks} tracks (5% drop, lengths U{{10..152}})",
+           "frames": batch.n_frames, "tracks": batch.n_tracks, "hits": batch.n_hits}
+    for mode in ("fast", "det"):
+        f = tf.Fitter(pool.geometry, pool.bz, deterministic=(mode == "det"))
+        tf.tpcfit_reserve(f.h, batch.n_tracks, batch.n_hits)
+        out = tf.empty_outputs(batch.n_tracks)
+        best = autotune.tune(f, batch.dev(), lengths, mode=mode, reps=2, cache_path=None,
+                             fit_call=lambda: fit_frames(f, batch, out))
+        del out
+        g = GraphedFrameFit(f, batch)
+        for _ in range(3):
+            g.replay()
+        torch.cuda.synchronize()
+        s, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        reps = 10
+        s.record()
+        for _ in range(reps):
+            g.replay()
+        e.record()
+        torch.cuda.synchronize()
+        ms = s.elapsed_time(e) / reps
+        tfl = flops.fit_flops(lengths) / (ms / 1e3) / 1e12
+        res[mode] = {"tracks_per_s": batch.n_tracks / (ms / 1e3), "ms_per_batch": ms,
+                     "hits_per_s": batch.n_hits / (ms / 1e3), "frac_fp32_peak": tfl / peak_tf,
+                     "config": {k: best[k] for k in ("lanes_per_track", "rows_per_stage", "warps_per_block",
+                                                     "sort_by_length")},
+                     "fitted_fraction": float((g.out["ndf"] > 0).float().mean().item())}
+        del g
+        f.close()
+    del batch
+    torch.cuda.empty_cache()
+    return res
+
+
+def run_alignment_loop(args, tf, torch, synth):
+    """2,000,000 tracks with injected offsets N(0, 0.05 cm); 50 iterations of
+    fit + adjoint + Adam on the device (CUDA graph)."""
+    from paper_2511_17018_gb300 import align
+    d_true = synth.alignment_offsets(5)
+    fr = synth.generate(args.align_tracks, 5, drop_p=0.05, cap_lengths=True, d_true=d_true)
+    dev = tf.frame_to_device(fr)
+    f = tf.Fitter(fr.geometry, fr.bz)
+    loop = align.AlignmentLoop(f, dev, lr=5e-3)
+    torch.cuda.synchronize()
+    s, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    s.record()
+    losses = loop.run(args.align_iters)
+    e.record()
+    torch.cuda.synchronize()
+    ms = s.elapsed_time(e) / args.align_iters
+    raw0, proj0 = align.recovery(np.zeros_like(d_true), d_true, fr.geometry.row_x)
+    raw, proj = align.recovery(loop.d.cpu().numpy(), d_true, fr.geometry.row_x)
+    f.close()
+    return {"workload": f"{fr.n_tracks} tracks, injected offsets N(0, 0.05 cm), {args.align_iters} iterations, "
+                        "Adam lr 5e-3", "tracks_per_s_per_iteration": fr.n_tracks / (ms / 1e3), "ms_per_iteration": ms,
+            "loss_first_last": [float(losses[0]), float(losses[-1])],
+            "rms_cm_initial": {"raw": raw0, "weak_modes_removed": proj0},
+            "rms_cm_final": {"raw": raw, "weak_modes_removed": proj}}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -243,6 +312,10 @@ def main():
     ap.add_argument("--mode", choices=["fast", "det"], default="fast")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-extra", action="store_true", help="skip the batched-frames and alignment-loop workloads")
+    ap.add_argument("--pool-tracks", type=int, default=1_000_000)
+    ap.add_argument("--align-tracks", type=int, default=2_000_000)
+    ap.add_argument("--align-iters", type=int, default=50)
     ap.add_argument("--tracks", type=int, default=N_TRACKS,
                     help="batch size override (profiling of smaller cases only; the bench value uses the default)")
     args = ap.parse_args()
@@ -403,6 +476,11 @@ def main():
     if not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(fr)
     fitter.close()
+    if not args.no_extra and world == 1:
+        del dev, out
+        torch.cuda.empty_cache()
+        line["batched_frames"] = run_batched_frames(args, tf, torch, synth, flops, peak_tf)
+        line["alignment_loop"] = run_alignment_loop(args, tf, torch, synth)
     print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()
