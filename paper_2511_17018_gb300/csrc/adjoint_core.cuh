@@ -10,9 +10,10 @@
 //
 // Checkpoints: the forward writes the filter state (p, L, x, sector, chi2)
 // before every 16th step of each pass.  The backward walks the segments of a
-// track in reverse: it recomputes a segment's 16 steps from its checkpoint into
-// a per-thread state array, then reverses the steps one by one (recomputing
-// each step's intermediates from the state before it).
+// track in reverse and recomputes between checkpoints in two levels kept on
+// chip (shared memory): the 16 steps once, keeping sub-checkpoints every 4
+// steps, then each 4-step sub-segment, keeping the state before each step,
+// which it reverses (recomputing each step's intermediates from that state).
 #pragma once
 
 namespace tpcfit {
@@ -322,11 +323,11 @@ struct StepState {
   int sec;
 };
 
-__device__ __forceinline__ void load_ckpt(const float* src, StepState& S, float& chi2) {
+__device__ __forceinline__ void load_ckpt(const float* src, StepState& S) {
   const float4* s4 = reinterpret_cast<const float4*>(src);
-  float v[kCkptFloats];
+  float v[32];
 #pragma unroll
-  for (int j = 0; j < kCkptFloats / 4; ++j) {
+  for (int j = 0; j < 8; ++j) {
     const float4 f = __ldg(s4 + j);
     v[4 * j] = f.x;
     v[4 * j + 1] = f.y;
@@ -341,25 +342,22 @@ __device__ __forceinline__ void load_ckpt(const float* src, StepState& S, float&
     for (int c = 0; c < 5; ++c) S.L[i][c] = v[5 + 5 * i + c];
   S.x = v[30];
   S.sec = __float_as_int(v[31]);
-  chi2 = v[32];
 }
 
-// Cluster h of the pass: measurement (alignment subtracted), row, sector.
-__device__ __forceinline__ bool read_hit(const BwdArgs& a, const float* align_s, int h, float& m0, float& m1,
-                                         int& row, int& sec) {
+// One cluster of a pass: measurement (alignment subtracted), row, sector.
+__device__ __forceinline__ void read_hit(const BwdArgs& a, int h, float& m0, float& m1, int& row, int& sec) {
   const int rsv = (int)__ldg(a.rowsec + h);
   row = rsv >> 6;
   sec = rsv & 63;
-  if (row >= c_geo.n_rows || sec >= kNSectors) return false;
-  const float2 d = reinterpret_cast<const float2*>(align_s)[sec * kMaxRows + row];
+  const float2 d = __ldg(reinterpret_cast<const float2*>(a.align) + (sec * kMaxRows + row));
   m0 = __ldg(a.y + h) - d.x;
   m1 = __ldg(a.z + h) - d.y;
-  return true;
 }
 
 // Forward of one step on a StepState (the same operations as the fit).
-__device__ __forceinline__ void step_fwd(const SmemTables& T, StepState& S, float& chi2, bool first, int row,
-                                         int sec18, float m0, float m1) {
+__device__ __forceinline__ void step_fwd(const SmemTables& T, StepState& S, bool first, int row, int sec18, float m0,
+                                         float m1) {
+  float chi2 = 0.0f;
   if (first) {
     S.x = T.row_x[row];
     S.sec = sec18;
@@ -422,18 +420,56 @@ __device__ __forceinline__ void step_rev(const SmemTables& T, const StepState& S
   for (int c = 0; c < 5; ++c) b_p[c] = b_pi[c];
 }
 
+// On-chip state store of a warp: kSlots filter states (p, L) per lane, laid
+// out [slot][component][lane] so that every access is conflict-free.
+constexpr int kSub = 4;                  // sub-segment length
+constexpr int kSlots = kCkptEvery / kSub + kSub;  // sub-checkpoints + step states
+constexpr int kStateFloats = 30;
+
+struct WarpStore {
+  float v[kSlots][kStateFloats][kWarp];
+};
+
+__device__ __forceinline__ void put_state(WarpStore& w, int slot, int lane, const StepState& S) {
+#pragma unroll
+  for (int c = 0; c < 5; ++c) w.v[slot][c][lane] = S.p[c];
+#pragma unroll
+  for (int i = 0; i < 5; ++i)
+#pragma unroll
+    for (int c = 0; c < 5; ++c) w.v[slot][5 + 5 * i + c][lane] = S.L[i][c];
+}
+
+__device__ __forceinline__ void get_state(const WarpStore& w, int slot, int lane, StepState& S) {
+#pragma unroll
+  for (int c = 0; c < 5; ++c) S.p[c] = w.v[slot][c][lane];
+#pragma unroll
+  for (int i = 0; i < 5; ++i)
+#pragma unroll
+    for (int c = 0; c < 5; ++c) S.L[i][c] = w.v[slot][5 + 5 * i + c][lane];
+}
+
+// Frame (x, sector) of the state before step i of a pass: that of cluster i-1.
+__device__ __forceinline__ void frame_before(const BwdArgs& a, const SmemTables& T, int h_prev, StepState& S) {
+  const int rsv = (int)__ldg(a.rowsec + h_prev);
+  S.x = T.row_x[rsv >> 6];
+  S.sec = (rsv & 63) % kNSide;
+}
+
+// Per track, per pass (inward reversed first): for every 16-step segment, from
+// its checkpoint, recompute the segment keeping sub-checkpoints every 4 steps;
+// then for every 4-step sub-segment (last first) recompute its steps keeping
+// the state before each step and reverse them.  All states stay in shared memory.
 template <int WARPS>
-__global__ void __launch_bounds__(WARPS * 32, 1) backward_kernel(BwdArgs a) {
+__global__ void __launch_bounds__(WARPS * 32, 1) backward_kernel_2l(BwdArgs a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  BlockSmem& B = *reinterpret_cast<BlockSmem*>(smem_raw);
-  load_tables(B.T);
-  for (int i = threadIdx.x; i < kAlignFloats; i += blockDim.x) B.align[i] = __ldg(a.align + i);
+  SmemTables& T = *reinterpret_cast<SmemTables*>(smem_raw);
+  WarpStore* stores = reinterpret_cast<WarpStore*>(smem_raw + sizeof(SmemTables));
+  load_tables(T);
   __syncthreads();
-  const SmemTables& T = B.T;
   const int lane = threadIdx.x & 31;
+  WarpStore& W = stores[threadIdx.x >> 5];
   const int64_t n_chunks = ((int64_t)a.n_tracks + kWarp - 1) / kWarp;
   const int64_t N = a.n_tracks;
-  StepState seg[kCkptEvery];
 
 #pragma unroll 1
   for (;;) {
@@ -451,7 +487,119 @@ __global__ void __launch_bounds__(WARPS * 32, 1) backward_kernel(BwdArgs a) {
       const int begin = a.off[trk];
       const int last = a.ck_last[trk];
       float b_L[5][5];
-      // pass 1 (inward) is reversed first, then pass 0 (outward)
+#pragma unroll 1
+      for (int pass = 1; pass >= 0; --pass) {
+#pragma unroll
+        for (int i = 0; i < 5; ++i)
+#pragma unroll
+          for (int c = 0; c < 5; ++c) b_L[i][c] = 0.0f;
+        const float b_chi = pass == 1 ? g : 0.0f;
+        const int steps = last + 1;
+        const int nseg = (steps + kCkptEvery - 1) / kCkptEvery;
+        const float* ckp = a.ck + ((int64_t)pass * a.ck_slots + (begin >> 4) + trk) * kCkptFloats;
+        // cluster of local step i of this pass
+        auto hit_of = [&](int i) { return pass == 0 ? begin + i : begin + last - i; };
+#pragma unroll 1
+        for (int s = nseg - 1; s >= 0; --s) {
+          const int i0 = s * kCkptEvery;
+          const int cnt = min(kCkptEvery, steps - i0);
+          StepState S;
+          load_ckpt(ckp + (int64_t)s * kCkptFloats, S);
+          // level 1: the segment, keeping the state before every 4th step
+#pragma unroll 1
+          for (int kk = 0; kk < cnt; ++kk) {
+            if ((kk & (kSub - 1)) == 0) put_state(W, kk / kSub, lane, S);
+            float m0, m1;
+            int row, sec;
+            read_hit(a, hit_of(i0 + kk), m0, m1, row, sec);
+            step_fwd(T, S, i0 + kk == 0, row, sec % kNSide, m0, m1);
+          }
+          // level 2: sub-segments, last first
+#pragma unroll 1
+          for (int q = (cnt - 1) / kSub; q >= 0; --q) {
+            const int j0 = i0 + q * kSub;
+            const int qc = min(kSub, cnt - q * kSub);
+            get_state(W, q, lane, S);
+            if (j0 > 0) frame_before(a, T, hit_of(j0 - 1), S);
+#pragma unroll 1
+            for (int j = 0; j < qc; ++j) {
+              put_state(W, kCkptEvery / kSub + j, lane, S);
+              float m0, m1;
+              int row, sec;
+              read_hit(a, hit_of(j0 + j), m0, m1, row, sec);
+              step_fwd(T, S, j0 + j == 0, row, sec % kNSide, m0, m1);
+            }
+#pragma unroll 1
+            for (int j = qc - 1; j >= 0; --j) {
+              const int i = j0 + j;
+              const int h = hit_of(i);
+              StepState S0;
+              get_state(W, kCkptEvery / kSub + j, lane, S0);
+              if (i > 0) frame_before(a, T, hit_of(i - 1), S0);
+              float m0, m1;
+              int row, sec;
+              read_hit(a, h, m0, m1, row, sec);
+              float b_m0 = 0.0f, b_m1 = 0.0f;
+              step_rev(T, S0, i == 0, row, sec % kNSide, m0, m1, b_p, b_L, b_chi, b_m0, b_m1);
+              if (a.grad_meas) {
+                float2* gm = reinterpret_cast<float2*>(a.grad_meas) + h;
+                if (pass == 1) {
+                  *gm = make_float2(b_m0, b_m1);
+                } else {
+                  const float2 o = *gm;
+                  *gm = make_float2(o.x + b_m0, o.y + b_m1);
+                }
+              }
+              if (a.grad_align_atomic) {
+                float* dst = a.grad_align_atomic + (sec * kMaxRows + row) * 2;
+                atomicAdd(dst, -b_m0);
+                atomicAdd(dst + 1, -b_m1);
+              }
+            }
+          }
+        }
+        // the inward pass starts from the outward result with the factor reset:
+        // b_p carries over, b_L does not
+      }
+    } else if (a.grad_meas) {
+      const int begin = a.off[trk];
+      const int end = a.off[trk + 1];
+      for (int h = begin; h < end; ++h) reinterpret_cast<float2*>(a.grad_meas)[h] = make_float2(0.0f, 0.0f);
+    }
+#pragma unroll
+    for (int c = 0; c < 5; ++c) a.grad_seeds[(int64_t)c * N + trk] = b_p[c];
+  }
+}
+
+// One-level variant: the 16 states of a segment in a per-thread array (local
+// memory, cached in L1/L2); one forward recomputation per step fewer than the
+// two-level kernel, more memory traffic.
+template <int WARPS>
+__global__ void __launch_bounds__(WARPS * 32, 1) backward_kernel_1l(BwdArgs a) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  SmemTables& T = *reinterpret_cast<SmemTables*>(smem_raw);
+  load_tables(T);
+  __syncthreads();
+  const int lane = threadIdx.x & 31;
+  const int64_t n_chunks = ((int64_t)a.n_tracks + kWarp - 1) / kWarp;
+  const int64_t N = a.n_tracks;
+  StepState seg[kCkptEvery];
+#pragma unroll 1
+  for (;;) {
+    int64_t chunk = 0;
+    if (lane == 0) chunk = (int64_t)atomicAdd(a.work, 1u);
+    chunk = __shfl_sync(0xffffffffu, chunk, 0);
+    if (chunk >= n_chunks) break;
+    const int64_t slot = chunk * kWarp + lane;
+    if (slot >= N) continue;
+    const int32_t trk = a.perm ? a.perm[slot] : (int32_t)slot;
+    const float g = __ldg(a.grad_chi2 + trk);
+    const bool fitted = a.ndf[trk] > 0;
+    float b_p[5] = {0.0f, 0.0f, 0.0f, 0.0f, 0.0f};
+    if (fitted) {
+      const int begin = a.off[trk];
+      const int last = a.ck_last[trk];
+      float b_L[5][5];
 #pragma unroll 1
       for (int pass = 1; pass >= 0; --pass) {
 #pragma unroll
@@ -465,29 +613,26 @@ __global__ void __launch_bounds__(WARPS * 32, 1) backward_kernel(BwdArgs a) {
 #pragma unroll 1
         for (int s = nseg - 1; s >= 0; --s) {
           StepState S;
-          float chi2;
-          load_ckpt(ckp + (int64_t)s * kCkptFloats, S, chi2);
+          load_ckpt(ckp + (int64_t)s * kCkptFloats, S);
           const int i0 = s * kCkptEvery;
           const int cnt = min(kCkptEvery, steps - i0);
-          // recompute the segment, keeping the state before each step
 #pragma unroll 1
           for (int kk = 0; kk < cnt; ++kk) {
             const int i = i0 + kk;
             const int h = pass == 0 ? begin + i : begin + last - i;
-            float m0 = 0.0f, m1 = 0.0f;
-            int row = 0, sec = 0;
-            read_hit(a, B.align, h, m0, m1, row, sec);
+            float m0, m1;
+            int row, sec;
+            read_hit(a, h, m0, m1, row, sec);
             seg[kk] = S;
-            step_fwd(T, S, chi2, i == 0, row, sec % kNSide, m0, m1);
+            step_fwd(T, S, i == 0, row, sec % kNSide, m0, m1);
           }
-          // reverse the segment
 #pragma unroll 1
           for (int kk = cnt - 1; kk >= 0; --kk) {
             const int i = i0 + kk;
             const int h = pass == 0 ? begin + i : begin + last - i;
-            float m0 = 0.0f, m1 = 0.0f;
-            int row = 0, sec = 0;
-            read_hit(a, B.align, h, m0, m1, row, sec);
+            float m0, m1;
+            int row, sec;
+            read_hit(a, h, m0, m1, row, sec);
             float b_m0 = 0.0f, b_m1 = 0.0f;
             step_rev(T, seg[kk], i == 0, row, sec % kNSide, m0, m1, b_p, b_L, b_chi, b_m0, b_m1);
             if (a.grad_meas) {
@@ -506,8 +651,6 @@ __global__ void __launch_bounds__(WARPS * 32, 1) backward_kernel(BwdArgs a) {
             }
           }
         }
-        // the inward pass starts from the outward result with the factor reset:
-        // b_p carries over, b_L does not
       }
     } else if (a.grad_meas) {
       const int begin = a.off[trk];
@@ -519,18 +662,24 @@ __global__ void __launch_bounds__(WARPS * 32, 1) backward_kernel(BwdArgs a) {
   }
 }
 
-template <int WARPS>
+template <bool TWO_LEVEL, int WARPS>
 cudaError_t launch_backward_cfg(const BwdArgs& a, cudaStream_t s) {
   constexpr int kThreads = WARPS * 32;
-  const size_t smem = sizeof(BlockSmem);
+  const size_t smem = sizeof(SmemTables) + (TWO_LEVEL ? WARPS * sizeof(WarpStore) : 0);
+  void (*kern)(BwdArgs);
+  if constexpr (TWO_LEVEL) kern = backward_kernel_2l<WARPS>;
+  else kern = backward_kernel_1l<WARPS>;
   static int grid = 0;
   if (grid == 0) {
-    cudaError_t e = cudaFuncSetAttribute(backward_kernel<WARPS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    // the one-level kernel keeps its states in local memory: leave L1 as large as possible
+    if (e == cudaSuccess && !TWO_LEVEL)
+      e = cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, 0);
     if (e != cudaSuccess) return e;
     int dev = 0, sms = 0, per_sm = 0;
     e = cudaGetDevice(&dev);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, backward_kernel<WARPS>, kThreads, smem);
+    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kThreads, smem);
     if (e != cudaSuccess) return e;
     if (per_sm < 1) return cudaErrorInvalidConfiguration;
     grid = sms * per_sm;
@@ -540,13 +689,20 @@ cudaError_t launch_backward_cfg(const BwdArgs& a, cudaStream_t s) {
   const int blocks = (int)(need < grid ? need : grid);
   cudaError_t e = cudaMemsetAsync(a.work, 0, sizeof(unsigned int), s);
   if (e != cudaSuccess) return e;
-  backward_kernel<WARPS><<<blocks, kThreads, smem, s>>>(a);
+  kern<<<blocks, kThreads, smem, s>>>(a);
   return cudaGetLastError();
 }
 
-inline cudaError_t launch_backward(const BwdArgs& a, cudaStream_t s) {
+// scheme 0: one level, states in local memory; scheme 1: two levels in shared memory.
+inline cudaError_t launch_backward(const BwdArgs& a, int scheme, int warps, cudaStream_t s) {
   if (a.n_tracks <= 0) return cudaSuccess;
-  return launch_backward_cfg<8>(a, s);
+  if (scheme == 0 && warps == 4) return launch_backward_cfg<false, 4>(a, s);
+  if (scheme == 0 && warps == 8) return launch_backward_cfg<false, 8>(a, s);
+  if (scheme == 0 && warps == 12) return launch_backward_cfg<false, 12>(a, s);
+  if (scheme == 0 && warps == 16) return launch_backward_cfg<false, 16>(a, s);
+  if (scheme == 0 && warps == 24) return launch_backward_cfg<false, 24>(a, s);
+  if (scheme == 1 && warps == 7) return launch_backward_cfg<true, 7>(a, s);
+  return cudaErrorInvalidValue;
 }
 
 }  // namespace TPCFIT_NS

@@ -32,10 +32,11 @@ def case():
     return fr, d_true, w, ref
 
 
-def _gpu_grad(fr, d_true, w, det, rps=4, warps=24, srt=True):
+def _gpu_grad(fr, d_true, w, det, rps=4, warps=24, srt=True, bwd=(0, 12)):
     dev = tf.frame_to_device(fr)
     f = tf.Fitter(fr.geometry, fr.bz, deterministic=det, rows_per_stage=rps, warps_per_block=warps,
                   sort_by_length=srt)
+    f.set_backward_config(*bwd)
     try:
         f.set_alignment(torch.from_numpy(d_true).cuda())
         f.set_record(True)
@@ -62,10 +63,11 @@ def test_adjoint_matches_forward_mode_oracle(case, det):
 def test_deterministic_adjoint_is_bitwise_reproducible(case):
     fr, d_true, w, _ = case
     base = _gpu_grad(fr, d_true, w, True)
-    for rps, warps, srt in ((4, 24, True), (8, 8, False), (16, 8, True)):
-        got = _gpu_grad(fr, d_true, w, True, rps, warps, srt)
+    for rps, warps, srt, bwd in ((4, 24, True, (0, 8)), (8, 8, False, (0, 4)), (16, 8, True, (1, 7)),
+                                 (4, 24, True, (0, 16)), (4, 12, True, (0, 24))):
+        got = _gpu_grad(fr, d_true, w, True, rps, warps, srt, bwd)
         for a, b in zip(got[:3], base[:3]):
-            assert np.array_equal(a.view(np.int32), b.view(np.int32)), (rps, warps, srt)
+            assert np.array_equal(a.view(np.int32), b.view(np.int32)), (rps, warps, srt, bwd)
 
 
 def test_alignment_gradient_matches_fp64_finite_differences():
