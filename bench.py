@@ -176,6 +176,22 @@ def run_reference(args, rank: int, world: int):
     print(json.dumps(line), flush=True)
 
 
+def rank_seed(rank: int) -> int:
+    """Each rank fits its own batch of the same size (weak scaling)."""
+    return 2 + 1000 * rank
+
+
+def combine_ranks(dist, torch, device, step_ms: float, rates: list) -> tuple:
+    """Whole-job view of per-rank numbers: the slowest rank's step time (MAX)
+    and, for per-rank throughputs, world size x the slowest rank (MIN)."""
+    world = dist.get_world_size()
+    t = torch.tensor([step_ms], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    r = torch.tensor(rates if rates else [0.0], dtype=torch.float64, device=device)
+    dist.all_reduce(r, op=dist.ReduceOp.MIN)
+    return float(t.item()), [float(v) * world for v in r.tolist()][: len(rates)]
+
+
 def e2e_run(fitter, fr, out, steps, tf, torch):
     """Tracks/s through tpcfit_fit_host with pinned host buffers: every step
     copies the batch to the device, fits and copies the results back."""
@@ -338,7 +354,7 @@ def main():
     from paper_2511_17018_gb300 import flops, synth
     from paper_2511_17018_gb300 import tpcfit as tf
 
-    fr = synth.generate(args.tracks, 2 + 1000 * rank, drop_p=0.05, cap_lengths=True)
+    fr = synth.generate(args.tracks, rank_seed(rank), drop_p=0.05, cap_lengths=True)
     lengths = fr.lengths()
     dev = tf.frame_to_device(fr)
     fitter = tf.Fitter(fr.geometry, fr.bz, deterministic=(args.mode == "det"))
@@ -392,9 +408,7 @@ def main():
         dist.barrier()
     torch.cuda.synchronize()
     if world > 1:
-        t = torch.tensor([total_ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
+        total_ms, _ = combine_ranks(dist, torch, "cuda", total_ms, [])
     st, code, trk = fitter.status()
     if st != 0:
         raise RuntimeError(f"device reported invalid input: code {code} track {trk}")
@@ -421,9 +435,7 @@ def main():
         fitter.set_record(True)
         v, hb, db = e2e_fit_adjoint(fitter, fr, args.steps, tf, torch)
         if world > 1:  # whole job: every rank streams its own batch; the slowest rank sets the pace
-            t = torch.tensor([v, e2e_plain["value"]], device="cuda")
-            dist.all_reduce(t, op=dist.ReduceOp.MIN)
-            v, e2e_plain["value"] = float(t[0]) * world, float(t[1]) * world
+            _, (v, e2e_plain["value"]) = combine_ranks(dist, torch, "cuda", 0.0, [v, e2e_plain["value"]])
         e2e = {"value": v, "unit": UNIT, "h2d_bytes_per_step": hb, "d2h_bytes_per_step": db}
 
     if rank != 0:
