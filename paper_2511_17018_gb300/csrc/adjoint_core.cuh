@@ -29,6 +29,13 @@ struct JacBar {
 // d/du of asinc_f(u), consistent with the branch asinc_f takes.
 __device__ __forceinline__ float asinc_deriv(float u) {
   const float au = u < 0.0f ? -u : u;
+#if !TPCFIT_DET
+  if (au < 0.05f) {  // derivative of the three-term fast-mode polynomial
+    const float q = u * u;
+    return (2.0f * u) * (static_cast<float>(1.0 / 6.0) +
+                         q * (2.0f * static_cast<float>(3.0 / 40.0) + q * (3.0f * static_cast<float>(5.0 / 112.0))));
+  }
+#endif
   if (au <= 0.25f) {
     const float c1 = static_cast<float>(1.0 / 6.0);
     const float c2 = static_cast<float>(3.0 / 40.0);
@@ -199,7 +206,11 @@ __device__ __forceinline__ void predict_rev(const PredTape& tp, const Jac& J, fl
     const float i2 = ic1 * ic1, i3 = i2 * ic1, i5 = i3 * i2, i7 = i5 * i2, s1s = s1 * s1;
     const float a1 = (s1 * i3) * 0.5f;
     const float a2 = ((1.0f + 2.0f * s1s) * i5) * static_cast<float>(1.0 / 3.0);
+#if TPCFIT_DET
     const float a3 = ((s1 * (3.0f + 2.0f * s1s)) * i7) * 0.125f;
+#else
+    const float a3 = 0.0f;  // the fast forward keeps two terms of the series
+#endif
     const float kdx = tp.kdx, Q = a2 + kdx * a3, P = a1 + kdx * Q;
     b_dx += 2.0f * dx * P * b_Lk;
     const float b_P = dx * dx * b_Lk;

@@ -72,6 +72,13 @@ __device__ __noinline__ double asin_f64(double u) {
 // |u| <= 1/4, else the FP64 island (deterministic) or asinf (fast).
 __device__ __forceinline__ float asinc_f(float u) {
   const float au = u < 0.0f ? -u : u;
+#if !TPCFIT_DET
+  if (au < 0.05f) {  // fast: three terms reach FP32 accuracy here (next term < 3e-11)
+    const float q = u * u;
+    return 1.0f + q * (static_cast<float>(1.0 / 6.0) + q * (static_cast<float>(3.0 / 40.0) +
+                                                           q * static_cast<float>(5.0 / 112.0)));
+  }
+#endif
   if (au <= 0.25f) {
     const float c0 = 1.0f;
     const float c1 = static_cast<float>(1.0 / 6.0);
@@ -226,8 +233,13 @@ __device__ __forceinline__ bool predict_t(const SmemTables& T, const float pin[5
     const float s1s = s1 * s1;
     const float a1 = (s1 * i3) * 0.5f;
     const float a2 = ((1.0f + 2.0f * s1s) * i5) * static_cast<float>(1.0 / 3.0);
+#if TPCFIT_DET
     const float a3 = ((s1 * (3.0f + 2.0f * s1s)) * i7) * 0.125f;
     Lk = (dx * dx) * (a1 + kdx * (a2 + kdx * a3));
+#else
+    (void)i7;
+    Lk = (dx * dx) * (a1 + kdx * a2);
+#endif
   } else {
     Lk = (dx * ic2 - dl) / k;
   }
@@ -297,6 +309,8 @@ __device__ __forceinline__ void scalar_update(float p[5], float L[5][5], float& 
   float alpha, beta, gamma;
   potter_coeffs(s2, v, c_geo.sqrt_v, alpha, beta, gamma);
   const float r = mv - p[H];
+#if TPCFIT_DET
+  // canonical sequence: K = alpha L a, p += K r, gain factors gamma K
   float K[5];
 #pragma unroll
   for (int i = 0; i < 5; ++i) {
@@ -315,6 +329,29 @@ __device__ __forceinline__ void scalar_update(float p[5], float L[5][5], float& 
 #pragma unroll
     for (int c = 0; c < 5; ++c) L[i][c] = L[i][c] - gk * a[c];
   }
+#else
+  // fast: the same algebra with alpha folded into the fused multiply-adds
+  const float ar = alpha * r;
+  const float ga = gamma * alpha;
+  float la[5];
+#pragma unroll
+  for (int i = 0; i < 5; ++i) {
+    float acc = L[i][0] * a[0];
+#pragma unroll
+    for (int c = 1; c < 5; ++c) acc = acc + L[i][c] * a[c];
+    la[i] = acc;
+  }
+#pragma unroll
+  for (int i = 0; i < 5; ++i) p[i] = p[i] + la[i] * ar;
+  chi2 = chi2 + r * ar;
+#pragma unroll
+  for (int i = 0; i < 5; ++i) {
+    if (i == H) continue;
+    const float gk = la[i] * ga;
+#pragma unroll
+    for (int c = 0; c < 5; ++c) L[i][c] = L[i][c] - gk * a[c];
+  }
+#endif
 #pragma unroll
   for (int c = 0; c < 5; ++c) L[H][c] = a[c] * beta;
 }
