@@ -161,12 +161,11 @@ tpcfit_status tpcfit_fit_frames(tpcfit_handle* h, const tpcfit_hits* hits, const
  * recording. */
 tpcfit_status tpcfit_set_record(tpcfit_handle* h, int record);
 
-/* Launch configuration of the adjoint: the storage of the states between two
- * checkpoints.  scheme 0: one level, the 16 states of a segment in per-thread
- * local memory (warps_per_block 4, 8, 12, 16 or 24); scheme 1: two levels kept in
- * shared memory, sub-checkpoints every 4 steps (warps_per_block 7).  Default
- * (0, 12).  Results do not depend on it.  EINVAL for other values. */
-tpcfit_status tpcfit_set_backward_config(tpcfit_handle* h, int scheme, int warps_per_block);
+/* Launch configuration of the adjoint: warps per block (4, 8, 12, 16 or 24;
+ * default 12).  The states between two checkpoints live in per-thread local
+ * memory, so fewer warps leave more L1 per warp and more warps hide more
+ * latency.  Results do not depend on it.  EINVAL for other values. */
+tpcfit_status tpcfit_set_backward_config(tpcfit_handle* h, int warps_per_block);
 
 /* Adjoint of the recorded fit: gradients of L = sum_i grad_chi2[i] * chi2_i.
  * Inputs must be those of the last tpcfit_fit on this handle, which must have

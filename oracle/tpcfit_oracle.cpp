@@ -28,7 +28,8 @@
 // float one the square-root form (see Filter below).
 //
 // Every formula is written with explicit evaluation order; the float
-// instantiation therefore defines the canonical FP32 operation sequence.
+// instantiation therefore defines the canonical FP32 operation sequence,
+// including the residual coordinates for y and z (see fit_track).
 
 #include <cmath>
 #include <cstdint>
@@ -36,6 +37,7 @@
 #include <cstring>
 #include <atomic>
 #include <vector>
+#include <type_traits>
 #ifdef _OPENMP
 #include <omp.h>
 #endif
@@ -529,24 +531,58 @@ FitResult fit_track(const Geo<typename Traits<T>::S>& g, const HitView<T>& h, co
   Filter<T, kSqrt> F;
   T x;
   T chi2(0.0);
+  constexpr bool kRes = std::is_same<T, float>::value;  // residual coordinates (see below)
+  T my(0.0), mz(0.0);                                    // measurement of the current cluster
   auto record = [&](int pass, int j) {
     if (!trace) return;
     double* o = trace + ((size_t)j * 2 + pass) * 22;
     T C[15];
     F.cov(C);
     for (int i = 0; i < 5; ++i) o[i] = V(p[i]);
+    if (kRes && !ref) {  // residual form: report positions
+      o[0] = (double)(float)(V(my) + V(p[0]));
+      o[1] = (double)(float)(V(mz) + V(p[1]));
+    }
     for (int e = 0; e < 15; ++e) o[5 + e] = V(C[e]);
     o[20] = V(chi2);
     o[21] = V(x);
   };
+  // FP32 sequence: y and z are carried as residuals from the measurement of the
+  // current cluster (p[0] = y - m_y, p[1] = z - m_z), so that their rounding is
+  // that of ~0.1 cm quantities instead of positions up to 250 cm.  The helix
+  // step adds the exact difference of consecutive measurements; across a
+  // sector rotation the absolute position is formed, rotated and re-referenced.
+  // The FP64 and dual instantiations keep absolute coordinates.
   auto step = [&](int from, int to) -> bool {
     const int r = hit_row(h, to);
     if (r < 0 || r >= g.n_rows) return false;
     Jac<T> J;
     T pn[5];
     T xn;
+    T mt[2];
+    meas<T>(h, to, yv[to], zv[to], mt);
     if (!ref) {
-      if (!predict<T>(g, p, x, hit_sec(h, from), hit_sec(h, to), g.row_x[r], pn, xn, J)) return false;
+      if (kRes) {
+        const bool rot = (hit_sec(h, from) % kNSectorsPerSide) != (hit_sec(h, to) % kNSectorsPerSide);
+        T pin[5];
+        for (int i = 0; i < 5; ++i) pin[i] = p[i];
+        if (rot) {
+          pin[0] = my + p[0];
+          pin[1] = mz + p[1];
+        }
+        if (!predict<T>(g, pin, x, hit_sec(h, from), hit_sec(h, to), g.row_x[r], pn, xn, J)) return false;
+        if (rot) {
+          pn[0] = pn[0] - mt[0];
+          pn[1] = pn[1] - mt[1];
+        } else {
+          pn[0] = pn[0] + (my - mt[0]);
+          pn[1] = pn[1] + (mz - mt[1]);
+        }
+        my = mt[0];
+        mz = mt[1];
+      } else if (!predict<T>(g, p, x, hit_sec(h, from), hit_sec(h, to), g.row_x[r], pn, xn, J)) {
+        return false;
+      }
     } else {
       T pr[5];
       for (int i = 0; i < 5; ++i) pr[i] = T((S)ref[(size_t)from * 5 + i]);
@@ -565,8 +601,11 @@ FitResult fit_track(const Geo<typename Traits<T>::S>& g, const HitView<T>& h, co
     for (int i = 0; i < 5; ++i) p[i] = pn[i];
     x = xn;
     F.transport_(J);
-    T m[2];
-    meas<T>(h, to, yv[to], zv[to], m);
+    T m[2] = {mt[0], mt[1]};
+    if (kRes && !ref) {
+      m[0] = T((S)0.0);
+      m[1] = T((S)0.0);
+    }
     return F.update(g, p, chi2, m);
   };
   // ---- outward pass
@@ -579,6 +618,14 @@ FitResult fit_track(const Geo<typename Traits<T>::S>& g, const HitView<T>& h, co
   {
     T m[2];
     meas<T>(h, 0, yv[0], zv[0], m);
+    if (kRes && !ref) {
+      my = m[0];
+      mz = m[1];
+      p[0] = p[0] - my;
+      p[1] = p[1] - mz;
+      m[0] = T((S)0.0);
+      m[1] = T((S)0.0);
+    }
     if (!F.update(g, p, chi2, m)) return res;
   }
   record(0, 0);
@@ -595,6 +642,10 @@ FitResult fit_track(const Geo<typename Traits<T>::S>& g, const HitView<T>& h, co
   {
     T m[2];
     meas<T>(h, last, yv[last], zv[last], m);
+    if (kRes && !ref) {
+      m[0] = T((S)0.0);
+      m[1] = T((S)0.0);
+    }
     if (!F.update(g, p, chi2, m)) return res;
   }
   ++used;
@@ -606,6 +657,10 @@ FitResult fit_track(const Geo<typename Traits<T>::S>& g, const HitView<T>& h, co
   }
   if (used < 3) return res;
   for (int i = 0; i < 5; ++i) p_out[i] = p[i];
+  if (kRes && !ref) {
+    p_out[0] = my + p[0];
+    p_out[1] = mz + p[1];
+  }
   F.cov(C_out);
   chi2_out = chi2;
   res.ok = 1;

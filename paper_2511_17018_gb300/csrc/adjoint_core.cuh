@@ -10,10 +10,10 @@
 //
 // Checkpoints: the forward writes the filter state (p, L, x, sector, chi2)
 // before every 16th step of each pass.  The backward walks the segments of a
-// track in reverse and recomputes between checkpoints in two levels kept on
-// chip (shared memory): the 16 steps once, keeping sub-checkpoints every 4
-// steps, then each 4-step sub-segment, keeping the state before each step,
-// which it reverses (recomputing each step's intermediates from that state).
+// track in reverse: it recomputes a segment's steps from its checkpoint into
+// a per-thread state array, then reverses the steps one by one (recomputing
+// each step's intermediates from the state before it).  States carry y and z
+// as residuals from the current cluster's measurement, like the fit.
 #pragma once
 
 namespace tpcfit {
@@ -365,44 +365,61 @@ __device__ __forceinline__ void read_hit(const BwdArgs& a, int h, float& m0, flo
   m1 = __ldg(a.z + h) - d.y;
 }
 
-// Forward of one step on a StepState (the same operations as the fit).
-__device__ __forceinline__ void step_fwd(const SmemTables& T, StepState& S, bool first, int row, int sec18, float m0,
-                                         float m1) {
+// Forward of one step on a StepState (the same operations as the fit, in
+// residual coordinates).  my, mz: measurement of the previous cluster on
+// entry, of this cluster on exit.  conv: the first step of the outward pass,
+// whose state is the seed in absolute coordinates.
+__device__ __forceinline__ void step_fwd(const SmemTables& T, StepState& S, float& my, float& mz, bool first, bool conv,
+                                         int row, int sec18, float m0, float m1) {
   float chi2 = 0.0f;
   if (first) {
     S.x = T.row_x[row];
     S.sec = sec18;
+    if (conv) {
+      S.p[0] = S.p[0] - m0;
+      S.p[1] = S.p[1] - m1;
+    }
   } else {
     float pn[5];
     Jac J;
-    predict(T, S.p, S.x, S.sec, sec18, T.row_x[row], pn, J);
+    PredTape tp;
+    predict_residual(T, S.p, S.x, S.sec, my, mz, sec18, T.row_x[row], m0, m1, pn, J, tp);
 #pragma unroll
     for (int c = 0; c < 5; ++c) S.p[c] = pn[c];
     S.x = T.row_x[row];
     S.sec = sec18;
     transport(S.L, J);
   }
-  scalar_update<0>(S.p, S.L, chi2, m0);
-  scalar_update<1>(S.p, S.L, chi2, m1);
+  my = m0;
+  mz = m1;
+  scalar_update<0>(S.p, S.L, chi2, 0.0f);
+  scalar_update<1>(S.p, S.L, chi2, 0.0f);
 }
 
-// Reverse of one step from the state before it.  b_p, b_L: in = adjoint after
-// the step, out = adjoint before it.
-__device__ __forceinline__ void step_rev(const SmemTables& T, const StepState& S0, bool first, int row, int sec18,
-                                         float m0, float m1, float b_p[5], float b_L[5][5], float b_chi, float& b_m0,
-                                         float& b_m1) {
+// Reverse of one step from the state before it (my_prev, mz_prev: measurement
+// of the previous cluster).  b_p, b_L: in = adjoint after the step, out =
+// adjoint before it.  The measurements enter only through the residual
+// shifts: b_mc = adjoint of this cluster's (y, z), b_mp = of the previous one's.
+__device__ __forceinline__ void step_rev(const SmemTables& T, const StepState& S0, float my_prev, float mz_prev,
+                                         bool first, bool conv, int row, int sec18, float m0, float m1, float b_p[5],
+                                         float b_L[5][5], float b_chi, float b_mc[2], float b_mp[2]) {
   float p1[5];
   Jac J;
   float L[5][5];
+  PredTape tp;
   if (first) {
 #pragma unroll
     for (int c = 0; c < 5; ++c) p1[c] = S0.p[c];
+    if (conv) {
+      p1[0] = S0.p[0] - m0;
+      p1[1] = S0.p[1] - m1;
+    }
   } else {
-    predict(T, S0.p, S0.x, S0.sec, sec18, T.row_x[row], p1, J);
+    predict_residual(T, S0.p, S0.x, S0.sec, my_prev, mz_prev, sec18, T.row_x[row], m0, m1, p1, J, tp);
   }
   // state before the z update
   float p2[5];
-  float chi_dummy = 0.0f;
+  float chi_dummy = 0.0f, b_dummy = 0.0f;
 #pragma unroll
   for (int c = 0; c < 5; ++c) p2[c] = p1[c];
 #pragma unroll
@@ -410,183 +427,73 @@ __device__ __forceinline__ void step_rev(const SmemTables& T, const StepState& S
 #pragma unroll
     for (int c = 0; c < 5; ++c) L[i][c] = S0.L[i][c];
   if (!first) transport(L, J);
-  scalar_update<0>(p2, L, chi_dummy, m0);
-  scalar_update_rev<1>(p2, L, m1, b_p, b_L, b_chi, b_m1);
+  scalar_update<0>(p2, L, chi_dummy, 0.0f);
+  scalar_update_rev<1>(p2, L, 0.0f, b_p, b_L, b_chi, b_dummy);
   // state before the y update (recomputed)
 #pragma unroll
   for (int i = 0; i < 5; ++i)
 #pragma unroll
     for (int c = 0; c < 5; ++c) L[i][c] = S0.L[i][c];
   if (!first) transport(L, J);
-  scalar_update_rev<0>(p1, L, m0, b_p, b_L, b_chi, b_m0);
-  if (first) return;
+  scalar_update_rev<0>(p1, L, 0.0f, b_p, b_L, b_chi, b_dummy);
+  // b_p is now the adjoint of the predicted (shifted) state p1
+  b_mc[0] = -b_p[0];
+  b_mc[1] = -b_p[1];
+  b_mp[0] = 0.0f;
+  b_mp[1] = 0.0f;
+  if (first) {
+    if (!conv) b_mc[0] = b_mc[1] = 0.0f;  // the inward pass starts from residuals already
+    return;
+  }
   JacBar bJ;
   transport_rev(S0.L, J, b_L, bJ);
+  const bool rot = S0.sec != sec18;
+  if (!rot) {
+    b_mp[0] = b_p[0];
+    b_mp[1] = b_p[1];
+  }
+  float pin[5];
+#pragma unroll
+  for (int c = 0; c < 5; ++c) pin[c] = S0.p[c];
+  if (rot) {
+    pin[0] = my_prev + S0.p[0];
+    pin[1] = mz_prev + S0.p[1];
+  }
   float pn[5];
-  PredTape tp;
-  predict_t(T, S0.p, S0.x, S0.sec, sec18, T.row_x[row], pn, J, tp);
+  predict_t(T, pin, S0.x, S0.sec, sec18, T.row_x[row], pn, J, tp);
   float b_pi[5];
   predict_rev(tp, J, S0.p[3], b_p, bJ, b_pi);
+  if (rot) {
+    b_mp[0] = b_pi[0];
+    b_mp[1] = b_pi[1];
+  }
 #pragma unroll
   for (int c = 0; c < 5; ++c) b_p[c] = b_pi[c];
 }
 
-// On-chip state store of a warp: kSlots filter states (p, L) per lane, laid
-// out [slot][component][lane] so that every access is conflict-free.
-constexpr int kSub = 4;                  // sub-segment length
-constexpr int kSlots = kCkptEvery / kSub + kSub;  // sub-checkpoints + step states
-constexpr int kStateFloats = 30;
-
-struct WarpStore {
-  float v[kSlots][kStateFloats][kWarp];
-};
-
-__device__ __forceinline__ void put_state(WarpStore& w, int slot, int lane, const StepState& S) {
-#pragma unroll
-  for (int c = 0; c < 5; ++c) w.v[slot][c][lane] = S.p[c];
-#pragma unroll
-  for (int i = 0; i < 5; ++i)
-#pragma unroll
-    for (int c = 0; c < 5; ++c) w.v[slot][5 + 5 * i + c][lane] = S.L[i][c];
-}
-
-__device__ __forceinline__ void get_state(const WarpStore& w, int slot, int lane, StepState& S) {
-#pragma unroll
-  for (int c = 0; c < 5; ++c) S.p[c] = w.v[slot][c][lane];
-#pragma unroll
-  for (int i = 0; i < 5; ++i)
-#pragma unroll
-    for (int c = 0; c < 5; ++c) S.L[i][c] = w.v[slot][5 + 5 * i + c][lane];
-}
-
-// Frame (x, sector) of the state before step i of a pass: that of cluster i-1.
-__device__ __forceinline__ void frame_before(const BwdArgs& a, const SmemTables& T, int h_prev, StepState& S) {
-  const int rsv = (int)__ldg(a.rowsec + h_prev);
-  S.x = T.row_x[rsv >> 6];
-  S.sec = (rsv & 63) % kNSide;
-}
-
-// Per track, per pass (inward reversed first): for every 16-step segment, from
-// its checkpoint, recompute the segment keeping sub-checkpoints every 4 steps;
-// then for every 4-step sub-segment (last first) recompute its steps keeping
-// the state before each step and reverse them.  All states stay in shared memory.
-template <int WARPS>
-__global__ void __launch_bounds__(WARPS * 32, 1) backward_kernel_2l(BwdArgs a) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  SmemTables& T = *reinterpret_cast<SmemTables*>(smem_raw);
-  WarpStore* stores = reinterpret_cast<WarpStore*>(smem_raw + sizeof(SmemTables));
-  load_tables(T);
-  __syncthreads();
-  const int lane = threadIdx.x & 31;
-  WarpStore& W = stores[threadIdx.x >> 5];
-  const int64_t n_chunks = ((int64_t)a.n_tracks + kWarp - 1) / kWarp;
-  const int64_t N = a.n_tracks;
-
-#pragma unroll 1
-  for (;;) {
-    int64_t chunk = 0;
-    if (lane == 0) chunk = (int64_t)atomicAdd(a.work, 1u);
-    chunk = __shfl_sync(0xffffffffu, chunk, 0);
-    if (chunk >= n_chunks) break;
-    const int64_t slot = chunk * kWarp + lane;
-    if (slot >= N) continue;
-    const int32_t trk = a.perm ? a.perm[slot] : (int32_t)slot;
-    const float g = __ldg(a.grad_chi2 + trk);
-    const bool fitted = a.ndf[trk] > 0;
-    float b_p[5] = {0.0f, 0.0f, 0.0f, 0.0f, 0.0f};
-    if (fitted) {
-      const int begin = a.off[trk];
-      const int last = a.ck_last[trk];
-      float b_L[5][5];
-#pragma unroll 1
-      for (int pass = 1; pass >= 0; --pass) {
-#pragma unroll
-        for (int i = 0; i < 5; ++i)
-#pragma unroll
-          for (int c = 0; c < 5; ++c) b_L[i][c] = 0.0f;
-        const float b_chi = pass == 1 ? g : 0.0f;
-        const int steps = last + 1;
-        const int nseg = (steps + kCkptEvery - 1) / kCkptEvery;
-        const float* ckp = a.ck + ((int64_t)pass * a.ck_slots + (begin >> 4) + trk) * kCkptFloats;
-        // cluster of local step i of this pass
-        auto hit_of = [&](int i) { return pass == 0 ? begin + i : begin + last - i; };
-#pragma unroll 1
-        for (int s = nseg - 1; s >= 0; --s) {
-          const int i0 = s * kCkptEvery;
-          const int cnt = min(kCkptEvery, steps - i0);
-          StepState S;
-          load_ckpt(ckp + (int64_t)s * kCkptFloats, S);
-          // level 1: the segment, keeping the state before every 4th step
-#pragma unroll 1
-          for (int kk = 0; kk < cnt; ++kk) {
-            if ((kk & (kSub - 1)) == 0) put_state(W, kk / kSub, lane, S);
-            float m0, m1;
-            int row, sec;
-            read_hit(a, hit_of(i0 + kk), m0, m1, row, sec);
-            step_fwd(T, S, i0 + kk == 0, row, sec % kNSide, m0, m1);
-          }
-          // level 2: sub-segments, last first
-#pragma unroll 1
-          for (int q = (cnt - 1) / kSub; q >= 0; --q) {
-            const int j0 = i0 + q * kSub;
-            const int qc = min(kSub, cnt - q * kSub);
-            get_state(W, q, lane, S);
-            if (j0 > 0) frame_before(a, T, hit_of(j0 - 1), S);
-#pragma unroll 1
-            for (int j = 0; j < qc; ++j) {
-              put_state(W, kCkptEvery / kSub + j, lane, S);
-              float m0, m1;
-              int row, sec;
-              read_hit(a, hit_of(j0 + j), m0, m1, row, sec);
-              step_fwd(T, S, j0 + j == 0, row, sec % kNSide, m0, m1);
-            }
-#pragma unroll 1
-            for (int j = qc - 1; j >= 0; --j) {
-              const int i = j0 + j;
-              const int h = hit_of(i);
-              StepState S0;
-              get_state(W, kCkptEvery / kSub + j, lane, S0);
-              if (i > 0) frame_before(a, T, hit_of(i - 1), S0);
-              float m0, m1;
-              int row, sec;
-              read_hit(a, h, m0, m1, row, sec);
-              float b_m0 = 0.0f, b_m1 = 0.0f;
-              step_rev(T, S0, i == 0, row, sec % kNSide, m0, m1, b_p, b_L, b_chi, b_m0, b_m1);
-              if (a.grad_meas) {
-                float2* gm = reinterpret_cast<float2*>(a.grad_meas) + h;
-                if (pass == 1) {
-                  *gm = make_float2(b_m0, b_m1);
-                } else {
-                  const float2 o = *gm;
-                  *gm = make_float2(o.x + b_m0, o.y + b_m1);
-                }
-              }
-              if (a.grad_align_atomic) {
-                float* dst = a.grad_align_atomic + (sec * kMaxRows + row) * 2;
-                atomicAdd(dst, -b_m0);
-                atomicAdd(dst + 1, -b_m1);
-              }
-            }
-          }
-        }
-        // the inward pass starts from the outward result with the factor reset:
-        // b_p carries over, b_L does not
-      }
-    } else if (a.grad_meas) {
-      const int begin = a.off[trk];
-      const int end = a.off[trk + 1];
-      for (int h = begin; h < end; ++h) reinterpret_cast<float2*>(a.grad_meas)[h] = make_float2(0.0f, 0.0f);
+__device__ __forceinline__ void accumulate_meas_grad(const BwdArgs& a, int pass, int h, int row, int sec, float g0,
+                                                     float g1) {
+  if (a.grad_meas) {
+    float2* gm = reinterpret_cast<float2*>(a.grad_meas) + h;
+    if (pass == 1) {
+      *gm = make_float2(g0, g1);
+    } else {
+      const float2 o = *gm;
+      *gm = make_float2(o.x + g0, o.y + g1);
     }
-#pragma unroll
-    for (int c = 0; c < 5; ++c) a.grad_seeds[(int64_t)c * N + trk] = b_p[c];
+  }
+  if (a.grad_align_atomic) {
+    float* dst = a.grad_align_atomic + (sec * kMaxRows + row) * 2;
+    atomicAdd(dst, -g0);
+    atomicAdd(dst + 1, -g1);
   }
 }
 
-// One-level variant: the 16 states of a segment in a per-thread array (local
-// memory, cached in L1/L2); one forward recomputation per step fewer than the
-// two-level kernel, more memory traffic.
+// Per track, per pass (inward reversed first): for every 16-step segment, from
+// its checkpoint, recompute the segment keeping the state before each step in
+// a per-thread array (local memory), then reverse the steps.
 template <int WARPS>
-__global__ void __launch_bounds__(WARPS * 32, 1) backward_kernel_1l(BwdArgs a) {
+__global__ void __launch_bounds__(WARPS * 32, 1) backward_kernel(BwdArgs a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   SmemTables& T = *reinterpret_cast<SmemTables*>(smem_raw);
   load_tables(T);
@@ -621,12 +528,18 @@ __global__ void __launch_bounds__(WARPS * 32, 1) backward_kernel_1l(BwdArgs a) {
         const int steps = last + 1;
         const int nseg = (steps + kCkptEvery - 1) / kCkptEvery;
         const float* ckp = a.ck + ((int64_t)pass * a.ck_slots + (begin >> 4) + trk) * kCkptFloats;
+        float pend0 = 0.0f, pend1 = 0.0f;  // gradient owed to the measurement of the step before
 #pragma unroll 1
         for (int s = nseg - 1; s >= 0; --s) {
           StepState S;
           load_ckpt(ckp + (int64_t)s * kCkptFloats, S);
           const int i0 = s * kCkptEvery;
           const int cnt = min(kCkptEvery, steps - i0);
+          float my = 0.0f, mz = 0.0f;
+          if (i0 > 0) {
+            int row, sec;
+            read_hit(a, pass == 0 ? begin + i0 - 1 : begin + last - (i0 - 1), my, mz, row, sec);
+          }
 #pragma unroll 1
           for (int kk = 0; kk < cnt; ++kk) {
             const int i = i0 + kk;
@@ -635,33 +548,34 @@ __global__ void __launch_bounds__(WARPS * 32, 1) backward_kernel_1l(BwdArgs a) {
             int row, sec;
             read_hit(a, h, m0, m1, row, sec);
             seg[kk] = S;
-            step_fwd(T, S, i == 0, row, sec % kNSide, m0, m1);
+            step_fwd(T, S, my, mz, i == 0, pass == 0, row, sec % kNSide, m0, m1);
           }
+          // reverse; the previous cluster of a step is the current one of the next
+          // step reversed, so each cluster is read once here
+          float m0, m1;
+          int row, sec;
+          read_hit(a, pass == 0 ? begin + i0 + cnt - 1 : begin + last - (i0 + cnt - 1), m0, m1, row, sec);
 #pragma unroll 1
           for (int kk = cnt - 1; kk >= 0; --kk) {
             const int i = i0 + kk;
             const int h = pass == 0 ? begin + i : begin + last - i;
-            float m0, m1;
-            int row, sec;
-            read_hit(a, h, m0, m1, row, sec);
-            float b_m0 = 0.0f, b_m1 = 0.0f;
-            step_rev(T, seg[kk], i == 0, row, sec % kNSide, m0, m1, b_p, b_L, b_chi, b_m0, b_m1);
-            if (a.grad_meas) {
-              float2* gm = reinterpret_cast<float2*>(a.grad_meas) + h;
-              if (pass == 1) {
-                *gm = make_float2(b_m0, b_m1);
-              } else {
-                const float2 o = *gm;
-                *gm = make_float2(o.x + b_m0, o.y + b_m1);
-              }
-            }
-            if (a.grad_align_atomic) {
-              float* dst = a.grad_align_atomic + (sec * kMaxRows + row) * 2;
-              atomicAdd(dst, -b_m0);
-              atomicAdd(dst + 1, -b_m1);
-            }
+            float mpy = 0.0f, mpz = 0.0f;
+            int prow = 0, psec = 0;
+            if (i > 0) read_hit(a, pass == 0 ? h - 1 : h + 1, mpy, mpz, prow, psec);
+            float b_mc[2], b_mp[2];
+            step_rev(T, seg[kk], mpy, mpz, i == 0, pass == 0, row, sec % kNSide, m0, m1, b_p, b_L, b_chi, b_mc,
+                     b_mp);
+            accumulate_meas_grad(a, pass, h, row, sec, b_mc[0] + pend0, b_mc[1] + pend1);
+            pend0 = b_mp[0];
+            pend1 = b_mp[1];
+            m0 = mpy;
+            m1 = mpz;
+            row = prow;
+            sec = psec;
           }
         }
+        // the inward pass starts from the outward result with the factor reset:
+        // b_p carries over, b_L does not
       }
     } else if (a.grad_meas) {
       const int begin = a.off[trk];
@@ -673,24 +587,20 @@ __global__ void __launch_bounds__(WARPS * 32, 1) backward_kernel_1l(BwdArgs a) {
   }
 }
 
-template <bool TWO_LEVEL, int WARPS>
+template <int WARPS>
 cudaError_t launch_backward_cfg(const BwdArgs& a, cudaStream_t s) {
   constexpr int kThreads = WARPS * 32;
-  const size_t smem = sizeof(SmemTables) + (TWO_LEVEL ? WARPS * sizeof(WarpStore) : 0);
-  void (*kern)(BwdArgs);
-  if constexpr (TWO_LEVEL) kern = backward_kernel_2l<WARPS>;
-  else kern = backward_kernel_1l<WARPS>;
+  const size_t smem = sizeof(SmemTables);
   static int grid = 0;
   if (grid == 0) {
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    // the one-level kernel keeps its states in local memory: leave L1 as large as possible
-    if (e == cudaSuccess && !TWO_LEVEL)
-      e = cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, 0);
+    cudaError_t e = cudaFuncSetAttribute(backward_kernel<WARPS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    // the states live in local memory: leave L1 as large as possible
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(backward_kernel<WARPS>, cudaFuncAttributePreferredSharedMemoryCarveout, 0);
     if (e != cudaSuccess) return e;
     int dev = 0, sms = 0, per_sm = 0;
     e = cudaGetDevice(&dev);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kThreads, smem);
+    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, backward_kernel<WARPS>, kThreads, smem);
     if (e != cudaSuccess) return e;
     if (per_sm < 1) return cudaErrorInvalidConfiguration;
     grid = sms * per_sm;
@@ -700,20 +610,20 @@ cudaError_t launch_backward_cfg(const BwdArgs& a, cudaStream_t s) {
   const int blocks = (int)(need < grid ? need : grid);
   cudaError_t e = cudaMemsetAsync(a.work, 0, sizeof(unsigned int), s);
   if (e != cudaSuccess) return e;
-  kern<<<blocks, kThreads, smem, s>>>(a);
+  backward_kernel<WARPS><<<blocks, kThreads, smem, s>>>(a);
   return cudaGetLastError();
 }
 
-// scheme 0: one level, states in local memory; scheme 1: two levels in shared memory.
-inline cudaError_t launch_backward(const BwdArgs& a, int scheme, int warps, cudaStream_t s) {
+inline cudaError_t launch_backward(const BwdArgs& a, int warps, cudaStream_t s) {
   if (a.n_tracks <= 0) return cudaSuccess;
-  if (scheme == 0 && warps == 4) return launch_backward_cfg<false, 4>(a, s);
-  if (scheme == 0 && warps == 8) return launch_backward_cfg<false, 8>(a, s);
-  if (scheme == 0 && warps == 12) return launch_backward_cfg<false, 12>(a, s);
-  if (scheme == 0 && warps == 16) return launch_backward_cfg<false, 16>(a, s);
-  if (scheme == 0 && warps == 24) return launch_backward_cfg<false, 24>(a, s);
-  if (scheme == 1 && warps == 7) return launch_backward_cfg<true, 7>(a, s);
-  return cudaErrorInvalidValue;
+  switch (warps) {
+    case 4: return launch_backward_cfg<4>(a, s);
+    case 8: return launch_backward_cfg<8>(a, s);
+    case 12: return launch_backward_cfg<12>(a, s);
+    case 16: return launch_backward_cfg<16>(a, s);
+    case 24: return launch_backward_cfg<24>(a, s);
+    default: return cudaErrorInvalidValue;
+  }
 }
 
 }  // namespace TPCFIT_NS

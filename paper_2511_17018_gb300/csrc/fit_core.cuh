@@ -271,6 +271,33 @@ __device__ __forceinline__ bool predict(const SmemTables& T, const float pin[5],
   return predict_t(T, pin, xin, a, b, X, pout, J, tp);
 }
 
+// Prediction in residual coordinates: p[0..1] are residuals from (my, mz), the
+// output is relative to the next cluster's measurement (m0, m1).  Without a
+// rotation the exact difference of the two measurements is added; across a
+// rotation the absolute position is formed, rotated, propagated and
+// re-referenced.
+__device__ __forceinline__ bool predict_residual(const SmemTables& T, const float p[5], float x, int sec, float my,
+                                                 float mz, int sec_to, float X, float m0, float m1, float pout[5],
+                                                 Jac& J, PredTape& tp) {
+  float pin[5];
+#pragma unroll
+  for (int c = 0; c < 5; ++c) pin[c] = p[c];
+  const bool rot = sec != sec_to;
+  if (rot) {
+    pin[0] = my + p[0];
+    pin[1] = mz + p[1];
+  }
+  if (!predict_t(T, pin, x, sec, sec_to, X, pout, J, tp)) return false;
+  if (rot) {
+    pout[0] = pout[0] - m0;
+    pout[1] = pout[1] - m1;
+  } else {
+    pout[0] = pout[0] + (my - m0);
+    pout[1] = pout[1] + (mz - m1);
+  }
+  return true;
+}
+
 // L <- J L (rows t, q of J are identity).
 __device__ __forceinline__ void transport(float L[5][5], const Jac& J) {
   if (!J.rot) {
@@ -370,11 +397,14 @@ __device__ __forceinline__ void record_error(unsigned long long* err, unsigned l
 
 // ---------------------------------------------------------------- the fit kernel
 // Lane state across the two passes.
+// y and z are carried as residuals from the measurement (my, mz) of the
+// current cluster: p[0] = y - my, p[1] = z - mz.
 struct TrackState {
   float p[5];
   float L[5][5];
   float x;
   float chi2;
+  float my, mz;
   int sec;      // sector (mod 18) of the current frame
   int used;
 };
@@ -434,6 +464,12 @@ struct BlockSmem {
   SmemTables T;
   float align[kAlignFloats];
 };
+
+__device__ __forceinline__ bool step_predict(const SmemTables& T, const TrackState& S, int sec_to, float X, float m0,
+                                             float m1, float pout[5], Jac& J) {
+  PredTape tp;
+  return predict_residual(T, S.p, S.x, S.sec, S.my, S.mz, sec_to, X, m0, m1, pout, J, tp);
+}
 
 __device__ __forceinline__ void write_ckpt(const FitArgs& a, int pass, int begin, int trk, int seg,
                                            const TrackState& S) {
@@ -572,13 +608,20 @@ __global__ void __launch_bounds__(WARPS * 32, MINB) fit_kernel(FitArgs a) {
           const int sec18 = sec % kNSide;
           if (RECORD && (i & 15) == 0) write_ckpt(a, pass, begin, trk, i >> 4, S);
           if (i == 0) {
-            // first cluster of the pass: the state sits on its row already
+            // first cluster of the pass: the state sits on its row already; the
+            // outward pass turns the seed's (y, z) into residuals
             S.x = T.row_x[row];
             S.sec = sec18;
+            if (pass == 0) {
+              S.my = m0;
+              S.mz = m1;
+              S.p[0] = S.p[0] - m0;
+              S.p[1] = S.p[1] - m1;
+            }
           } else {
             float pn[5];
             Jac J;
-            if (!predict(T, S.p, S.x, S.sec, sec18, T.row_x[row], pn, J)) {
+            if (!step_predict(T, S, sec18, T.row_x[row], m0, m1, pn, J)) {
               go = false;
               if (pass == 1) status = 2;  // the inward pass must reach the first cluster
               continue;
@@ -587,10 +630,12 @@ __global__ void __launch_bounds__(WARPS * 32, MINB) fit_kernel(FitArgs a) {
             for (int c = 0; c < 5; ++c) S.p[c] = pn[c];
             S.x = T.row_x[row];
             S.sec = sec18;
+            S.my = m0;
+            S.mz = m1;
             transport(S.L, J);
           }
-          scalar_update<0>(S.p, S.L, S.chi2, m0);
-          scalar_update<1>(S.p, S.L, S.chi2, m1);
+          scalar_update<0>(S.p, S.L, S.chi2, 0.0f);
+          scalar_update<1>(S.p, S.L, S.chi2, 0.0f);
           S.used += 1;
           if (pass == 0) last = i;
         }
@@ -604,8 +649,10 @@ __global__ void __launch_bounds__(WARPS * 32, MINB) fit_kernel(FitArgs a) {
     if (RECORD) a.ck_last[trk] = last;
     const int64_t N = a.n_tracks;
     if (status == 0 && S.used >= 3) {
+      a.params[trk] = S.my + S.p[0];
+      a.params[N + trk] = S.mz + S.p[1];
 #pragma unroll
-      for (int c = 0; c < 5; ++c) a.params[(int64_t)c * N + trk] = S.p[c];
+      for (int c = 2; c < 5; ++c) a.params[(int64_t)c * N + trk] = S.p[c];
       int e = 0;
 #pragma unroll
       for (int i = 0; i < 5; ++i)

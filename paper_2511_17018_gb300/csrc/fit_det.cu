@@ -12,7 +12,7 @@ static ConstRegistration reg_det("fit_det", &det::upload);
 cudaError_t launch_fit_det(const FitArgs& a, int lanes_per_track, int rows_per_stage, int warps, cudaStream_t s) {
   return det::launch(a, lanes_per_track, rows_per_stage, warps, s);
 }
-cudaError_t launch_backward_det(const BwdArgs& a, int scheme, int warps, cudaStream_t s) {
-  return det::launch_backward(a, scheme, warps, s);
+cudaError_t launch_backward_det(const BwdArgs& a, int warps, cudaStream_t s) {
+  return det::launch_backward(a, warps, s);
 }
 }  // namespace tpcfit

@@ -11,7 +11,7 @@ static ConstRegistration reg_fast("fit_fast", &fast::upload);
 cudaError_t launch_fit_fast(const FitArgs& a, int lanes_per_track, int rows_per_stage, int warps, cudaStream_t s) {
   return fast::launch(a, lanes_per_track, rows_per_stage, warps, s);
 }
-cudaError_t launch_backward_fast(const BwdArgs& a, int scheme, int warps, cudaStream_t s) {
-  return fast::launch_backward(a, scheme, warps, s);
+cudaError_t launch_backward_fast(const BwdArgs& a, int warps, cudaStream_t s) {
+  return fast::launch_backward(a, warps, s);
 }
 }  // namespace tpcfit

@@ -102,10 +102,10 @@ bool build_geo(const tpcfit_geometry* g, double bz, GeoConst& out);
 // ---- kernel launchers, one per module
 cudaError_t launch_fit_fast(const FitArgs& a, int lanes_per_track, int rows_per_stage, int warps, cudaStream_t s);
 cudaError_t launch_fit_det(const FitArgs& a, int lanes_per_track, int rows_per_stage, int warps, cudaStream_t s);
-cudaError_t launch_backward_fast(const BwdArgs& a, int scheme, int warps, cudaStream_t s);
-cudaError_t launch_backward_det(const BwdArgs& a, int scheme, int warps, cudaStream_t s);
-// true if (scheme, warps) is a compiled backward shape
-bool backward_shape_supported(int scheme, int warps);
+cudaError_t launch_backward_fast(const BwdArgs& a, int warps, cudaStream_t s);
+cudaError_t launch_backward_det(const BwdArgs& a, int warps, cudaStream_t s);
+// true if `warps` is a compiled backward block shape
+bool backward_shape_supported(int warps);
 
 // Deterministic per-key reduction of cluster gradients (key_reduce.cu).
 size_t key_sort_scratch_bytes(int64_t n_hits);

@@ -17,9 +17,8 @@
 
 namespace tpcfit {
 
-bool backward_shape_supported(int scheme, int warps) {
-  return (scheme == 0 && (warps == 4 || warps == 8 || warps == 12 || warps == 16 || warps == 24)) ||
-         (scheme == 1 && warps == 7);
+bool backward_shape_supported(int warps) {
+  return warps == 4 || warps == 8 || warps == 12 || warps == 16 || warps == 24;
 }
 
 bool fit_shape_supported(int lanes_per_track, int rows_per_stage, int warps) {
@@ -127,7 +126,6 @@ struct tpcfit_handle {
   size_t stage_cap = 0;
   // adjoint: checkpoints of the last recorded fit
   int record = 0;
-  int bwd_scheme = 0;
   int bwd_warps = 12;
   float* d_ck = nullptr;
   int64_t ck_cap = 0;          // floats
@@ -408,9 +406,8 @@ tpcfit_status tpcfit_fit_frames(tpcfit_handle* h, const tpcfit_hits* hits, const
   return from_cuda(e);
 }
 
-tpcfit_status tpcfit_set_backward_config(tpcfit_handle* h, int scheme, int warps_per_block) {
-  if (!h || !backward_shape_supported(scheme, warps_per_block)) return TPCFIT_EINVAL;
-  h->bwd_scheme = scheme;
+tpcfit_status tpcfit_set_backward_config(tpcfit_handle* h, int warps_per_block) {
+  if (!h || !backward_shape_supported(warps_per_block)) return TPCFIT_EINVAL;
   h->bwd_warps = warps_per_block;
   return TPCFIT_OK;
 }
@@ -460,7 +457,7 @@ tpcfit_status tpcfit_fit_backward(tpcfit_handle* h, const tpcfit_hits* hits, con
     b.grad_meas = grad_meas;
     b.grad_align_atomic = grad_align;
     e = cudaMemsetAsync(grad_align, 0, sizeof(float) * kAlignFloats, s);
-    if (e == cudaSuccess) e = launch_backward_fast(b, h->bwd_scheme, h->bwd_warps, s);
+    if (e == cudaSuccess) e = launch_backward_fast(b, h->bwd_warps, s);
     return from_cuda(e);
   }
   // deterministic: per-cluster gradients, then a stable key sort and
@@ -482,7 +479,7 @@ tpcfit_status tpcfit_fit_backward(tpcfit_handle* h, const tpcfit_hits* hits, con
   }
   b.grad_meas = gm;
   b.grad_align_atomic = nullptr;
-  e = launch_backward_det(b, h->bwd_scheme, h->bwd_warps, s);
+  e = launch_backward_det(b, h->bwd_warps, s);
   int* sorted = nullptr;
   int* key_start = nullptr;
   if (e == cudaSuccess) e = launch_key_sort(hits->rowsec, hits->n_hits, h->geo.n_rows, h->d_keys, &sorted, &key_start, s);

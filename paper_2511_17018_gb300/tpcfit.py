@@ -58,7 +58,7 @@ def load():
         "tpcfit_fit_noalloc": (C.c_int, [C.POINTER(_Geometry), C.c_double, vp, C.c_int, C.POINTER(_Hits), vp, i32, vp,
                                          vp, vp, vp, vp, vp]),
         "tpcfit_set_record": (C.c_int, [vp, C.c_int]),
-        "tpcfit_set_backward_config": (C.c_int, [vp, C.c_int, C.c_int]),
+        "tpcfit_set_backward_config": (C.c_int, [vp, C.c_int]),
         "tpcfit_fit_frames": (C.c_int, [vp, C.POINTER(_Hits), vp, i32, vp, i32, vp, vp, i64, vp, vp, vp, vp, vp,
                                         vp]),
         "tpcfit_fit_backward": (C.c_int, [vp, C.POINTER(_Hits), vp, i32, vp, vp, vp, vp, vp, vp]),
@@ -180,8 +180,8 @@ def tpcfit_fit_frames(h, y, z, rowsec, offsets, frame_base, seeds, params, cov, 
     _check(st, "tpcfit_fit_frames")
 
 
-def tpcfit_set_backward_config(h, scheme: int = 0, warps_per_block: int = 12) -> None:
-    _check(load().tpcfit_set_backward_config(h, int(scheme), int(warps_per_block)), "tpcfit_set_backward_config")
+def tpcfit_set_backward_config(h, warps_per_block: int = 12) -> None:
+    _check(load().tpcfit_set_backward_config(h, int(warps_per_block)), "tpcfit_set_backward_config")
 
 
 def tpcfit_set_record(h, record: bool) -> None:
@@ -317,8 +317,8 @@ class Fitter:
     def status(self, stream=None):
         return tpcfit_get_status(self.h, stream)
 
-    def set_backward_config(self, scheme: int = 0, warps_per_block: int = 12):
-        tpcfit_set_backward_config(self.h, scheme, warps_per_block)
+    def set_backward_config(self, warps_per_block: int = 12):
+        tpcfit_set_backward_config(self.h, warps_per_block)
 
     def set_record(self, record: bool):
         tpcfit_set_record(self.h, record)

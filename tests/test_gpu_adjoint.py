@@ -32,11 +32,11 @@ def case():
     return fr, d_true, w, ref
 
 
-def _gpu_grad(fr, d_true, w, det, rps=4, warps=24, srt=True, bwd=(0, 12)):
+def _gpu_grad(fr, d_true, w, det, rps=4, warps=24, srt=True, bwd=12):
     dev = tf.frame_to_device(fr)
     f = tf.Fitter(fr.geometry, fr.bz, deterministic=det, rows_per_stage=rps, warps_per_block=warps,
                   sort_by_length=srt)
-    f.set_backward_config(*bwd)
+    f.set_backward_config(bwd)
     try:
         f.set_alignment(torch.from_numpy(d_true).cuda())
         f.set_record(True)
@@ -63,8 +63,7 @@ def test_adjoint_matches_forward_mode_oracle(case, det):
 def test_deterministic_adjoint_is_bitwise_reproducible(case):
     fr, d_true, w, _ = case
     base = _gpu_grad(fr, d_true, w, True)
-    for rps, warps, srt, bwd in ((4, 24, True, (0, 8)), (8, 8, False, (0, 4)), (16, 8, True, (1, 7)),
-                                 (4, 24, True, (0, 16)), (4, 12, True, (0, 24))):
+    for rps, warps, srt, bwd in ((4, 24, True, 8), (8, 8, False, 4), (16, 8, True, 16), (4, 12, True, 24)):
         got = _gpu_grad(fr, d_true, w, True, rps, warps, srt, bwd)
         for a, b in zip(got[:3], base[:3]):
             assert np.array_equal(a.view(np.int32), b.view(np.int32)), (rps, warps, srt, bwd)
