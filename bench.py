@@ -354,6 +354,7 @@ def main():
     ap.add_argument("--align-iters", type=int, default=50)
     ap.add_argument("--tracks", type=int, default=N_TRACKS,
                     help="batch size override (profiling of smaller cases only; the bench value uses the default)")
+    ap.add_argument("--bwd-warps", type=int, default=None, help="adjoint warps per block (library default if unset)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -378,6 +379,8 @@ def main():
     lengths = fr.lengths()
     dev = tf.frame_to_device(fr)
     fitter = tf.Fitter(fr.geometry, fr.bz, deterministic=(args.mode == "det"))
+    if args.bwd_warps:
+        fitter.set_backward_config(args.bwd_warps)
     tf.tpcfit_reserve(fitter.h, fr.n_tracks, fr.n_hits)
     out = tf.empty_outputs(fr.n_tracks)
     g_chi2 = torch.full((fr.n_tracks,), 1.0 / fr.n_tracks, dtype=torch.float32, device="cuda")

@@ -161,10 +161,11 @@ tpcfit_status tpcfit_fit_frames(tpcfit_handle* h, const tpcfit_hits* hits, const
  * recording. */
 tpcfit_status tpcfit_set_record(tpcfit_handle* h, int record);
 
-/* Launch configuration of the adjoint: warps per block (4, 8, 12, 16 or 24;
- * default 12).  The states between two checkpoints live in per-thread local
- * memory, so fewer warps leave more L1 per warp and more warps hide more
- * latency.  Results do not depend on it.  EINVAL for other values. */
+/* Launch configuration of the adjoint: warps per block (4, 8 or 12; default
+ * 8).  Each resident warp owns a segment store in device memory (the handle
+ * allocates it on the first backward) and 12 KB of shared memory that holds the
+ * states it copies ahead.  Results do not depend on it.  EINVAL for other
+ * values. */
 tpcfit_status tpcfit_set_backward_config(tpcfit_handle* h, int warps_per_block);
 
 /* Adjoint of the recorded fit: gradients of L = sum_i grad_chi2[i] * chi2_i.
@@ -177,8 +178,9 @@ tpcfit_status tpcfit_set_backward_config(tpcfit_handle* h, int warps_per_block);
  *   grad_align: float [36][152][2], dL/d(dy, dz) of the alignment offsets;
  *   grad_seeds: float [5][n_tracks], dL/dseed;
  *   grad_meas:  float [n_hits][2], dL/d(measured y, z) per cluster, or NULL.
- * The backward recomputes each 16-step segment from its checkpoint and runs the
- * hand-written reverse of every step.  Fast mode accumulates grad_align with
+ * The backward recomputes each 16-step segment from its checkpoint into a
+ * per-warp segment store and runs the hand-written reverse of every step,
+ * copying the state before each step into shared memory one step ahead.  Fast mode accumulates grad_align with
  * atomics; deterministic mode writes per-cluster gradients, sorts the clusters
  * by (sector, row) with a stable radix sort and sums each key in a fixed order,
  * so grad_align is bitwise reproducible.  Tracks with ndf <= 0 contribute 0. */

@@ -9,18 +9,16 @@
 // state (the covariance is reset, the outward chi2 is not part of L).
 //
 // Checkpoints: the forward writes the filter state (p, L, x, sector, chi2)
-// before every 16th step of each pass.  The backward walks the segments of a
-// track in reverse: it recomputes a segment's steps from its checkpoint into
-// a per-thread state array, then reverses the steps one by one (recomputing
-// each step's intermediates from the state before it).  States carry y and z
+// before every kCkptEvery-th step of each pass.  The backward walks the
+// segments of a track in reverse: it recomputes a segment's steps from its
+// checkpoint into a per-warp segment store, then reverses the steps one by one
+// (recomputing each step's intermediates from the state before it).  States carry y and z
 // as residuals from the current cluster's measurement, like the fit.
 #pragma once
 
 namespace tpcfit {
 namespace TPCFIT_NS {
 
-constexpr int kCkptEvery = 16;
-constexpr int kCkptFloats = 36;  // p 5, L 25, x, sector (bits), chi2, 3 pad
 
 struct JacBar {
   float yy, ys, yq, zy, zs, zt, zq, sy, ss, sq;
@@ -355,14 +353,123 @@ __device__ __forceinline__ void load_ckpt(const float* src, StepState& S) {
   S.sec = __float_as_int(v[31]);
 }
 
-// One cluster of a pass: measurement (alignment subtracted), row, sector.
-__device__ __forceinline__ void read_hit(const BwdArgs& a, int h, float& m0, float& m1, int& row, int& sec) {
-  const int rsv = (int)__ldg(a.rowsec + h);
-  row = rsv >> 6;
-  sec = rsv & 63;
-  const float2 d = __ldg(reinterpret_cast<const float2*>(a.align) + (sec * kMaxRows + row));
-  m0 = __ldg(a.y + h) - d.x;
-  m1 = __ldg(a.z + h) - d.y;
+// One cluster as stored (y, z, packed row/sector), loaded ahead of its use.
+struct HitRaw {
+  float y, z;
+  int rs;
+};
+
+__device__ __forceinline__ HitRaw load_hit(const BwdArgs& a, int h) {
+  HitRaw r;
+  r.y = __ldg(a.y + h);
+  r.z = __ldg(a.z + h);
+  r.rs = (int)__ldg(a.rowsec + h);
+  return r;
+}
+
+// Measurement (alignment subtracted), row and sector of a loaded cluster.  Row
+// and sector are clamped into the table: the recorded fit has validated them,
+// the clamp only keeps a mismatched call inside shared memory.
+__device__ __forceinline__ void decode_hit(const float* align, const HitRaw& r, float& m0, float& m1, int& row,
+                                           int& sec) {
+  row = min(r.rs >> 6, kMaxRows - 1);
+  sec = min(r.rs & 63, kNSectors - 1);
+  const float2 d = reinterpret_cast<const float2*>(align)[sec * kMaxRows + row];
+  m0 = r.y - d.x;
+  m1 = r.z - d.y;
+}
+
+// States between checkpoints: 8 float4 (p 5, L 25, x, sector bits), stored
+// lane-interleaved ([float4 j][lane]) so that a warp's stores and copies coalesce.
+constexpr int kStateF4 = 8;
+
+__device__ __forceinline__ void pack_state(const StepState& S, float v[32]) {
+#pragma unroll
+  for (int c = 0; c < 5; ++c) v[c] = S.p[c];
+#pragma unroll
+  for (int i = 0; i < 5; ++i)
+#pragma unroll
+    for (int c = 0; c < 5; ++c) v[5 + 5 * i + c] = S.L[i][c];
+  v[30] = S.x;
+  v[31] = __int_as_float(S.sec);
+}
+
+__device__ __forceinline__ void unpack_state(const float v[32], StepState& S) {
+#pragma unroll
+  for (int c = 0; c < 5; ++c) S.p[c] = v[c];
+#pragma unroll
+  for (int i = 0; i < 5; ++i)
+#pragma unroll
+    for (int c = 0; c < 5; ++c) S.L[i][c] = v[5 + 5 * i + c];
+  S.x = v[30];
+  S.sec = __float_as_int(v[31]);
+}
+
+// dst[j * kWarp] = float4 j of the state (dst already offset by the lane).
+__device__ __forceinline__ void store_state(float4* dst, const StepState& S) {
+  float v[32];
+  pack_state(S, v);
+#pragma unroll
+  for (int j = 0; j < kStateF4; ++j) dst[j * kWarp] = make_float4(v[4 * j], v[4 * j + 1], v[4 * j + 2], v[4 * j + 3]);
+}
+
+// The same read, but never merged with an earlier one: the state is read again
+// from shared memory where it is needed instead of being kept in registers.
+__device__ __forceinline__ float4 lds_volatile(const float4* p) {
+  float4 r;
+  asm volatile("ld.volatile.shared.v4.f32 {%0, %1, %2, %3}, [%4];\n"
+               : "=f"(r.x), "=f"(r.y), "=f"(r.z), "=f"(r.w)
+               : "r"((unsigned)__cvta_generic_to_shared(p)));
+  return r;
+}
+
+__device__ __forceinline__ void reread_state(const float4* src, StepState& S) {
+  float v[32];
+#pragma unroll
+  for (int j = 0; j < kStateF4; ++j) {
+    const float4 f = lds_volatile(src + j * kWarp);
+    v[4 * j] = f.x;
+    v[4 * j + 1] = f.y;
+    v[4 * j + 2] = f.z;
+    v[4 * j + 3] = f.w;
+  }
+  unpack_state(v, S);
+}
+
+__device__ __forceinline__ void read_state(const float4* src, StepState& S) {
+  float v[32];
+#pragma unroll
+  for (int j = 0; j < kStateF4; ++j) {
+    const float4 f = src[j * kWarp];
+    v[4 * j] = f.x;
+    v[4 * j + 1] = f.y;
+    v[4 * j + 2] = f.z;
+    v[4 * j + 3] = f.w;
+  }
+  unpack_state(v, S);
+}
+
+// Asynchronous 16-byte global -> shared copies (L2 only, no L1 allocation).
+__device__ __forceinline__ void cp_async16(void* smem_dst, const void* gmem_src) {
+  const unsigned d = (unsigned)__cvta_generic_to_shared(smem_dst);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(d), "l"(gmem_src) : "memory");
+}
+
+// One lane's state: 8 float4 from a lane-interleaved global slot into its
+// lane-interleaved shared slot, as one commit group.
+__device__ __forceinline__ void fetch_state(float4* sdst, const float4* gsrc) {
+#pragma unroll
+  for (int j = 0; j < kStateF4; ++j) cp_async16(sdst + j * kWarp, gsrc + j * kWarp);
+  cp_async_commit();
+}
+
+// A checkpoint (36 contiguous floats, 16-byte aligned; its first 32 are the
+// state) into a lane-interleaved shared slot, as one commit group.
+__device__ __forceinline__ void fetch_ckpt(float4* sdst, const float* ck) {
+  const float4* g = reinterpret_cast<const float4*>(ck);
+#pragma unroll
+  for (int j = 0; j < kStateF4; ++j) cp_async16(sdst + j * kWarp, g + j);
+  cp_async_commit();
 }
 
 // Forward of one step on a StepState (the same operations as the fit, in
@@ -396,13 +503,17 @@ __device__ __forceinline__ void step_fwd(const SmemTables& T, StepState& S, floa
   scalar_update<1>(S.p, S.L, chi2, 0.0f);
 }
 
-// Reverse of one step from the state before it (my_prev, mz_prev: measurement
-// of the previous cluster).  b_p, b_L: in = adjoint after the step, out =
-// adjoint before it.  The measurements enter only through the residual
-// shifts: b_mc = adjoint of this cluster's (y, z), b_mp = of the previous one's.
-__device__ __forceinline__ void step_rev(const SmemTables& T, const StepState& S0, float my_prev, float mz_prev,
+// Reverse of one step from the state before it, which sits in shared memory
+// at src ([float4 j][lane]; read twice so that it need not stay in registers
+// through the update reverses).  my_prev, mz_prev: measurement of the previous
+// cluster.  b_p, b_L: in = adjoint after the step, out = adjoint before it.
+// The measurements enter only through the residual shifts: b_mc = adjoint of
+// this cluster's (y, z), b_mp = of the previous one's.
+__device__ __forceinline__ void step_rev(const SmemTables& T, const float4* src, float my_prev, float mz_prev,
                                          bool first, bool conv, int row, int sec18, float m0, float m1, float b_p[5],
                                          float b_L[5][5], float b_chi, float b_mc[2], float b_mp[2]) {
+  StepState S0;
+  read_state(src, S0);
   float p1[5];
   Jac J;
   float L[5][5];
@@ -445,6 +556,7 @@ __device__ __forceinline__ void step_rev(const SmemTables& T, const StepState& S
     if (!conv) b_mc[0] = b_mc[1] = 0.0f;  // the inward pass starts from residuals already
     return;
   }
+  reread_state(src, S0);
   JacBar bJ;
   transport_rev(S0.L, J, b_L, bJ);
   const bool rot = S0.sec != sec18;
@@ -471,6 +583,11 @@ __device__ __forceinline__ void step_rev(const SmemTables& T, const StepState& S
   for (int c = 0; c < 5; ++c) b_p[c] = b_pi[c];
 }
 
+// Fire-and-forget global float add (no value returned, nothing to wait for).
+__device__ __forceinline__ void red_add(float* p, float v) {
+  asm volatile("red.global.add.f32 [%0], %1;\n" ::"l"(__cvta_generic_to_global(p)), "f"(v) : "memory");
+}
+
 __device__ __forceinline__ void accumulate_meas_grad(const BwdArgs& a, int pass, int h, int row, int sec, float g0,
                                                      float g1) {
   if (a.grad_meas) {
@@ -484,24 +601,49 @@ __device__ __forceinline__ void accumulate_meas_grad(const BwdArgs& a, int pass,
   }
   if (a.grad_align_atomic) {
     float* dst = a.grad_align_atomic + (sec * kMaxRows + row) * 2;
-    atomicAdd(dst, -g0);
-    atomicAdd(dst + 1, -g1);
+    red_add(dst, -g0);
+    red_add(dst + 1, -g1);
   }
 }
 
-// Per track, per pass (inward reversed first): for every 16-step segment, from
-// its checkpoint, recompute the segment keeping the state before each step in
-// a per-thread array (local memory), then reverse the steps.
+// Shared memory of a backward block: geometry tables, the alignment table
+// and, per warp, a double buffer for the state before the step being reversed
+// and a buffer for the next segment's checkpoint (all [float4 j][lane]).
+struct BwdSmem {
+  SmemTables T;
+  float align[kAlignFloats];
+};
+struct BwdWarpBufs {
+  float4 st[2][kStateF4][kWarp];
+  float4 ck[kStateF4][kWarp];
+};
+
+template <int WARPS>
+constexpr size_t backward_smem_bytes() {
+  return sizeof(BwdSmem) + WARPS * sizeof(BwdWarpBufs);
+}
+
+// Per track, per pass (inward reversed first), segment by segment from the
+// last: recompute the segment from its checkpoint, storing the state before
+// each step in the warp's global segment store; then reverse the steps, last
+// first, each state copied into shared memory asynchronously one step ahead.
+// Clusters are loaded one step ahead as well; the next segment's checkpoint
+// is copied while the current segment is reversed.
 template <int WARPS>
 __global__ void __launch_bounds__(WARPS * 32, 1) backward_kernel(BwdArgs a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  SmemTables& T = *reinterpret_cast<SmemTables*>(smem_raw);
-  load_tables(T);
+  BwdSmem& B = *reinterpret_cast<BwdSmem*>(smem_raw);
+  load_tables(B.T);
+  for (int i = threadIdx.x; i < kAlignFloats; i += blockDim.x) B.align[i] = __ldg(a.align + i);
   __syncthreads();
+  const SmemTables& T = B.T;
   const int lane = threadIdx.x & 31;
+  const int warp = threadIdx.x >> 5;
+  BwdWarpBufs& W = reinterpret_cast<BwdWarpBufs*>(smem_raw + sizeof(BwdSmem))[warp];
+  // this warp's segment store: [step kk][float4 j][lane]
+  float4* const gs = a.seg + ((int64_t)blockIdx.x * WARPS + warp) * (kCkptEvery * kStateF4 * kWarp) + lane;
   const int64_t n_chunks = ((int64_t)a.n_tracks + kWarp - 1) / kWarp;
   const int64_t N = a.n_tracks;
-  StepState seg[kCkptEvery];
 #pragma unroll 1
   for (;;) {
     int64_t chunk = 0;
@@ -527,44 +669,66 @@ __global__ void __launch_bounds__(WARPS * 32, 1) backward_kernel(BwdArgs a) {
         const float b_chi = pass == 1 ? g : 0.0f;
         const int steps = last + 1;
         const int nseg = (steps + kCkptEvery - 1) / kCkptEvery;
-        const float* ckp = a.ck + ((int64_t)pass * a.ck_slots + (begin >> 4) + trk) * kCkptFloats;
+        // hit index of step i of this pass
+        const int h0 = pass == 0 ? begin : begin + last;
+        const int hd = pass == 0 ? 1 : -1;
+        const float* ckp = a.ck + ((int64_t)pass * a.ck_slots + (begin >> kCkptShift) + trk) * kCkptFloats;
         float pend0 = 0.0f, pend1 = 0.0f;  // gradient owed to the measurement of the step before
+        fetch_ckpt(&W.ck[0][lane], ckp + (int64_t)(nseg - 1) * kCkptFloats);
 #pragma unroll 1
         for (int s = nseg - 1; s >= 0; --s) {
-          StepState S;
-          load_ckpt(ckp + (int64_t)s * kCkptFloats, S);
           const int i0 = s * kCkptEvery;
           const int cnt = min(kCkptEvery, steps - i0);
+          StepState S;
           float my = 0.0f, mz = 0.0f;
+          HitRaw nx = load_hit(a, h0 + hd * i0);
           if (i0 > 0) {
             int row, sec;
-            read_hit(a, pass == 0 ? begin + i0 - 1 : begin + last - (i0 - 1), my, mz, row, sec);
+            decode_hit(B.align, load_hit(a, h0 + hd * (i0 - 1)), my, mz, row, sec);
           }
+          cp_async_wait<0>();
+          read_state(&W.ck[0][lane], S);
+          // level 1: the segment, storing the state before each step
+          float m0 = 0.0f, m1 = 0.0f;
+          int row = 0, sec = 0;
 #pragma unroll 1
           for (int kk = 0; kk < cnt; ++kk) {
             const int i = i0 + kk;
-            const int h = pass == 0 ? begin + i : begin + last - i;
-            float m0, m1;
-            int row, sec;
-            read_hit(a, h, m0, m1, row, sec);
-            seg[kk] = S;
+            const HitRaw cur = nx;
+            if (kk + 1 < cnt) nx = load_hit(a, h0 + hd * (i + 1));
+            decode_hit(B.align, cur, m0, m1, row, sec);
+            store_state(gs + kk * (kStateF4 * kWarp), S);
             step_fwd(T, S, my, mz, i == 0, pass == 0, row, sec % kNSide, m0, m1);
           }
-          // reverse; the previous cluster of a step is the current one of the next
-          // step reversed, so each cluster is read once here
-          float m0, m1;
-          int row, sec;
-          read_hit(a, pass == 0 ? begin + i0 + cnt - 1 : begin + last - (i0 + cnt - 1), m0, m1, row, sec);
+          // the states just stored are read back by this thread's copies below
+          __threadfence_block();
+          // the next segment's checkpoint travels while this one is reversed
+          if (s > 0) fetch_ckpt(&W.ck[0][lane], ckp + (int64_t)(s - 1) * kCkptFloats);
+          // reverse; (m0, m1, row, sec) hold the segment's last cluster, which is
+          // the current cluster of its last step; each step's previous cluster
+          // becomes the current one of the step before it
+          fetch_state(&W.st[(cnt - 1) & 1][0][lane], gs + (cnt - 1) * (kStateF4 * kWarp));
+          HitRaw pv{};
+          if (i0 + cnt - 1 > 0) pv = load_hit(a, h0 + hd * (i0 + cnt - 2));
 #pragma unroll 1
           for (int kk = cnt - 1; kk >= 0; --kk) {
             const int i = i0 + kk;
-            const int h = pass == 0 ? begin + i : begin + last - i;
+            const int h = h0 + hd * i;
+            if (kk > 0) {
+              fetch_state(&W.st[(kk - 1) & 1][0][lane], gs + (kk - 1) * (kStateF4 * kWarp));
+              cp_async_wait<1>();
+            } else {
+              cp_async_wait<0>();
+            }
             float mpy = 0.0f, mpz = 0.0f;
             int prow = 0, psec = 0;
-            if (i > 0) read_hit(a, pass == 0 ? h - 1 : h + 1, mpy, mpz, prow, psec);
+            if (i > 0) {
+              const HitRaw pc = pv;
+              if (i > 1) pv = load_hit(a, h - 2 * hd);
+              decode_hit(B.align, pc, mpy, mpz, prow, psec);
+            }
             float b_mc[2], b_mp[2];
-            step_rev(T, seg[kk], mpy, mpz, i == 0, pass == 0, row, sec % kNSide, m0, m1, b_p, b_L, b_chi, b_mc,
-                     b_mp);
+            step_rev(T, &W.st[kk & 1][0][lane], mpy, mpz, i == 0, pass == 0, row, sec % kNSide, m0, m1, b_p, b_L, b_chi, b_mc, b_mp);
             accumulate_meas_grad(a, pass, h, row, sec, b_mc[0] + pend0, b_mc[1] + pend1);
             pend0 = b_mp[0];
             pend1 = b_mp[1];
@@ -587,15 +751,14 @@ __global__ void __launch_bounds__(WARPS * 32, 1) backward_kernel(BwdArgs a) {
   }
 }
 
+// Persistent grid of the backward (blocks resident at once over all SMs).
 template <int WARPS>
-cudaError_t launch_backward_cfg(const BwdArgs& a, cudaStream_t s) {
-  constexpr int kThreads = WARPS * 32;
-  const size_t smem = sizeof(SmemTables);
-  static int grid = 0;
-  if (grid == 0) {
+cudaError_t backward_grid(int& grid) {
+  static int cached = 0;
+  if (cached == 0) {
+    constexpr int kThreads = WARPS * 32;
+    const size_t smem = backward_smem_bytes<WARPS>();
     cudaError_t e = cudaFuncSetAttribute(backward_kernel<WARPS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    // the states live in local memory: leave L1 as large as possible
-    if (e == cudaSuccess) e = cudaFuncSetAttribute(backward_kernel<WARPS>, cudaFuncAttributePreferredSharedMemoryCarveout, 0);
     if (e != cudaSuccess) return e;
     int dev = 0, sms = 0, per_sm = 0;
     e = cudaGetDevice(&dev);
@@ -603,15 +766,43 @@ cudaError_t launch_backward_cfg(const BwdArgs& a, cudaStream_t s) {
     if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, backward_kernel<WARPS>, kThreads, smem);
     if (e != cudaSuccess) return e;
     if (per_sm < 1) return cudaErrorInvalidConfiguration;
-    grid = sms * per_sm;
+    cached = sms * per_sm;
   }
+  grid = cached;
+  return cudaSuccess;
+}
+
+template <int WARPS>
+cudaError_t backward_store_cfg(int64_t& float4s) {
+  int grid = 0;
+  cudaError_t e = backward_grid<WARPS>(grid);
+  float4s = (int64_t)grid * WARPS * kCkptEvery * kStateF4 * kWarp;
+  return e;
+}
+
+template <int WARPS>
+cudaError_t launch_backward_cfg(const BwdArgs& a, cudaStream_t s) {
+  int grid = 0;
+  cudaError_t e = backward_grid<WARPS>(grid);
+  if (e != cudaSuccess) return e;
   const int64_t chunks = ((int64_t)a.n_tracks + kWarp - 1) / kWarp;
   const int64_t need = (chunks + WARPS - 1) / WARPS;
   const int blocks = (int)(need < grid ? need : grid);
-  cudaError_t e = cudaMemsetAsync(a.work, 0, sizeof(unsigned int), s);
+  e = cudaMemsetAsync(a.work, 0, sizeof(unsigned int), s);
   if (e != cudaSuccess) return e;
-  backward_kernel<WARPS><<<blocks, kThreads, smem, s>>>(a);
+  backward_kernel<WARPS><<<blocks, WARPS * 32, backward_smem_bytes<WARPS>(), s>>>(a);
   return cudaGetLastError();
+}
+
+// Segment store (float4 count) the backward needs for `warps` warps per block.
+inline cudaError_t backward_store(int warps, int64_t& float4s) {
+  switch (warps) {
+    case 4: return backward_store_cfg<4>(float4s);
+    case 8: return backward_store_cfg<8>(float4s);
+    case 10: return backward_store_cfg<10>(float4s);
+    case 12: return backward_store_cfg<12>(float4s);
+    default: return cudaErrorInvalidValue;
+  }
 }
 
 inline cudaError_t launch_backward(const BwdArgs& a, int warps, cudaStream_t s) {
@@ -619,9 +810,8 @@ inline cudaError_t launch_backward(const BwdArgs& a, int warps, cudaStream_t s) 
   switch (warps) {
     case 4: return launch_backward_cfg<4>(a, s);
     case 8: return launch_backward_cfg<8>(a, s);
+    case 10: return launch_backward_cfg<10>(a, s);
     case 12: return launch_backward_cfg<12>(a, s);
-    case 16: return launch_backward_cfg<16>(a, s);
-    case 24: return launch_backward_cfg<24>(a, s);
     default: return cudaErrorInvalidValue;
   }
 }

@@ -473,7 +473,7 @@ __device__ __forceinline__ bool step_predict(const SmemTables& T, const TrackSta
 
 __device__ __forceinline__ void write_ckpt(const FitArgs& a, int pass, int begin, int trk, int seg,
                                            const TrackState& S) {
-  float4* dst = reinterpret_cast<float4*>(a.ck + ((int64_t)pass * a.ck_slots + (begin >> 4) + trk + seg) * 36);
+  float4* dst = reinterpret_cast<float4*>(a.ck + ((int64_t)pass * a.ck_slots + (begin >> kCkptShift) + trk + seg) * kCkptFloats);
   float v[36];
 #pragma unroll
   for (int c = 0; c < 5; ++c) v[c] = S.p[c];
@@ -606,7 +606,7 @@ __global__ void __launch_bounds__(WARPS * 32, MINB) fit_kernel(FitArgs a) {
           const float m0 = st.y[buf][lane][k] - d.x;
           const float m1 = st.z[buf][lane][k] - d.y;
           const int sec18 = sec % kNSide;
-          if (RECORD && (i & 15) == 0) write_ckpt(a, pass, begin, trk, i >> 4, S);
+          if (RECORD && (i & (kCkptEvery - 1)) == 0) write_ckpt(a, pass, begin, trk, i >> kCkptShift, S);
           if (i == 0) {
             // first cluster of the pass: the state sits on its row already; the
             // outward pass turns the seed's (y, z) into residuals

@@ -14,6 +14,11 @@ constexpr int kNSide = 18;
 constexpr int kMaxRows = 152;
 constexpr int kAlignFloats = kNSectors * kMaxRows * 2;
 constexpr int kWarp = 32;
+// The adjoint's checkpoints: the filter state before every kCkptEvery-th step
+// of each pass, kCkptFloats floats each (p 5, L 25, x, sector bits, chi2, 3 pad).
+constexpr int kCkptShift = 4;
+constexpr int kCkptEvery = 1 << kCkptShift;
+constexpr int kCkptFloats = 36;
 
 // Per-time-frame constants of the fit, uploaded to the __constant__ bank of
 // every kernel module (each compilation unit has its own copy, Sec. 4.1).
@@ -48,9 +53,9 @@ struct FitArgs {
   unsigned long long* err;     // error word: code << 56 | track
   unsigned int* work;          // work-item counter (zeroed by the launcher)
   // checkpoint recording for the adjoint (null = off)
-  float* ck;                   // [2][ck_slots][36] filter state before every 16th step of each pass
+  float* ck;                   // [2][ck_slots][36] filter state before every kCkptEvery-th step of each pass
   int32_t* ck_last;            // [n_tracks] index of the last cluster of the outward pass
-  int64_t ck_slots;            // slots per pass: n_hits / 16 + n_tracks + 1
+  int64_t ck_slots;            // slots per pass: n_hits / kCkptEvery + n_tracks + 1
   // several time frames in one launch (frame_base = null: one frame)
   const int64_t* frame_base;   // [n_frames + 1] first track of each frame
   int32_t n_frames;
@@ -78,6 +83,7 @@ struct BwdArgs {
   float* grad_meas;            // [n_hits][2] dL/dm per cluster, or null
   float* grad_align_atomic;    // [36][152][2] accumulated with atomics, or null
   unsigned int* work;
+  float4* seg;                 // segment store: [resident warps][kCkptEvery][8][32] float4
 };
 
 // Error codes recorded in the device error word.
@@ -104,6 +110,9 @@ cudaError_t launch_fit_fast(const FitArgs& a, int lanes_per_track, int rows_per_
 cudaError_t launch_fit_det(const FitArgs& a, int lanes_per_track, int rows_per_stage, int warps, cudaStream_t s);
 cudaError_t launch_backward_fast(const BwdArgs& a, int warps, cudaStream_t s);
 cudaError_t launch_backward_det(const BwdArgs& a, int warps, cudaStream_t s);
+// float4 elements of the segment store a backward launch with `warps` needs
+cudaError_t backward_store_fast(int warps, int64_t& float4s);
+cudaError_t backward_store_det(int warps, int64_t& float4s);
 // true if `warps` is a compiled backward block shape
 bool backward_shape_supported(int warps);
 

@@ -17,9 +17,7 @@
 
 namespace tpcfit {
 
-bool backward_shape_supported(int warps) {
-  return warps == 4 || warps == 8 || warps == 12 || warps == 16 || warps == 24;
-}
+bool backward_shape_supported(int warps) { return warps == 4 || warps == 8 || warps == 10 || warps == 12; }
 
 bool fit_shape_supported(int lanes_per_track, int rows_per_stage, int warps) {
   if (lanes_per_track != 1) return false;
@@ -126,7 +124,7 @@ struct tpcfit_handle {
   size_t stage_cap = 0;
   // adjoint: checkpoints of the last recorded fit
   int record = 0;
-  int bwd_warps = 12;
+  int bwd_warps = 8;
   float* d_ck = nullptr;
   int64_t ck_cap = 0;          // floats
   int32_t* d_ck_last = nullptr;
@@ -136,6 +134,8 @@ struct tpcfit_handle {
   int64_t rec_tracks = 0, rec_hits = 0;
   int rec_det = 0;
   // adjoint scratch: per-cluster gradients and the key sort
+  float4* d_seg = nullptr;     // the backward's segment store
+  int64_t seg_cap = 0;         // float4 elements
   float* d_gm = nullptr;
   int64_t gm_cap = 0;          // floats
   unsigned char* d_keys = nullptr;
@@ -250,6 +250,7 @@ void tpcfit_destroy(tpcfit_handle* h) {
   if (h->d_ck) cudaFree(h->d_ck);
   if (h->d_ck_last) cudaFree(h->d_ck_last);
   if (h->d_gm) cudaFree(h->d_gm);
+  if (h->d_seg) cudaFree(h->d_seg);
   if (h->d_keys) cudaFree(h->d_keys);
   if (h->d_frame_scratch) cudaFree(h->d_frame_scratch);
   {
@@ -324,8 +325,8 @@ tpcfit_status tpcfit_fit(tpcfit_handle* h, const tpcfit_hits* hits, const int32_
   a.work = h->d_work;
   h->rec_valid = false;
   if (h->record) {
-    const int64_t slots = hits->n_hits / 16 + (int64_t)n_tracks + 1;
-    st = grow(h->d_ck, h->ck_cap, 2 * slots * 36);
+    const int64_t slots = hits->n_hits / kCkptEvery + (int64_t)n_tracks + 1;
+    st = grow(h->d_ck, h->ck_cap, 2 * slots * kCkptFloats);
     if (st == TPCFIT_OK) st = grow(h->d_ck_last, h->ck_last_cap, (int64_t)n_tracks);
     if (st != TPCFIT_OK) return st;
     a.ck = h->d_ck;
@@ -452,6 +453,14 @@ tpcfit_status tpcfit_fit_backward(tpcfit_handle* h, const tpcfit_hits* hits, con
   b.grad_seeds = grad_seeds;
   b.work = h->d_work;
   cudaError_t e = cudaSuccess;
+  {
+    int64_t need = 0;
+    e = h->deterministic ? backward_store_det(h->bwd_warps, need) : backward_store_fast(h->bwd_warps, need);
+    if (e != cudaSuccess) return from_cuda(e);
+    st = grow(h->d_seg, h->seg_cap, need);
+    if (st != TPCFIT_OK) return st;
+    b.seg = h->d_seg;
+  }
   if (!h->deterministic) {
     // fast: atomics straight into the alignment gradient
     b.grad_meas = grad_meas;

@@ -180,7 +180,7 @@ def tpcfit_fit_frames(h, y, z, rowsec, offsets, frame_base, seeds, params, cov, 
     _check(st, "tpcfit_fit_frames")
 
 
-def tpcfit_set_backward_config(h, warps_per_block: int = 12) -> None:
+def tpcfit_set_backward_config(h, warps_per_block: int = 8) -> None:
     _check(load().tpcfit_set_backward_config(h, int(warps_per_block)), "tpcfit_set_backward_config")
 
 
@@ -317,7 +317,7 @@ class Fitter:
     def status(self, stream=None):
         return tpcfit_get_status(self.h, stream)
 
-    def set_backward_config(self, warps_per_block: int = 12):
+    def set_backward_config(self, warps_per_block: int = 8):
         tpcfit_set_backward_config(self.h, warps_per_block)
 
     def set_record(self, record: bool):
