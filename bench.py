@@ -448,6 +448,23 @@ def main():
     plain_total, plain_per = timed(step_fit, plain_steps)
     plain_ms = statistics.mean(p[0] for p in plain_per)
 
+    # ---- the same plain fit with the kernel compiled at run time for this
+    # frame's constants (Sec. 5); the first call compiles and loads it
+    rtc = None
+    if tf.tpcfit_rtc_available():
+        fitter.set_rtc(True)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        fitter.fit(dev, out)
+        torch.cuda.synchronize()
+        first_s = time.perf_counter() - t0
+        for _ in range(args.warmup):
+            fitter.fit(dev, out)
+        torch.cuda.synchronize()
+        _, rtc_per = timed(step_fit, plain_steps)
+        rtc = {"ms": statistics.mean(p[0] for p in rtc_per), "first_call_s": first_s}
+        fitter.set_rtc(False)
+
     # ---- end to end through the public API with host buffers
     h2d = 10 * fr.n_hits + 4 * (fr.n_tracks + 1) + 20 * fr.n_tracks
     d2h = 88 * fr.n_tracks
@@ -508,6 +525,11 @@ def main():
         "gpu_launches": 4 * args.steps,
         "clocks": clocks,
     }
+    if rtc is not None:
+        rtc_tf = fit_fl / (rtc["ms"] / 1e3) / 1e12
+        line["plain_fit"]["rtc"] = {"tracks_per_s": fr.n_tracks / (rtc["ms"] / 1e3), "ms": rtc["ms"],
+                                    "frac": rtc_tf / peak_tf, "first_call_s": rtc["first_call_s"],
+                                    "kernel": "fit_kernel<4,24> compiled with NVRTC for this frame's constants"}
     if not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(fr)
     fitter.close()

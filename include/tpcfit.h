@@ -46,7 +46,8 @@ typedef enum {
   TPCFIT_ENOMEM = 3,   /* device allocation failed */
   TPCFIT_EDEVICE = 4,  /* a kernel found invalid input (see tpcfit_get_status) */
   TPCFIT_ETIMEOUT = 5, /* a bounded device-side wait ran out */
-  TPCFIT_ESTATE = 6    /* call not allowed in the handle's current state */
+  TPCFIT_ESTATE = 6,   /* call not allowed in the handle's current state */
+  TPCFIT_ERTC = 7      /* run-time compilation unavailable or failed (see tpcfit_rtc_log) */
 } tpcfit_status;
 
 /* Detector geometry (copied at tpcfit_create; row_x is a host array). */
@@ -153,6 +154,36 @@ tpcfit_status tpcfit_fit_frames(tpcfit_handle* h, const tpcfit_hits* hits, const
                                 const float* frame_alignment, const int32_t* frame_ready, int64_t wait_timeout_ns,
                                 const float* seeds, float* params_out, float* cov_out, float* chi2_out,
                                 int32_t* ndf_out, void* stream);
+
+/* Run-time compilation of the fit (Sec. 5).  enable = 1: tpcfit_fit and
+ * tpcfit_fit_frames run a fit kernel compiled with NVRTC for this handle's
+ * geometry, field, mode and launch shape, in which those per-time-frame values
+ * are compile-time constants.  Each variant (constants, mode, shape, recording,
+ * batched frames) is compiled on its first use, which takes about a second,
+ * and kept for the life of the process; with cache_dir (NULL: none) its CUBIN
+ * is also kept in that directory for later processes.  The first fit of a
+ * variant therefore belongs outside stream capture.  The device code is the
+ * one compiled ahead of time, with the same flags: deterministic results are
+ * bit-identical to the ahead-of-time kernels, fast-mode results are within the
+ * fast-mode tolerance.  enable = 0 (default): ahead-of-time kernels.  ERTC if
+ * NVRTC cannot be loaded; a failed compilation or load reports ERTC / ECUDA
+ * from the fit. */
+tpcfit_status tpcfit_set_rtc(tpcfit_handle* h, int enable, const char* cache_dir);
+
+/* Compile one fit variant with NVRTC and store its CUBIN in cache_dir (NULL:
+ * compile only), without a device: fills the cache before a run.  Arguments as
+ * for tpcfit_create, tpcfit_set_mode, tpcfit_set_config and tpcfit_set_record;
+ * frames != 0 for the batched-frame variant.  EINVAL for an invalid geometry
+ * or shape, ERTC if NVRTC is missing or the compilation fails. */
+tpcfit_status tpcfit_rtc_build(const tpcfit_geometry* geometry, double bz_tesla, int deterministic, int rows_per_stage,
+                               int warps_per_block, int record, int frames, const char* cache_dir);
+
+/* 1 if NVRTC can be loaded in this process. */
+int tpcfit_rtc_available(void);
+/* NVRTC compilations this process has run (cache hits do not count). */
+long long tpcfit_rtc_compile_count(void);
+/* Log of the last NVRTC compilation (empty if none); valid until the next one. */
+const char* tpcfit_rtc_log(void);
 
 /* Record checkpoints for the adjoint (record = 1) or not (0, default).  With
  * recording on, tpcfit_fit also stores the filter state before every 16th step

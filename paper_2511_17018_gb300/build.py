@@ -29,12 +29,38 @@ DET = ["-fmad=false", "-prec-div=true", "-prec-sqrt=true", "-ftz=false"]
 
 UNITS = {
     "tpcfit_host.cpp": [],
+    "rtc.cpp": [],
     "fit_fast.cu": FAST,
     "fit_det.cu": DET,
     "length_order.cu": [],
     "tpcfit_noalloc.cu": [],
     "key_reduce.cu": [],
 }
+
+
+# Device sources the library carries for run-time compilation (Sec. 5).
+RTC_SOURCES = ("kernel_abi.h", "device_util.cuh", "fit_core.cuh")
+RTC_EMBED = os.path.join(BUILD, "rtc_sources.cpp")
+
+
+def write_rtc_embed() -> str:
+    """The device sources as string constants (kRtcSources), for NVRTC."""
+    delim = "TPCFIT_SRC"
+    parts = ["// Generated by build.py: device sources embedded for run-time compilation.",
+             "namespace tpcfit {", f"extern const int kRtcSourceCount = {len(RTC_SOURCES)};",
+             "extern const char* const kRtcSourceNames[] = {" + ", ".join(f'"{n}"' for n in RTC_SOURCES) + "};",
+             "extern const char* const kRtcSources[] = {"]
+    for n in RTC_SOURCES:
+        with open(os.path.join(CSRC, n)) as f:
+            text = f.read()
+        assert f"){delim}\"" not in text
+        parts.append(f'R"{delim}({text}){delim}",')
+    parts += ["};", "}  // namespace tpcfit", ""]
+    body = "\n".join(parts)
+    if not os.path.exists(RTC_EMBED) or open(RTC_EMBED).read() != body:
+        with open(RTC_EMBED, "w") as f:
+            f.write(body)
+    return RTC_EMBED
 
 
 def nvcc() -> str:
@@ -56,8 +82,8 @@ def up_to_date() -> bool:
 
 
 def _compile(unit: str, extra, verbose_ptxas: bool):
-    src = os.path.join(CSRC, unit)
-    obj = os.path.join(BUILD, unit + ".o")
+    src = unit if os.path.isabs(unit) else os.path.join(CSRC, unit)
+    obj = os.path.join(BUILD, os.path.basename(unit) + ".o")
     lang = ["-x", "cu"] if unit.endswith(".cu") else []
     cmd = [nvcc(), *ARCH, *COMMON, *extra, *lang, "-c", src, "-o", obj]
     if verbose_ptxas and unit.endswith(".cu"):
@@ -72,8 +98,10 @@ def build(force: bool = False, verbose_ptxas: bool = False) -> str:
     if not force and up_to_date():
         return LIB
     os.makedirs(BUILD, exist_ok=True)
-    with cf.ThreadPoolExecutor(max_workers=len(UNITS)) as ex:
-        futs = [ex.submit(_compile, u, f, verbose_ptxas) for u, f in UNITS.items()]
+    units = dict(UNITS)
+    units[write_rtc_embed()] = []
+    with cf.ThreadPoolExecutor(max_workers=len(units)) as ex:
+        futs = [ex.submit(_compile, u, f, verbose_ptxas) for u, f in units.items()]
         results = [f.result() for f in futs]
     if verbose_ptxas:
         for _, log in results:
@@ -82,7 +110,7 @@ def build(force: bool = False, verbose_ptxas: bool = False) -> str:
     objs = [o for o, _ in results]
     tmp = LIB + ".tmp"
     cmd = [nvcc(), *ARCH, "-shared", "-cudart", "static", "-o", tmp, *objs,
-           "-Xlinker", f"--version-script={os.path.join(CSRC, 'exports.map')}"]
+           "-Xlinker", f"--version-script={os.path.join(CSRC, 'exports.map')}", "-ldl"]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"link failed:\n{' '.join(cmd)}\n{r.stdout}\n{r.stderr}")

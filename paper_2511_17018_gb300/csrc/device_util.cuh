@@ -1,8 +1,10 @@
 // Small device helpers shared by the kernel modules.
 #pragma once
 
+#ifndef __CUDACC_RTC__
 #include <cuda_runtime.h>
 #include <stdint.h>
+#endif
 
 namespace tpcfit {
 

@@ -23,22 +23,36 @@
 // double buffer.  The alignment table and the geometry live in shared memory.
 // Tracks are taken in an order that puts tracks of equal length into the same
 // warp (length_order.cu) so that a warp's lanes finish together.
+//
+// Compiled ahead of time by the two kernel modules, and at run time by NVRTC
+// (TPCFIT_RTC = 1, Sec. 5): the run-time source first defines c_geo with the
+// time frame's scalars as compile-time constants and its tables as
+// initialised constant memory, so the compiler folds them into the code.
 #pragma once
 
+#ifndef __CUDACC_RTC__
 #include <cuda_runtime.h>
 #include <stdint.h>
 
 #include "internal.h"
+#else
+#include "kernel_abi.h"
+#endif
 #include "device_util.cuh"
 
 #ifndef TPCFIT_DET
 #error "define TPCFIT_DET before including fit_core.cuh"
 #endif
+#ifndef TPCFIT_RTC
+#define TPCFIT_RTC 0
+#endif
 
 namespace tpcfit {
 namespace TPCFIT_NS {
 
+#if !TPCFIT_RTC
 __constant__ GeoConst c_geo;
+#endif
 
 struct Jac {
   bool rot;
@@ -464,6 +478,10 @@ struct BlockSmem {
   SmemTables T;
   float align[kAlignFloats];
 };
+static_assert(sizeof(BlockSmem) == kFitBlockSmemBytes, "kernel_abi.h block shared-memory size");
+static_assert(sizeof(WarpStage<4>) == fit_warp_stage_bytes(4) && sizeof(WarpStage<8>) == fit_warp_stage_bytes(8) &&
+                  sizeof(WarpStage<16>) == fit_warp_stage_bytes(16),
+              "kernel_abi.h staging size");
 
 __device__ __forceinline__ bool step_predict(const SmemTables& T, const TrackState& S, int sec_to, float X, float m0,
                                              float m1, float pout[5], Jac& J) {
@@ -678,6 +696,7 @@ __global__ void __launch_bounds__(WARPS * 32, MINB) fit_kernel(FitArgs a) {
   }
 }
 
+#ifndef __CUDACC_RTC__
 template <int RPS, int WARPS, int MINB, bool RECORD, bool FRAMES>
 cudaError_t launch_cfg(const FitArgs& a, cudaStream_t s) {
   constexpr int kThreads = WARPS * 32;
@@ -709,12 +728,12 @@ cudaError_t launch_cfg(const FitArgs& a, cudaStream_t s) {
 // (alignment table + double buffer) decides how many blocks fit on an SM.
 template <bool RECORD, bool FRAMES>
 inline cudaError_t launch_rec(const FitArgs& a, int rps, int warps, cudaStream_t s) {
-  if (rps == 4 && warps == 8) return launch_cfg<4, 8, 2, RECORD, FRAMES>(a, s);
-  if (rps == 4 && warps == 12) return launch_cfg<4, 12, 2, RECORD, FRAMES>(a, s);
-  if (rps == 4 && warps == 24) return launch_cfg<4, 24, 1, RECORD, FRAMES>(a, s);
-  if (rps == 8 && warps == 8) return launch_cfg<8, 8, 2, RECORD, FRAMES>(a, s);
-  if (rps == 8 && warps == 16) return launch_cfg<8, 16, 1, RECORD, FRAMES>(a, s);
-  if (rps == 16 && warps == 8) return launch_cfg<16, 8, 1, RECORD, FRAMES>(a, s);
+  if (rps == 4 && warps == 8) return launch_cfg<4, 8, fit_min_blocks(4, 8), RECORD, FRAMES>(a, s);
+  if (rps == 4 && warps == 12) return launch_cfg<4, 12, fit_min_blocks(4, 12), RECORD, FRAMES>(a, s);
+  if (rps == 4 && warps == 24) return launch_cfg<4, 24, fit_min_blocks(4, 24), RECORD, FRAMES>(a, s);
+  if (rps == 8 && warps == 8) return launch_cfg<8, 8, fit_min_blocks(8, 8), RECORD, FRAMES>(a, s);
+  if (rps == 8 && warps == 16) return launch_cfg<8, 16, fit_min_blocks(8, 16), RECORD, FRAMES>(a, s);
+  if (rps == 16 && warps == 8) return launch_cfg<16, 8, fit_min_blocks(16, 8), RECORD, FRAMES>(a, s);
   return cudaErrorInvalidValue;
 }
 
@@ -728,6 +747,8 @@ inline cudaError_t launch(const FitArgs& a, int lanes_per_track, int rps, int wa
 cudaError_t upload(const GeoConst& g, cudaStream_t s) {
   return cudaMemcpyToSymbolAsync(c_geo, &g, sizeof(GeoConst), 0, cudaMemcpyHostToDevice, s);
 }
+
+#endif  // !__CUDACC_RTC__
 
 }  // namespace TPCFIT_NS
 }  // namespace tpcfit

@@ -3,93 +3,13 @@
 #pragma once
 
 #include <cstdint>
+#include <string>
 #include <cuda_runtime.h>
 
+#include "kernel_abi.h"
 #include "tpcfit.h"
 
 namespace tpcfit {
-
-constexpr int kNSectors = 36;
-constexpr int kNSide = 18;
-constexpr int kMaxRows = 152;
-constexpr int kAlignFloats = kNSectors * kMaxRows * 2;
-constexpr int kWarp = 32;
-// The adjoint's checkpoints: the filter state before every kCkptEvery-th step
-// of each pass, kCkptFloats floats each (p 5, L 25, x, sector bits, chi2, 3 pad).
-constexpr int kCkptShift = 4;
-constexpr int kCkptEvery = 1 << kCkptShift;
-constexpr int kCkptFloats = 36;
-
-// Per-time-frame constants of the fit, uploaded to the __constant__ bank of
-// every kernel module (each compilation unit has its own copy, Sec. 4.1).
-struct GeoConst {
-  float row_x[kMaxRows];      // local x of each pad-row plane (FP64 -> FP32)
-  float rot_c[kNSide * kNSide];  // cos / sin of the rotation from sector a to b
-  float rot_s[kNSide * kNSide];  //   (index a * 18 + b), FP64 -> FP32
-  double asin_a[30];          // Maclaurin coefficients of arcsin (FP64 island)
-  float kappa;                // -0.00299792458 * Bz  [1/cm per (c/GeV)]
-  float v_meas;               // cluster variance (0.1 cm)^2
-  float sqrt_v;               // its square root (fast-mode Potter coefficients)
-  float l0;                   // sqrt of the initial covariance diagonal (10)
-  float max_snp;              // |sin phi| limit (0.999)
-  int32_t n_rows;
-};
-
-// Arguments of one fit launch.
-struct FitArgs {
-  const float* y;
-  const float* z;
-  const uint16_t* rowsec;
-  int64_t n_hits;
-  const int32_t* off;
-  int32_t n_tracks;
-  const float* seeds;
-  const float* align;          // [36][152][2], always valid (zeros when unset)
-  const int32_t* perm;         // [n_tracks] processing order, or null
-  float* params;
-  float* cov;
-  float* chi2;
-  int32_t* ndf;
-  unsigned long long* err;     // error word: code << 56 | track
-  unsigned int* work;          // work-item counter (zeroed by the launcher)
-  // checkpoint recording for the adjoint (null = off)
-  float* ck;                   // [2][ck_slots][36] filter state before every kCkptEvery-th step of each pass
-  int32_t* ck_last;            // [n_tracks] index of the last cluster of the outward pass
-  int64_t ck_slots;            // slots per pass: n_hits / kCkptEvery + n_tracks + 1
-  // several time frames in one launch (frame_base = null: one frame)
-  const int64_t* frame_base;   // [n_frames + 1] first track of each frame
-  int32_t n_frames;
-  const float* frame_align;    // [n_frames][36][152][2] per-frame offsets, or null (handle's table)
-  const int32_t* frame_ready;  // [n_frames] ready flags (!= 0 when the frame's clusters are in place), or null
-  int64_t wait_ns;             // bound of a ready-flag wait
-};
-
-// Arguments of one backward launch (same frame as the recorded fit).
-struct BwdArgs {
-  const float* y;
-  const float* z;
-  const uint16_t* rowsec;
-  int64_t n_hits;
-  const int32_t* off;
-  int32_t n_tracks;
-  const float* align;
-  const int32_t* perm;
-  const int32_t* ndf;          // outputs of the recorded fit
-  const float* ck;
-  const int32_t* ck_last;
-  int64_t ck_slots;
-  const float* grad_chi2;      // [n_tracks] dL/dchi2_i
-  float* grad_seeds;           // [5][n_tracks]
-  float* grad_meas;            // [n_hits][2] dL/dm per cluster, or null
-  float* grad_align_atomic;    // [36][152][2] accumulated with atomics, or null
-  unsigned int* work;
-  float4* seg;                 // segment store: [resident warps][kCkptEvery][8][32] float4
-};
-
-// Error codes recorded in the device error word.
-constexpr unsigned long long kErrOffsets = 1;
-constexpr unsigned long long kErrRowSector = 2;
-constexpr unsigned long long kErrTimeout = 3;
 
 // ---- constant-memory registry (Sec. 4.1): every kernel module registers an
 // uploader for its own __constant__ copy; the host updates all of them.
@@ -124,6 +44,20 @@ cudaError_t launch_key_reduce(const float* grad_meas, const int* sorted, const i
                               cudaStream_t s);
 // true if (lanes_per_track, rows_per_stage, warps) is a compiled launch shape
 bool fit_shape_supported(int lanes_per_track, int rows_per_stage, int warps);
+
+// ---- run-time compilation of the fit (rtc.cpp, Sec. 5)
+bool rtc_available();
+long long rtc_compile_count();
+const char* rtc_log();
+// The NVRTC source of the fit for these constants and mode.
+std::string rtc_fit_source(const GeoConst& g, bool det);
+// NVRTC only (no device needed): the CUBIN of a variant, stored in cache_dir
+// when given.
+tpcfit_status rtc_build(const GeoConst& g, bool det, int rps, int warps, bool record, bool frames,
+                        const char* cache_dir);
+// Compile (once per source and variant) and launch the fit specialised for g.
+tpcfit_status rtc_launch_fit(const GeoConst& g, bool det, int rps, int warps, const FitArgs& a, const char* cache_dir,
+                             cudaStream_t s);
 
 // Ordering by (frame ascending, length descending) for batched frames.
 // scratch: int32 [2 * n_frames * 256 + scan_tmp_ints(n_frames * 256)].

@@ -125,6 +125,8 @@ struct tpcfit_handle {
   // adjoint: checkpoints of the last recorded fit
   int record = 0;
   int bwd_warps = 8;
+  int rtc = 0;                 // fit kernels compiled at run time (Sec. 5)
+  std::string rtc_dir;         // their on-disk cache, or empty
   float* d_ck = nullptr;
   int64_t ck_cap = 0;          // floats
   int32_t* d_ck_last = nullptr;
@@ -196,6 +198,20 @@ extern "C" {
 
 int32_t tpcfit_version(void) { return 1 * 10000 + 0 * 100 + 0; }
 
+namespace {
+// The fit launch of a handle: ahead-of-time kernels, or the kernel compiled
+// at run time for the handle's constants.
+tpcfit_status launch_fit(const tpcfit_handle* h, const FitArgs& a, cudaStream_t s) {
+  if (h->rtc)
+    return rtc_launch_fit(h->geo, h->deterministic != 0, h->rows_per_stage, h->warps_per_block, a,
+                          h->rtc_dir.empty() ? nullptr : h->rtc_dir.c_str(), s);
+  const cudaError_t e = h->deterministic
+                            ? launch_fit_det(a, h->lanes_per_track, h->rows_per_stage, h->warps_per_block, s)
+                            : launch_fit_fast(a, h->lanes_per_track, h->rows_per_stage, h->warps_per_block, s);
+  return from_cuda(e);
+}
+}  // namespace
+
 const char* tpcfit_status_string(tpcfit_status s) {
   switch (s) {
     case TPCFIT_OK: return "ok";
@@ -205,6 +221,7 @@ const char* tpcfit_status_string(tpcfit_status s) {
     case TPCFIT_EDEVICE: return "a kernel found invalid input";
     case TPCFIT_ETIMEOUT: return "a bounded device-side wait ran out";
     case TPCFIT_ESTATE: return "call not allowed in the current state";
+    case TPCFIT_ERTC: return "run-time compilation unavailable or failed";
   }
   return "unknown status";
 }
@@ -341,15 +358,15 @@ tpcfit_status tpcfit_fit(tpcfit_handle* h, const tpcfit_hits* hits, const int32_
     if (e != cudaSuccess) return from_cuda(e);
     a.perm = h->d_perm;
   }
-  cudaError_t e = h->deterministic ? launch_fit_det(a, h->lanes_per_track, h->rows_per_stage, h->warps_per_block, s)
-                                   : launch_fit_fast(a, h->lanes_per_track, h->rows_per_stage, h->warps_per_block, s);
-  if (e == cudaSuccess && h->record) {
+  st = launch_fit(h, a, s);
+  if (st != TPCFIT_OK) return st;
+  if (h->record) {
     h->rec_valid = true;
     h->rec_tracks = n_tracks;
     h->rec_hits = hits->n_hits;
     h->rec_det = h->deterministic;
   }
-  return from_cuda(e);
+  return TPCFIT_OK;
 }
 
 tpcfit_status tpcfit_fit_frames(tpcfit_handle* h, const tpcfit_hits* hits, const int32_t* track_offsets,
@@ -401,10 +418,8 @@ tpcfit_status tpcfit_fit_frames(tpcfit_handle* h, const tpcfit_hits* hits, const
   h->rec_valid = false;  // the adjoint follows single-frame fits only
   cudaError_t e =
       launch_frame_length_order(track_offsets, n_tracks, frame_track_base, n_frames, h->d_perm, h->d_frame_scratch, s);
-  if (e == cudaSuccess)
-    e = h->deterministic ? launch_fit_det(a, h->lanes_per_track, h->rows_per_stage, h->warps_per_block, s)
-                         : launch_fit_fast(a, h->lanes_per_track, h->rows_per_stage, h->warps_per_block, s);
-  return from_cuda(e);
+  if (e != cudaSuccess) return from_cuda(e);
+  return launch_fit(h, a, s);
 }
 
 tpcfit_status tpcfit_set_backward_config(tpcfit_handle* h, int warps_per_block) {
@@ -412,6 +427,26 @@ tpcfit_status tpcfit_set_backward_config(tpcfit_handle* h, int warps_per_block) 
   h->bwd_warps = warps_per_block;
   return TPCFIT_OK;
 }
+
+tpcfit_status tpcfit_set_rtc(tpcfit_handle* h, int enable, const char* cache_dir) {
+  if (!h || (enable != 0 && enable != 1)) return TPCFIT_EINVAL;
+  if (enable && !rtc_available()) return TPCFIT_ERTC;
+  h->rtc = enable;
+  h->rtc_dir = cache_dir ? cache_dir : "";
+  return TPCFIT_OK;
+}
+
+tpcfit_status tpcfit_rtc_build(const tpcfit_geometry* geometry, double bz_tesla, int deterministic, int rows_per_stage,
+                               int warps_per_block, int record, int frames, const char* cache_dir) {
+  GeoConst g{};
+  if (!geometry || !build_geo(geometry, bz_tesla, g)) return TPCFIT_EINVAL;
+  if (!fit_shape_supported(1, rows_per_stage, warps_per_block)) return TPCFIT_EINVAL;
+  return rtc_build(g, deterministic != 0, rows_per_stage, warps_per_block, record != 0, frames != 0, cache_dir);
+}
+
+int tpcfit_rtc_available(void) { return rtc_available() ? 1 : 0; }
+long long tpcfit_rtc_compile_count(void) { return rtc_compile_count(); }
+const char* tpcfit_rtc_log(void) { return rtc_log(); }
 
 tpcfit_status tpcfit_set_record(tpcfit_handle* h, int record) {
   if (!h || (record != 0 && record != 1)) return TPCFIT_EINVAL;

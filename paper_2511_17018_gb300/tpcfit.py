@@ -15,7 +15,7 @@ import numpy as np
 _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libtpcfit.so")
 
-OK, EINVAL, ECUDA, ENOMEM, EDEVICE, ETIMEOUT, ESTATE = range(7)
+OK, EINVAL, ECUDA, ENOMEM, EDEVICE, ETIMEOUT, ESTATE, ERTC = range(8)
 
 
 class TpcfitError(RuntimeError):
@@ -62,6 +62,12 @@ def load():
         "tpcfit_fit_frames": (C.c_int, [vp, C.POINTER(_Hits), vp, i32, vp, i32, vp, vp, i64, vp, vp, vp, vp, vp,
                                         vp]),
         "tpcfit_fit_backward": (C.c_int, [vp, C.POINTER(_Hits), vp, i32, vp, vp, vp, vp, vp, vp]),
+        "tpcfit_set_rtc": (C.c_int, [vp, C.c_int, C.c_char_p]),
+        "tpcfit_rtc_build": (C.c_int, [C.POINTER(_Geometry), C.c_double, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int,
+                                       C.c_char_p]),
+        "tpcfit_rtc_available": (C.c_int, []),
+        "tpcfit_rtc_compile_count": (C.c_longlong, []),
+        "tpcfit_rtc_log": (C.c_char_p, []),
         "tpcfit_status_string": (C.c_char_p, [C.c_int]),
         "tpcfit_version": (i32, []),
     }
@@ -102,15 +108,48 @@ def tpcfit_version() -> int:
     return int(load().tpcfit_version())
 
 
-def tpcfit_create(geometry, bz: float):
-    """geometry: object with row_x (float64 array), n_sectors, sector_width_deg, z_max."""
-    L = load()
+def _geometry(geometry):
+    """(ctypes geometry, the row array it points into)."""
     rx = np.ascontiguousarray(geometry.row_x, dtype=np.float64)
     g = _Geometry(int(geometry.n_sectors), int(rx.shape[0]), rx.ctypes.data_as(C.POINTER(C.c_double)),
                   float(geometry.sector_width_deg), float(getattr(geometry, "z_max", 250.0)))
+    return g, rx
+
+
+def tpcfit_create(geometry, bz: float):
+    """geometry: object with row_x (float64 array), n_sectors, sector_width_deg, z_max."""
+    L = load()
+    g, rx = _geometry(geometry)
     h = C.c_void_p()
     _check(L.tpcfit_create(C.byref(g), float(bz), C.byref(h)), "tpcfit_create")
     return h
+
+
+def tpcfit_set_rtc(h, enable: bool = True, cache_dir: str | None = None) -> None:
+    _check(load().tpcfit_set_rtc(h, int(bool(enable)), cache_dir.encode() if cache_dir else None), "tpcfit_set_rtc")
+
+
+def tpcfit_rtc_build(geometry, bz: float, deterministic: bool = False, rows_per_stage: int = 4,
+                     warps_per_block: int = 24, record: bool = False, frames: bool = False,
+                     cache_dir: str | None = None) -> None:
+    g, rx = _geometry(geometry)
+    st = load().tpcfit_rtc_build(C.byref(g), float(bz), int(bool(deterministic)), int(rows_per_stage),
+                                 int(warps_per_block), int(bool(record)), int(bool(frames)),
+                                 cache_dir.encode() if cache_dir else None)
+    if st != OK:
+        raise TpcfitError(st, "tpcfit_rtc_build: " + tpcfit_rtc_log()[-2000:])
+
+
+def tpcfit_rtc_available() -> bool:
+    return bool(load().tpcfit_rtc_available())
+
+
+def tpcfit_rtc_compile_count() -> int:
+    return int(load().tpcfit_rtc_compile_count())
+
+
+def tpcfit_rtc_log() -> str:
+    return (load().tpcfit_rtc_log() or b"").decode(errors="replace")
 
 
 def tpcfit_destroy(h) -> None:
@@ -300,6 +339,9 @@ class Fitter:
 
     def set_mode(self, deterministic: bool):
         tpcfit_set_mode(self.h, deterministic)
+
+    def set_rtc(self, enable: bool = True, cache_dir: str | None = None):
+        tpcfit_set_rtc(self.h, enable, cache_dir)
 
     def set_config(self, lanes_per_track=1, rows_per_stage=4, warps_per_block=24, sort_by_length=True):
         tpcfit_set_config(self.h, lanes_per_track, rows_per_stage, warps_per_block, sort_by_length)
