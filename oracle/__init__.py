@@ -27,7 +27,8 @@ def lib():
         path = _build.build()
         L = C.CDLL(path)
         vp = C.c_void_p
-        for name in ("oracle_fit_f64", "oracle_fit_f32", "oracle_fit_sqrt_f64", "oracle_fit_cov_f32"):
+        for name in ("oracle_fit_f64", "oracle_fit_f32", "oracle_fit_sqrt_f64", "oracle_fit_cov_f32",
+                     "oracle_fit_pred_f64"):
             f = getattr(L, name)
             f.restype = C.c_int
             f.argtypes = [C.POINTER(_Geo), C.c_double, C.c_int32, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp,
@@ -131,6 +132,68 @@ def grad(frame, weights=None, align=None, nthreads: int | None = None, exact_inp
     if rc != 0:
         raise ValueError(f"oracle grad rejected its inputs (rc={rc})")
     return dict(grad_meas=gm, grad_seed=gs, chi2=chi2, ndf=ndf)
+
+
+# Cluster variance of the fit: sigma_y = sigma_z = 0.1 cm.
+V_MEAS = 0.01
+
+
+def smooth(frame, align=None, ref=None, exact_inputs: bool = False, seeds=None, nthreads: int | None = None):
+    """Two-filter smoother of the FP64 fit (Fraser & Potter, 1969): for every
+    cluster, the estimate from all the other clusters is the information-
+    weighted mean of the outward prediction (clusters before it, seed prior)
+    and the inward prediction (clusters after it, the inward pass's prior):
+
+        C_u = (C_out^-1 + C_in^-1)^-1,   x_u = C_u (C_out^-1 x_out + C_in^-1 x_in).
+
+    Per cluster h: resid[h] = m_h - (y, z) of x_u (m = measured y, z minus the
+    alignment offsets), rcov[h] = (R00, R10, R11) of R = V + H C_u H^T, and
+    chi2[h] = resid^T R^-1 resid.  NaN for the clusters of unfitted tracks and
+    for clusters the outward pass did not reach.
+    Returns dict(resid[H,2], rcov[H,3], chi2[H], ndf[n]).
+    """
+    L = lib()
+    n = frame.n_tracks
+    H = frame.n_hits
+    y = np.ascontiguousarray(frame.y64 if exact_inputs else frame.y, dtype=np.float64)
+    z = np.ascontiguousarray(frame.z64 if exact_inputs else frame.z, dtype=np.float64)
+    sd = frame.seeds64 if exact_inputs else frame.seeds
+    sd = np.ascontiguousarray(sd if seeds is None else seeds, dtype=np.float64)
+    rs = np.ascontiguousarray(frame.rowsec, dtype=np.uint16)
+    off = np.ascontiguousarray(frame.offsets, dtype=np.int32)
+    al = None if align is None else np.ascontiguousarray(align, dtype=np.float64).reshape(-1)
+    rf = None if ref is None else np.ascontiguousarray(ref, dtype=np.float64)
+    params = np.empty((5, n)); cov = np.empty((15, n)); chi2 = np.empty(n); ndf = np.empty(n, np.int32)
+    pt = np.empty((H, 2, 20))
+    g, _keep = _geo(frame.geometry)
+    rc = L.oracle_fit_pred_f64(C.byref(g), float(frame.bz), n, _ptr(off), _ptr(y), _ptr(z), _ptr(rs), _ptr(sd),
+                               _ptr(al), _ptr(rf), _ptr(params), _ptr(cov), _ptr(chi2), _ptr(ndf), _ptr(pt),
+                               nthreads or default_threads())
+    if rc != 0:
+        raise ValueError(f"oracle fit rejected its inputs (rc={rc})")
+    m = np.stack([y, z], axis=1)
+    if al is not None:
+        a = al.reshape(36 * 152, 2)
+        key = (rs.astype(np.int64) & 63) * 152 + (rs.astype(np.int64) >> 6)
+        m = m - a[key]
+    fitted = np.repeat(ndf > 0, np.diff(off))
+    ok = fitted & np.all(np.isfinite(pt.reshape(H, -1)), axis=1)
+    resid = np.full((H, 2), np.nan)
+    rcov = np.full((H, 3), np.nan)
+    c2 = np.full(H, np.nan)
+    if ok.any():
+        x1, x2 = pt[ok, 0, :5], pt[ok, 1, :5]
+        C1 = np.moveaxis(unpack(pt[ok, 0, 5:].T), -1, 0)
+        C2 = np.moveaxis(unpack(pt[ok, 1, 5:].T), -1, 0)
+        I1, I2 = np.linalg.inv(C1), np.linalg.inv(C2)
+        Cu = np.linalg.inv(I1 + I2)
+        xu = np.einsum("nij,nj->ni", Cu, np.einsum("nij,nj->ni", I1, x1) + np.einsum("nij,nj->ni", I2, x2))
+        r = m[ok] - xu[:, :2]
+        R = V_MEAS * np.eye(2) + Cu[:, :2, :2]
+        resid[ok] = r
+        rcov[ok] = np.stack([R[:, 0, 0], R[:, 1, 0], R[:, 1, 1]], axis=1)
+        c2[ok] = np.einsum("ni,ni->n", r, np.linalg.solve(R, r[..., None])[..., 0])
+    return dict(resid=resid, rcov=rcov, chi2=c2, ndf=ndf)
 
 
 def align_grad_from_meas(frame, grad_meas):

@@ -522,7 +522,7 @@ struct FitResult {
 template <class T, bool kSqrt>
 FitResult fit_track(const Geo<typename Traits<T>::S>& g, const HitView<T>& h, const T* yv, const T* zv,
                     const T seed[5], const double* ref /*[n][5] or null*/, T p_out[5], T C_out[15], T& chi2_out,
-                    double* trace /*[n][2][22] or null*/) {
+                    double* trace /*[n][2][22] or null*/, double* ptrace = nullptr /*[n][2][20] or null*/) {
   using S = typename Traits<T>::S;
   FitResult res{0, 0};
   const int n = h.n;
@@ -547,13 +547,27 @@ FitResult fit_track(const Geo<typename Traits<T>::S>& g, const HitView<T>& h, co
     o[20] = V(chi2);
     o[21] = V(x);
   };
+  // predicted state (p, C) at hit j of a pass, before its update: the two
+  // predictions of a hit are the inputs of the two-filter smoother
+  auto precord = [&](int pass, int j) {
+    if (!ptrace) return;
+    double* o = ptrace + ((size_t)j * 2 + pass) * 20;
+    T C[15];
+    F.cov(C);
+    for (int i = 0; i < 5; ++i) o[i] = V(p[i]);
+    if (kRes && !ref) {
+      o[0] = (double)(float)(V(my) + V(p[0]));
+      o[1] = (double)(float)(V(mz) + V(p[1]));
+    }
+    for (int e = 0; e < 15; ++e) o[5 + e] = V(C[e]);
+  };
   // FP32 sequence: y and z are carried as residuals from the measurement of the
   // current cluster (p[0] = y - m_y, p[1] = z - m_z), so that their rounding is
   // that of ~0.1 cm quantities instead of positions up to 250 cm.  The helix
   // step adds the exact difference of consecutive measurements; across a
   // sector rotation the absolute position is formed, rotated and re-referenced.
   // The FP64 and dual instantiations keep absolute coordinates.
-  auto step = [&](int from, int to) -> bool {
+  auto step = [&](int from, int to, int pass) -> bool {
     const int r = hit_row(h, to);
     if (r < 0 || r >= g.n_rows) return false;
     Jac<T> J;
@@ -606,6 +620,7 @@ FitResult fit_track(const Geo<typename Traits<T>::S>& g, const HitView<T>& h, co
       m[0] = T((S)0.0);
       m[1] = T((S)0.0);
     }
+    precord(pass, to);
     return F.update(g, p, chi2, m);
   };
   // ---- outward pass
@@ -626,12 +641,13 @@ FitResult fit_track(const Geo<typename Traits<T>::S>& g, const HitView<T>& h, co
       m[0] = T((S)0.0);
       m[1] = T((S)0.0);
     }
+    precord(0, 0);
     if (!F.update(g, p, chi2, m)) return res;
   }
   record(0, 0);
   int last = 0;
   for (int j = 1; j < n; ++j) {
-    if (!step(j - 1, j)) break;  // the outward pass ends at the last good hit
+    if (!step(j - 1, j, 0)) break;  // the outward pass ends at the last good hit
     last = j;
     record(0, j);
   }
@@ -646,12 +662,13 @@ FitResult fit_track(const Geo<typename Traits<T>::S>& g, const HitView<T>& h, co
       m[0] = T((S)0.0);
       m[1] = T((S)0.0);
     }
+    precord(1, last);
     if (!F.update(g, p, chi2, m)) return res;
   }
   ++used;
   record(1, last);
   for (int j = last - 1; j >= 0; --j) {
-    if (!step(j + 1, j)) return res;
+    if (!step(j + 1, j, 1)) return res;
     ++used;
     record(1, j);
   }
@@ -687,7 +704,7 @@ int check_inputs(const OracleGeometry* geo, int32_t n_tracks, const int32_t* off
 template <class T, bool kSqrt>
 int fit_all(const OracleGeometry* geo, double bz, int32_t n_tracks, const int32_t* off, const T* y, const T* z,
             const uint16_t* rowsec, const T* seeds, const T* align, const double* ref, T* params, T* cov, T* chi2,
-            int32_t* ndf, double* trace, int32_t nthreads) {
+            int32_t* ndf, double* trace, int32_t nthreads, double* ptrace = nullptr) {
   using S = typename Traits<T>::S;
   if (check_inputs(geo, n_tracks, off)) return 1;
   Geo<S> g;
@@ -703,7 +720,10 @@ int fit_all(const OracleGeometry* geo, double bz, int32_t n_tracks, const int32_
     double* ttr = trace ? trace + (size_t)off[i] * 2 * 22 : nullptr;
     if (ttr)
       for (int64_t e = 0; e < (int64_t)h.n * 2 * 22; ++e) ttr[e] = NAN;
-    FitResult r = fit_track<T, kSqrt>(g, h, y + off[i], z + off[i], seed, tref, p, C, c2, ttr);
+    double* tpt = ptrace ? ptrace + (size_t)off[i] * 2 * 20 : nullptr;
+    if (tpt)
+      for (int64_t e = 0; e < (int64_t)h.n * 2 * 20; ++e) tpt[e] = NAN;
+    FitResult r = fit_track<T, kSqrt>(g, h, y + off[i], z + off[i], seed, tref, p, C, c2, ttr, tpt);
     if (r.ok) {
       for (int c = 0; c < 5; ++c) params[(size_t)c * n_tracks + i] = p[c];
       for (int e = 0; e < 15; ++e) cov[(size_t)e * n_tracks + i] = C[e];
@@ -734,6 +754,17 @@ int oracle_fit_f64(const OracleGeometry* geo, double bz, int32_t n_tracks, const
                    int32_t nthreads) {
   return fit_all<double, false>(geo, bz, n_tracks, off, y, z, rowsec, seeds, align, ref, params, cov, chi2, ndf,
                                 trace, nthreads);
+}
+
+// The FP64 fit with the predicted state (p, C) of every hit of both passes,
+// before its update: ptrace[H][2][20] (NaN where a pass does not reach a hit).
+// They are the inputs of the two-filter smoother (Fraser & Potter, 1969).
+int oracle_fit_pred_f64(const OracleGeometry* geo, double bz, int32_t n_tracks, const int32_t* off, const double* y,
+                        const double* z, const uint16_t* rowsec, const double* seeds, const double* align,
+                        const double* ref, double* params, double* cov, double* chi2, int32_t* ndf, double* ptrace,
+                        int32_t nthreads) {
+  return fit_all<double, false>(geo, bz, n_tracks, off, y, z, rowsec, seeds, align, ref, params, cov, chi2, ndf,
+                                nullptr, nthreads, ptrace);
 }
 
 // The square-root (Potter) form in FP64: the pin that ties the FP32 canonical

@@ -228,6 +228,81 @@ def _gls(order, A, bb, m, prior, C0):
     return x0, obj, np.linalg.inv(N)
 
 
+def _short_tracks(synth, seed, n=60):
+    """A frame of n tracks cut to their first 3..8 hits."""
+    rng = np.random.default_rng(seed)
+    base = synth.generate(n, 23, drop_p=0.05)
+    keep = [np.arange(o, o + int(rng.integers(3, 9))) for o in base.offsets[:-1]]
+    fr = base.subset(np.arange(base.n_tracks))
+    lens = np.array([len(k) for k in keep])
+    idx = np.concatenate(keep)
+    fr.y, fr.z, fr.rowsec = base.y[idx], base.z[idx], base.rowsec[idx]
+    fr.y64, fr.z64 = base.y64[idx], base.z64[idx]
+    fr.offsets = np.concatenate([[0], np.cumsum(lens)]).astype(np.int32)
+    return fr, lens
+
+
+def test_smoother_equals_leave_one_out_least_squares(oracle_mod, synth):
+    # Linearised about the exact trajectory, the outward and inward steps are
+    # exact inverses of each other and the model is linear-Gaussian.  The
+    # smoothed residual of a cluster must then equal the dense weighted least-
+    # squares solve without that cluster, under the two priors the passes use:
+    # the seed (C0) on the first state and the outward result (C0) on the last.
+    fr, lens = _short_tracks(synth, 11)
+    ref = truth_trajectory(oracle_mod, fr)
+    s = oracle_mod.smooth(fr, ref=ref, exact_inputs=True)
+    r = oracle_mod.fit(fr, "f64", ref=ref, trace=True, exact_inputs=True)
+    m = np.stack([fr.y64, fr.z64], axis=1)
+    H = np.zeros((2, 5)); H[0, 0] = 1; H[1, 1] = 1
+    checked = 0
+    for i in range(fr.n_tracks):
+        order, A, bb = _affine_chain(oracle_mod, fr, ref, i, backward=False)
+        last = order[-1]
+        p_out = r["trace"][last, 0, :5]
+        for k, h in enumerate(order):
+            N = np.eye(5) / 100.0
+            rhs = fr.seeds64[:, i] / 100.0
+            N += A[-1].T @ A[-1] / 100.0
+            rhs += A[-1].T @ (p_out - bb[-1]) / 100.0
+            for kk, j in enumerate(order):
+                if kk == k:
+                    continue
+                HA = H @ A[kk]
+                N += HA.T @ HA / 0.01
+                rhs += HA.T @ (m[j] - H @ bb[kk]) / 0.01
+            x0 = np.linalg.solve(N, rhs)
+            P = np.linalg.inv(N)
+            xc = A[k] @ x0 + bb[k]
+            Rc = 0.01 * np.eye(2) + (A[k] @ P @ A[k].T)[:2, :2]
+            rc = m[h] - xc[:2]
+            assert np.allclose(s["resid"][h], rc, rtol=1e-7, atol=1e-10)
+            assert np.allclose(s["rcov"][h], [Rc[0, 0], Rc[1, 0], Rc[1, 1]], rtol=1e-7, atol=1e-13)
+            assert abs(s["chi2"][h] - rc @ np.linalg.solve(Rc, rc)) < 1e-7 * max(1.0, s["chi2"][h])
+            checked += 1
+    assert checked == lens.sum()
+
+
+def test_smoother_flags_a_displaced_cluster(oracle_mod, synth):
+    # a cluster moved by 1 cm (10 sigma) stands out: the largest chi2 of its
+    # track, far beyond the 2-dof tail; the rest follow the 2-dof distribution
+    fr = synth.generate(300, 31, drop_p=0.05, cap_lengths=True)
+    off = fr.offsets
+    moved = off[:-1] + np.diff(off) // 2
+    fr.y = fr.y.copy()
+    fr.y[moved] += np.float32(1.0)
+    s = oracle_mod.smooth(fr)
+    c2 = s["chi2"]
+    for i in range(fr.n_tracks):
+        if s["ndf"][i] <= 0:
+            continue
+        seg = c2[off[i]:off[i + 1]]
+        assert np.nanargmax(seg) == moved[i] - off[i]
+        assert seg[moved[i] - off[i]] > 40.0
+    rest = np.delete(c2, moved)
+    rest = rest[np.isfinite(rest)]
+    assert abs(rest.mean() - 2.0) < 0.25
+
+
 @pytest.mark.parametrize("form", ["f64", "sqrt_f64"])
 def test_linearised_filter_equals_dense_least_squares(oracle_mod, synth, form):
     # with a fixed linearisation the filter is linear-Gaussian: each pass must
