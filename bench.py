@@ -439,6 +439,22 @@ def main():
     fit_rec_ms = statistics.mean(p[0] for p in per)
     bwd_ms = statistics.mean(p[1] for p in per)
 
+    # ---- the two-filter smoother of the recorded fit (per-cluster outlier test)
+    sm = dict(resid=torch.empty((fr.n_hits, 2), device="cuda"), rcov=torch.empty((fr.n_hits, 3), device="cuda"),
+              chi2=torch.empty(fr.n_hits, device="cuda"))
+
+    def step_smooth(mid):
+        tf.tpcfit_smooth(fitter.h, dev["y"], dev["z"], dev["rowsec"], dev["offsets"], out["ndf"], sm["resid"],
+                         sm["rcov"], sm["chi2"])
+        mid.record(stream)
+
+    for _ in range(args.warmup):
+        step_smooth(torch.cuda.Event())
+    torch.cuda.synchronize()
+    _, sm_per = timed(step_smooth, max(5, args.steps // 4))
+    smooth_ms = statistics.mean(p[0] for p in sm_per)
+    del sm
+
     # ---- the plain fit (no checkpoints)
     fitter.set_record(False)
     for _ in range(args.warmup):
@@ -525,6 +541,11 @@ def main():
         "gpu_launches": 4 * args.steps,
         "clocks": clocks,
     }
+    sm_tf = flops.smooth_flops(lengths) / (smooth_ms / 1e3) / 1e12
+    line["smoother"] = {"tracks_per_s": fr.n_tracks / (smooth_ms / 1e3), "clusters_per_s": fr.n_hits / (smooth_ms / 1e3),
+                        "ms": smooth_ms, "achieved_tflops": sm_tf, "frac": sm_tf / peak_tf,
+                        "kernel": "smooth_kernel<8> (two-filter smoother of the recorded fit)",
+                        "algorithmic_flops_per_launch": flops.smooth_flops(lengths)}
     if rtc is not None:
         rtc_tf = fit_fl / (rtc["ms"] / 1e3) / 1e12
         line["plain_fit"]["rtc"] = {"tracks_per_s": fr.n_tracks / (rtc["ms"] / 1e3), "ms": rtc["ms"],

@@ -219,6 +219,23 @@ tpcfit_status tpcfit_fit_backward(tpcfit_handle* h, const tpcfit_hits* hits, con
                                   int32_t n_tracks, const int32_t* ndf, const float* grad_chi2, float* grad_align,
                                   float* grad_seeds, float* grad_meas, void* stream);
 
+/* Two-filter smoother of the recorded fit: for every cluster, the residual
+ * against the estimate from all the other clusters of its track (the outward
+ * prediction from the seed and the clusters before it, combined with the
+ * inward prediction from the clusters after it).  Inputs as for
+ * tpcfit_fit_backward (the last tpcfit_fit on this handle, with recording on,
+ * same mode; otherwise ESTATE).  Outputs (device, overwritten):
+ *   resid: float [n_hits][2], measured (y, z) minus alignment minus the
+ *          smoothed (y, z);
+ *   rcov:  float [n_hits][3], (R00, R10, R11) of R = V + H C H^T;
+ *   chi2:  float [n_hits], resid^T R^-1 resid (2 degrees of freedom), the
+ *          outlier test of the cluster.
+ * NaN for the clusters of tracks with ndf <= 0 and for clusters the outward
+ * pass did not reach.  Uses the handle's segment store (as the adjoint does):
+ * calls on one handle must not overlap. */
+tpcfit_status tpcfit_smooth(tpcfit_handle* h, const tpcfit_hits* hits, const int32_t* track_offsets, int32_t n_tracks,
+                            const int32_t* ndf, float* resid, float* rcov, float* chi2, void* stream);
+
 /* Fit with HOST buffers: copies hits, offsets and seeds to the device, fits and
  * copies the outputs back, all on `stream`, then synchronises the stream.
  * Same argument meaning as tpcfit_fit with every array in host memory

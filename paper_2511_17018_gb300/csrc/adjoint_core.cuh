@@ -359,13 +359,14 @@ struct HitRaw {
   int rs;
 };
 
-__device__ __forceinline__ HitRaw load_hit(const BwdArgs& a, int h) {
+__device__ __forceinline__ HitRaw load_hit(const float* y, const float* z, const uint16_t* rowsec, int h) {
   HitRaw r;
-  r.y = __ldg(a.y + h);
-  r.z = __ldg(a.z + h);
-  r.rs = (int)__ldg(a.rowsec + h);
+  r.y = __ldg(y + h);
+  r.z = __ldg(z + h);
+  r.rs = (int)__ldg(rowsec + h);
   return r;
 }
+__device__ __forceinline__ HitRaw load_hit(const BwdArgs& a, int h) { return load_hit(a.y, a.z, a.rowsec, h); }
 
 // Measurement (alignment subtracted), row and sector of a loaded cluster.  Row
 // and sector are clamped into the table: the recorded fit has validated them,

@@ -6,6 +6,7 @@
 #define TPCFIT_NS det
 #include "fit_core.cuh"
 #include "adjoint_core.cuh"
+#include "smooth_core.cuh"
 
 namespace tpcfit {
 static ConstRegistration reg_det("fit_det", &det::upload);
@@ -16,4 +17,6 @@ cudaError_t launch_backward_det(const BwdArgs& a, int warps, cudaStream_t s) {
   return det::launch_backward(a, warps, s);
 }
 cudaError_t backward_store_det(int warps, int64_t& float4s) { return det::backward_store(warps, float4s); }
+cudaError_t launch_smooth_det(const SmoothArgs& a, cudaStream_t s) { return det::launch_smooth(a, s); }
+cudaError_t smooth_store_det(int64_t& float4s) { return det::smooth_store(float4s); }
 }  // namespace tpcfit

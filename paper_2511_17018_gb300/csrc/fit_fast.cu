@@ -5,6 +5,7 @@
 #define TPCFIT_NS fast
 #include "fit_core.cuh"
 #include "adjoint_core.cuh"
+#include "smooth_core.cuh"
 
 namespace tpcfit {
 static ConstRegistration reg_fast("fit_fast", &fast::upload);
@@ -15,4 +16,6 @@ cudaError_t launch_backward_fast(const BwdArgs& a, int warps, cudaStream_t s) {
   return fast::launch_backward(a, warps, s);
 }
 cudaError_t backward_store_fast(int warps, int64_t& float4s) { return fast::backward_store(warps, float4s); }
+cudaError_t launch_smooth_fast(const SmoothArgs& a, cudaStream_t s) { return fast::launch_smooth(a, s); }
+cudaError_t smooth_store_fast(int64_t& float4s) { return fast::smooth_store(float4s); }
 }  // namespace tpcfit

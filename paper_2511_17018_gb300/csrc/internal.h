@@ -33,6 +33,11 @@ cudaError_t launch_backward_det(const BwdArgs& a, int warps, cudaStream_t s);
 // float4 elements of the segment store a backward launch with `warps` needs
 cudaError_t backward_store_fast(int warps, int64_t& float4s);
 cudaError_t backward_store_det(int warps, int64_t& float4s);
+// the two-filter smoother of a recorded fit, and its segment store (float4s)
+cudaError_t launch_smooth_fast(const SmoothArgs& a, cudaStream_t s);
+cudaError_t launch_smooth_det(const SmoothArgs& a, cudaStream_t s);
+cudaError_t smooth_store_fast(int64_t& float4s);
+cudaError_t smooth_store_det(int64_t& float4s);
 // true if `warps` is a compiled backward block shape
 bool backward_shape_supported(int warps);
 

@@ -97,6 +97,27 @@ struct BwdArgs {
   float4* seg;                 // segment store: [resident warps][kCkptEvery][8][32] float4
 };
 
+// Arguments of one smoother launch (same frame as the recorded fit).
+struct SmoothArgs {
+  const float* y;
+  const float* z;
+  const uint16_t* rowsec;
+  int64_t n_hits;
+  const int32_t* off;
+  int32_t n_tracks;
+  const float* align;
+  const int32_t* perm;
+  const int32_t* ndf;          // outputs of the recorded fit
+  const float* ck;
+  const int32_t* ck_last;
+  int64_t ck_slots;
+  float* resid;                // [n_hits][2] m - H x_u
+  float* rcov;                 // [n_hits][3] R00, R10, R11 of V + H C_u H^T
+  float* chi2;                 // [n_hits] r^T R^-1 r
+  unsigned int* work;
+  float4* seg;                 // segment store, as for the adjoint
+};
+
 // Error codes recorded in the device error word.
 constexpr unsigned long long kErrOffsets = 1;
 constexpr unsigned long long kErrRowSector = 2;

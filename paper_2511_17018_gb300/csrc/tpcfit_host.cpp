@@ -531,6 +531,46 @@ tpcfit_status tpcfit_fit_backward(tpcfit_handle* h, const tpcfit_hits* hits, con
   return from_cuda(e);
 }
 
+tpcfit_status tpcfit_smooth(tpcfit_handle* h, const tpcfit_hits* hits, const int32_t* track_offsets, int32_t n_tracks,
+                            const int32_t* ndf, float* resid, float* rcov, float* chi2, void* stream) {
+  if (!h || !hits || n_tracks < 0 || hits->n_hits < 0) return TPCFIT_EINVAL;
+  if (n_tracks == 0) return TPCFIT_OK;
+  if (!track_offsets || !ndf || !resid || !rcov || !chi2) return TPCFIT_EINVAL;
+  if (hits->n_hits > 0 && (!hits->y || !hits->z || !hits->rowsec)) return TPCFIT_EINVAL;
+  if (!aligned(resid, 8) || !aligned(rcov, 4) || !aligned(chi2, 4) || !aligned(ndf, 4)) return TPCFIT_EINVAL;
+  if (!h->rec_valid || h->rec_tracks != n_tracks || h->rec_hits != hits->n_hits ||
+      h->rec_det != h->deterministic)
+    return TPCFIT_ESTATE;
+  cudaStream_t s = (cudaStream_t)stream;
+  tpcfit_status st = make_resident(h, s);
+  if (st != TPCFIT_OK) return st;
+  SmoothArgs a{};
+  a.y = hits->y;
+  a.z = hits->z;
+  a.rowsec = hits->rowsec;
+  a.n_hits = hits->n_hits;
+  a.off = track_offsets;
+  a.n_tracks = n_tracks;
+  a.align = h->d_align;
+  a.perm = h->sort_by_length ? h->d_perm : nullptr;
+  a.ndf = ndf;
+  a.ck = h->d_ck;
+  a.ck_last = h->d_ck_last;
+  a.ck_slots = h->ck_slots;
+  a.resid = resid;
+  a.rcov = rcov;
+  a.chi2 = chi2;
+  a.work = h->d_work;
+  int64_t need = 0;
+  cudaError_t e = h->deterministic ? smooth_store_det(need) : smooth_store_fast(need);
+  if (e != cudaSuccess) return from_cuda(e);
+  st = grow(h->d_seg, h->seg_cap, need);
+  if (st != TPCFIT_OK) return st;
+  a.seg = h->d_seg;
+  e = h->deterministic ? launch_smooth_det(a, s) : launch_smooth_fast(a, s);
+  return from_cuda(e);
+}
+
 tpcfit_status tpcfit_fit_host(tpcfit_handle* h, const float* y, const float* z, const uint16_t* rowsec,
                               int64_t n_hits, const int32_t* track_offsets, int32_t n_tracks, const float* seeds,
                               float* params_out, float* cov_out, float* chi2_out, int32_t* ndf_out, void* stream) {

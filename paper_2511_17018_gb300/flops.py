@@ -56,3 +56,19 @@ def backward_flops(lengths) -> float:
 
 def fit_adjoint_flops(lengths) -> float:
     return fit_flops(lengths) + backward_flops(lengths)
+
+
+# Two-filter smoother, per cluster: the outward filter it runs (a fit step,
+# STEP; FIRST at the first cluster) and the square-root combination of the two
+# predictions (Householder QR of the stacked 10x5 factors with the two 2x10
+# row blocks carried along: 1100; the triangular solve 30; the corrections and
+# H C H^T 54; R and chi2 20).  Recomputing the inward predictions from the
+# checkpoints is overhead and is not counted.
+SMOOTH_COMBINE = 1100 + 30 + 54 + 20
+
+
+def smooth_flops(lengths) -> float:
+    """Algorithmic flops of the smoother over all clusters of fitted tracks."""
+    n = np.asarray(lengths, dtype=np.int64)
+    n = n[n >= 1]
+    return float(np.sum((n - 1) * STEP + FIRST + n * SMOOTH_COMBINE))

@@ -62,6 +62,7 @@ def load():
         "tpcfit_fit_frames": (C.c_int, [vp, C.POINTER(_Hits), vp, i32, vp, i32, vp, vp, i64, vp, vp, vp, vp, vp,
                                         vp]),
         "tpcfit_fit_backward": (C.c_int, [vp, C.POINTER(_Hits), vp, i32, vp, vp, vp, vp, vp, vp]),
+        "tpcfit_smooth": (C.c_int, [vp, C.POINTER(_Hits), vp, i32, vp, vp, vp, vp, vp]),
         "tpcfit_set_rtc": (C.c_int, [vp, C.c_int, C.c_char_p]),
         "tpcfit_rtc_build": (C.c_int, [C.POINTER(_Geometry), C.c_double, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int,
                                        C.c_char_p]),
@@ -244,6 +245,20 @@ def tpcfit_fit_backward(h, y, z, rowsec, offsets, ndf, grad_chi2, grad_align, gr
     _check(st, "tpcfit_fit_backward")
 
 
+def tpcfit_smooth(h, y, z, rowsec, offsets, ndf, resid, rcov, chi2, stream=None) -> None:
+    """Enqueue the two-filter smoother of the last recorded fit (device tensors; see include/tpcfit.h)."""
+    import torch
+    n = int(offsets.numel()) - 1
+    H = int(y.numel())
+    hits = _Hits(_dev(y, torch.float32, "y"), _dev(z, torch.float32, "z"), _dev(rowsec, torch.int16, "rowsec"), H)
+    if resid.numel() != 2 * H or rcov.numel() != 3 * H or chi2.numel() != H:
+        raise ValueError("smoother output sizes do not match the clusters")
+    st = load().tpcfit_smooth(h, C.byref(hits), _dev(offsets, torch.int32, "offsets"), n, _dev(ndf, torch.int32, "ndf"),
+                              _dev(resid, torch.float32, "resid"), _dev(rcov, torch.float32, "rcov"),
+                              _dev(chi2, torch.float32, "chi2"), _stream(stream))
+    _check(st, "tpcfit_smooth")
+
+
 def tpcfit_fit_host(h, y, z, rowsec, offsets, seeds, stream=None, out=None):
     """Fit from host arrays (numpy or pinned CPU tensors); returns host outputs."""
     def arr(a, dt):
@@ -364,6 +379,18 @@ class Fitter:
 
     def set_record(self, record: bool):
         tpcfit_set_record(self.h, record)
+
+    def smooth(self, dev: dict, out: dict, stream=None) -> dict:
+        """Per-cluster leave-one-out residuals of the last recorded fit."""
+        import torch
+        H = int(dev["y"].numel())
+        d = dev["y"].device
+        res = dict(resid=torch.empty((H, 2), dtype=torch.float32, device=d),
+                   rcov=torch.empty((H, 3), dtype=torch.float32, device=d),
+                   chi2=torch.empty(H, dtype=torch.float32, device=d))
+        tpcfit_smooth(self.h, dev["y"], dev["z"], dev["rowsec"], dev["offsets"], out["ndf"], res["resid"], res["rcov"],
+                      res["chi2"], stream)
+        return res
 
     def backward(self, dev: dict, out: dict, grad_chi2, grad_meas=None, stream=None):
         """Gradients of sum_i grad_chi2[i] chi2_i for the last recorded fit."""
