@@ -183,11 +183,16 @@ template <class S> struct Geo {
   S sa[kNSectorsPerSide][kNSectorsPerSide];
   S kappa;
   S v_meas, c0, max_snp;
+  // material along the path (off when mat = false): inverse radiation length,
+  // minimum-ionising energy loss, squared mass of the particle (a pion)
+  bool mat;
+  S x0_inv, dedx, mass2, d_row;
 };
 
 // Rotation angle from sector a to b: m = (b - a) mod 18 taken in [-8, 9],
 // dalpha = m * (w * pi / 180), cos / sin in FP64, then the constant type.
-template <class S> void make_geo(Geo<S>& g, const double* row_x, int n_rows, double width_deg, double bz) {
+template <class S> void make_geo(Geo<S>& g, const double* row_x, int n_rows, double width_deg, double bz,
+                                  double x0_cm = 0.0, double dedx = 0.0, double mass = 0.0, double d_row = 0.0) {
   g.n_rows = n_rows;
   for (int r = 0; r < n_rows; ++r) g.row_x[r] = (S)row_x[r];
   const double w_rad = width_deg * 3.14159265358979323846 / 180.0;
@@ -203,6 +208,11 @@ template <class S> void make_geo(Geo<S>& g, const double* row_x, int n_rows, dou
   g.v_meas = (S)0.01;   // sigma_y = sigma_z = 0.1 cm
   g.c0 = (S)100.0;      // initial covariance diag(1e2)
   g.max_snp = (S)0.999;
+  g.mat = x0_cm > 0.0 && std::isfinite(x0_cm);
+  g.x0_inv = (S)(g.mat ? 1.0 / x0_cm : 0.0);
+  g.dedx = (S)(g.mat ? dedx : 0.0);
+  g.mass2 = (S)(mass * mass);
+  g.d_row = (S)d_row;
 }
 
 // packed index of (i, j), i >= j
@@ -213,6 +223,68 @@ template <class T> struct Jac {
   bool rot;
   T yy, ys, yq, zy, zs, zt, zq, sy, ss, sq;
 };
+
+// ------------------------------------------------------------------ material
+// A thin layer of material at every pad row (a uniform material budget per
+// row), in the reading fixed for this project.  The state at a row is the one
+// the track leaves it with.  The particle is a pion.  With the state at the
+// row (s, t, q) the layer is crossed over l = d sqrt(1 + t^2) / c,
+// c = sqrt(1 - s^2) (d its thickness at normal incidence); p^2 = (1 + t^2)/q^2,
+// E^2 = p^2 + m^2, beta^2 = p^2 / E^2:
+//  * energy loss: dE = dEdx_mip l / beta^2 (the 1/beta^2 rise, no logarithmic
+//    term); E' = E - dir dE (dir = +1: crossed along the flight, which the
+//    outward pass does on arriving at a row; -1: undone, which the inward pass
+//    does before leaving a row against the flight); q' = q p / p'; the
+//    Jacobian's q row is scaled by p / p' (its dependence on the state is
+//    neglected);
+//  * multiple scattering (Highland without its logarithmic term):
+//    theta0^2 = 0.0136^2 l / X0 / (beta^2 p^2); two independent plane angles
+//    th1 (bending plane), th2: ds = c / cos(lambda) th1, dt = (1 + t^2) th2,
+//    dq = q' t th2, i.e. process noise Q = B B^T with
+//    B = [theta0 c sqrt(1 + t^2) e_s | theta0 ((1 + t^2) e_t + q' t e_q)].
+// A particle that would stop (E' <= m) makes the step impossible.
+template <class T> struct Noise {
+  T qq;        // p / p'
+  T b_s;       // B: s entry of the first column
+  T b_t, b_q;  // t and q entries of the second column
+};
+
+template <class T>
+bool material_step(const Geo<typename Traits<T>::S>& g, T p[5], int dir, Noise<T>& N) {
+  using S = typename Traits<T>::S;
+  const S one = (S)1.0;
+  const T& s = p[2];
+  const T& t = p[3];
+  const T q = p[4];
+  const T q2 = q * q;
+  if (!(V(q2) > 0.0)) {  // infinite momentum: no scattering, no loss
+    N.qq = T(one);
+    N.b_s = T((S)0.0);
+    N.b_t = T((S)0.0);
+    N.b_q = T((S)0.0);
+    return true;
+  }
+  const T tt1 = one + t * t;
+  const T c = Sqrt((one - s) * (one + s));
+  const T st1 = Sqrt(tt1);
+  const T ell = (g.d_row * st1) / c;
+  const T p2 = tt1 / q2;
+  const T e2 = p2 + g.mass2;
+  const T th2 = (((S)(0.0136 * 0.0136) * ell) * g.x0_inv) * (e2 / (p2 * p2));
+  const T de = (g.dedx * ell) * (e2 / p2);
+  const T e = Sqrt(e2);
+  const T en = dir > 0 ? e - de : e + de;
+  const T pn2 = en * en - g.mass2;
+  if (!(V(pn2) > 0.0)) return false;
+  const T ratio = Sqrt(p2 / pn2);
+  p[4] = q * ratio;
+  const T th = Sqrt(th2);
+  N.qq = ratio;
+  N.b_s = (th * c) * st1;
+  N.b_t = th * tt1;
+  N.b_q = (th * p[4]) * t;
+  return true;
+}
 
 // ------------------------------------------------------------------ one prediction step
 // Moves state (p, x) in sector sec_from to pad row X in sector sec_to:
@@ -359,6 +431,15 @@ template <class T> struct Filter<T, false> {
   }
   void transport_(const Jac<T>& J) { transport<T>(C, J); }
   void cov(T out[15]) const { for (int e = 0; e < 15; ++e) out[e] = C[e]; }
+  // C <- D C D + B B^T, D = diag(1, 1, 1, 1, qq)
+  void material_(const Noise<T>& N) {
+    for (int j = 0; j < 4; ++j) C[P(4, j)] = C[P(4, j)] * N.qq;
+    C[P(4, 4)] = (C[P(4, 4)] * N.qq) * N.qq;
+    C[P(2, 2)] = C[P(2, 2)] + N.b_s * N.b_s;
+    C[P(3, 3)] = C[P(3, 3)] + N.b_t * N.b_t;
+    C[P(4, 3)] = C[P(4, 3)] + N.b_q * N.b_t;
+    C[P(4, 4)] = C[P(4, 4)] + N.b_q * N.b_q;
+  }
 
   // 2D measurement of (y, z), V = diag(v, v).  Gain from the 2x2 innovation
   // covariance S; chi2 increment r^T S^-1 r with the predicted residual r.
@@ -441,6 +522,44 @@ template <class T> struct Filter<T, true> {
       L[1][c] = nz;
       L[2][c] = ns;
     }
+  }
+  // L <- D L, then the noise folded in: with X = [L^T; B^T] (7x5) and its
+  // Householder QR X = Q R, L R^T R = L L^T + B B^T, so L <- R^T (lower
+  // triangular).  Canonical sequence, column k = 0..4: |x|^2 of rows k..6 (row
+  // ascending), alpha = -sign(x_k) |x|, v = x - alpha e_k, g = 1 / (alpha v_k);
+  // every later column j (ascending): t = (v_k X_kj + sum_{r>k} X_rk X_rj) g,
+  // X_kj += t v_k, X_rj += t X_rk (r ascending); then X_kk = alpha.
+  void material_(const Noise<T>& N) {
+    using SS = typename Traits<T>::S;
+    for (int c = 0; c < 5; ++c) L[4][c] = L[4][c] * N.qq;
+    T X[7][5];
+    for (int r = 0; r < 5; ++r)
+      for (int i = 0; i < 5; ++i) X[r][i] = L[i][r];
+    for (int i = 0; i < 5; ++i) {
+      X[5][i] = T((SS)0.0);
+      X[6][i] = T((SS)0.0);
+    }
+    X[5][2] = N.b_s;
+    X[6][3] = N.b_t;
+    X[6][4] = N.b_q;
+    for (int k = 0; k < 5; ++k) {
+      T nrm2 = X[k][k] * X[k][k];
+      for (int r = k + 1; r < 7; ++r) nrm2 = nrm2 + X[r][k] * X[r][k];
+      const T nrm = Sqrt(nrm2);
+      const T alpha = V(X[k][k]) > 0.0 ? T((SS)0.0) - nrm : nrm;
+      const T v0 = X[k][k] - alpha;
+      const T gk = T((SS)1.0) / (alpha * v0);
+      for (int j = k + 1; j < 5; ++j) {
+        T t = v0 * X[k][j];
+        for (int r = k + 1; r < 7; ++r) t = t + X[r][k] * X[r][j];
+        t = t * gk;
+        X[k][j] = X[k][j] + t * v0;
+        for (int r = k + 1; r < 7; ++r) X[r][j] = X[r][j] + t * X[r][k];
+      }
+      X[k][k] = alpha;
+    }
+    for (int i = 0; i < 5; ++i)
+      for (int j = 0; j < 5; ++j) L[i][j] = j <= i ? X[j][i] : T((SS)0.0);
   }
   // C_ij = sum_c L_ic L_jc, c ascending
   void cov(T out[15]) const {
@@ -568,6 +687,11 @@ FitResult fit_track(const Geo<typename Traits<T>::S>& g, const HitView<T>& h, co
   // sector rotation the absolute position is formed, rotated and re-referenced.
   // The FP64 and dual instantiations keep absolute coordinates.
   auto step = [&](int from, int to, int pass) -> bool {
+    if (g.mat && pass == 1) {  // the layer of the row left against the flight, undone first
+      Noise<T> N;
+      if (!material_step<T>(g, p, -1, N)) return false;
+      F.material_(N);
+    }
     const int r = hit_row(h, to);
     if (r < 0 || r >= g.n_rows) return false;
     Jac<T> J;
@@ -615,6 +739,11 @@ FitResult fit_track(const Geo<typename Traits<T>::S>& g, const HitView<T>& h, co
     for (int i = 0; i < 5; ++i) p[i] = pn[i];
     x = xn;
     F.transport_(J);
+    if (g.mat && pass == 0) {  // the layer of the row arrived at, crossed along the flight
+      Noise<T> N;
+      if (!material_step<T>(g, p, 1, N)) return false;
+      F.material_(N);
+    }
     T m[2] = {mt[0], mt[1]};
     if (kRes && !ref) {
       m[0] = T((S)0.0);
@@ -690,6 +819,10 @@ struct OracleGeometry {
   int32_t n_rows;
   int32_t n_sectors;
   double sector_width_deg;
+  double x0_cm;        // radiation length of the material (<= 0: no material)
+  double dedx_gev_cm;  // minimum-ionising energy loss
+  double mass_gev;     // particle mass
+  double row_cm;       // thickness of the material layer at each pad row (normal incidence)
 };
 
 int check_inputs(const OracleGeometry* geo, int32_t n_tracks, const int32_t* off) {
@@ -708,7 +841,8 @@ int fit_all(const OracleGeometry* geo, double bz, int32_t n_tracks, const int32_
   using S = typename Traits<T>::S;
   if (check_inputs(geo, n_tracks, off)) return 1;
   Geo<S> g;
-  make_geo<S>(g, geo->row_x, geo->n_rows, geo->sector_width_deg, bz);
+  make_geo<S>(g, geo->row_x, geo->n_rows, geo->sector_width_deg, bz, geo->x0_cm, geo->dedx_gev_cm, geo->mass_gev, geo->row_cm);
+  if (g.mat && ref) return 1;  // the linearised filter has no material
   const T nan = T((S)NAN);
 #pragma omp parallel for schedule(dynamic, 64) num_threads(nthreads > 0 ? nthreads : 1)
   for (int32_t i = 0; i < n_tracks; ++i) {
@@ -808,7 +942,7 @@ int oracle_grad_f64(const OracleGeometry* geo, double bz, int32_t n_tracks, cons
   for (int32_t i = 0; i < n_tracks; ++i)
     if (off[i + 1] - off[i] > 152) return 1;
   Geo<double> g;
-  make_geo<double>(g, geo->row_x, geo->n_rows, geo->sector_width_deg, bz);
+  make_geo<double>(g, geo->row_x, geo->n_rows, geo->sector_width_deg, bz, geo->x0_cm, geo->dedx_gev_cm, geo->mass_gev, geo->row_cm);
 #pragma omp parallel for schedule(dynamic, 4) num_threads(nthreads > 0 ? nthreads : 1)
   for (int32_t i = 0; i < n_tracks; ++i) {
     const int n = off[i + 1] - off[i];

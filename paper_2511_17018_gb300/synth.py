@@ -58,6 +58,22 @@ def default_geometry() -> Geometry:
     return Geometry()
 
 
+@dataclass
+class Material:
+    """A thin material layer at every pad row: radiation length (cm) and
+    minimum-ionising energy loss (GeV/cm) of the material, its thickness at
+    normal incidence (cm) and the particle's mass (a pion)."""
+    x0_cm: float
+    dedx_gev_cm: float
+    mass_gev: float = 0.13957
+    row_cm: float = 160.0 / 151.0
+
+
+# TPC drift gas (Ne-CO2-N2 90-10-5 at 1 atm): X0 ~ 3.1e4 cm, dE/dx_mip ~ 1.6 MeV/m;
+# one row pitch of gas per row.
+TPC_GAS = Material(3.1e4, 1.6e-5)
+
+
 def sector_alpha(sector, width_deg: float = 20.0):
     """Azimuth of a sector's centre in radians (A and C side share alphas)."""
     return ((np.asarray(sector) % 18) + 0.5) * (width_deg * math.pi / 180.0)
@@ -84,6 +100,7 @@ class Frame:
     y64: np.ndarray | None = None     # float64 copies of the hits (noise-free closed-form tests)
     z64: np.ndarray | None = None
     seeds64: np.ndarray | None = None
+    material: Material | None = None  # material the tracks crossed (for the fit's material correction)
 
     @property
     def n_tracks(self) -> int:
@@ -109,7 +126,7 @@ class Frame:
                      self.seeds[:, idx].copy(), self.truth[:, idx].copy(), self.d_true,
                      None if self.y64 is None else self.y64[gather].copy(),
                      None if self.z64 is None else self.z64[gather].copy(),
-                     None if self.seeds64 is None else self.seeds64[:, idx].copy())
+                     None if self.seeds64 is None else self.seeds64[:, idx].copy(), self.material)
 
 
 def _wrap(a):
@@ -385,3 +402,96 @@ def config4(pool_tracks: int = 1_000_000, n_frames: int = 256, seed: int = 4):
     rng = _streams(seed + 1000, ["pick"])["pick"]
     picks = [rng.integers(0, pool.n_tracks, int(s)) for s in sizes]
     return pool, picks
+
+
+def simulate_material(qpt, tanl, phi0, z0, geometry: Geometry, bz: float, material: Material, *, rng=None,
+                      scatter: bool = True, eloss: bool = True, smear: float = 0.1, sector: int = 0):
+    """Tracks through thin material layers at the pad rows, row by row, in the
+    local frame of one sector (the caller picks tracks that stay in it).
+    Between two rows the track follows the exact circle through its current
+    point and direction (centre form, as ``simulate``).  At a row it crosses the
+    layer over l = d sqrt(1 + t^2) / cos(phi): the energy drops by
+    dE = dEdx l / beta^2 and the direction turns by two independent plane
+    angles drawn from N(0, theta0), theta0^2 = 0.0136^2 l / X0 / (beta p)^2
+    (Highland without its logarithmic term; phi by th1 / cos(lambda), lambda by
+    th2), before the cluster is recorded: the state at a cluster is the one the
+    track leaves it with.  Tracks that leave the sector, curl or stop are cut
+    there.  Returns a Frame (material attached) with truth at the first
+    cluster."""
+    rng = np.random.default_rng(0) if rng is None else rng
+    kappa = KAPPA_PER_TESLA * bz
+    width = geometry.sector_width_deg * math.pi / 180.0
+    half_tan = math.tan(0.5 * width)
+    alpha = (sector % 18 + 0.5) * width
+    m2 = material.mass_gev ** 2
+    ys, zs, secs, rows, offs, truth = [], [], [], [], [0], []
+    for i in range(len(qpt)):
+        q = float(qpt[i]); t = float(tanl[i]); phi = float(phi0[i]) - alpha
+        # start: the vertex (0, 0, z0) in global = local (0, 0) for the sector frame
+        x, y, z = 0.0, 0.0, float(z0[i])
+        hy, hz, hr = [], [], []
+        first = None
+        for r in range(geometry.n_rows):
+            X = float(geometry.row_x[r])
+            k = kappa * q
+            if abs(k) < 1e-15:
+                if math.cos(phi) <= 1e-9:
+                    break
+                dxl = X - x
+                y2 = y + dxl * math.tan(phi)
+                lt = dxl / math.cos(phi)
+                phi2 = phi
+            else:
+                xc = x - math.sin(phi) / k
+                yc = y + math.cos(phi) / k
+                u = k * (X - xc)
+                if abs(u) >= 0.99:
+                    break
+                phi2 = math.asin(u)
+                y2 = yc - math.cos(phi2) / k
+                lt = (phi2 - phi) / k
+            if lt <= 0.0 or abs(y2) > X * half_tan:
+                break
+            z2 = z + t * lt
+            if abs(z2) > geometry.z_max:
+                break
+            x, y, z, phi = X, y2, z2, phi2
+            # the row's material layer, crossed on arrival; the state recorded
+            # at the row is the one the track leaves it with
+            ell = material.row_cm * math.sqrt(1.0 + t * t) / math.cos(phi)
+            p2 = (1.0 + t * t) / (q * q)
+            e2 = p2 + m2
+            if eloss:
+                en = math.sqrt(e2) - material.dedx_gev_cm * ell * e2 / p2
+                pn2 = en * en - m2
+                if pn2 <= 0.0:
+                    break
+                q = math.copysign(math.sqrt((1.0 + t * t) / pn2), q)
+            if scatter:
+                th0 = math.sqrt(0.0136 ** 2 * ell / material.x0_cm * e2 / (p2 * p2))
+                th1, th2 = rng.normal(0.0, th0, 2)
+                lam = math.atan(t)
+                phi += th1 / math.cos(lam)
+                tn = math.tan(lam + th2)
+                q = q * math.sqrt((1.0 + tn * tn) / (1.0 + t * t))  # |p| kept: pt follows the new dip
+                t = tn
+            hy.append(y); hz.append(z); hr.append(r)
+            if first is None:
+                first = (y, z, math.sin(phi), t, q)
+        if len(hy) < 10:
+            continue
+        ys += hy; zs += hz; rows += hr; secs += [sector + (18 if zz < 0 else 0) for zz in hz]
+        offs.append(offs[-1] + len(hy))
+        truth.append(first)
+    y64 = np.asarray(ys); z64 = np.asarray(zs)
+    if smear > 0.0:
+        y64 = y64 + rng.normal(0.0, smear, y64.shape[0])
+        z64 = z64 + rng.normal(0.0, smear, z64.shape[0])
+    rowsec = ((np.asarray(rows, np.int64) << ROWSEC_SHIFT) | np.asarray(secs, np.int64)).astype(np.uint16)
+    n = len(truth)
+    fr = Frame(geometry, bz, y64.astype(np.float32), z64.astype(np.float32), rowsec,
+               np.asarray(offs, np.int32), np.zeros((5, n), np.float32), np.asarray(truth, np.float64).T.reshape(5, n),
+               None, y64, z64, None, material)
+    fr.seeds64 = three_point_seeds(fr, as_f64=True)
+    fr.seeds = fr.seeds64.astype(np.float32)
+    return fr

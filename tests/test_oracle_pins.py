@@ -503,3 +503,76 @@ def test_forward_mode_gradient_matches_central_differences(oracle_mod, synth):
             gs[c, i] = (L(y, z, sp) - L(y, z, sm)) / 2e-5
     assert np.abs(gr["grad_seed"] - gs).max() < 1e-5 * np.abs(gfd).max()
     assert np.linalg.norm(gr["grad_seed"] - gs) < 0.1 * np.linalg.norm(gs)
+
+
+# ---------------------------------------------------------------- material (per-row layers)
+def _material_tracks(synth, n, seed, **kw):
+    """Tracks of 2-5 GeV/c near the centre of sector 0 (they stay in it)
+    through thick layers (X0 = 300 cm, 0.2 MeV/cm per cm of layer)."""
+    rng = np.random.default_rng(seed)
+    qpt = rng.choice([-1, 1], n) / rng.uniform(2.0, 5.0, n)
+    tanl = rng.uniform(-0.5, 0.5, n)
+    phi0 = np.full(n, 0.5 * math.pi / 9) + rng.uniform(-0.03, 0.03, n)
+    z0 = rng.normal(0, 5, n)
+    mat = synth.Material(300.0, 2e-4)
+    return synth.simulate_material(qpt, tanl, phi0, z0, synth.default_geometry(), 0.5, mat, rng=rng, **kw), mat
+
+
+def test_material_pulls_are_standard_normal(oracle_mod, synth):
+    # the generator scatters the direction by drawn angles and lowers the energy
+    # row by row (not through the fit's covariance formulas); with the material
+    # correction the fitted parameters scatter as their covariance says, without
+    # it they do not
+    fr, mat = _material_tracks(synth, 400, 1)
+    pulls = {}
+    for use in (True, False):
+        fr.material = mat if use else None
+        r = oracle_mod.fit(fr, "f64")
+        ok = r["ndf"] > 0
+        C = oracle_mod.unpack(r["cov"][:, ok])
+        sig = np.sqrt(np.stack([C[i, i] for i in range(5)]))
+        pulls[use] = (r["params"][:, ok] - fr.truth[:, ok]) / sig
+    p = pulls[True]
+    assert np.all(np.abs(p.mean(axis=1)) < 0.15), p.mean(axis=1)
+    assert np.all((p.std(axis=1) > 0.88) & (p.std(axis=1) < 1.12)), p.std(axis=1)
+    assert pulls[False].std(axis=1).max() > 2.0
+
+
+def test_material_noise_free_energy_loss(oracle_mod, synth):
+    # energy loss without scattering or smearing: the refit to convergence returns
+    # the generating parameters (the inward pass undoes a layer with the momentum
+    # after it, a second-order difference); without the correction q/pt is off
+    fr, mat = _material_tracks(synth, 40, 3, scatter=False, smear=0.0)
+    seeds = fr.seeds64.copy()
+    for _ in range(4):
+        r = oracle_mod.fit(fr, "f64", exact_inputs=True, seeds=seeds)
+        seeds = r["params"].copy()
+    assert np.all(r["ndf"] > 0)
+    assert np.abs(r["params"][:4] - fr.truth[:4]).max() < 1e-7
+    assert (np.abs(r["params"][4] - fr.truth[4]) / np.abs(fr.truth[4])).max() < 1e-7
+    fr.material = None
+    r0 = oracle_mod.fit(fr, "f64", exact_inputs=True, seeds=seeds)
+    assert (np.abs(r0["params"][4] - fr.truth[4]) / np.abs(fr.truth[4])).max() > 1e-3
+
+
+@pytest.mark.parametrize("thick", [False, True])
+def test_material_square_root_form_equals_covariance_form(oracle_mod, synth, thick):
+    # C <- D C D + B B^T (covariance form) against L <- R^T of the QR of
+    # [(D L)^T; B^T] (square-root form), both in FP64
+    fr = synth.generate(1000, 5, drop_p=0.05, cap_lengths=True)
+    fr.material = synth.Material(300.0, 2e-4) if thick else synth.TPC_GAS
+    a = oracle_mod.fit(fr, "f64")
+    b = oracle_mod.fit(fr, "sqrt_f64")
+    assert np.array_equal(a["ndf"], b["ndf"])
+    ok = a["ndf"] > 0
+    assert np.allclose(a["params"][:, ok], b["params"][:, ok], rtol=1e-8, atol=1e-10)
+    assert np.allclose(a["cov"][:, ok], b["cov"][:, ok], rtol=1e-6, atol=1e-14)
+    assert np.allclose(a["chi2"][ok], b["chi2"][ok], rtol=1e-8)
+
+
+def test_material_strict_fp32_within_fast_mode_tolerance(oracle_mod, synth):
+    from paper_2511_17018_gb300 import tolerance
+    fr = synth.generate(3000, 6, drop_p=0.05, cap_lengths=True)
+    fr.material = synth.TPC_GAS
+    rep = tolerance.compare_to_fp64(oracle_mod.fit(fr, "f32"), oracle_mod.fit(fr, "f64"))
+    assert rep["ok"], rep
