@@ -736,14 +736,14 @@ FitResult fit_track(const Geo<typename Traits<T>::S>& g, const HitView<T>& h, co
       pn[3] = fr[3] + d[3];
       pn[4] = fr[4] + d[4];
     }
+    Noise<T> N;
+    // the layer of the row arrived at, crossed along the flight (a particle
+    // that stops there ends the pass with the state before the step)
+    if (g.mat && pass == 0 && !material_step<T>(g, pn, 1, N)) return false;
     for (int i = 0; i < 5; ++i) p[i] = pn[i];
     x = xn;
     F.transport_(J);
-    if (g.mat && pass == 0) {  // the layer of the row arrived at, crossed along the flight
-      Noise<T> N;
-      if (!material_step<T>(g, p, 1, N)) return false;
-      F.material_(N);
-    }
+    if (g.mat && pass == 0) F.material_(N);
     T m[2] = {mt[0], mt[1]};
     if (kRes && !ref) {
       m[0] = T((S)0.0);
