@@ -716,8 +716,6 @@ FitResult fit_track(const Geo<typename Traits<T>::S>& g, const HitView<T>& h, co
           pn[0] = pn[0] + (my - mt[0]);
           pn[1] = pn[1] + (mz - mt[1]);
         }
-        my = mt[0];
-        mz = mt[1];
       } else if (!predict<T>(g, p, x, hit_sec(h, from), hit_sec(h, to), g.row_x[r], pn, xn, J)) {
         return false;
       }
@@ -740,8 +738,14 @@ FitResult fit_track(const Geo<typename Traits<T>::S>& g, const HitView<T>& h, co
     // the layer of the row arrived at, crossed along the flight (a particle
     // that stops there ends the pass with the state before the step)
     if (g.mat && pass == 0 && !material_step<T>(g, pn, 1, N)) return false;
+    // the step is taken: state, position and (residual form) the reference
+    // measurement move to the new cluster together
     for (int i = 0; i < 5; ++i) p[i] = pn[i];
     x = xn;
+    if (kRes && !ref) {
+      my = mt[0];
+      mz = mt[1];
+    }
     F.transport_(J);
     if (g.mat && pass == 0) F.material_(N);
     T m[2] = {mt[0], mt[1]};
