@@ -481,6 +481,16 @@ def main():
         rtc = {"ms": statistics.mean(p[0] for p in rtc_per), "first_call_s": first_s}
         fitter.set_rtc(False)
 
+    # ---- the same plain fit with the material layers of the TPC gas at every row
+    from paper_2511_17018_gb300 import synth as _synth
+    fitter.set_material(_synth.TPC_GAS)
+    for _ in range(args.warmup):
+        fitter.fit(dev, out)
+    torch.cuda.synchronize()
+    _, mat_per = timed(step_fit, plain_steps)
+    mat_ms = statistics.mean(p[0] for p in mat_per)
+    fitter.set_material(None)
+
     # ---- end to end through the public API with host buffers
     h2d = 10 * fr.n_hits + 4 * (fr.n_tracks + 1) + 20 * fr.n_tracks
     d2h = 88 * fr.n_tracks
@@ -546,6 +556,9 @@ def main():
                         "ms": smooth_ms, "achieved_tflops": sm_tf, "frac": sm_tf / peak_tf,
                         "kernel": "smooth_kernel<8> (two-filter smoother of the recorded fit)",
                         "algorithmic_flops_per_launch": flops.smooth_flops(lengths)}
+    line["plain_fit"]["material"] = {"tracks_per_s": fr.n_tracks / (mat_ms / 1e3), "ms": mat_ms,
+                                     "material": "TPC gas layer at every row (X0 3.1e4 cm, 1.6 MeV/m, one row pitch)",
+                                     "kernel": "fit_kernel<4,24> with the material layers"}
     if rtc is not None:
         rtc_tf = fit_fl / (rtc["ms"] / 1e3) / 1e12
         line["plain_fit"]["rtc"] = {"tracks_per_s": fr.n_tracks / (rtc["ms"] / 1e3), "ms": rtc["ms"],

@@ -155,6 +155,20 @@ tpcfit_status tpcfit_fit_frames(tpcfit_handle* h, const tpcfit_hits* hits, const
                                 const float* seeds, float* params_out, float* cov_out, float* chi2_out,
                                 int32_t* ndf_out, void* stream);
 
+/* Material correction (Sec. 4: the material budget is part of the shared
+ * propagation): a thin layer at every pad row, of radiation length x0_cm,
+ * minimum-ionising energy loss dedx_gev_cm and thickness row_cm at normal
+ * incidence, for a particle of mass mass_gev.  The state at a row is the one
+ * the track leaves it with; the outward pass crosses a row's layer on
+ * arriving, the inward pass undoes it before leaving the row.  A layer is
+ * crossed over l = row_cm sqrt(1 + tan^2 lambda) / cos phi; the energy drops by
+ * dedx l / beta^2 and the direction scatters with the Highland angle (without
+ * its logarithmic term), added as process noise.  x0_cm <= 0: no material
+ * (default).  The fit, the smoother and the batched and run-time-compiled
+ * fits follow it; tpcfit_fit_backward answers ESTATE while material is set.
+ * EINVAL for non-finite or non-positive values. */
+tpcfit_status tpcfit_set_material(tpcfit_handle* h, double x0_cm, double dedx_gev_cm, double mass_gev, double row_cm);
+
 /* Run-time compilation of the fit (Sec. 5).  enable = 1: tpcfit_fit and
  * tpcfit_fit_frames run a fit kernel compiled with NVRTC for this handle's
  * geometry, field, mode and launch shape, in which those per-time-frame values

@@ -477,6 +477,8 @@ __device__ __forceinline__ void fetch_ckpt(float4* sdst, const float* ck) {
 // residual coordinates).  my, mz: measurement of the previous cluster on
 // entry, of this cluster on exit.  conv: the first step of the outward pass,
 // whose state is the seed in absolute coordinates.
+// MAT: the material layers of the rows (the smoother; the adjoint runs without).
+template <bool MAT = false>
 __device__ __forceinline__ void step_fwd(const SmemTables& T, StepState& S, float& my, float& mz, bool first, bool conv,
                                          int row, int sec18, float m0, float m1) {
   float chi2 = 0.0f;
@@ -491,12 +493,19 @@ __device__ __forceinline__ void step_fwd(const SmemTables& T, StepState& S, floa
     float pn[5];
     Jac J;
     PredTape tp;
+    MatNoise N;
+    if (MAT && !conv) {  // inward: the layer of the row left
+      material_step(S.p, -1, N);
+      material_factor(S.L, N);
+    }
     predict_residual(T, S.p, S.x, S.sec, my, mz, sec18, T.row_x[row], m0, m1, pn, J, tp);
+    if (MAT && conv) material_step(pn, 1, N);
 #pragma unroll
     for (int c = 0; c < 5; ++c) S.p[c] = pn[c];
     S.x = T.row_x[row];
     S.sec = sec18;
     transport(S.L, J);
+    if (MAT && conv) material_factor(S.L, N);
   }
   my = m0;
   mz = m1;

@@ -397,6 +397,100 @@ __device__ __forceinline__ void scalar_update(float p[5], float L[5][5], float& 
   for (int c = 0; c < 5; ++c) L[H][c] = a[c] * beta;
 }
 
+// ---------------------------------------------------------------- material
+// A thin material layer at every pad row (c_geo.mat): the state at a row is
+// the one the track leaves it with; the outward pass crosses a row's layer on
+// arriving (dir = +1), the inward pass undoes it before leaving the row
+// against the flight (dir = -1).  Path through the layer
+// l = d sqrt(1 + t^2) / c; energy loss dE/dx_mip l / beta^2 (pion); multiple
+// scattering with the Highland angle (no logarithmic term) as the process
+// noise Q = B B^T; the q row of the factor scaled by p / p'.  Returns false if
+// the particle would stop.  The operation sequence is the canonical one of the
+// strict-FP32 reference (the deterministic mode matches it bit for bit).
+struct MatNoise {
+  float qq, b_s, b_t, b_q;
+};
+
+__device__ __forceinline__ bool material_step(float p[5], int dir, MatNoise& N) {
+  const float s = p[2];
+  const float t = p[3];
+  const float q = p[4];
+  const float q2 = q * q;
+  if (!(q2 > 0.0f)) {
+    N.qq = 1.0f;
+    N.b_s = N.b_t = N.b_q = 0.0f;
+    return true;
+  }
+  const float tt1 = 1.0f + t * t;
+  const float c = sqrtf((1.0f - s) * (1.0f + s));
+  const float st1 = sqrtf(tt1);
+  const float ell = (c_geo.d_row * st1) / c;
+  const float p2 = tt1 / q2;
+  const float e2 = p2 + c_geo.mass2;
+  const float th2 = ((static_cast<float>(0.0136 * 0.0136) * ell) * c_geo.x0_inv) * (e2 / (p2 * p2));
+  const float de = (c_geo.dedx * ell) * (e2 / p2);
+  const float e = sqrtf(e2);
+  const float en = dir > 0 ? e - de : e + de;
+  const float pn2 = en * en - c_geo.mass2;
+  if (!(pn2 > 0.0f)) return false;
+  const float ratio = sqrtf(p2 / pn2);
+  p[4] = q * ratio;
+  const float th = sqrtf(th2);
+  N.qq = ratio;
+  N.b_s = (th * c) * st1;
+  N.b_t = th * tt1;
+  N.b_q = (th * p[4]) * t;
+  return true;
+}
+
+// L <- D L (D = diag(1, 1, 1, 1, qq)), then B folded in: the Householder QR of
+// X = [L^T; B^T] (7x5) gives L L^T + B B^T = R^T R, and L <- R^T.  Column k:
+// |x|^2 of rows k..6, alpha = -sign(x_k) |x|, v = x - alpha e_k,
+// g = 1 / (alpha v_k); later columns j: t = (v_k X_kj + sum_r X_rk X_rj) g,
+// X_kj += t v_k, X_rj += t X_rk; X_kk = alpha.
+__device__ __forceinline__ void material_factor(float L[5][5], const MatNoise& N) {
+#pragma unroll
+  for (int c = 0; c < 5; ++c) L[4][c] = L[4][c] * N.qq;
+  float X[7][5];
+#pragma unroll
+  for (int r = 0; r < 5; ++r)
+#pragma unroll
+    for (int i = 0; i < 5; ++i) X[r][i] = L[i][r];
+#pragma unroll
+  for (int i = 0; i < 5; ++i) {
+    X[5][i] = 0.0f;
+    X[6][i] = 0.0f;
+  }
+  X[5][2] = N.b_s;
+  X[6][3] = N.b_t;
+  X[6][4] = N.b_q;
+#pragma unroll
+  for (int k = 0; k < 5; ++k) {
+    float nrm2 = X[k][k] * X[k][k];
+#pragma unroll
+    for (int r = k + 1; r < 7; ++r) nrm2 = nrm2 + X[r][k] * X[r][k];
+    const float nrm = sqrtf(nrm2);
+    const float alpha = X[k][k] > 0.0f ? 0.0f - nrm : nrm;
+    const float v0 = X[k][k] - alpha;
+    const float gk = 1.0f / (alpha * v0);
+#pragma unroll
+    for (int j = k + 1; j < 5; ++j) {
+      float t = v0 * X[k][j];
+#pragma unroll
+      for (int r = k + 1; r < 7; ++r) t = t + X[r][k] * X[r][j];
+      t = t * gk;
+      X[k][j] = X[k][j] + t * v0;
+#pragma unroll
+      for (int r = k + 1; r < 7; ++r) X[r][j] = X[r][j] + t * X[r][k];
+    }
+    X[k][k] = alpha;
+  }
+#pragma unroll
+  for (int i = 0; i < 5; ++i)
+#pragma unroll
+    for (int j = 0; j < 5; ++j) L[i][j] = j <= i ? X[j][i] : 0.0f;
+}
+
 __device__ __forceinline__ void reset_factor(float L[5][5]) {
 #pragma unroll
   for (int i = 0; i < 5; ++i)
@@ -507,7 +601,7 @@ __device__ __forceinline__ void write_ckpt(const FitArgs& a, int pass, int begin
   for (int j = 0; j < 9; ++j) dst[j] = make_float4(v[4 * j], v[4 * j + 1], v[4 * j + 2], v[4 * j + 3]);
 }
 
-template <int RPS, int WARPS, int MINB, bool RECORD, bool FRAMES>
+template <int RPS, int WARPS, int MINB, bool RECORD, bool FRAMES, bool MAT>
 __global__ void __launch_bounds__(WARPS * 32, MINB) fit_kernel(FitArgs a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   BlockSmem& B = *reinterpret_cast<BlockSmem*>(smem_raw);
@@ -639,9 +733,25 @@ __global__ void __launch_bounds__(WARPS * 32, MINB) fit_kernel(FitArgs a) {
           } else {
             float pn[5];
             Jac J;
+            if (MAT && pass == 1) {  // the layer of the row left, undone against the flight
+              MatNoise N;
+              if (!material_step(S.p, -1, N)) {
+                go = false;
+                status = 2;
+                continue;
+              }
+              material_factor(S.L, N);
+            }
             if (!step_predict(T, S, sec18, T.row_x[row], m0, m1, pn, J)) {
               go = false;
               if (pass == 1) status = 2;  // the inward pass must reach the first cluster
+              continue;
+            }
+            MatNoise N;
+            // the layer of the row arrived at (a particle that stops there ends
+            // the outward pass with the state before the step)
+            if (MAT && pass == 0 && !material_step(pn, 1, N)) {
+              go = false;
               continue;
             }
 #pragma unroll
@@ -651,6 +761,7 @@ __global__ void __launch_bounds__(WARPS * 32, MINB) fit_kernel(FitArgs a) {
             S.my = m0;
             S.mz = m1;
             transport(S.L, J);
+            if (MAT && pass == 0) material_factor(S.L, N);
           }
           scalar_update<0>(S.p, S.L, S.chi2, 0.0f);
           scalar_update<1>(S.p, S.L, S.chi2, 0.0f);
@@ -697,20 +808,20 @@ __global__ void __launch_bounds__(WARPS * 32, MINB) fit_kernel(FitArgs a) {
 }
 
 #ifndef __CUDACC_RTC__
-template <int RPS, int WARPS, int MINB, bool RECORD, bool FRAMES>
+template <int RPS, int WARPS, int MINB, bool RECORD, bool FRAMES, bool MAT>
 cudaError_t launch_cfg(const FitArgs& a, cudaStream_t s) {
   constexpr int kThreads = WARPS * 32;
   const size_t smem = sizeof(BlockSmem) + WARPS * sizeof(WarpStage<RPS>);
   static int grid = 0;
   if (grid == 0) {
     cudaError_t e =
-        cudaFuncSetAttribute(fit_kernel<RPS, WARPS, MINB, RECORD, FRAMES>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        cudaFuncSetAttribute(fit_kernel<RPS, WARPS, MINB, RECORD, FRAMES, MAT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     int dev = 0, sms = 0, per_sm = 0;
     e = cudaGetDevice(&dev);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     if (e == cudaSuccess)
-      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fit_kernel<RPS, WARPS, MINB, RECORD, FRAMES>, kThreads, smem);
+      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fit_kernel<RPS, WARPS, MINB, RECORD, FRAMES, MAT>, kThreads, smem);
     if (e != cudaSuccess) return e;
     if (per_sm < 1) return cudaErrorInvalidConfiguration;
     grid = sms * per_sm;
@@ -720,20 +831,25 @@ cudaError_t launch_cfg(const FitArgs& a, cudaStream_t s) {
   const int blocks = (int)(need < grid ? need : grid);
   cudaError_t e = cudaMemsetAsync(a.work, 0, sizeof(unsigned int), s);
   if (e != cudaSuccess) return e;
-  fit_kernel<RPS, WARPS, MINB, RECORD, FRAMES><<<blocks, kThreads, smem, s>>>(a);
+  fit_kernel<RPS, WARPS, MINB, RECORD, FRAMES, MAT><<<blocks, kThreads, smem, s>>>(a);
   return cudaGetLastError();
 }
 
 // Supported (rows per stage, warps per block) shapes; the shared-memory budget
 // (alignment table + double buffer) decides how many blocks fit on an SM.
+// With material the fit runs at (4, 12) or, for any other shape, (4, 24).
 template <bool RECORD, bool FRAMES>
 inline cudaError_t launch_rec(const FitArgs& a, int rps, int warps, cudaStream_t s) {
-  if (rps == 4 && warps == 8) return launch_cfg<4, 8, fit_min_blocks(4, 8), RECORD, FRAMES>(a, s);
-  if (rps == 4 && warps == 12) return launch_cfg<4, 12, fit_min_blocks(4, 12), RECORD, FRAMES>(a, s);
-  if (rps == 4 && warps == 24) return launch_cfg<4, 24, fit_min_blocks(4, 24), RECORD, FRAMES>(a, s);
-  if (rps == 8 && warps == 8) return launch_cfg<8, 8, fit_min_blocks(8, 8), RECORD, FRAMES>(a, s);
-  if (rps == 8 && warps == 16) return launch_cfg<8, 16, fit_min_blocks(8, 16), RECORD, FRAMES>(a, s);
-  if (rps == 16 && warps == 8) return launch_cfg<16, 8, fit_min_blocks(16, 8), RECORD, FRAMES>(a, s);
+  if (a.mat) {
+    if (rps == 4 && warps == 12) return launch_cfg<4, 12, fit_min_blocks(4, 12), RECORD, FRAMES, true>(a, s);
+    return launch_cfg<4, 24, fit_min_blocks(4, 24), RECORD, FRAMES, true>(a, s);
+  }
+  if (rps == 4 && warps == 8) return launch_cfg<4, 8, fit_min_blocks(4, 8), RECORD, FRAMES, false>(a, s);
+  if (rps == 4 && warps == 12) return launch_cfg<4, 12, fit_min_blocks(4, 12), RECORD, FRAMES, false>(a, s);
+  if (rps == 4 && warps == 24) return launch_cfg<4, 24, fit_min_blocks(4, 24), RECORD, FRAMES, false>(a, s);
+  if (rps == 8 && warps == 8) return launch_cfg<8, 8, fit_min_blocks(8, 8), RECORD, FRAMES, false>(a, s);
+  if (rps == 8 && warps == 16) return launch_cfg<8, 16, fit_min_blocks(8, 16), RECORD, FRAMES, false>(a, s);
+  if (rps == 16 && warps == 8) return launch_cfg<16, 8, fit_min_blocks(16, 8), RECORD, FRAMES, false>(a, s);
   return cudaErrorInvalidValue;
 }
 

@@ -44,6 +44,12 @@ struct GeoConst {
   float l0;                   // sqrt of the initial covariance diagonal (10)
   float max_snp;              // |sin phi| limit (0.999)
   int32_t n_rows;
+  // a thin material layer at every pad row (mat = 0: none)
+  int32_t mat;
+  float x0_inv;               // 1 / radiation length [1/cm]
+  float dedx;                 // minimum-ionising energy loss [GeV/cm]
+  float mass2;                // particle mass squared [GeV^2]
+  float d_row;                // layer thickness at normal incidence [cm]
 };
 
 // Arguments of one fit launch.
@@ -73,6 +79,7 @@ struct FitArgs {
   const float* frame_align;    // [n_frames][36][152][2] per-frame offsets, or null (handle's table)
   const int32_t* frame_ready;  // [n_frames] ready flags (!= 0 when the frame's clusters are in place), or null
   int64_t wait_ns;             // bound of a ready-flag wait
+  int32_t mat;                 // material layers on (selects the kernel variant that crosses them)
 };
 
 // Arguments of one backward launch (same frame as the recorded fit).
@@ -116,6 +123,7 @@ struct SmoothArgs {
   float* chi2;                 // [n_hits] r^T R^-1 r
   unsigned int* work;
   float4* seg;                 // segment store, as for the adjoint
+  int32_t mat;                 // material layers on (the recorded fit had them)
 };
 
 // Error codes recorded in the device error word.

@@ -219,6 +219,11 @@ std::string rtc_fit_source(const GeoConst& g, bool det) {
   s += "  static constexpr float l0 = " + hexf(g.l0) + ";\n";
   s += "  static constexpr float max_snp = " + hexf(g.max_snp) + ";\n";
   s += "  static constexpr int32_t n_rows = " + std::to_string(g.n_rows) + ";\n";
+  s += "  static constexpr int32_t mat = " + std::to_string(g.mat) + ";\n";
+  s += "  static constexpr float x0_inv = " + hexf(g.x0_inv) + ";\n";
+  s += "  static constexpr float dedx = " + hexf(g.dedx) + ";\n";
+  s += "  static constexpr float mass2 = " + hexf(g.mass2) + ";\n";
+  s += "  static constexpr float d_row = " + hexf(g.d_row) + ";\n";
   s += "};\n";
   s += "__constant__ GeoFold c_geo = {";
   append_list(s, g.row_x, kMaxRows, hexf);
@@ -245,7 +250,7 @@ Variant variant(const GeoConst& g, bool det, int rps, int warps, bool record, bo
   v.src = rtc_fit_source(g, det);
   v.expr = "tpcfit::rtc::fit_kernel<" + std::to_string(rps) + ", " + std::to_string(warps) + ", " +
            std::to_string(fit_min_blocks(rps, warps)) + ", " + (record ? "true" : "false") + ", " +
-           (frames ? "true" : "false") + ">";
+           (frames ? "true" : "false") + ", " + (g.mat ? "true" : "false") + ">";
   std::string opt;
   for (const std::string& x : options(det)) opt += x + " ";
   char keyb[32];

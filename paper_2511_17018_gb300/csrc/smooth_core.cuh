@@ -133,7 +133,7 @@ __device__ __forceinline__ void write_nan_clusters(const SmoothArgs& a, int h0, 
   }
 }
 
-template <int WARPS>
+template <int WARPS, bool MAT>
 __global__ void __launch_bounds__(WARPS * 32, 1) smooth_kernel(SmoothArgs a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   BwdSmem& B = *reinterpret_cast<BwdSmem*>(smem_raw);
@@ -197,7 +197,7 @@ __global__ void __launch_bounds__(WARPS * 32, 1) smooth_kernel(SmoothArgs a) {
         int row, sec;
         decode_hit(B.align, cur, m0, m1, row, sec);
         store_state(gs + kk * (kStateF4 * kWarp), S);
-        step_fwd(T, S, my, mz, j == 0, false, row, sec % kNSide, m0, m1);
+        step_fwd<MAT>(T, S, my, mz, j == 0, false, row, sec % kNSide, m0, m1);
       }
       __threadfence_block();  // the states just stored are read back by this thread's copies below
       if (s > 0) fetch_ckpt(&W.ck[0][lane], ckp + (int64_t)(s - 1) * kCkptFloats);
@@ -232,6 +232,11 @@ __global__ void __launch_bounds__(WARPS * 32, 1) smooth_kernel(SmoothArgs a) {
           decode_hit(B.align, load_hit(a.y, a.z, a.rowsec, h + 1), mpy, mpz, prow, psec);
           Jac J;
           PredTape tp;
+          if (MAT) {  // the layer of row c + 1, undone against the flight
+            MatNoise N;
+            material_step(SI.p, -1, N);
+            material_factor(SI.L, N);
+          }
           predict_residual(T, SI.p, SI.x, SI.sec, mpy, mpz, sec18, X, m0, m1, pi, J, tp);
           transport(SI.L, J);
         }
@@ -246,7 +251,10 @@ __global__ void __launch_bounds__(WARPS * 32, 1) smooth_kernel(SmoothArgs a) {
           Jac J;
           PredTape tp;
           predict_residual(T, O.p, O.x, O.sec, omy, omz, sec18, X, m0, m1, po, J, tp);
+          MatNoise N;
+          if (MAT) material_step(po, 1, N);  // the layer of row c
           transport(O.L, J);
+          if (MAT) material_factor(O.L, N);
         }
         float r[2], R[3], c2;
         smooth_combine(po, O.L, pi, SI.L, r, R, c2);
@@ -271,17 +279,19 @@ __global__ void __launch_bounds__(WARPS * 32, 1) smooth_kernel(SmoothArgs a) {
 }
 
 #ifndef __CUDACC_RTC__
-template <int WARPS>
+template <int WARPS, bool MAT>
 cudaError_t smooth_grid(int& grid) {
   static int cached = 0;
   if (cached == 0) {
     const size_t smem = backward_smem_bytes<WARPS>();
-    cudaError_t e = cudaFuncSetAttribute(smooth_kernel<WARPS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e =
+        cudaFuncSetAttribute(smooth_kernel<WARPS, MAT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     int dev = 0, sms = 0, per_sm = 0;
     e = cudaGetDevice(&dev);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, smooth_kernel<WARPS>, WARPS * 32, smem);
+    if (e == cudaSuccess)
+      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, smooth_kernel<WARPS, MAT>, WARPS * 32, smem);
     if (e != cudaSuccess) return e;
     if (per_sm < 1) return cudaErrorInvalidConfiguration;
     cached = sms * per_sm;
@@ -292,26 +302,32 @@ cudaError_t smooth_grid(int& grid) {
 
 constexpr int kSmoothWarps = 8;
 
-// Segment store (float4 count) the smoother needs.
+// Segment store (float4 count) the smoother needs (the larger of its variants).
 inline cudaError_t smooth_store(int64_t& float4s) {
-  int grid = 0;
-  cudaError_t e = smooth_grid<kSmoothWarps>(grid);
-  float4s = (int64_t)grid * kSmoothWarps * kCkptEvery * kStateF4 * kWarp;
+  int g0 = 0, g1 = 0;
+  cudaError_t e = smooth_grid<kSmoothWarps, false>(g0);
+  if (e == cudaSuccess) e = smooth_grid<kSmoothWarps, true>(g1);
+  float4s = (int64_t)(g0 > g1 ? g0 : g1) * kSmoothWarps * kCkptEvery * kStateF4 * kWarp;
   return e;
 }
 
-inline cudaError_t launch_smooth(const SmoothArgs& a, cudaStream_t s) {
-  if (a.n_tracks <= 0) return cudaSuccess;
+template <bool MAT>
+cudaError_t launch_smooth_cfg(const SmoothArgs& a, cudaStream_t s) {
   int grid = 0;
-  cudaError_t e = smooth_grid<kSmoothWarps>(grid);
+  cudaError_t e = smooth_grid<kSmoothWarps, MAT>(grid);
   if (e != cudaSuccess) return e;
   const int64_t chunks = ((int64_t)a.n_tracks + kWarp - 1) / kWarp;
   const int64_t need = (chunks + kSmoothWarps - 1) / kSmoothWarps;
   const int blocks = (int)(need < grid ? need : grid);
   e = cudaMemsetAsync(a.work, 0, sizeof(unsigned int), s);
   if (e != cudaSuccess) return e;
-  smooth_kernel<kSmoothWarps><<<blocks, kSmoothWarps * 32, backward_smem_bytes<kSmoothWarps>(), s>>>(a);
+  smooth_kernel<kSmoothWarps, MAT><<<blocks, kSmoothWarps * 32, backward_smem_bytes<kSmoothWarps>(), s>>>(a);
   return cudaGetLastError();
+}
+
+inline cudaError_t launch_smooth(const SmoothArgs& a, cudaStream_t s) {
+  if (a.n_tracks <= 0) return cudaSuccess;
+  return a.mat ? launch_smooth_cfg<true>(a, s) : launch_smooth_cfg<false>(a, s);
 }
 #endif
 

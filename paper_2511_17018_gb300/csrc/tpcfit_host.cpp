@@ -340,6 +340,7 @@ tpcfit_status tpcfit_fit(tpcfit_handle* h, const tpcfit_hits* hits, const int32_
   a.ndf = ndf_out;
   a.err = h->d_err;
   a.work = h->d_work;
+  a.mat = h->geo.mat;
   h->rec_valid = false;
   if (h->record) {
     const int64_t slots = hits->n_hits / kCkptEvery + (int64_t)n_tracks + 1;
@@ -410,6 +411,7 @@ tpcfit_status tpcfit_fit_frames(tpcfit_handle* h, const tpcfit_hits* hits, const
   a.ndf = ndf_out;
   a.err = h->d_err;
   a.work = h->d_work;
+  a.mat = h->geo.mat;
   a.frame_base = frame_track_base;
   a.n_frames = n_frames;
   a.frame_align = frame_alignment;
@@ -425,6 +427,27 @@ tpcfit_status tpcfit_fit_frames(tpcfit_handle* h, const tpcfit_hits* hits, const
 tpcfit_status tpcfit_set_backward_config(tpcfit_handle* h, int warps_per_block) {
   if (!h || !backward_shape_supported(warps_per_block)) return TPCFIT_EINVAL;
   h->bwd_warps = warps_per_block;
+  return TPCFIT_OK;
+}
+
+tpcfit_status tpcfit_set_material(tpcfit_handle* h, double x0_cm, double dedx_gev_cm, double mass_gev,
+                                  double row_cm) {
+  if (!h) return TPCFIT_EINVAL;
+  if (x0_cm <= 0.0) {  // no material
+    h->geo.mat = 0;
+    h->geo.x0_inv = h->geo.dedx = h->geo.mass2 = h->geo.d_row = 0.0f;
+  } else {
+    if (!std::isfinite(x0_cm) || !std::isfinite(dedx_gev_cm) || dedx_gev_cm < 0.0 || !(mass_gev > 0.0) ||
+        !std::isfinite(mass_gev) || !(row_cm > 0.0) || !std::isfinite(row_cm))
+      return TPCFIT_EINVAL;
+    h->geo.mat = 1;
+    h->geo.x0_inv = (float)(1.0 / x0_cm);
+    h->geo.dedx = (float)dedx_gev_cm;
+    h->geo.mass2 = (float)(mass_gev * mass_gev);
+    h->geo.d_row = (float)row_cm;
+  }
+  h->rec_valid = false;
+  forget_resident_constants();  // the handle's constants changed: upload them again
   return TPCFIT_OK;
 }
 
@@ -469,6 +492,7 @@ tpcfit_status tpcfit_fit_backward(tpcfit_handle* h, const tpcfit_hits* hits, con
   if (!h->rec_valid || h->rec_tracks != n_tracks || h->rec_hits != hits->n_hits ||
       h->rec_det != h->deterministic)
     return TPCFIT_ESTATE;
+  if (h->geo.mat) return TPCFIT_ESTATE;  // the adjoint has no reverse of the material layers
   tpcfit_status st = make_resident(h, s);
   if (st != TPCFIT_OK) return st;
   BwdArgs b{};
@@ -561,6 +585,7 @@ tpcfit_status tpcfit_smooth(tpcfit_handle* h, const tpcfit_hits* hits, const int
   a.rcov = rcov;
   a.chi2 = chi2;
   a.work = h->d_work;
+  a.mat = h->geo.mat;
   int64_t need = 0;
   cudaError_t e = h->deterministic ? smooth_store_det(need) : smooth_store_fast(need);
   if (e != cudaSuccess) return from_cuda(e);

@@ -63,6 +63,7 @@ def load():
                                         vp]),
         "tpcfit_fit_backward": (C.c_int, [vp, C.POINTER(_Hits), vp, i32, vp, vp, vp, vp, vp, vp]),
         "tpcfit_smooth": (C.c_int, [vp, C.POINTER(_Hits), vp, i32, vp, vp, vp, vp, vp]),
+        "tpcfit_set_material": (C.c_int, [vp, C.c_double, C.c_double, C.c_double, C.c_double]),
         "tpcfit_set_rtc": (C.c_int, [vp, C.c_int, C.c_char_p]),
         "tpcfit_rtc_build": (C.c_int, [C.POINTER(_Geometry), C.c_double, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int,
                                        C.c_char_p]),
@@ -124,6 +125,12 @@ def tpcfit_create(geometry, bz: float):
     h = C.c_void_p()
     _check(L.tpcfit_create(C.byref(g), float(bz), C.byref(h)), "tpcfit_create")
     return h
+
+
+def tpcfit_set_material(h, x0_cm: float = 0.0, dedx_gev_cm: float = 0.0, mass_gev: float = 0.13957,
+                        row_cm: float = 160.0 / 151.0) -> None:
+    _check(load().tpcfit_set_material(h, float(x0_cm), float(dedx_gev_cm), float(mass_gev), float(row_cm)),
+           "tpcfit_set_material")
 
 
 def tpcfit_set_rtc(h, enable: bool = True, cache_dir: str | None = None) -> None:
@@ -354,6 +361,13 @@ class Fitter:
 
     def set_mode(self, deterministic: bool):
         tpcfit_set_mode(self.h, deterministic)
+
+    def set_material(self, material=None):
+        """material: object with x0_cm, dedx_gev_cm, mass_gev, row_cm (synth.Material), or None for none."""
+        if material is None:
+            tpcfit_set_material(self.h, 0.0)
+        else:
+            tpcfit_set_material(self.h, material.x0_cm, material.dedx_gev_cm, material.mass_gev, material.row_cm)
 
     def set_rtc(self, enable: bool = True, cache_dir: str | None = None):
         tpcfit_set_rtc(self.h, enable, cache_dir)

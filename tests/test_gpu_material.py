@@ -1,0 +1,117 @@
+"""Material layers at the pad rows on the GPU (run on a GB300 with -m gpu).
+
+Deterministic mode: bit-exact against the strict-FP32 oracle with material
+(energy loss and the square-root noise folding in their canonical order);
+fast mode within the FP32 tolerance of the FP64 oracle; the smoother, the
+batched-frame and run-time-compiled fits follow the material; the adjoint
+refuses it."""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+import oracle  # noqa: E402
+from paper_2511_17018_gb300 import synth, tolerance  # noqa: E402
+from paper_2511_17018_gb300 import tpcfit as tf  # noqa: E402
+
+THICK = synth.Material(300.0, 2e-4)
+
+
+def _host(out):
+    torch.cuda.synchronize()
+    return {k: v.cpu().numpy() for k, v in out.items()}
+
+
+def _bits_equal(a, b):
+    return all(np.array_equal(np.ascontiguousarray(a[k]).view(np.int32), np.ascontiguousarray(b[k]).view(np.int32))
+               for k in ("params", "cov", "chi2", "ndf"))
+
+
+@pytest.fixture(scope="module")
+def frame():
+    return synth.generate(8000, 12, drop_p=0.05, cap_lengths=True)
+
+
+@pytest.mark.parametrize("mat", [synth.TPC_GAS, THICK], ids=["gas", "thick"])
+def test_deterministic_fit_with_material_bit_exact(frame, mat):
+    fr = frame.subset(np.arange(frame.n_tracks))
+    fr.material = mat
+    ref = oracle.fit(fr, "f32")
+    f = tf.Fitter(fr.geometry, fr.bz, deterministic=True)
+    try:
+        f.set_material(mat)
+        dev = tf.frame_to_device(fr)
+        for rps, warps, srt in ((4, 24, True), (4, 12, False), (8, 16, True)):
+            f.set_config(1, rps, warps, srt)
+            assert _bits_equal(_host(f.fit(dev)), ref), (rps, warps, srt)
+    finally:
+        f.close()
+
+
+@pytest.mark.parametrize("mat", [synth.TPC_GAS, THICK], ids=["gas", "thick"])
+def test_fast_fit_with_material_within_tolerance(frame, mat):
+    fr = frame.subset(np.arange(frame.n_tracks))
+    fr.material = mat
+    f = tf.Fitter(fr.geometry, fr.bz)
+    try:
+        f.set_material(mat)
+        got = _host(f.fit(tf.frame_to_device(fr)))
+    finally:
+        f.close()
+    rep = tolerance.compare_to_fp64(got, oracle.fit(fr, "f64"))
+    assert rep["ok"], rep
+
+
+def test_material_off_again_restores_the_plain_fit(frame):
+    dev = tf.frame_to_device(frame)
+    f = tf.Fitter(frame.geometry, frame.bz, deterministic=True)
+    try:
+        base = _host(f.fit(dev))
+        f.set_material(THICK)
+        with_mat = _host(f.fit(dev))
+        f.set_material(None)
+        again = _host(f.fit(dev))
+    finally:
+        f.close()
+    assert _bits_equal(base, again)
+    assert not _bits_equal(base, with_mat)
+
+
+def test_smoother_with_material_matches_oracle(frame):
+    from test_gpu_smooth import compare
+    fr = frame.subset(np.arange(frame.n_tracks))
+    fr.material = THICK
+    dev = tf.frame_to_device(fr)
+    f = tf.Fitter(fr.geometry, fr.bz)
+    try:
+        f.set_material(THICK)
+        f.set_record(True)
+        out = f.fit(dev)
+        got = _host(f.smooth(dev, out))
+        # the adjoint has no reverse of the material layers
+        with pytest.raises(tf.TpcfitError) as e:
+            f.backward(dev, out, torch.ones(fr.n_tracks, device="cuda"))
+        assert e.value.status == tf.ESTATE
+    finally:
+        f.close()
+    rep = compare(got, oracle.smooth(fr))
+    assert rep["nan_agree"] > 0.9999, rep
+    assert rep["resid_ok"] > 0.999 and rep["rcov_ok"] > 0.999 and rep["chi2_ok"] > 0.999, rep
+
+
+def test_batched_frames_and_run_time_compiled_fit_with_material(frame):
+    from paper_2511_17018_gb300.frames import FrameBatch, fit_frames
+    parts = [frame.subset(np.arange(a, b)) for a, b in ((0, 3000), (3000, 3500), (3500, 8000))]
+    f = tf.Fitter(frame.geometry, frame.bz, deterministic=True)
+    try:
+        f.set_material(THICK)
+        dev = tf.frame_to_device(frame)
+        ref = _host(f.fit(dev))
+        got = _host(fit_frames(f, FrameBatch.from_frames(parts)))
+        assert _bits_equal(got, ref)
+        if tf.tpcfit_rtc_available():
+            f.set_rtc(True)
+            assert _bits_equal(_host(f.fit(dev)), ref)
+    finally:
+        f.close()
