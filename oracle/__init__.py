@@ -19,7 +19,8 @@ _lib = None
 class _Geo(C.Structure):
     _fields_ = [("row_x", C.POINTER(C.c_double)), ("n_rows", C.c_int32), ("n_sectors", C.c_int32),
                 ("sector_width_deg", C.c_double), ("x0_cm", C.c_double), ("dedx_gev_cm", C.c_double),
-                ("mass_gev", C.c_double), ("row_cm", C.c_double)]
+                ("mass_gev", C.c_double), ("row_cm", C.c_double), ("field_cr", C.c_double),
+                ("field_cz", C.c_double)]
 
 
 def lib():
@@ -58,14 +59,16 @@ def _ptr(a):
     return None if a is None else a.ctypes.data
 
 
-def _geo(geometry, material=None):
-    """ctypes geometry; material: object with x0_cm, dedx_gev_cm, mass_gev, row_cm (None: none)."""
+def _geo(geometry, material=None, field=None):
+    """ctypes geometry; material: object with x0_cm, dedx_gev_cm, mass_gev, row_cm (None: none);
+    field: object with c_r, c_z of the field map (None: uniform)."""
     rx = np.ascontiguousarray(geometry.row_x, dtype=np.float64)
     m = material
     g = _Geo(rx.ctypes.data_as(C.POINTER(C.c_double)), rx.shape[0], geometry.n_sectors,
              float(geometry.sector_width_deg), float(m.x0_cm) if m is not None else 0.0,
              float(m.dedx_gev_cm) if m is not None else 0.0, float(m.mass_gev) if m is not None else 0.0,
-             float(m.row_cm) if m is not None else 0.0)
+             float(m.row_cm) if m is not None else 0.0, float(field.c_r) if field is not None else 0.0,
+             float(field.c_z) if field is not None else 0.0)
     return g, rx
 
 
@@ -103,7 +106,7 @@ def fit(frame, precision: str = "f64", align=None, ref=None, trace: bool = False
     params = np.empty((5, n), dt); cov = np.empty((15, n), dt); chi2 = np.empty(n, dt)
     ndf = np.empty(n, np.int32)
     tr = np.empty((H, 2, 22), np.float64) if trace else None
-    g, _keep = _geo(frame.geometry, getattr(frame, "material", None))
+    g, _keep = _geo(frame.geometry, getattr(frame, "material", None), getattr(frame, "field", None))
     fn = {"f64": L.oracle_fit_f64, "f32": L.oracle_fit_f32, "sqrt_f64": L.oracle_fit_sqrt_f64,
           "cov_f32": L.oracle_fit_cov_f32}[precision]
     rc = fn(C.byref(g), float(frame.bz), n, _ptr(off), _ptr(y), _ptr(z), _ptr(rs), _ptr(sd), _ptr(al), _ptr(rf),
@@ -130,7 +133,7 @@ def grad(frame, weights=None, align=None, nthreads: int | None = None, exact_inp
     al = None if align is None else np.ascontiguousarray(align, dtype=np.float64).reshape(-1)
     w = None if weights is None else np.ascontiguousarray(weights, dtype=np.float64)
     gm = np.zeros((H, 2)); gs = np.zeros((5, n)); chi2 = np.empty(n); ndf = np.empty(n, np.int32)
-    g, _keep = _geo(frame.geometry, getattr(frame, "material", None))
+    g, _keep = _geo(frame.geometry, getattr(frame, "material", None), getattr(frame, "field", None))
     rc = L.oracle_grad_f64(C.byref(g), float(frame.bz), n, _ptr(off), _ptr(y), _ptr(z), _ptr(rs), _ptr(sd),
                            _ptr(al), _ptr(w), _ptr(gm), _ptr(gs), _ptr(chi2), _ptr(ndf),
                            nthreads or default_threads())
@@ -170,7 +173,7 @@ def smooth(frame, align=None, ref=None, exact_inputs: bool = False, seeds=None, 
     rf = None if ref is None else np.ascontiguousarray(ref, dtype=np.float64)
     params = np.empty((5, n)); cov = np.empty((15, n)); chi2 = np.empty(n); ndf = np.empty(n, np.int32)
     pt = np.empty((H, 2, 20))
-    g, _keep = _geo(frame.geometry, getattr(frame, "material", None))
+    g, _keep = _geo(frame.geometry, getattr(frame, "material", None), getattr(frame, "field", None))
     rc = L.oracle_fit_pred_f64(C.byref(g), float(frame.bz), n, _ptr(off), _ptr(y), _ptr(z), _ptr(rs), _ptr(sd),
                                _ptr(al), _ptr(rf), _ptr(params), _ptr(cov), _ptr(chi2), _ptr(ndf), _ptr(pt),
                                nthreads or default_threads())

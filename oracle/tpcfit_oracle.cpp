@@ -187,12 +187,16 @@ template <class S> struct Geo {
   // minimum-ionising energy loss, squared mass of the particle (a pion)
   bool mat;
   S x0_inv, dedx, mass2, d_row;
+  // field map Bz(r, z) = Bz0 (1 + c_r (r / 250)^2 + c_z (z / 250)^2) (off when field = false)
+  bool field;
+  S f_r, f_z;  // c_r / 250^2, c_z / 250^2 [1/cm^2]
 };
 
 // Rotation angle from sector a to b: m = (b - a) mod 18 taken in [-8, 9],
 // dalpha = m * (w * pi / 180), cos / sin in FP64, then the constant type.
 template <class S> void make_geo(Geo<S>& g, const double* row_x, int n_rows, double width_deg, double bz,
-                                  double x0_cm = 0.0, double dedx = 0.0, double mass = 0.0, double d_row = 0.0) {
+                                  double x0_cm = 0.0, double dedx = 0.0, double mass = 0.0, double d_row = 0.0,
+                                  double c_r = 0.0, double c_z = 0.0) {
   g.n_rows = n_rows;
   for (int r = 0; r < n_rows; ++r) g.row_x[r] = (S)row_x[r];
   const double w_rad = width_deg * 3.14159265358979323846 / 180.0;
@@ -213,6 +217,9 @@ template <class S> void make_geo(Geo<S>& g, const double* row_x, int n_rows, dou
   g.dedx = (S)(g.mat ? dedx : 0.0);
   g.mass2 = (S)(mass * mass);
   g.d_row = (S)d_row;
+  g.field = c_r != 0.0 || c_z != 0.0;
+  g.f_r = (S)(c_r / (250.0 * 250.0));
+  g.f_z = (S)(c_z / (250.0 * 250.0));
 }
 
 // packed index of (i, j), i >= j
@@ -290,12 +297,20 @@ bool material_step(const Geo<typename Traits<T>::S>& g, T p[5], int dir, Noise<T
 // Moves state (p, x) in sector sec_from to pad row X in sector sec_to:
 // optional rotation to the new sector's frame, then helix propagation to local
 // x = X.  Returns false (state untouched) if the step is not possible.
+//
+// Field map (g.field): the step's curvature uses Bz at the step's midpoint,
+// estimated by a straight half step from the start point (after the
+// rotation): x_m = x1 + dx/2, y_m = y1 + (dx/2) s1/c1, z_m = z1 + (dx/2) t/c1,
+// kappa_step = kappa (1 + f_r (x_m^2 + y_m^2) + f_z z_m^2).  The midpoint makes
+// an arc's curvature the same in both directions.  The Jacobian treats
+// kappa_step as a constant (its dependence on the state is neglected).
+// (yo, zo): what to add to pin[0], pin[1] for absolute positions (residual form).
 template <class T>
 bool predict(const Geo<typename Traits<T>::S>& g, const T pin[5], const T& xin, int sec_from, int sec_to,
-             typename Traits<T>::S X, T pout[5], T& xout, Jac<T>& J) {
+             typename Traits<T>::S X, T pout[5], T& xout, Jac<T>& J, const T& yo = T(0.0), const T& zo = T(0.0)) {
   using S = typename Traits<T>::S;
   const S one = (S)1.0, half = (S)0.5;
-  const S kappa = g.kappa;
+  T kappa = T(g.kappa);
   const double maxsnp = (double)g.max_snp;
   const int a = sec_from % kNSectorsPerSide, b = sec_to % kNSectorsPerSide;
   T x1 = xin, y1 = pin[0], s1 = pin[2];
@@ -318,6 +333,14 @@ bool predict(const Geo<typename Traits<T>::S>& g, const T pin[5], const T& xin, 
     x1 = xr; y1 = yr; s1 = sr; cprev = c; crot = cr;
   }
   const T dx = T(X) - x1;
+  if (g.field) {
+    const T c1f = Sqrt((one - s1) * (one + s1));
+    const T hdx = dx * half;
+    const T ym = (yo + y1) + hdx * (s1 / c1f);
+    const T zm = (zo + pin[1]) + hdx * (t / c1f);
+    const T xm = x1 + hdx;
+    kappa = kappa * ((one + g.f_r * (xm * xm + ym * ym)) + g.f_z * (zm * zm));
+  }
   const T k = q * kappa;
   const T kdx = k * dx;
   const T s2 = s1 + kdx;
@@ -708,7 +731,10 @@ FitResult fit_track(const Geo<typename Traits<T>::S>& g, const HitView<T>& h, co
           pin[0] = my + p[0];
           pin[1] = mz + p[1];
         }
-        if (!predict<T>(g, pin, x, hit_sec(h, from), hit_sec(h, to), g.row_x[r], pn, xn, J)) return false;
+        const T zero((S)0.0);
+        if (!predict<T>(g, pin, x, hit_sec(h, from), hit_sec(h, to), g.row_x[r], pn, xn, J, rot ? zero : my,
+                        rot ? zero : mz))
+          return false;
         if (rot) {
           pn[0] = pn[0] - mt[0];
           pn[1] = pn[1] - mt[1];
@@ -827,6 +853,8 @@ struct OracleGeometry {
   double dedx_gev_cm;  // minimum-ionising energy loss
   double mass_gev;     // particle mass
   double row_cm;       // thickness of the material layer at each pad row (normal incidence)
+  double field_cr;     // field map Bz(r, z) = Bz0 (1 + field_cr (r/250)^2 + field_cz (z/250)^2)
+  double field_cz;
 };
 
 int check_inputs(const OracleGeometry* geo, int32_t n_tracks, const int32_t* off) {
@@ -845,8 +873,9 @@ int fit_all(const OracleGeometry* geo, double bz, int32_t n_tracks, const int32_
   using S = typename Traits<T>::S;
   if (check_inputs(geo, n_tracks, off)) return 1;
   Geo<S> g;
-  make_geo<S>(g, geo->row_x, geo->n_rows, geo->sector_width_deg, bz, geo->x0_cm, geo->dedx_gev_cm, geo->mass_gev, geo->row_cm);
-  if (g.mat && ref) return 1;  // the linearised filter has no material
+  make_geo<S>(g, geo->row_x, geo->n_rows, geo->sector_width_deg, bz, geo->x0_cm, geo->dedx_gev_cm, geo->mass_gev, geo->row_cm,
+               geo->field_cr, geo->field_cz);
+  if ((g.mat || g.field) && ref) return 1;  // the linearised filter has neither material nor a field map
   const T nan = T((S)NAN);
 #pragma omp parallel for schedule(dynamic, 64) num_threads(nthreads > 0 ? nthreads : 1)
   for (int32_t i = 0; i < n_tracks; ++i) {
@@ -946,7 +975,8 @@ int oracle_grad_f64(const OracleGeometry* geo, double bz, int32_t n_tracks, cons
   for (int32_t i = 0; i < n_tracks; ++i)
     if (off[i + 1] - off[i] > 152) return 1;
   Geo<double> g;
-  make_geo<double>(g, geo->row_x, geo->n_rows, geo->sector_width_deg, bz, geo->x0_cm, geo->dedx_gev_cm, geo->mass_gev, geo->row_cm);
+  make_geo<double>(g, geo->row_x, geo->n_rows, geo->sector_width_deg, bz, geo->x0_cm, geo->dedx_gev_cm, geo->mass_gev, geo->row_cm,
+               geo->field_cr, geo->field_cz);
 #pragma omp parallel for schedule(dynamic, 4) num_threads(nthreads > 0 ? nthreads : 1)
   for (int32_t i = 0; i < n_tracks; ++i) {
     const int n = off[i + 1] - off[i];

@@ -495,3 +495,92 @@ def simulate_material(qpt, tanl, phi0, z0, geometry: Geometry, bz: float, materi
     fr.seeds64 = three_point_seeds(fr, as_f64=True)
     fr.seeds = fr.seeds64.astype(np.float32)
     return fr
+
+
+@dataclass
+class FieldMap:
+    """Analytic map Bz(r, z) = Bz0 (1 + c_r (r / 250 cm)^2 + c_z (z / 250 cm)^2)."""
+    c_r: float
+    c_z: float
+
+
+def simulate_field(qpt, tanl, phi0, z0, geometry: Geometry, bz: float, field: FieldMap, *, rng=None,
+                   smear: float = 0.1, step_cm: float = 0.2, sector: int = 0):
+    """Tracks in a non-uniform Bz field, by Runge-Kutta (4th order) integration
+    of the direction along the path, d u / ds = 0.00299792458 (q / p) u x B,
+    in the local frame of one sector (the caller picks tracks that stay in it).
+    A row plane crossed inside a step is reached by a last step of the exact
+    remaining length, so hits sit on the planes.  Returns a Frame (field
+    attached) with truth (y, z, sin phi, tan lambda, q/pt) at the first cluster;
+    without material pt and tan lambda stay constant along the track."""
+    rng = np.random.default_rng(0) if rng is None else rng
+    width = geometry.sector_width_deg * math.pi / 180.0
+    half_tan = math.tan(0.5 * width)
+    alpha = (sector % 18 + 0.5) * width
+    c = 0.00299792458
+    fr2, fz2 = field.c_r / 250.0 ** 2, field.c_z / 250.0 ** 2
+
+    def deriv(st, qp):
+        x, y, z, ux, uy, uz = st
+        b = bz * (1.0 + fr2 * (x * x + y * y) + fz2 * z * z)
+        a = c * qp * b
+        return np.array([ux, uy, uz, a * uy, -a * ux, 0.0])
+
+    def rk4(st, h, qp):
+        k1 = deriv(st, qp)
+        k2 = deriv(st + 0.5 * h * k1, qp)
+        k3 = deriv(st + 0.5 * h * k2, qp)
+        k4 = deriv(st + h * k3, qp)
+        return st + (h / 6.0) * (k1 + 2 * k2 + 2 * k3 + k4)
+
+    ys, zs, rows, secs, offs, truth = [], [], [], [], [0], []
+    for i in range(len(qpt)):
+        q = float(qpt[i]); t = float(tanl[i]); phi = float(phi0[i]) - alpha
+        cl = 1.0 / math.sqrt(1.0 + t * t)
+        p = 1.0 / (abs(q) * cl)                 # |p| = pt / cos(lambda)
+        qp = math.copysign(1.0 / p, q)
+        st = np.array([0.0, 0.0, float(z0[i]), math.cos(phi) * cl, math.sin(phi) * cl, t * cl])
+        hy, hz, hr = [], [], []
+        first = None
+        r = 0
+        for _ in range(200000):
+            if r >= geometry.n_rows:
+                break
+            X = float(geometry.row_x[r])
+            nxt = rk4(st, step_cm, qp)
+            if nxt[0] < X:
+                st = nxt
+                if st[3] <= 0.0:
+                    break
+                continue
+            # the plane is inside this step: shrink the step to reach it (two refinements)
+            h = step_cm * (X - st[0]) / (nxt[0] - st[0])
+            for _ in range(3):
+                trial = rk4(st, h, qp)
+                h = h + (X - trial[0]) / max(trial[3], 1e-9)
+            st = rk4(st, h, qp)
+            st[0] = X
+            if abs(st[1]) > X * half_tan or abs(st[2]) > geometry.z_max:
+                break
+            hy.append(st[1]); hz.append(st[2]); hr.append(r)
+            if first is None:
+                upt = math.hypot(st[3], st[4])
+                first = (st[1], st[2], st[4] / upt, st[5] / upt, qp / upt)
+            r += 1
+        if len(hy) < 10:
+            continue
+        ys += hy; zs += hz; rows += hr; secs += [sector + (18 if zz < 0 else 0) for zz in hz]
+        offs.append(offs[-1] + len(hy))
+        truth.append(first)
+    y64 = np.asarray(ys); z64 = np.asarray(zs)
+    if smear > 0.0:
+        y64 = y64 + rng.normal(0.0, smear, y64.shape[0])
+        z64 = z64 + rng.normal(0.0, smear, z64.shape[0])
+    rowsec = ((np.asarray(rows, np.int64) << ROWSEC_SHIFT) | np.asarray(secs, np.int64)).astype(np.uint16)
+    n = len(truth)
+    fr = Frame(geometry, bz, y64.astype(np.float32), z64.astype(np.float32), rowsec, np.asarray(offs, np.int32),
+               np.zeros((5, n), np.float32), np.asarray(truth, np.float64).T.reshape(5, n), None, y64, z64, None)
+    fr.field = field
+    fr.seeds64 = three_point_seeds(fr, as_f64=True)
+    fr.seeds = fr.seeds64.astype(np.float32)
+    return fr

@@ -576,3 +576,64 @@ def test_material_strict_fp32_within_fast_mode_tolerance(oracle_mod, synth):
     fr.material = synth.TPC_GAS
     rep = tolerance.compare_to_fp64(oracle_mod.fit(fr, "f32"), oracle_mod.fit(fr, "f64"))
     assert rep["ok"], rep
+
+
+# ---------------------------------------------------------------- field map
+def _field_tracks(synth, n, seed, **kw):
+    """Tracks of 2-5 GeV/c near the centre of sector 0 in the map
+    Bz = 0.5 T (1 + 0.3 (r/250)^2 - 0.2 (z/250)^2), integrated by RK4."""
+    rng = np.random.default_rng(seed)
+    qpt = rng.choice([-1, 1], n) / rng.uniform(2.0, 5.0, n)
+    tanl = rng.uniform(-0.5, 0.5, n)
+    phi0 = np.full(n, 0.5 * math.pi / 9) + rng.uniform(-0.03, 0.03, n)
+    z0 = rng.normal(0, 5, n)
+    fm = synth.FieldMap(0.3, -0.2)
+    return synth.simulate_field(qpt, tanl, phi0, z0, synth.default_geometry(), 0.5, fm, rng=rng, step_cm=0.5,
+                                **kw), fm
+
+
+def test_field_map_pulls_are_standard_normal(oracle_mod, synth):
+    # the generator integrates the equation of motion in the map (Runge-Kutta),
+    # the fit takes a helix per step with Bz at the step's midpoint; with the map
+    # the parameters scatter as their covariance says, with a uniform field not
+    fr, fm = _field_tracks(synth, 250, 1)
+    widths = {}
+    for use in (True, False):
+        fr.field = fm if use else None
+        r = oracle_mod.fit(fr, "f64")
+        ok = r["ndf"] > 0
+        C = oracle_mod.unpack(r["cov"][:, ok])
+        sig = np.sqrt(np.stack([C[i, i] for i in range(5)]))
+        pull = (r["params"][:, ok] - fr.truth[:, ok]) / sig
+        widths[use] = pull.std(axis=1)
+        if use:
+            assert np.all(np.abs(pull.mean(axis=1)) < 0.15), pull.mean(axis=1)
+    assert np.all((widths[True] > 0.85) & (widths[True] < 1.15)), widths[True]
+    assert widths[False].max() > 3.0
+
+
+def test_field_map_noise_free_refit(oracle_mod, synth):
+    # exact clusters of Runge-Kutta tracks: the refit to convergence returns the
+    # generating parameters (the midpoint helix differs from the exact path at
+    # second order in the step)
+    fr, fm = _field_tracks(synth, 30, 3, smear=0.0)
+    seeds = fr.seeds64.copy()
+    for _ in range(4):
+        r = oracle_mod.fit(fr, "f64", exact_inputs=True, seeds=seeds)
+        seeds = r["params"].copy()
+    assert np.all(r["ndf"] > 0)
+    assert np.abs(r["params"][:4] - fr.truth[:4]).max() < 1e-6
+    assert (np.abs(r["params"][4] - fr.truth[4]) / np.abs(fr.truth[4])).max() < 3e-6
+
+
+def test_field_map_forms_and_strict_fp32(oracle_mod, synth):
+    from paper_2511_17018_gb300 import tolerance
+    fr = synth.generate(1000, 5, drop_p=0.05, cap_lengths=True)
+    fr.field = synth.FieldMap(0.3, -0.2)
+    a = oracle_mod.fit(fr, "f64")
+    b = oracle_mod.fit(fr, "sqrt_f64")
+    ok = a["ndf"] > 0
+    assert np.array_equal(a["ndf"], b["ndf"])
+    assert np.allclose(a["params"][:, ok], b["params"][:, ok], rtol=1e-8, atol=1e-10)
+    rep = tolerance.compare_to_fp64(oracle_mod.fit(fr, "f32"), a)
+    assert rep["ok"], rep
