@@ -491,6 +491,15 @@ def main():
     mat_ms = statistics.mean(p[0] for p in mat_per)
     fitter.set_material(None)
 
+    # ---- the same plain fit in the field map Bz (1 + 0.3 (r/250)^2 - 0.2 (z/250)^2)
+    fitter.set_field(_synth.FieldMap(0.3, -0.2))
+    for _ in range(args.warmup):
+        fitter.fit(dev, out)
+    torch.cuda.synchronize()
+    _, fld_per = timed(step_fit, plain_steps)
+    fld_ms = statistics.mean(p[0] for p in fld_per)
+    fitter.set_field(None)
+
     # ---- end to end through the public API with host buffers
     h2d = 10 * fr.n_hits + 4 * (fr.n_tracks + 1) + 20 * fr.n_tracks
     d2h = 88 * fr.n_tracks
@@ -556,6 +565,9 @@ def main():
                         "ms": smooth_ms, "achieved_tflops": sm_tf, "frac": sm_tf / peak_tf,
                         "kernel": "smooth_kernel<8> (two-filter smoother of the recorded fit)",
                         "algorithmic_flops_per_launch": flops.smooth_flops(lengths)}
+    line["plain_fit"]["field_map"] = {"tracks_per_s": fr.n_tracks / (fld_ms / 1e3), "ms": fld_ms,
+                                      "field": "Bz (1 + 0.3 (r/250 cm)^2 - 0.2 (z/250 cm)^2), midpoint per step",
+                                      "kernel": "fit_kernel<4,24> with the field map"}
     line["plain_fit"]["material"] = {"tracks_per_s": fr.n_tracks / (mat_ms / 1e3), "ms": mat_ms,
                                      "material": "TPC gas layer at every row (X0 3.1e4 cm, 1.6 MeV/m, one row pitch)",
                                      "kernel": "fit_kernel<4,24> with the material layers"}

@@ -169,6 +169,16 @@ tpcfit_status tpcfit_fit_frames(tpcfit_handle* h, const tpcfit_hits* hits, const
  * EINVAL for non-finite or non-positive values. */
 tpcfit_status tpcfit_set_material(tpcfit_handle* h, double x0_cm, double dedx_gev_cm, double mass_gev, double row_cm);
 
+/* Non-uniform field (Sec. 4: propagation through the magnetic field): the
+ * analytic map Bz(r, z) = bz_tesla (1 + c_r (r / 250 cm)^2 + c_z (z / 250 cm)^2)
+ * (bz_tesla from tpcfit_create).  Each step is a helix with Bz at the step's
+ * midpoint, estimated by a straight half step from its start; the Jacobian
+ * treats the step's curvature as constant.  c_r = c_z = 0: uniform (default).
+ * The fit, the smoother and the batched and run-time-compiled fits follow it;
+ * tpcfit_fit_backward answers ESTATE while a map is set.  EINVAL for
+ * non-finite values. */
+tpcfit_status tpcfit_set_field_map(tpcfit_handle* h, double c_r, double c_z);
+
 /* Run-time compilation of the fit (Sec. 5).  enable = 1: tpcfit_fit and
  * tpcfit_fit_frames run a fit kernel compiled with NVRTC for this handle's
  * geometry, field, mode and launch shape, in which those per-time-frame values

@@ -477,8 +477,9 @@ __device__ __forceinline__ void fetch_ckpt(float4* sdst, const float* ck) {
 // residual coordinates).  my, mz: measurement of the previous cluster on
 // entry, of this cluster on exit.  conv: the first step of the outward pass,
 // whose state is the seed in absolute coordinates.
-// MAT: the material layers of the rows (the smoother; the adjoint runs without).
-template <bool MAT = false>
+// MAT: the material layers of the rows; FIELD as for predict_t (the smoother
+// follows both; the adjoint runs without either).
+template <bool MAT = false, int FIELD = 0>
 __device__ __forceinline__ void step_fwd(const SmemTables& T, StepState& S, float& my, float& mz, bool first, bool conv,
                                          int row, int sec18, float m0, float m1) {
   float chi2 = 0.0f;
@@ -498,7 +499,7 @@ __device__ __forceinline__ void step_fwd(const SmemTables& T, StepState& S, floa
       material_step(S.p, -1, N);
       material_factor(S.L, N);
     }
-    predict_residual(T, S.p, S.x, S.sec, my, mz, sec18, T.row_x[row], m0, m1, pn, J, tp);
+    predict_residual<FIELD>(T, S.p, S.x, S.sec, my, mz, sec18, T.row_x[row], m0, m1, pn, J, tp);
     if (MAT && conv) material_step(pn, 1, N);
 #pragma unroll
     for (int c = 0; c < 5; ++c) S.p[c] = pn[c];
@@ -536,7 +537,7 @@ __device__ __forceinline__ void step_rev(const SmemTables& T, const float4* src,
       p1[1] = S0.p[1] - m1;
     }
   } else {
-    predict_residual(T, S0.p, S0.x, S0.sec, my_prev, mz_prev, sec18, T.row_x[row], m0, m1, p1, J, tp);
+    predict_residual<0>(T, S0.p, S0.x, S0.sec, my_prev, mz_prev, sec18, T.row_x[row], m0, m1, p1, J, tp);
   }
   // state before the z update
   float p2[5];
@@ -582,7 +583,7 @@ __device__ __forceinline__ void step_rev(const SmemTables& T, const float4* src,
     pin[1] = mz_prev + S0.p[1];
   }
   float pn[5];
-  predict_t(T, pin, S0.x, S0.sec, sec18, T.row_x[row], pn, J, tp);
+  predict_t<0>(T, pin, S0.x, S0.sec, sec18, T.row_x[row], pn, J, tp, rot ? 0.0f : my_prev, rot ? 0.0f : mz_prev);
   float b_pi[5];
   predict_rev(tp, J, S0.p[3], b_p, bJ, b_pi);
   if (rot) {

@@ -180,9 +180,17 @@ struct PredTape {
 // From state (p, x) in sector-frame a (mod 18) to pad row X in frame b: optional
 // rotation at the current point, then helix propagation at fixed Bz.  Returns
 // false, leaving nothing changed, if the step is impossible.
+//
+// Field map (c_geo.field): the step's curvature uses Bz at its midpoint,
+// estimated by a straight half step from the start point (after the rotation),
+// kappa_step = kappa (1 + f_r (x_m^2 + y_m^2) + f_z z_m^2); the Jacobian
+// treats kappa_step as a constant.  (yo, zo) turn pin's y, z into absolute
+// positions (residual form).  FIELD: 0 uniform (no map code), 1 the map,
+// 2 decided at run time by c_geo.field.
+template <int FIELD = 2>
 __device__ __forceinline__ bool predict_t(const SmemTables& T, const float pin[5], float xin, int a, int b, float X,
-                                          float pout[5], Jac& J, PredTape& tp) {
-  const float kappa = c_geo.kappa;
+                                          float pout[5], Jac& J, PredTape& tp, float yo = 0.0f, float zo = 0.0f) {
+  float kappa = c_geo.kappa;
   const float maxsnp = c_geo.max_snp;
   float x1 = xin, y1 = pin[0], s1 = pin[2];
   const float t = pin[3];
@@ -214,6 +222,14 @@ __device__ __forceinline__ bool predict_t(const SmemTables& T, const float pin[5
   tp.ca = ca;
   tp.sa = sa;
   const float dx = X - x1;
+  if (FIELD == 1 || (FIELD == 2 && c_geo.field)) {
+    const float c1f = sqrtf((1.0f - s1) * (1.0f + s1));
+    const float hdx = dx * 0.5f;
+    const float ym = (yo + y1) + hdx * (s1 / c1f);
+    const float zm = (zo + pin[1]) + hdx * (t / c1f);
+    const float xm = x1 + hdx;
+    kappa = kappa * ((1.0f + c_geo.f_r * (xm * xm + ym * ym)) + c_geo.f_z * (zm * zm));
+  }
   const float k = q * kappa;
   const float kdx = k * dx;
   const float s2 = s1 + kdx;
@@ -282,7 +298,7 @@ __device__ __forceinline__ bool predict_t(const SmemTables& T, const float pin[5
 __device__ __forceinline__ bool predict(const SmemTables& T, const float pin[5], float xin, int a, int b, float X,
                                         float pout[5], Jac& J) {
   PredTape tp;
-  return predict_t(T, pin, xin, a, b, X, pout, J, tp);
+  return predict_t<2>(T, pin, xin, a, b, X, pout, J, tp);
 }
 
 // Prediction in residual coordinates: p[0..1] are residuals from (my, mz), the
@@ -290,6 +306,7 @@ __device__ __forceinline__ bool predict(const SmemTables& T, const float pin[5],
 // rotation the exact difference of the two measurements is added; across a
 // rotation the absolute position is formed, rotated, propagated and
 // re-referenced.
+template <int FIELD = 2>
 __device__ __forceinline__ bool predict_residual(const SmemTables& T, const float p[5], float x, int sec, float my,
                                                  float mz, int sec_to, float X, float m0, float m1, float pout[5],
                                                  Jac& J, PredTape& tp) {
@@ -301,7 +318,7 @@ __device__ __forceinline__ bool predict_residual(const SmemTables& T, const floa
     pin[0] = my + p[0];
     pin[1] = mz + p[1];
   }
-  if (!predict_t(T, pin, x, sec, sec_to, X, pout, J, tp)) return false;
+  if (!predict_t<FIELD>(T, pin, x, sec, sec_to, X, pout, J, tp, rot ? 0.0f : my, rot ? 0.0f : mz)) return false;
   if (rot) {
     pout[0] = pout[0] - m0;
     pout[1] = pout[1] - m1;
@@ -577,10 +594,11 @@ static_assert(sizeof(WarpStage<4>) == fit_warp_stage_bytes(4) && sizeof(WarpStag
                   sizeof(WarpStage<16>) == fit_warp_stage_bytes(16),
               "kernel_abi.h staging size");
 
+template <int FIELD>
 __device__ __forceinline__ bool step_predict(const SmemTables& T, const TrackState& S, int sec_to, float X, float m0,
                                              float m1, float pout[5], Jac& J) {
   PredTape tp;
-  return predict_residual(T, S.p, S.x, S.sec, S.my, S.mz, sec_to, X, m0, m1, pout, J, tp);
+  return predict_residual<FIELD>(T, S.p, S.x, S.sec, S.my, S.mz, sec_to, X, m0, m1, pout, J, tp);
 }
 
 __device__ __forceinline__ void write_ckpt(const FitArgs& a, int pass, int begin, int trk, int seg,
@@ -601,8 +619,12 @@ __device__ __forceinline__ void write_ckpt(const FitArgs& a, int pass, int begin
   for (int j = 0; j < 9; ++j) dst[j] = make_float4(v[4 * j], v[4 * j + 1], v[4 * j + 2], v[4 * j + 3]);
 }
 
-template <int RPS, int WARPS, int MINB, bool RECORD, bool FRAMES, bool MAT>
+// PHYS: bit 0 the material layers, bit 1 the field map (compile-time variants,
+// so that the plain fit carries neither).
+template <int RPS, int WARPS, int MINB, bool RECORD, bool FRAMES, int PHYS>
 __global__ void __launch_bounds__(WARPS * 32, MINB) fit_kernel(FitArgs a) {
+  constexpr bool MAT = (PHYS & 1) != 0;
+  constexpr int FIELD = (PHYS & 2) ? 1 : 0;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   BlockSmem& B = *reinterpret_cast<BlockSmem*>(smem_raw);
   WarpStage<RPS>* stages = reinterpret_cast<WarpStage<RPS>*>(smem_raw + sizeof(BlockSmem));
@@ -742,7 +764,7 @@ __global__ void __launch_bounds__(WARPS * 32, MINB) fit_kernel(FitArgs a) {
               }
               material_factor(S.L, N);
             }
-            if (!step_predict(T, S, sec18, T.row_x[row], m0, m1, pn, J)) {
+            if (!step_predict<FIELD>(T, S, sec18, T.row_x[row], m0, m1, pn, J)) {
               go = false;
               if (pass == 1) status = 2;  // the inward pass must reach the first cluster
               continue;
@@ -808,20 +830,20 @@ __global__ void __launch_bounds__(WARPS * 32, MINB) fit_kernel(FitArgs a) {
 }
 
 #ifndef __CUDACC_RTC__
-template <int RPS, int WARPS, int MINB, bool RECORD, bool FRAMES, bool MAT>
+template <int RPS, int WARPS, int MINB, bool RECORD, bool FRAMES, int PHYS>
 cudaError_t launch_cfg(const FitArgs& a, cudaStream_t s) {
   constexpr int kThreads = WARPS * 32;
   const size_t smem = sizeof(BlockSmem) + WARPS * sizeof(WarpStage<RPS>);
   static int grid = 0;
   if (grid == 0) {
     cudaError_t e =
-        cudaFuncSetAttribute(fit_kernel<RPS, WARPS, MINB, RECORD, FRAMES, MAT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        cudaFuncSetAttribute(fit_kernel<RPS, WARPS, MINB, RECORD, FRAMES, PHYS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     int dev = 0, sms = 0, per_sm = 0;
     e = cudaGetDevice(&dev);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     if (e == cudaSuccess)
-      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fit_kernel<RPS, WARPS, MINB, RECORD, FRAMES, MAT>, kThreads, smem);
+      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fit_kernel<RPS, WARPS, MINB, RECORD, FRAMES, PHYS>, kThreads, smem);
     if (e != cudaSuccess) return e;
     if (per_sm < 1) return cudaErrorInvalidConfiguration;
     grid = sms * per_sm;
@@ -831,25 +853,25 @@ cudaError_t launch_cfg(const FitArgs& a, cudaStream_t s) {
   const int blocks = (int)(need < grid ? need : grid);
   cudaError_t e = cudaMemsetAsync(a.work, 0, sizeof(unsigned int), s);
   if (e != cudaSuccess) return e;
-  fit_kernel<RPS, WARPS, MINB, RECORD, FRAMES, MAT><<<blocks, kThreads, smem, s>>>(a);
+  fit_kernel<RPS, WARPS, MINB, RECORD, FRAMES, PHYS><<<blocks, kThreads, smem, s>>>(a);
   return cudaGetLastError();
 }
 
 // Supported (rows per stage, warps per block) shapes; the shared-memory budget
 // (alignment table + double buffer) decides how many blocks fit on an SM.
-// With material the fit runs at (4, 12) or, for any other shape, (4, 24).
+// With material or a field map the fit runs at (4, 24).
 template <bool RECORD, bool FRAMES>
 inline cudaError_t launch_rec(const FitArgs& a, int rps, int warps, cudaStream_t s) {
-  if (a.mat) {
-    if (rps == 4 && warps == 12) return launch_cfg<4, 12, fit_min_blocks(4, 12), RECORD, FRAMES, true>(a, s);
-    return launch_cfg<4, 24, fit_min_blocks(4, 24), RECORD, FRAMES, true>(a, s);
-  }
-  if (rps == 4 && warps == 8) return launch_cfg<4, 8, fit_min_blocks(4, 8), RECORD, FRAMES, false>(a, s);
-  if (rps == 4 && warps == 12) return launch_cfg<4, 12, fit_min_blocks(4, 12), RECORD, FRAMES, false>(a, s);
-  if (rps == 4 && warps == 24) return launch_cfg<4, 24, fit_min_blocks(4, 24), RECORD, FRAMES, false>(a, s);
-  if (rps == 8 && warps == 8) return launch_cfg<8, 8, fit_min_blocks(8, 8), RECORD, FRAMES, false>(a, s);
-  if (rps == 8 && warps == 16) return launch_cfg<8, 16, fit_min_blocks(8, 16), RECORD, FRAMES, false>(a, s);
-  if (rps == 16 && warps == 8) return launch_cfg<16, 8, fit_min_blocks(16, 8), RECORD, FRAMES, false>(a, s);
+  const int phys = (a.mat ? 1 : 0) | (a.field ? 2 : 0);
+  if (phys == 1) return launch_cfg<4, 24, fit_min_blocks(4, 24), RECORD, FRAMES, 1>(a, s);
+  if (phys == 2) return launch_cfg<4, 24, fit_min_blocks(4, 24), RECORD, FRAMES, 2>(a, s);
+  if (phys == 3) return launch_cfg<4, 24, fit_min_blocks(4, 24), RECORD, FRAMES, 3>(a, s);
+  if (rps == 4 && warps == 8) return launch_cfg<4, 8, fit_min_blocks(4, 8), RECORD, FRAMES, 0>(a, s);
+  if (rps == 4 && warps == 12) return launch_cfg<4, 12, fit_min_blocks(4, 12), RECORD, FRAMES, 0>(a, s);
+  if (rps == 4 && warps == 24) return launch_cfg<4, 24, fit_min_blocks(4, 24), RECORD, FRAMES, 0>(a, s);
+  if (rps == 8 && warps == 8) return launch_cfg<8, 8, fit_min_blocks(8, 8), RECORD, FRAMES, 0>(a, s);
+  if (rps == 8 && warps == 16) return launch_cfg<8, 16, fit_min_blocks(8, 16), RECORD, FRAMES, 0>(a, s);
+  if (rps == 16 && warps == 8) return launch_cfg<16, 8, fit_min_blocks(16, 8), RECORD, FRAMES, 0>(a, s);
   return cudaErrorInvalidValue;
 }
 

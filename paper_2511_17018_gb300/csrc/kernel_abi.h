@@ -50,6 +50,9 @@ struct GeoConst {
   float dedx;                 // minimum-ionising energy loss [GeV/cm]
   float mass2;                // particle mass squared [GeV^2]
   float d_row;                // layer thickness at normal incidence [cm]
+  // field map Bz(r, z) = Bz0 (1 + c_r (r / 250)^2 + c_z (z / 250)^2) (field = 0: uniform)
+  int32_t field;
+  float f_r, f_z;             // c_r / 250^2, c_z / 250^2 [1/cm^2]
 };
 
 // Arguments of one fit launch.
@@ -80,6 +83,7 @@ struct FitArgs {
   const int32_t* frame_ready;  // [n_frames] ready flags (!= 0 when the frame's clusters are in place), or null
   int64_t wait_ns;             // bound of a ready-flag wait
   int32_t mat;                 // material layers on (selects the kernel variant that crosses them)
+  int32_t field;               // field map on (selects the kernel variant that follows it)
 };
 
 // Arguments of one backward launch (same frame as the recorded fit).

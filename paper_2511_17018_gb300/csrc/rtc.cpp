@@ -224,6 +224,9 @@ std::string rtc_fit_source(const GeoConst& g, bool det) {
   s += "  static constexpr float dedx = " + hexf(g.dedx) + ";\n";
   s += "  static constexpr float mass2 = " + hexf(g.mass2) + ";\n";
   s += "  static constexpr float d_row = " + hexf(g.d_row) + ";\n";
+  s += "  static constexpr int32_t field = " + std::to_string(g.field) + ";\n";
+  s += "  static constexpr float f_r = " + hexf(g.f_r) + ";\n";
+  s += "  static constexpr float f_z = " + hexf(g.f_z) + ";\n";
   s += "};\n";
   s += "__constant__ GeoFold c_geo = {";
   append_list(s, g.row_x, kMaxRows, hexf);
@@ -250,7 +253,7 @@ Variant variant(const GeoConst& g, bool det, int rps, int warps, bool record, bo
   v.src = rtc_fit_source(g, det);
   v.expr = "tpcfit::rtc::fit_kernel<" + std::to_string(rps) + ", " + std::to_string(warps) + ", " +
            std::to_string(fit_min_blocks(rps, warps)) + ", " + (record ? "true" : "false") + ", " +
-           (frames ? "true" : "false") + ", " + (g.mat ? "true" : "false") + ">";
+           (frames ? "true" : "false") + ", " + std::to_string((g.mat ? 1 : 0) | (g.field ? 2 : 0)) + ">";
   std::string opt;
   for (const std::string& x : options(det)) opt += x + " ";
   char keyb[32];

@@ -197,7 +197,7 @@ __global__ void __launch_bounds__(WARPS * 32, 1) smooth_kernel(SmoothArgs a) {
         int row, sec;
         decode_hit(B.align, cur, m0, m1, row, sec);
         store_state(gs + kk * (kStateF4 * kWarp), S);
-        step_fwd<MAT>(T, S, my, mz, j == 0, false, row, sec % kNSide, m0, m1);
+        step_fwd<MAT, 2>(T, S, my, mz, j == 0, false, row, sec % kNSide, m0, m1);
       }
       __threadfence_block();  // the states just stored are read back by this thread's copies below
       if (s > 0) fetch_ckpt(&W.ck[0][lane], ckp + (int64_t)(s - 1) * kCkptFloats);
@@ -237,7 +237,7 @@ __global__ void __launch_bounds__(WARPS * 32, 1) smooth_kernel(SmoothArgs a) {
             material_step(SI.p, -1, N);
             material_factor(SI.L, N);
           }
-          predict_residual(T, SI.p, SI.x, SI.sec, mpy, mpz, sec18, X, m0, m1, pi, J, tp);
+          predict_residual<2>(T, SI.p, SI.x, SI.sec, mpy, mpz, sec18, X, m0, m1, pi, J, tp);
           transport(SI.L, J);
         }
         // outward prediction at c
@@ -250,7 +250,7 @@ __global__ void __launch_bounds__(WARPS * 32, 1) smooth_kernel(SmoothArgs a) {
         } else {
           Jac J;
           PredTape tp;
-          predict_residual(T, O.p, O.x, O.sec, omy, omz, sec18, X, m0, m1, po, J, tp);
+          predict_residual<2>(T, O.p, O.x, O.sec, omy, omz, sec18, X, m0, m1, po, J, tp);
           MatNoise N;
           if (MAT) material_step(po, 1, N);  // the layer of row c
           transport(O.L, J);

@@ -341,6 +341,7 @@ tpcfit_status tpcfit_fit(tpcfit_handle* h, const tpcfit_hits* hits, const int32_
   a.err = h->d_err;
   a.work = h->d_work;
   a.mat = h->geo.mat;
+  a.field = h->geo.field;
   h->rec_valid = false;
   if (h->record) {
     const int64_t slots = hits->n_hits / kCkptEvery + (int64_t)n_tracks + 1;
@@ -412,6 +413,7 @@ tpcfit_status tpcfit_fit_frames(tpcfit_handle* h, const tpcfit_hits* hits, const
   a.err = h->d_err;
   a.work = h->d_work;
   a.mat = h->geo.mat;
+  a.field = h->geo.field;
   a.frame_base = frame_track_base;
   a.n_frames = n_frames;
   a.frame_align = frame_alignment;
@@ -448,6 +450,16 @@ tpcfit_status tpcfit_set_material(tpcfit_handle* h, double x0_cm, double dedx_ge
   }
   h->rec_valid = false;
   forget_resident_constants();  // the handle's constants changed: upload them again
+  return TPCFIT_OK;
+}
+
+tpcfit_status tpcfit_set_field_map(tpcfit_handle* h, double c_r, double c_z) {
+  if (!h || !std::isfinite(c_r) || !std::isfinite(c_z)) return TPCFIT_EINVAL;
+  h->geo.field = (c_r != 0.0 || c_z != 0.0) ? 1 : 0;
+  h->geo.f_r = (float)(c_r / (250.0 * 250.0));
+  h->geo.f_z = (float)(c_z / (250.0 * 250.0));
+  h->rec_valid = false;
+  forget_resident_constants();
   return TPCFIT_OK;
 }
 
@@ -492,7 +504,8 @@ tpcfit_status tpcfit_fit_backward(tpcfit_handle* h, const tpcfit_hits* hits, con
   if (!h->rec_valid || h->rec_tracks != n_tracks || h->rec_hits != hits->n_hits ||
       h->rec_det != h->deterministic)
     return TPCFIT_ESTATE;
-  if (h->geo.mat) return TPCFIT_ESTATE;  // the adjoint has no reverse of the material layers
+  if (h->geo.mat) return TPCFIT_ESTATE;    // the adjoint has no reverse of the material layers
+  if (h->geo.field) return TPCFIT_ESTATE;  // nor of the field map's midpoint curvature
   tpcfit_status st = make_resident(h, s);
   if (st != TPCFIT_OK) return st;
   BwdArgs b{};

@@ -64,6 +64,7 @@ def load():
         "tpcfit_fit_backward": (C.c_int, [vp, C.POINTER(_Hits), vp, i32, vp, vp, vp, vp, vp, vp]),
         "tpcfit_smooth": (C.c_int, [vp, C.POINTER(_Hits), vp, i32, vp, vp, vp, vp, vp]),
         "tpcfit_set_material": (C.c_int, [vp, C.c_double, C.c_double, C.c_double, C.c_double]),
+        "tpcfit_set_field_map": (C.c_int, [vp, C.c_double, C.c_double]),
         "tpcfit_set_rtc": (C.c_int, [vp, C.c_int, C.c_char_p]),
         "tpcfit_rtc_build": (C.c_int, [C.POINTER(_Geometry), C.c_double, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int,
                                        C.c_char_p]),
@@ -131,6 +132,10 @@ def tpcfit_set_material(h, x0_cm: float = 0.0, dedx_gev_cm: float = 0.0, mass_ge
                         row_cm: float = 160.0 / 151.0) -> None:
     _check(load().tpcfit_set_material(h, float(x0_cm), float(dedx_gev_cm), float(mass_gev), float(row_cm)),
            "tpcfit_set_material")
+
+
+def tpcfit_set_field_map(h, c_r: float = 0.0, c_z: float = 0.0) -> None:
+    _check(load().tpcfit_set_field_map(h, float(c_r), float(c_z)), "tpcfit_set_field_map")
 
 
 def tpcfit_set_rtc(h, enable: bool = True, cache_dir: str | None = None) -> None:
@@ -368,6 +373,10 @@ class Fitter:
             tpcfit_set_material(self.h, 0.0)
         else:
             tpcfit_set_material(self.h, material.x0_cm, material.dedx_gev_cm, material.mass_gev, material.row_cm)
+
+    def set_field(self, field=None):
+        """field: object with c_r, c_z (synth.FieldMap), or None for the uniform field."""
+        tpcfit_set_field_map(self.h, 0.0 if field is None else field.c_r, 0.0 if field is None else field.c_z)
 
     def set_rtc(self, enable: bool = True, cache_dir: str | None = None):
         tpcfit_set_rtc(self.h, enable, cache_dir)

@@ -1,10 +1,11 @@
-"""Material layers at the pad rows on the GPU (run on a GB300 with -m gpu).
+"""Material layers at the pad rows and the field map on the GPU (run on a
+GB300 with -m gpu).
 
 Deterministic mode: bit-exact against the strict-FP32 oracle with material
-(energy loss and the square-root noise folding in their canonical order);
-fast mode within the FP32 tolerance of the FP64 oracle; the smoother, the
-batched-frame and run-time-compiled fits follow the material; the adjoint
-refuses it."""
+(energy loss and the square-root noise folding in their canonical order) and
+with the field map (midpoint curvature); fast mode within the FP32 tolerance
+of the FP64 oracle; the smoother, the batched-frame and run-time-compiled fits
+follow both; the adjoint refuses them."""
 import numpy as np
 import pytest
 
@@ -115,3 +116,61 @@ def test_batched_frames_and_run_time_compiled_fit_with_material(frame):
             assert _bits_equal(_host(f.fit(dev)), ref)
     finally:
         f.close()
+
+
+FIELD = synth.FieldMap(0.3, -0.2)
+
+
+@pytest.mark.parametrize("with_mat", [False, True], ids=["field", "field+gas"])
+def test_field_map_fit_parity(frame, with_mat):
+    # (the thick layers stop the 0.2 GeV/c tracks of this frame within a few
+    # rows, where FP32 and FP64 may part at the stopping row; the gas does not)
+    fr = frame.subset(np.arange(frame.n_tracks))
+    fr.field = FIELD
+    fr.material = synth.TPC_GAS if with_mat else None
+    ref32, ref64 = oracle.fit(fr, "f32"), oracle.fit(fr, "f64")
+    for det in (True, False):
+        f = tf.Fitter(fr.geometry, fr.bz, deterministic=det)
+        try:
+            f.set_field(FIELD)
+            f.set_material(fr.material)
+            got = _host(f.fit(tf.frame_to_device(fr)))
+        finally:
+            f.close()
+        if det:
+            assert _bits_equal(got, ref32)
+        else:
+            rep = tolerance.compare_to_fp64(got, ref64)
+            assert rep["ok"], {k: v for k, v in rep.items() if k != "worst"}
+
+
+def test_field_map_smoother_frames_rtc_and_adjoint(frame):
+    from test_gpu_smooth import compare
+    from paper_2511_17018_gb300.frames import FrameBatch, fit_frames
+    fr = frame.subset(np.arange(frame.n_tracks))
+    fr.field = FIELD
+    dev = tf.frame_to_device(fr)
+    f = tf.Fitter(fr.geometry, fr.bz, deterministic=True)
+    try:
+        f.set_field(FIELD)
+        f.set_record(True)
+        out = f.fit(dev)
+        ref = _host(out)
+        sm = _host(f.smooth(dev, out))
+        with pytest.raises(tf.TpcfitError) as e:
+            f.backward(dev, out, torch.ones(fr.n_tracks, device="cuda"))
+        assert e.value.status == tf.ESTATE
+        f.set_record(False)
+        parts = [fr.subset(np.arange(a, b)) for a, b in ((0, 5000), (5000, 8000))]
+        assert _bits_equal(_host(fit_frames(f, FrameBatch.from_frames(parts))), ref)
+        if tf.tpcfit_rtc_available():
+            f.set_rtc(True)
+            assert _bits_equal(_host(f.fit(dev)), ref)
+        f.set_rtc(False)
+        f.set_field(None)
+        assert not _bits_equal(_host(f.fit(dev)), ref)
+    finally:
+        f.close()
+    rep = compare(sm, oracle.smooth(fr))
+    assert rep["nan_agree"] > 0.9999, rep
+    assert rep["resid_ok"] > 0.999 and rep["rcov_ok"] > 0.999 and rep["chi2_ok"] > 0.999, rep
