@@ -539,7 +539,7 @@ __device__ __forceinline__ void step_rev(const SmemTables& T, const float4* src,
   } else {
     predict_residual<0>(T, S0.p, S0.x, S0.sec, my_prev, mz_prev, sec18, T.row_x[row], m0, m1, p1, J, tp);
   }
-  // state before the z update
+  // the factor before the y update (kept) and before the z update
   float p2[5];
   float chi_dummy = 0.0f, b_dummy = 0.0f;
 #pragma unroll
@@ -549,14 +549,13 @@ __device__ __forceinline__ void step_rev(const SmemTables& T, const float4* src,
 #pragma unroll
     for (int c = 0; c < 5; ++c) L[i][c] = S0.L[i][c];
   if (!first) transport(L, J);
-  scalar_update<0>(p2, L, chi_dummy, 0.0f);
-  scalar_update_rev<1>(p2, L, 0.0f, b_p, b_L, b_chi, b_dummy);
-  // state before the y update (recomputed)
+  float L2[5][5];
 #pragma unroll
   for (int i = 0; i < 5; ++i)
 #pragma unroll
-    for (int c = 0; c < 5; ++c) L[i][c] = S0.L[i][c];
-  if (!first) transport(L, J);
+    for (int c = 0; c < 5; ++c) L2[i][c] = L[i][c];
+  scalar_update<0>(p2, L2, chi_dummy, 0.0f);
+  scalar_update_rev<1>(p2, L2, 0.0f, b_p, b_L, b_chi, b_dummy);
   scalar_update_rev<0>(p1, L, 0.0f, b_p, b_L, b_chi, b_dummy);
   // b_p is now the adjoint of the predicted (shifted) state p1
   b_mc[0] = -b_p[0];
@@ -575,15 +574,7 @@ __device__ __forceinline__ void step_rev(const SmemTables& T, const float4* src,
     b_mp[0] = b_p[0];
     b_mp[1] = b_p[1];
   }
-  float pin[5];
-#pragma unroll
-  for (int c = 0; c < 5; ++c) pin[c] = S0.p[c];
-  if (rot) {
-    pin[0] = my_prev + S0.p[0];
-    pin[1] = mz_prev + S0.p[1];
-  }
-  float pn[5];
-  predict_t<0>(T, pin, S0.x, S0.sec, sec18, T.row_x[row], pn, J, tp, rot ? 0.0f : my_prev, rot ? 0.0f : mz_prev);
+  // the prediction's intermediates (tp, J) are those of the forward above
   float b_pi[5];
   predict_rev(tp, J, S0.p[3], b_p, bJ, b_pi);
   if (rot) {
