@@ -590,15 +590,16 @@ __device__ __forceinline__ void red_add(float* p, float v) {
   asm volatile("red.global.add.f32 [%0], %1;\n" ::"l"(__cvta_generic_to_global(p)), "f"(v) : "memory");
 }
 
+// prev: what the inward pass left at cluster h (read ahead by the caller; only
+// the outward pass, pass 0, adds to it).
 __device__ __forceinline__ void accumulate_meas_grad(const BwdArgs& a, int pass, int h, int row, int sec, float g0,
-                                                     float g1) {
+                                                     float g1, float2 prev) {
   if (a.grad_meas) {
     float2* gm = reinterpret_cast<float2*>(a.grad_meas) + h;
     if (pass == 1) {
       *gm = make_float2(g0, g1);
     } else {
-      const float2 o = *gm;
-      *gm = make_float2(o.x + g0, o.y + g1);
+      *gm = make_float2(prev.x + g0, prev.y + g1);
     }
   }
   if (a.grad_align_atomic) {
@@ -676,6 +677,11 @@ __global__ void __launch_bounds__(WARPS * 32, 1) backward_kernel(BwdArgs a) {
         const int hd = pass == 0 ? 1 : -1;
         const float* ckp = a.ck + ((int64_t)pass * a.ck_slots + (begin >> kCkptShift) + trk) * kCkptFloats;
         float pend0 = 0.0f, pend1 = 0.0f;  // gradient owed to the measurement of the step before
+        // the outward pass adds to the inward pass's gradient of each cluster:
+        // that value is read one reversed step ahead
+        const float2* const gmr = reinterpret_cast<const float2*>(a.grad_meas);
+        const bool addg = pass == 0 && gmr != nullptr;
+        float2 gnx = addg ? gmr[h0 + hd * (steps - 1)] : make_float2(0.0f, 0.0f);
         fetch_ckpt(&W.ck[0][lane], ckp + (int64_t)(nseg - 1) * kCkptFloats);
 #pragma unroll 1
         for (int s = nseg - 1; s >= 0; --s) {
@@ -729,9 +735,11 @@ __global__ void __launch_bounds__(WARPS * 32, 1) backward_kernel(BwdArgs a) {
               if (i > 1) pv = load_hit(a, h - 2 * hd);
               decode_hit(B.align, pc, mpy, mpz, prow, psec);
             }
+            const float2 gcur = gnx;
+            if (addg && i > 0) gnx = gmr[h - hd];
             float b_mc[2], b_mp[2];
             step_rev(T, &W.st[kk & 1][0][lane], mpy, mpz, i == 0, pass == 0, row, sec % kNSide, m0, m1, b_p, b_L, b_chi, b_mc, b_mp);
-            accumulate_meas_grad(a, pass, h, row, sec, b_mc[0] + pend0, b_mc[1] + pend1);
+            accumulate_meas_grad(a, pass, h, row, sec, b_mc[0] + pend0, b_mc[1] + pend1, gcur);
             pend0 = b_mp[0];
             pend1 = b_mp[1];
             m0 = mpy;

@@ -133,6 +133,13 @@ __device__ __forceinline__ void write_nan_clusters(const SmoothArgs& a, int h0, 
   }
 }
 
+// Shared memory of a smoother block: the tables, the alignment table and,
+// per warp, a double buffer for the inward states and a checkpoint buffer.
+template <int WARPS>
+constexpr size_t smooth_smem_bytes() {
+  return sizeof(BwdSmem) + WARPS * sizeof(BwdWarpBufs);
+}
+
 template <int WARPS, bool MAT>
 __global__ void __launch_bounds__(WARPS * 32, 1) smooth_kernel(SmoothArgs a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -283,7 +290,7 @@ template <int WARPS, bool MAT>
 cudaError_t smooth_grid(int& grid) {
   static int cached = 0;
   if (cached == 0) {
-    const size_t smem = backward_smem_bytes<WARPS>();
+    const size_t smem = smooth_smem_bytes<WARPS>();
     cudaError_t e =
         cudaFuncSetAttribute(smooth_kernel<WARPS, MAT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
@@ -321,7 +328,7 @@ cudaError_t launch_smooth_cfg(const SmoothArgs& a, cudaStream_t s) {
   const int blocks = (int)(need < grid ? need : grid);
   e = cudaMemsetAsync(a.work, 0, sizeof(unsigned int), s);
   if (e != cudaSuccess) return e;
-  smooth_kernel<kSmoothWarps, MAT><<<blocks, kSmoothWarps * 32, backward_smem_bytes<kSmoothWarps>(), s>>>(a);
+  smooth_kernel<kSmoothWarps, MAT><<<blocks, kSmoothWarps * 32, smooth_smem_bytes<kSmoothWarps>(), s>>>(a);
   return cudaGetLastError();
 }
 
