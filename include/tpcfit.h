@@ -174,9 +174,10 @@ tpcfit_status tpcfit_set_material(tpcfit_handle* h, double x0_cm, double dedx_ge
  * (bz_tesla from tpcfit_create).  Each step is a helix with Bz at the step's
  * midpoint, estimated by a straight half step from its start; the Jacobian
  * treats the step's curvature as constant.  c_r = c_z = 0: uniform (default).
- * The fit, the smoother and the batched and run-time-compiled fits follow it;
- * tpcfit_fit_backward answers ESTATE while a map is set.  EINVAL for
- * non-finite values. */
+ * The fit, the smoother and the batched and run-time-compiled fits follow it,
+ * and so does tpcfit_fit_backward: its reverse runs through the midpoint
+ * curvature (in its 8-warp shape, whatever tpcfit_set_backward_config chose).
+ * EINVAL for non-finite values. */
 tpcfit_status tpcfit_set_field_map(tpcfit_handle* h, double c_r, double c_z);
 
 /* Run-time compilation of the fit (Sec. 5).  enable = 1: tpcfit_fit and
@@ -235,7 +236,9 @@ tpcfit_status tpcfit_set_backward_config(tpcfit_handle* h, int warps_per_block);
  *   grad_meas:  float [n_hits][2], dL/d(measured y, z) per cluster, or NULL.
  * The backward recomputes each 16-step segment from its checkpoint into a
  * per-warp segment store and runs the hand-written reverse of every step,
- * copying the state before each step into shared memory one step ahead.  Fast mode accumulates grad_align with
+ * copying the state before each step into shared memory one step ahead.  It
+ * follows the field map (tpcfit_set_field_map); with material layers set it
+ * answers ESTATE.  Fast mode accumulates grad_align with
  * atomics; deterministic mode writes per-cluster gradients, sorts the clusters
  * by (sector, row) with a stable radix sort and sums each key in a fixed order,
  * so grad_align is bitwise reproducible.  Tracks with ndf <= 0 contribute 0. */

@@ -175,11 +175,17 @@ __device__ __forceinline__ void transport_rev(const float L[5][5], const Jac& J,
   }
 }
 
-// Reverse of predict_t: b_po = adjoint of the predicted state, bJ = adjoint of
-// the Jacobian entries; b_pi receives the adjoint of the state before the step.
-__device__ __forceinline__ void predict_rev(const PredTape& tp, const Jac& J, float t, const float b_po[5],
-                                            const JacBar& bJ, float b_pi[5]) {
-  const float kappa = c_geo.kappa;
+// Reverse of predict_t<FIELD> (FIELD 0: uniform field, 1: the map): b_po =
+// adjoint of the predicted state, bJ = adjoint of the Jacobian entries; b_pi
+// receives the adjoint of the state before the step (t, q: its tan(lambda) and
+// q/pt).  With the map the curvature depends on the step's midpoint, hence on
+// y, z, s, t and on the offsets (yo, zo) of residual coordinates, whose
+// adjoints go to b_yo, b_zo (zero without the map).
+template <int FIELD = 0>
+__device__ __forceinline__ void predict_rev(const PredTape& tp, const Jac& J, float t, float q, const float b_po[5],
+                                            const JacBar& bJ, float b_pi[5], float& b_yo, float& b_zo) {
+  const float kappa = FIELD == 1 ? tp.kap : c_geo.kappa;
+  float b_kap = 0.0f;  // adjoint of the curvature per unit q/pt (map only)
   const float dx = tp.dx, s1 = tp.s1, s2 = tp.s2, ic1 = tp.ic1, ic2 = tp.ic2, Tm = tp.Tm, tt = tp.tt;
   float b_t = b_po[3], b_q = b_po[4], b_s2 = b_po[2];
   float b_s1 = 0.0f, b_dx = 0.0f, b_k = 0.0f, b_kdx = 0.0f, b_ic1 = 0.0f, b_ic2 = 0.0f, b_c1 = 0.0f, b_c2 = 0.0f;
@@ -200,6 +206,7 @@ __device__ __forceinline__ void predict_rev(const PredTape& tp, const Jac& J, fl
   b_dx += kappa * bJ.sq;
   b_t += kappa * tp.Lk * bJ.zq;
   const float b_Lk = t * kappa * bJ.zq;
+  if (FIELD == 1) b_kap += tp.dx * bJ.sq + (t * tp.Lk) * bJ.zq;
   if (tp.series) {
     const float i2 = ic1 * ic1, i3 = i2 * ic1, i5 = i3 * i2, i7 = i5 * i2, s1s = s1 * s1;
     const float a1 = (s1 * i3) * 0.5f;
@@ -257,6 +264,7 @@ __device__ __forceinline__ void predict_rev(const PredTape& tp, const Jac& J, fl
     b_dx += 2.0f * kappa * dx * (tt * (ic2 * 0.5f)) * bJ.yq;
     b_tt += ic2 * 0.5f * M * bJ.yq;
     b_ic2 += tt * 0.5f * M * bJ.yq;
+    if (FIELD == 1) b_kap += (dx * dx) * (tt * (ic2 * 0.5f)) * bJ.yq;
   }
   {  // Jys0 = (dx tt) ((ic1 + ic2) / 2)
     const float Hh = (ic1 + ic2) * 0.5f;
@@ -300,15 +308,36 @@ __device__ __forceinline__ void predict_rev(const PredTape& tp, const Jac& J, fl
   b_k += dx * b_kdx;
   b_dx += tp.k * b_kdx;
   b_q += kappa * b_k;
+  // the map: kappa = kappa0 (1 + f_r (xm^2 + ym^2) + f_z zm^2) at the midpoint of
+  // a straight half step, xm = x1 + dx/2, ym = (yo + y1) + (dx/2) s1/c1,
+  // zm = (zo + z1) + (dx/2) t/c1
+  float b_y1 = b_po[0], b_z1 = b_po[1], b_xm = 0.0f;
+  b_yo = 0.0f;
+  b_zo = 0.0f;
+  if (FIELD == 1) {
+    b_kap += q * b_k;
+    const float k0 = 2.0f * c_geo.kappa;
+    b_xm = (k0 * c_geo.f_r) * tp.xm * b_kap;
+    const float b_ym = (k0 * c_geo.f_r) * tp.ym * b_kap;
+    const float b_zm = (k0 * c_geo.f_z) * tp.zm * b_kap;
+    const float hdx = 0.5f * dx, ic1c = ic1 * ic1 * ic1;
+    b_yo = b_ym;
+    b_zo = b_zm;
+    b_y1 += b_ym;
+    b_z1 += b_zm;
+    b_t += (hdx * ic1) * b_zm;
+    b_s1 += hdx * ic1c * (b_ym + (t * s1) * b_zm);  // d(s/c)/ds = 1/c^3, d(1/c)/ds = s/c^3
+    b_dx += 0.5f * (b_xm + (s1 * ic1) * b_ym + (t * ic1) * b_zm);
+  }
   // dx = X - x1
-  const float b_x1 = -b_dx;
+  const float b_x1 = b_xm - b_dx;
   if (J.rot) {
     // x1 = x ca + y sa ; y1 = y ca - x sa ; s1 = s ca - c sa ; cr = c ca + s sa ;
     // rr = cr / c ; c = sqrt((1 - s)(1 + s))
     const float rr = J.ss;
     const float b_cr = b_rr / tp.c;
     float b_c = -rr * b_rr / tp.c;
-    b_pi[0] = tp.sa * b_x1 + tp.ca * b_po[0];
+    b_pi[0] = tp.sa * b_x1 + tp.ca * b_y1;
     float b_s = tp.ca * b_s1;
     b_c -= tp.sa * b_s1;
     b_c += tp.ca * b_cr;
@@ -316,10 +345,10 @@ __device__ __forceinline__ void predict_rev(const PredTape& tp, const Jac& J, fl
     b_s -= (tp.s / tp.c) * b_c;
     b_pi[2] = b_s;
   } else {
-    b_pi[0] = b_po[0];
+    b_pi[0] = b_y1;
     b_pi[2] = b_s1;
   }
-  b_pi[1] = b_po[1];
+  b_pi[1] = b_z1;
   b_pi[3] = b_t;
   b_pi[4] = b_q;
 }
@@ -520,6 +549,7 @@ __device__ __forceinline__ void step_fwd(const SmemTables& T, StepState& S, floa
 // cluster.  b_p, b_L: in = adjoint after the step, out = adjoint before it.
 // The measurements enter only through the residual shifts: b_mc = adjoint of
 // this cluster's (y, z), b_mp = of the previous one's.
+template <int FIELD = 0>
 __device__ __forceinline__ void step_rev(const SmemTables& T, const float4* src, float my_prev, float mz_prev,
                                          bool first, bool conv, int row, int sec18, float m0, float m1, float b_p[5],
                                          float b_L[5][5], float b_chi, float b_mc[2], float b_mp[2]) {
@@ -537,7 +567,7 @@ __device__ __forceinline__ void step_rev(const SmemTables& T, const float4* src,
       p1[1] = S0.p[1] - m1;
     }
   } else {
-    predict_residual<0>(T, S0.p, S0.x, S0.sec, my_prev, mz_prev, sec18, T.row_x[row], m0, m1, p1, J, tp);
+    predict_residual<FIELD>(T, S0.p, S0.x, S0.sec, my_prev, mz_prev, sec18, T.row_x[row], m0, m1, p1, J, tp);
   }
   // the factor before the y update (kept) and before the z update
   float p2[5];
@@ -575,11 +605,14 @@ __device__ __forceinline__ void step_rev(const SmemTables& T, const float4* src,
     b_mp[1] = b_p[1];
   }
   // the prediction's intermediates (tp, J) are those of the forward above
-  float b_pi[5];
-  predict_rev(tp, J, S0.p[3], b_p, bJ, b_pi);
+  float b_pi[5], b_yo, b_zo;
+  predict_rev<FIELD>(tp, J, S0.p[3], S0.p[4], b_p, bJ, b_pi, b_yo, b_zo);
   if (rot) {
     b_mp[0] = b_pi[0];
     b_mp[1] = b_pi[1];
+  } else if (FIELD == 1) {  // the map's midpoint sits at the previous cluster plus the residual
+    b_mp[0] += b_yo;
+    b_mp[1] += b_zo;
   }
 #pragma unroll
   for (int c = 0; c < 5; ++c) b_p[c] = b_pi[c];
@@ -632,8 +665,10 @@ constexpr size_t backward_smem_bytes() {
 // first, each state copied into shared memory asynchronously one step ahead.
 // Clusters are loaded one step ahead as well; the next segment's checkpoint
 // is copied while the current segment is reversed.
-template <int WARPS>
+// PHYS: 0 uniform field, 2 the field map (bit 1, material, has no reverse).
+template <int WARPS, int PHYS>
 __global__ void __launch_bounds__(WARPS * 32, 1) backward_kernel(BwdArgs a) {
+  constexpr int FIELD = (PHYS & 2) ? 1 : 0;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   BwdSmem& B = *reinterpret_cast<BwdSmem*>(smem_raw);
   load_tables(B.T);
@@ -706,7 +741,7 @@ __global__ void __launch_bounds__(WARPS * 32, 1) backward_kernel(BwdArgs a) {
             if (kk + 1 < cnt) nx = load_hit(a, h0 + hd * (i + 1));
             decode_hit(B.align, cur, m0, m1, row, sec);
             store_state(gs + kk * (kStateF4 * kWarp), S);
-            step_fwd(T, S, my, mz, i == 0, pass == 0, row, sec % kNSide, m0, m1);
+            step_fwd<false, FIELD>(T, S, my, mz, i == 0, pass == 0, row, sec % kNSide, m0, m1);
           }
           // the states just stored are read back by this thread's copies below
           __threadfence_block();
@@ -738,7 +773,7 @@ __global__ void __launch_bounds__(WARPS * 32, 1) backward_kernel(BwdArgs a) {
             const float2 gcur = gnx;
             if (addg && i > 0) gnx = gmr[h - hd];
             float b_mc[2], b_mp[2];
-            step_rev(T, &W.st[kk & 1][0][lane], mpy, mpz, i == 0, pass == 0, row, sec % kNSide, m0, m1, b_p, b_L, b_chi, b_mc, b_mp);
+            step_rev<FIELD>(T, &W.st[kk & 1][0][lane], mpy, mpz, i == 0, pass == 0, row, sec % kNSide, m0, m1, b_p, b_L, b_chi, b_mc, b_mp);
             accumulate_meas_grad(a, pass, h, row, sec, b_mc[0] + pend0, b_mc[1] + pend1, gcur);
             pend0 = b_mp[0];
             pend1 = b_mp[1];
@@ -762,18 +797,20 @@ __global__ void __launch_bounds__(WARPS * 32, 1) backward_kernel(BwdArgs a) {
 }
 
 // Persistent grid of the backward (blocks resident at once over all SMs).
-template <int WARPS>
+template <int WARPS, int PHYS>
 cudaError_t backward_grid(int& grid) {
   static int cached = 0;
   if (cached == 0) {
     constexpr int kThreads = WARPS * 32;
     const size_t smem = backward_smem_bytes<WARPS>();
-    cudaError_t e = cudaFuncSetAttribute(backward_kernel<WARPS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e =
+        cudaFuncSetAttribute(backward_kernel<WARPS, PHYS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     int dev = 0, sms = 0, per_sm = 0;
     e = cudaGetDevice(&dev);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, backward_kernel<WARPS>, kThreads, smem);
+    if (e == cudaSuccess)
+      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, backward_kernel<WARPS, PHYS>, kThreads, smem);
     if (e != cudaSuccess) return e;
     if (per_sm < 1) return cudaErrorInvalidConfiguration;
     cached = sms * per_sm;
@@ -782,46 +819,55 @@ cudaError_t backward_grid(int& grid) {
   return cudaSuccess;
 }
 
-template <int WARPS>
+template <int WARPS, int PHYS>
 cudaError_t backward_store_cfg(int64_t& float4s) {
   int grid = 0;
-  cudaError_t e = backward_grid<WARPS>(grid);
+  cudaError_t e = backward_grid<WARPS, PHYS>(grid);
   float4s = (int64_t)grid * WARPS * kCkptEvery * kStateF4 * kWarp;
   return e;
 }
 
-template <int WARPS>
+template <int WARPS, int PHYS>
 cudaError_t launch_backward_cfg(const BwdArgs& a, cudaStream_t s) {
   int grid = 0;
-  cudaError_t e = backward_grid<WARPS>(grid);
+  cudaError_t e = backward_grid<WARPS, PHYS>(grid);
   if (e != cudaSuccess) return e;
   const int64_t chunks = ((int64_t)a.n_tracks + kWarp - 1) / kWarp;
   const int64_t need = (chunks + WARPS - 1) / WARPS;
   const int blocks = (int)(need < grid ? need : grid);
   e = cudaMemsetAsync(a.work, 0, sizeof(unsigned int), s);
   if (e != cudaSuccess) return e;
-  backward_kernel<WARPS><<<blocks, WARPS * 32, backward_smem_bytes<WARPS>(), s>>>(a);
+  backward_kernel<WARPS, PHYS><<<blocks, WARPS * 32, backward_smem_bytes<WARPS>(), s>>>(a);
   return cudaGetLastError();
 }
 
-// Segment store (float4 count) the backward needs for `warps` warps per block.
-inline cudaError_t backward_store(int warps, int64_t& float4s) {
+// Warps per block of a backward launch: the configured shape in a uniform
+// field; the field map runs in the 8-warp shape only.
+inline int backward_warps(int warps, int phys) { return phys ? 8 : warps; }
+
+// Segment store (float4 count) the backward needs for `warps` warps per block
+// and the physics bits phys (2: the field map).
+inline cudaError_t backward_store(int warps, int phys, int64_t& float4s) {
+  if (phys == 2) return backward_store_cfg<8, 2>(float4s);
+  if (phys != 0) return cudaErrorInvalidValue;
   switch (warps) {
-    case 4: return backward_store_cfg<4>(float4s);
-    case 8: return backward_store_cfg<8>(float4s);
-    case 10: return backward_store_cfg<10>(float4s);
-    case 12: return backward_store_cfg<12>(float4s);
+    case 4: return backward_store_cfg<4, 0>(float4s);
+    case 8: return backward_store_cfg<8, 0>(float4s);
+    case 10: return backward_store_cfg<10, 0>(float4s);
+    case 12: return backward_store_cfg<12, 0>(float4s);
     default: return cudaErrorInvalidValue;
   }
 }
 
 inline cudaError_t launch_backward(const BwdArgs& a, int warps, cudaStream_t s) {
   if (a.n_tracks <= 0) return cudaSuccess;
+  if (a.phys == 2) return launch_backward_cfg<8, 2>(a, s);
+  if (a.phys != 0) return cudaErrorInvalidValue;
   switch (warps) {
-    case 4: return launch_backward_cfg<4>(a, s);
-    case 8: return launch_backward_cfg<8>(a, s);
-    case 10: return launch_backward_cfg<10>(a, s);
-    case 12: return launch_backward_cfg<12>(a, s);
+    case 4: return launch_backward_cfg<4, 0>(a, s);
+    case 8: return launch_backward_cfg<8, 0>(a, s);
+    case 10: return launch_backward_cfg<10, 0>(a, s);
+    case 12: return launch_backward_cfg<12, 0>(a, s);
     default: return cudaErrorInvalidValue;
   }
 }

@@ -174,6 +174,7 @@ struct PredTape {
   float x1, s1, dx, k, kdx, s2;
   float c1, ic1, c2, ic2, Tm, den, w, sig, A, dl, tt;
   float Jys0, Jzs0, Lk;
+  float kap, xm, ym, zm;        // curvature per unit q/pt used; the field map's midpoint
   bool series;
 };
 
@@ -229,7 +230,11 @@ __device__ __forceinline__ bool predict_t(const SmemTables& T, const float pin[5
     const float zm = (zo + pin[1]) + hdx * (t / c1f);
     const float xm = x1 + hdx;
     kappa = kappa * ((1.0f + c_geo.f_r * (xm * xm + ym * ym)) + c_geo.f_z * (zm * zm));
+    tp.xm = xm;
+    tp.ym = ym;
+    tp.zm = zm;
   }
+  tp.kap = kappa;
   const float k = q * kappa;
   const float kdx = k * dx;
   const float s2 = s1 + kdx;

@@ -504,8 +504,7 @@ tpcfit_status tpcfit_fit_backward(tpcfit_handle* h, const tpcfit_hits* hits, con
   if (!h->rec_valid || h->rec_tracks != n_tracks || h->rec_hits != hits->n_hits ||
       h->rec_det != h->deterministic)
     return TPCFIT_ESTATE;
-  if (h->geo.mat) return TPCFIT_ESTATE;    // the adjoint has no reverse of the material layers
-  if (h->geo.field) return TPCFIT_ESTATE;  // nor of the field map's midpoint curvature
+  if (h->geo.mat) return TPCFIT_ESTATE;  // the adjoint has no reverse of the material layers
   tpcfit_status st = make_resident(h, s);
   if (st != TPCFIT_OK) return st;
   BwdArgs b{};
@@ -524,10 +523,12 @@ tpcfit_status tpcfit_fit_backward(tpcfit_handle* h, const tpcfit_hits* hits, con
   b.grad_chi2 = grad_chi2;
   b.grad_seeds = grad_seeds;
   b.work = h->d_work;
+  b.phys = h->geo.field ? 2 : 0;
   cudaError_t e = cudaSuccess;
   {
     int64_t need = 0;
-    e = h->deterministic ? backward_store_det(h->bwd_warps, need) : backward_store_fast(h->bwd_warps, need);
+    e = h->deterministic ? backward_store_det(h->bwd_warps, b.phys, need)
+                         : backward_store_fast(h->bwd_warps, b.phys, need);
     if (e != cudaSuccess) return from_cuda(e);
     st = grow(h->d_seg, h->seg_cap, need);
     if (st != TPCFIT_OK) return st;

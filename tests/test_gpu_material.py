@@ -5,7 +5,8 @@ Deterministic mode: bit-exact against the strict-FP32 oracle with material
 (energy loss and the square-root noise folding in their canonical order) and
 with the field map (midpoint curvature); fast mode within the FP32 tolerance
 of the FP64 oracle; the smoother, the batched-frame and run-time-compiled fits
-follow both; the adjoint refuses them."""
+follow both; the adjoint follows the field map (against the oracle's FP64
+forward-mode gradient) and refuses the material layers."""
 import numpy as np
 import pytest
 
@@ -157,9 +158,6 @@ def test_field_map_smoother_frames_rtc_and_adjoint(frame):
         out = f.fit(dev)
         ref = _host(out)
         sm = _host(f.smooth(dev, out))
-        with pytest.raises(tf.TpcfitError) as e:
-            f.backward(dev, out, torch.ones(fr.n_tracks, device="cuda"))
-        assert e.value.status == tf.ESTATE
         f.set_record(False)
         parts = [fr.subset(np.arange(a, b)) for a, b in ((0, 5000), (5000, 8000))]
         assert _bits_equal(_host(fit_frames(f, FrameBatch.from_frames(parts))), ref)
@@ -174,3 +172,46 @@ def test_field_map_smoother_frames_rtc_and_adjoint(frame):
     rep = compare(sm, oracle.smooth(fr))
     assert rep["nan_agree"] > 0.9999, rep
     assert rep["resid_ok"] > 0.999 and rep["rcov_ok"] > 0.999 and rep["chi2_ok"] > 0.999, rep
+
+
+def _rel(a, b):
+    return float(np.linalg.norm(np.asarray(a, np.float64) - b) / np.linalg.norm(b))
+
+
+@pytest.mark.parametrize("det", [False, True], ids=["fast", "det"])
+def test_field_map_adjoint_matches_forward_mode_oracle(frame, det):
+    # the reverse runs through the midpoint curvature, which moves with the
+    # state and with the previous cluster (residual coordinates); bounds as in
+    # the uniform-field adjoint test
+    fr = frame.subset(np.arange(2500))
+    fr.field = FIELD
+    d = synth.alignment_offsets(3)
+    w = np.random.default_rng(6).uniform(0.5, 2.0, fr.n_tracks).astype(np.float32)
+    ref = oracle.grad(fr, weights=w.astype(np.float64), align=d)
+    dev = tf.frame_to_device(fr)
+    f = tf.Fitter(fr.geometry, fr.bz, deterministic=det)
+    try:
+        f.set_field(FIELD)
+        f.set_alignment(torch.from_numpy(d).cuda())
+        f.set_record(True)
+        out = f.fit(dev)
+        gm = torch.empty((fr.n_hits, 2), device="cuda")
+        ga, gs = f.backward(dev, out, torch.from_numpy(w).cuda(), gm)
+        torch.cuda.synchronize()
+        gm, ga, gs = gm.cpu().numpy(), ga.cpu().numpy(), gs.cpu().numpy()
+        ndf = out["ndf"].cpu().numpy()
+        if det:  # and run to run
+            gm2 = torch.empty((fr.n_hits, 2), device="cuda")
+            ga2, gs2 = f.backward(dev, out, torch.from_numpy(w).cuda(), gm2)
+            assert np.array_equal(ga2.cpu().numpy().view(np.int32), ga.view(np.int32))
+            assert np.array_equal(gm2.cpu().numpy().view(np.int32), gm.view(np.int32))
+    finally:
+        f.close()
+    assert np.array_equal(ndf, ref["ndf"])
+    assert _rel(gm, ref["grad_meas"]) < 5e-4
+    assert _rel(ga, oracle.align_grad_from_meas(fr, ref["grad_meas"])) < 5e-4
+    assert _rel(gs, ref["grad_seed"]) < 5e-3
+    # the uniform-field reverse would be far off
+    ref0 = oracle.grad(fr.subset(np.arange(fr.n_tracks)), weights=w.astype(np.float64), align=d)
+    assert _rel(ref0["grad_meas"], ref["grad_meas"]) > 1e-2
+

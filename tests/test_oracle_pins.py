@@ -505,6 +505,40 @@ def test_forward_mode_gradient_matches_central_differences(oracle_mod, synth):
     assert np.linalg.norm(gr["grad_seed"] - gs) < 0.1 * np.linalg.norm(gs)
 
 
+@pytest.mark.parametrize("phys", ["field", "gas", "field+gas"])
+def test_forward_mode_gradient_with_field_map_and_material_matches_central_differences(oracle_mod, synth, phys):
+    # the gradient reference through the midpoint curvature of the field map
+    # (which moves with the state) and through the material layers (energy
+    # loss and the process noise, which depend on the state)
+    fr = synth.generate(5, 31, drop_p=0.05, cap_lengths=True)
+    field = synth.FieldMap(0.3, -0.2) if "field" in phys else None
+    mat = synth.TPC_GAS if "gas" in phys else None
+    fr.field, fr.material = field, mat
+    gr = oracle_mod.grad(fr)
+    assert np.all(gr["ndf"] > 0)
+    y = fr.y.astype(np.float64); z = fr.z.astype(np.float64); sd = fr.seeds.astype(np.float64)
+
+    def L(yv, zv):
+        ff = fr.subset(np.arange(fr.n_tracks))
+        ff.y64, ff.z64, ff.seeds64 = yv, zv, sd
+        ff.field, ff.material = field, mat
+        return float(oracle_mod.fit(ff, "f64", exact_inputs=True)["chi2"].sum())
+
+    h = 1e-4
+    gfd = np.zeros((fr.n_hits, 2))
+    for j in range(fr.n_hits):
+        for c, arr in ((0, y), (1, z)):
+            ap = arr.copy(); ap[j] += h
+            am = arr.copy(); am[j] -= h
+            fp = L(ap, z) if c == 0 else L(y, ap)
+            fm = L(am, z) if c == 0 else L(y, am)
+            gfd[j, c] = (fp - fm) / (2 * h)
+    assert np.linalg.norm(gr["grad_meas"] - gfd) / np.linalg.norm(gfd) < 1e-6
+    # and the physics matters: the gradient without it is far off
+    fr.field = fr.material = None
+    assert np.linalg.norm(oracle_mod.grad(fr)["grad_meas"] - gfd) / np.linalg.norm(gfd) > 1e-3
+
+
 # ---------------------------------------------------------------- material (per-row layers)
 def _material_tracks(synth, n, seed, **kw):
     """Tracks of 2-5 GeV/c near the centre of sector 0 (they stay in it)
