@@ -489,6 +489,13 @@ def main():
     torch.cuda.synchronize()
     _, mat_per = timed(step_fit, plain_steps)
     mat_ms = statistics.mean(p[0] for p in mat_per)
+    # and the fit + adjoint step through the layers
+    fitter.set_record(True)
+    for _ in range(args.warmup):
+        step_fa(torch.cuda.Event())
+    torch.cuda.synchronize()
+    _, mat_fa_per = timed(step_fa, max(5, args.steps // 4))
+    fitter.set_record(False)
     fitter.set_material(None)
 
     # ---- the same plain fit in the field map Bz (1 + 0.3 (r/250)^2 - 0.2 (z/250)^2)
@@ -498,6 +505,12 @@ def main():
     torch.cuda.synchronize()
     _, fld_per = timed(step_fit, plain_steps)
     fld_ms = statistics.mean(p[0] for p in fld_per)
+    fitter.set_record(True)
+    for _ in range(args.warmup):
+        step_fa(torch.cuda.Event())
+    torch.cuda.synchronize()
+    _, fld_fa_per = timed(step_fa, max(5, args.steps // 4))
+    fitter.set_record(False)
     fitter.set_field(None)
 
     # ---- end to end through the public API with host buffers
@@ -571,6 +584,13 @@ def main():
     line["plain_fit"]["material"] = {"tracks_per_s": fr.n_tracks / (mat_ms / 1e3), "ms": mat_ms,
                                      "material": "TPC gas layer at every row (X0 3.1e4 cm, 1.6 MeV/m, one row pitch)",
                                      "kernel": "fit_kernel<4,24> with the material layers"}
+    for key, per_, what in (("material", mat_fa_per, "TPC gas layer at every row"),
+                            ("field_map", fld_fa_per, "Bz (1 + 0.3 (r/250 cm)^2 - 0.2 (z/250 cm)^2)")):
+        f_ms = statistics.mean(p[0] for p in per_)
+        b_ms = statistics.mean(p[1] for p in per_)
+        line["fit_adjoint"][key] = {"tracks_per_s": fr.n_tracks / ((f_ms + b_ms) / 1e3), "fit_ms": f_ms,
+                                    "backward_ms": b_ms, "physics": what,
+                                    "kernel": "backward_kernel<8> compiled for this physics"}
     if rtc is not None:
         rtc_tf = fit_fl / (rtc["ms"] / 1e3) / 1e12
         line["plain_fit"]["rtc"] = {"tracks_per_s": fr.n_tracks / (rtc["ms"] / 1e3), "ms": rtc["ms"],

@@ -164,9 +164,10 @@ tpcfit_status tpcfit_fit_frames(tpcfit_handle* h, const tpcfit_hits* hits, const
  * crossed over l = row_cm sqrt(1 + tan^2 lambda) / cos phi; the energy drops by
  * dedx l / beta^2 and the direction scatters with the Highland angle (without
  * its logarithmic term), added as process noise.  x0_cm <= 0: no material
- * (default).  The fit, the smoother and the batched and run-time-compiled
- * fits follow it; tpcfit_fit_backward answers ESTATE while material is set.
- * EINVAL for non-finite or non-positive values. */
+ * (default).  The fit, the smoother, the batched and run-time-compiled fits
+ * and tpcfit_fit_backward follow it (the backward in its 8-warp shape,
+ * whatever tpcfit_set_backward_config chose).  EINVAL for non-finite or
+ * non-positive values. */
 tpcfit_status tpcfit_set_material(tpcfit_handle* h, double x0_cm, double dedx_gev_cm, double mass_gev, double row_cm);
 
 /* Non-uniform field (Sec. 4: propagation through the magnetic field): the
@@ -237,8 +238,8 @@ tpcfit_status tpcfit_set_backward_config(tpcfit_handle* h, int warps_per_block);
  * The backward recomputes each 16-step segment from its checkpoint into a
  * per-warp segment store and runs the hand-written reverse of every step,
  * copying the state before each step into shared memory one step ahead.  It
- * follows the field map (tpcfit_set_field_map); with material layers set it
- * answers ESTATE.  Fast mode accumulates grad_align with
+ * follows the field map and the material layers (tpcfit_set_field_map,
+ * tpcfit_set_material).  Fast mode accumulates grad_align with
  * atomics; deterministic mode writes per-cluster gradients, sorts the clusters
  * by (sector, row) with a stable radix sort and sums each key in a fixed order,
  * so grad_align is bitwise reproducible.  Tracks with ndf <= 0 contribute 0. */

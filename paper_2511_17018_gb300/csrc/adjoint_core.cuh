@@ -618,6 +618,273 @@ __device__ __forceinline__ void step_rev(const SmemTables& T, const float4* src,
   for (int c = 0; c < 5; ++c) b_p[c] = b_pi[c];
 }
 
+// Reverse of material_step for a step that was taken.  p: the state before it;
+// b_p in: adjoint of the state after, out: of the state before; bN: adjoints of
+// the terms it handed on (qq, b_s, b_t, b_q).  Only s, t and q enter.
+__device__ __forceinline__ void material_step_rev(const float p[5], int dir, const MatNoise& bN, float b_p[5]) {
+  const float s = p[2], t = p[3], q = p[4];
+  const float q2 = q * q;
+  if (!(q2 > 0.0f)) return;  // no material effect: nothing depends on the state
+  const float tt1 = 1.0f + t * t;
+  const float c = sqrtf((1.0f - s) * (1.0f + s));
+  const float st1 = sqrtf(tt1);
+  const float ell = (c_geo.d_row * st1) / c;
+  const float p2 = tt1 / q2;
+  const float e2 = p2 + c_geo.mass2;
+  const float kx = static_cast<float>(0.0136 * 0.0136) * c_geo.x0_inv;
+  const float ip2 = 1.0f / p2;
+  const float th2 = (kx * ell) * (e2 * (ip2 * ip2));
+  const float e = sqrtf(e2);
+  const float de = (c_geo.dedx * ell) * (e2 * ip2);
+  const float en = dir > 0 ? e - de : e + de;
+  const float pn2 = en * en - c_geo.mass2;
+  const float ratio = sqrtf(p2 / pn2);
+  const float qo = q * ratio;
+  const float th = sqrtf(th2);
+  // b_s = th c st1, b_t = th tt1, b_q = th qo t, qq = ratio, q' = q ratio
+  const float b_qo = b_p[4] + (bN.b_q * th) * t;
+  float b_t = b_p[3] + (bN.b_q * th) * qo;
+  const float b_th = (bN.b_s * c) * st1 + bN.b_t * tt1 + (bN.b_q * qo) * t;
+  float b_c = (bN.b_s * th) * st1;
+  float b_st1 = (bN.b_s * th) * c;
+  float b_tt1 = bN.b_t * th;
+  const float b_ratio = bN.qq + b_qo * q;
+  float b_q = b_qo * ratio;
+  const float b_th2 = th > 0.0f ? 0.5f * b_th / th : 0.0f;
+  // ratio = sqrt(u), u = p2 / pn2; pn2 = en^2 - m^2; en = e -+ de; e = sqrt(e2)
+  const float b_u = 0.5f * b_ratio / ratio;
+  const float ipn2 = 1.0f / pn2;
+  float b_p2 = b_u * ipn2;
+  const float b_pn2 = -(b_u * (p2 * ipn2)) * ipn2;
+  const float b_en = 2.0f * en * b_pn2;
+  float b_e2 = 0.5f * b_en / e;
+  const float b_de = dir > 0 ? -b_en : b_en;
+  // de = (dedx ell) (e2 / p2); th2 = (kx ell) (e2 / p2^2); e2 = p2 + m^2
+  float b_ell = (c_geo.dedx * (e2 * ip2)) * b_de + (kx * (e2 * (ip2 * ip2))) * b_th2;
+  b_e2 += ((c_geo.dedx * ell) * ip2) * b_de + ((kx * ell) * (ip2 * ip2)) * b_th2;
+  b_p2 -= ((c_geo.dedx * ell) * (e2 * (ip2 * ip2))) * b_de + 2.0f * ((kx * ell) * (e2 * (ip2 * ip2 * ip2))) * b_th2;
+  b_p2 += b_e2;
+  // p2 = tt1 / q^2; ell = d st1 / c; st1 = sqrt(tt1); c = sqrt((1 - s)(1 + s)); tt1 = 1 + t^2
+  b_tt1 += b_p2 / q2;
+  b_q += 2.0f * q * (-(b_p2 * p2) / q2);
+  b_st1 += (c_geo.d_row / c) * b_ell;
+  b_c -= (ell / c) * b_ell;
+  b_tt1 += 0.5f * b_st1 / st1;
+  b_t += 2.0f * t * b_tt1;
+  b_p[2] = b_p[2] - (s / c) * b_c;
+  b_p[3] = b_t;
+  b_p[4] = b_q;
+}
+
+// Reverse of material_factor.  Lin: the factor it was given (row q not yet
+// scaled by qq); F: the factor it returned, lower triangular with
+// F F^T = M = G G^T + B B^T, G = diag(1, 1, 1, 1, qq) Lin, B the noise columns
+// (b_s in row s; b_t, b_q in rows t, q).  bL in: adjoint of F (its lower
+// triangle; the rest of F is structurally zero), out: adjoint of Lin; bN
+// receives the adjoints of qq, b_s, b_t, b_q.  From dM = dF F^T + F dF^T with
+// F^-1 dF lower triangular: F^-1 dF = Phi(F^-1 dM F^-T), Phi keeping the lower
+// triangle with the diagonal halved, hence b_M = F^-T Phi(F^T b_F) F^-1, and
+// b_G = (b_M + b_M^T) G, b_B = (b_M + b_M^T) B.  (The Householder arithmetic
+// of the forward is not reversed step by step: this is the derivative of the
+// map it computes.)
+__device__ __forceinline__ void material_factor_rev(const float Lin[5][5], const MatNoise& N, const float F[5][5],
+                                                    float bL[5][5], MatNoise& bN) {
+  float Fi[5][5];  // F^-1, lower triangular
+#pragma unroll
+  for (int i = 0; i < 5; ++i) Fi[i][i] = 1.0f / F[i][i];
+#pragma unroll
+  for (int i = 1; i < 5; ++i)
+#pragma unroll
+    for (int j = 0; j < i; ++j) {
+      float acc = F[i][j] * Fi[j][j];
+#pragma unroll
+      for (int k = j + 1; k < i; ++k) acc = acc + F[i][k] * Fi[k][j];
+      Fi[i][j] = -(acc * Fi[i][i]);
+    }
+  // P = Phi(F^T b_F): P_ij = sum_{k >= i} F_ki bF_kj (i >= j), diagonal halved
+  float P[5][5];
+#pragma unroll
+  for (int i = 0; i < 5; ++i)
+#pragma unroll
+    for (int j = 0; j <= i; ++j) {
+      float acc = F[i][i] * bL[i][j];
+#pragma unroll
+      for (int k = i + 1; k < 5; ++k) acc = acc + F[k][i] * bL[k][j];
+      P[i][j] = i == j ? 0.5f * acc : acc;
+    }
+  // T = P F^-1 (lower), then b_M = F^-T T
+  float Tm[5][5];
+#pragma unroll
+  for (int i = 0; i < 5; ++i)
+#pragma unroll
+    for (int j = 0; j <= i; ++j) {
+      float acc = P[i][j] * Fi[j][j];
+#pragma unroll
+      for (int k = j + 1; k <= i; ++k) acc = acc + P[i][k] * Fi[k][j];
+      Tm[i][j] = acc;
+    }
+  float Sm[5][5];  // b_M + b_M^T
+#pragma unroll
+  for (int i = 0; i < 5; ++i)
+#pragma unroll
+    for (int j = 0; j < 5; ++j) {
+      const int k0 = i > j ? i : j;
+      float acc = Fi[k0][i] * Tm[k0][j];
+#pragma unroll
+      for (int k = k0 + 1; k < 5; ++k) acc = acc + Fi[k][i] * Tm[k][j];
+      Sm[i][j] = acc;
+    }
+#pragma unroll
+  for (int i = 0; i < 5; ++i)
+#pragma unroll
+    for (int j = 0; j < i; ++j) {
+      const float v = Sm[i][j] + Sm[j][i];
+      Sm[i][j] = v;
+      Sm[j][i] = v;
+    }
+#pragma unroll
+  for (int i = 0; i < 5; ++i) Sm[i][i] = 2.0f * Sm[i][i];
+  // b_G = Sm G, G = D Lin
+  float qsum = 0.0f;
+#pragma unroll
+  for (int i = 0; i < 5; ++i)
+#pragma unroll
+    for (int c = 0; c < 5; ++c) {
+      float acc = Sm[i][0] * Lin[0][c];
+#pragma unroll
+      for (int j = 1; j < 4; ++j) acc = acc + Sm[i][j] * Lin[j][c];
+      acc = acc + Sm[i][4] * (N.qq * Lin[4][c]);
+      if (i == 4) {
+        qsum = qsum + Lin[4][c] * acc;
+        bL[i][c] = N.qq * acc;
+      } else {
+        bL[i][c] = acc;
+      }
+    }
+  bN.qq = qsum;
+  bN.b_s = Sm[2][2] * N.b_s;
+  bN.b_t = Sm[3][3] * N.b_t + Sm[3][4] * N.b_q;
+  bN.b_q = Sm[4][3] * N.b_t + Sm[4][4] * N.b_q;
+}
+
+// step_rev with the material layers of the rows.  Outward (conv): prediction,
+// layer crossed on arrival (material_step on the predicted state), transport,
+// noise folded (material_factor), updates.  Inward: the layer of the row left
+// undone first (on the state before the step), then prediction, transport and
+// updates.  Arguments as for step_rev.
+template <int FIELD = 0>
+__device__ __forceinline__ void step_rev_mat(const SmemTables& T, const float4* src, float my_prev, float mz_prev,
+                                             bool first, bool conv, int row, int sec18, float m0, float m1,
+                                             float b_p[5], float b_L[5][5], float b_chi, float b_mc[2],
+                                             float b_mp[2]) {
+  StepState S0;
+  read_state(src, S0);
+  float p1[5];   // the state the updates start from
+  float pb[5];   // outward: predicted state before the layer; inward: S0.p after undoing it
+  float Lb[5][5];  // outward: transported factor before the noise; inward: S0.L after the layer
+  Jac J;
+  float L[5][5];
+  PredTape tp;
+  MatNoise N;
+  if (first) {
+#pragma unroll
+    for (int c = 0; c < 5; ++c) p1[c] = S0.p[c];
+    if (conv) {
+      p1[0] = S0.p[0] - m0;
+      p1[1] = S0.p[1] - m1;
+    }
+#pragma unroll
+    for (int i = 0; i < 5; ++i)
+#pragma unroll
+      for (int c = 0; c < 5; ++c) L[i][c] = S0.L[i][c];
+  } else if (conv) {
+    predict_residual<FIELD>(T, S0.p, S0.x, S0.sec, my_prev, mz_prev, sec18, T.row_x[row], m0, m1, p1, J, tp);
+#pragma unroll
+    for (int c = 0; c < 5; ++c) pb[c] = p1[c];
+    material_step(p1, 1, N);
+#pragma unroll
+    for (int i = 0; i < 5; ++i)
+#pragma unroll
+      for (int c = 0; c < 5; ++c) L[i][c] = S0.L[i][c];
+    transport(L, J);
+#pragma unroll
+    for (int i = 0; i < 5; ++i)
+#pragma unroll
+      for (int c = 0; c < 5; ++c) Lb[i][c] = L[i][c];
+    material_factor(L, N);
+  } else {
+#pragma unroll
+    for (int c = 0; c < 5; ++c) pb[c] = S0.p[c];
+    material_step(pb, -1, N);
+#pragma unroll
+    for (int i = 0; i < 5; ++i)
+#pragma unroll
+      for (int c = 0; c < 5; ++c) Lb[i][c] = S0.L[i][c];
+    material_factor(Lb, N);
+    predict_residual<FIELD>(T, pb, S0.x, S0.sec, my_prev, mz_prev, sec18, T.row_x[row], m0, m1, p1, J, tp);
+#pragma unroll
+    for (int i = 0; i < 5; ++i)
+#pragma unroll
+      for (int c = 0; c < 5; ++c) L[i][c] = Lb[i][c];
+    transport(L, J);
+  }
+  float p2[5];
+  float chi_dummy = 0.0f, b_dummy = 0.0f;
+#pragma unroll
+  for (int c = 0; c < 5; ++c) p2[c] = p1[c];
+  float L2[5][5];
+#pragma unroll
+  for (int i = 0; i < 5; ++i)
+#pragma unroll
+    for (int c = 0; c < 5; ++c) L2[i][c] = L[i][c];
+  scalar_update<0>(p2, L2, chi_dummy, 0.0f);
+  scalar_update_rev<1>(p2, L2, 0.0f, b_p, b_L, b_chi, b_dummy);
+  scalar_update_rev<0>(p1, L, 0.0f, b_p, b_L, b_chi, b_dummy);
+  // b_p: adjoint of the (shifted) state the updates started from; the layers
+  // change only q, so its y, z entries are those of the prediction
+  b_mc[0] = -b_p[0];
+  b_mc[1] = -b_p[1];
+  b_mp[0] = 0.0f;
+  b_mp[1] = 0.0f;
+  if (first) {
+    if (!conv) b_mc[0] = b_mc[1] = 0.0f;
+    return;
+  }
+  reread_state(src, S0);
+  const bool rot = S0.sec != sec18;
+  JacBar bJ;
+  MatNoise bN;
+  float b_pi[5], b_yo, b_zo;
+  if (conv) {
+    material_factor_rev(Lb, N, L, b_L, bN);
+    material_step_rev(pb, 1, bN, b_p);
+    if (!rot) {
+      b_mp[0] = b_p[0];
+      b_mp[1] = b_p[1];
+    }
+    transport_rev(S0.L, J, b_L, bJ);
+    predict_rev<FIELD>(tp, J, S0.p[3], S0.p[4], b_p, bJ, b_pi, b_yo, b_zo);
+  } else {
+    if (!rot) {
+      b_mp[0] = b_p[0];
+      b_mp[1] = b_p[1];
+    }
+    transport_rev(Lb, J, b_L, bJ);
+    predict_rev<FIELD>(tp, J, pb[3], pb[4], b_p, bJ, b_pi, b_yo, b_zo);
+    material_factor_rev(S0.L, N, Lb, b_L, bN);
+    material_step_rev(S0.p, -1, bN, b_pi);
+  }
+  if (rot) {
+    b_mp[0] = b_pi[0];
+    b_mp[1] = b_pi[1];
+  } else if (FIELD == 1) {
+    b_mp[0] += b_yo;
+    b_mp[1] += b_zo;
+  }
+#pragma unroll
+  for (int c = 0; c < 5; ++c) b_p[c] = b_pi[c];
+}
+
 // Fire-and-forget global float add (no value returned, nothing to wait for).
 __device__ __forceinline__ void red_add(float* p, float v) {
   asm volatile("red.global.add.f32 [%0], %1;\n" ::"l"(__cvta_generic_to_global(p)), "f"(v) : "memory");
@@ -665,9 +932,10 @@ constexpr size_t backward_smem_bytes() {
 // first, each state copied into shared memory asynchronously one step ahead.
 // Clusters are loaded one step ahead as well; the next segment's checkpoint
 // is copied while the current segment is reversed.
-// PHYS: 0 uniform field, 2 the field map (bit 1, material, has no reverse).
+// PHYS: bit 1 the material layers, bit 2 the field map.
 template <int WARPS, int PHYS>
 __global__ void __launch_bounds__(WARPS * 32, 1) backward_kernel(BwdArgs a) {
+  constexpr bool MAT = (PHYS & 1) != 0;
   constexpr int FIELD = (PHYS & 2) ? 1 : 0;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   BwdSmem& B = *reinterpret_cast<BwdSmem*>(smem_raw);
@@ -741,7 +1009,7 @@ __global__ void __launch_bounds__(WARPS * 32, 1) backward_kernel(BwdArgs a) {
             if (kk + 1 < cnt) nx = load_hit(a, h0 + hd * (i + 1));
             decode_hit(B.align, cur, m0, m1, row, sec);
             store_state(gs + kk * (kStateF4 * kWarp), S);
-            step_fwd<false, FIELD>(T, S, my, mz, i == 0, pass == 0, row, sec % kNSide, m0, m1);
+            step_fwd<MAT, FIELD>(T, S, my, mz, i == 0, pass == 0, row, sec % kNSide, m0, m1);
           }
           // the states just stored are read back by this thread's copies below
           __threadfence_block();
@@ -773,7 +1041,12 @@ __global__ void __launch_bounds__(WARPS * 32, 1) backward_kernel(BwdArgs a) {
             const float2 gcur = gnx;
             if (addg && i > 0) gnx = gmr[h - hd];
             float b_mc[2], b_mp[2];
-            step_rev<FIELD>(T, &W.st[kk & 1][0][lane], mpy, mpz, i == 0, pass == 0, row, sec % kNSide, m0, m1, b_p, b_L, b_chi, b_mc, b_mp);
+            if (MAT)
+              step_rev_mat<FIELD>(T, &W.st[kk & 1][0][lane], mpy, mpz, i == 0, pass == 0, row, sec % kNSide, m0, m1,
+                                  b_p, b_L, b_chi, b_mc, b_mp);
+            else
+              step_rev<FIELD>(T, &W.st[kk & 1][0][lane], mpy, mpz, i == 0, pass == 0, row, sec % kNSide, m0, m1,
+                              b_p, b_L, b_chi, b_mc, b_mp);
             accumulate_meas_grad(a, pass, h, row, sec, b_mc[0] + pend0, b_mc[1] + pend1, gcur);
             pend0 = b_mp[0];
             pend1 = b_mp[1];
@@ -842,14 +1115,19 @@ cudaError_t launch_backward_cfg(const BwdArgs& a, cudaStream_t s) {
 }
 
 // Warps per block of a backward launch: the configured shape in a uniform
-// field; the field map runs in the 8-warp shape only.
+// field without material; the other physics run in the 8-warp shape only.
 inline int backward_warps(int warps, int phys) { return phys ? 8 : warps; }
 
 // Segment store (float4 count) the backward needs for `warps` warps per block
-// and the physics bits phys (2: the field map).
+// and the physics bits phys (1: material layers, 2: the field map).
 inline cudaError_t backward_store(int warps, int phys, int64_t& float4s) {
-  if (phys == 2) return backward_store_cfg<8, 2>(float4s);
-  if (phys != 0) return cudaErrorInvalidValue;
+  switch (phys) {
+    case 0: break;
+    case 1: return backward_store_cfg<8, 1>(float4s);
+    case 2: return backward_store_cfg<8, 2>(float4s);
+    case 3: return backward_store_cfg<8, 3>(float4s);
+    default: return cudaErrorInvalidValue;
+  }
   switch (warps) {
     case 4: return backward_store_cfg<4, 0>(float4s);
     case 8: return backward_store_cfg<8, 0>(float4s);
@@ -861,8 +1139,13 @@ inline cudaError_t backward_store(int warps, int phys, int64_t& float4s) {
 
 inline cudaError_t launch_backward(const BwdArgs& a, int warps, cudaStream_t s) {
   if (a.n_tracks <= 0) return cudaSuccess;
-  if (a.phys == 2) return launch_backward_cfg<8, 2>(a, s);
-  if (a.phys != 0) return cudaErrorInvalidValue;
+  switch (a.phys) {
+    case 0: break;
+    case 1: return launch_backward_cfg<8, 1>(a, s);
+    case 2: return launch_backward_cfg<8, 2>(a, s);
+    case 3: return launch_backward_cfg<8, 3>(a, s);
+    default: return cudaErrorInvalidValue;
+  }
   switch (warps) {
     case 4: return launch_backward_cfg<4, 0>(a, s);
     case 8: return launch_backward_cfg<8, 0>(a, s);

@@ -106,7 +106,7 @@ struct BwdArgs {
   float* grad_align_atomic;    // [36][152][2] accumulated with atomics, or null
   unsigned int* work;
   float4* seg;                 // segment store: [resident warps][kCkptEvery][8][32] float4
-  int32_t phys;                // physics of the recorded fit: 0 uniform field, 2 the field map
+  int32_t phys;                // physics of the recorded fit: bit 1 material layers, bit 2 the field map
 };
 
 // Arguments of one smoother launch (same frame as the recorded fit).

@@ -504,7 +504,6 @@ tpcfit_status tpcfit_fit_backward(tpcfit_handle* h, const tpcfit_hits* hits, con
   if (!h->rec_valid || h->rec_tracks != n_tracks || h->rec_hits != hits->n_hits ||
       h->rec_det != h->deterministic)
     return TPCFIT_ESTATE;
-  if (h->geo.mat) return TPCFIT_ESTATE;  // the adjoint has no reverse of the material layers
   tpcfit_status st = make_resident(h, s);
   if (st != TPCFIT_OK) return st;
   BwdArgs b{};
@@ -523,7 +522,7 @@ tpcfit_status tpcfit_fit_backward(tpcfit_handle* h, const tpcfit_hits* hits, con
   b.grad_chi2 = grad_chi2;
   b.grad_seeds = grad_seeds;
   b.work = h->d_work;
-  b.phys = h->geo.field ? 2 : 0;
+  b.phys = (h->geo.mat ? 1 : 0) | (h->geo.field ? 2 : 0);
   cudaError_t e = cudaSuccess;
   {
     int64_t need = 0;

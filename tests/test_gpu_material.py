@@ -5,8 +5,8 @@ Deterministic mode: bit-exact against the strict-FP32 oracle with material
 (energy loss and the square-root noise folding in their canonical order) and
 with the field map (midpoint curvature); fast mode within the FP32 tolerance
 of the FP64 oracle; the smoother, the batched-frame and run-time-compiled fits
-follow both; the adjoint follows the field map (against the oracle's FP64
-forward-mode gradient) and refuses the material layers."""
+follow both; so does the adjoint (against the oracle's FP64 forward-mode
+gradient)."""
 import numpy as np
 import pytest
 
@@ -91,10 +91,6 @@ def test_smoother_with_material_matches_oracle(frame):
         f.set_record(True)
         out = f.fit(dev)
         got = _host(f.smooth(dev, out))
-        # the adjoint has no reverse of the material layers
-        with pytest.raises(tf.TpcfitError) as e:
-            f.backward(dev, out, torch.ones(fr.n_tracks, device="cuda"))
-        assert e.value.status == tf.ESTATE
     finally:
         f.close()
     rep = compare(got, oracle.smooth(fr))
@@ -178,20 +174,45 @@ def _rel(a, b):
     return float(np.linalg.norm(np.asarray(a, np.float64) - b) / np.linalg.norm(b))
 
 
+PHYS = {"field": (FIELD, None), "gas": (None, synth.TPC_GAS), "thick": (None, THICK),
+        "field+gas": (FIELD, synth.TPC_GAS)}
+
+
+def _thick_frame(n, seed):
+    """Tracks of 1-5 GeV/c through the thick layers, simulated with their
+    scattering and energy loss (sector 0).  On the slow tracks of the generic
+    frame the thick layers make a few chi2 values extremely sensitive to their
+    clusters (derivatives of ~1e4 per cm), beyond what an FP32 gradient can
+    follow; these tracks are not."""
+    rng = np.random.default_rng(seed)
+    qpt = rng.choice([-1, 1], n) / rng.uniform(1.0, 5.0, n)
+    tanl = rng.uniform(-0.5, 0.5, n)
+    phi0 = np.full(n, 0.5 * np.pi / 9) + rng.uniform(-0.03, 0.03, n)
+    z0 = rng.normal(0, 5, n)
+    return synth.simulate_material(qpt, tanl, phi0, z0, synth.default_geometry(), 0.5, THICK, rng=rng)
+
+
+@pytest.mark.parametrize("phys", list(PHYS))
 @pytest.mark.parametrize("det", [False, True], ids=["fast", "det"])
-def test_field_map_adjoint_matches_forward_mode_oracle(frame, det):
-    # the reverse runs through the midpoint curvature, which moves with the
-    # state and with the previous cluster (residual coordinates); bounds as in
-    # the uniform-field adjoint test
-    fr = frame.subset(np.arange(2500))
-    fr.field = FIELD
+def test_adjoint_with_field_map_and_material_matches_forward_mode_oracle(frame, det, phys):
+    # the reverse runs through the midpoint curvature (which moves with the
+    # state and, in residual coordinates, with the previous cluster) and through
+    # the layers (energy loss, and the noise folded into the factor); bounds as
+    # in the uniform-field adjoint test.  Thick layers stop some of the slow
+    # tracks, and FP32 and FP64 may stop them one row apart: those few tracks
+    # are left out of the comparison (the thick case runs on fast tracks, see
+    # _thick_frame).
+    field, mat = PHYS[phys]
+    fr = _thick_frame(1200, 21) if phys == "thick" else frame.subset(np.arange(2500))
+    fr.field, fr.material = field, mat
     d = synth.alignment_offsets(3)
     w = np.random.default_rng(6).uniform(0.5, 2.0, fr.n_tracks).astype(np.float32)
     ref = oracle.grad(fr, weights=w.astype(np.float64), align=d)
     dev = tf.frame_to_device(fr)
     f = tf.Fitter(fr.geometry, fr.bz, deterministic=det)
     try:
-        f.set_field(FIELD)
+        f.set_field(field)
+        f.set_material(mat)
         f.set_alignment(torch.from_numpy(d).cuda())
         f.set_record(True)
         out = f.fit(dev)
@@ -202,16 +223,22 @@ def test_field_map_adjoint_matches_forward_mode_oracle(frame, det):
         ndf = out["ndf"].cpu().numpy()
         if det:  # and run to run
             gm2 = torch.empty((fr.n_hits, 2), device="cuda")
-            ga2, gs2 = f.backward(dev, out, torch.from_numpy(w).cuda(), gm2)
+            ga2, _ = f.backward(dev, out, torch.from_numpy(w).cuda(), gm2)
             assert np.array_equal(ga2.cpu().numpy().view(np.int32), ga.view(np.int32))
             assert np.array_equal(gm2.cpu().numpy().view(np.int32), gm.view(np.int32))
     finally:
         f.close()
-    assert np.array_equal(ndf, ref["ndf"])
-    assert _rel(gm, ref["grad_meas"]) < 5e-4
-    assert _rel(ga, oracle.align_grad_from_meas(fr, ref["grad_meas"])) < 5e-4
-    assert _rel(gs, ref["grad_seed"]) < 5e-3
-    # the uniform-field reverse would be far off
-    ref0 = oracle.grad(fr.subset(np.arange(fr.n_tracks)), weights=w.astype(np.float64), align=d)
-    assert _rel(ref0["grad_meas"], ref["grad_meas"]) > 1e-2
-
+    ok = ndf == ref["ndf"]
+    assert ok.mean() > (0.999 if phys == "thick" else 1.0 - 1e-12), ok.mean()
+    hit_ok = np.repeat(ok, np.diff(fr.offsets))
+    assert _rel(gm[hit_ok], ref["grad_meas"][hit_ok]) < 5e-4
+    assert _rel(gs[:, ok], ref["grad_seed"][:, ok]) < 5e-3
+    # the alignment gradient is the per-key sum of the cluster gradients
+    assert _rel(ga, oracle.align_grad_from_meas(fr, gm)) < 1e-5
+    if ok.all():
+        assert _rel(ga, oracle.align_grad_from_meas(fr, ref["grad_meas"])) < 5e-4
+    # without the physics the reverse would be far off
+    bare = fr.subset(np.arange(fr.n_tracks))
+    bare.field, bare.material = None, None
+    ref0 = oracle.grad(bare, weights=w.astype(np.float64), align=d)
+    assert _rel(ref0["grad_meas"][hit_ok], ref["grad_meas"][hit_ok]) > 1e-3
