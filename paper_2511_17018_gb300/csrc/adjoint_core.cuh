@@ -986,16 +986,22 @@ __global__ void __launch_bounds__(WARPS * 32, 1) backward_kernel(BwdArgs a) {
         const bool addg = pass == 0 && gmr != nullptr;
         float2 gnx = addg ? gmr[h0 + hd * (steps - 1)] : make_float2(0.0f, 0.0f);
         fetch_ckpt(&W.ck[0][lane], ckp + (int64_t)(nseg - 1) * kCkptFloats);
+        // a segment's first cluster and the one before it, loaded a segment
+        // ahead; pv: the reverse's previous cluster, carried across segments
+        HitRaw seg_first = load_hit(a, h0 + hd * ((nseg - 1) * kCkptEvery));
+        HitRaw seg_prev{};
+        if (nseg > 1) seg_prev = load_hit(a, h0 + hd * ((nseg - 1) * kCkptEvery - 1));
+        HitRaw pv{};
 #pragma unroll 1
         for (int s = nseg - 1; s >= 0; --s) {
           const int i0 = s * kCkptEvery;
           const int cnt = min(kCkptEvery, steps - i0);
           StepState S;
           float my = 0.0f, mz = 0.0f;
-          HitRaw nx = load_hit(a, h0 + hd * i0);
+          HitRaw nx = seg_first;
           if (i0 > 0) {
             int row, sec;
-            decode_hit(B.align, load_hit(a, h0 + hd * (i0 - 1)), my, mz, row, sec);
+            decode_hit(B.align, seg_prev, my, mz, row, sec);
           }
           cp_async_wait<0>();
           read_state(&W.ck[0][lane], S);
@@ -1019,8 +1025,13 @@ __global__ void __launch_bounds__(WARPS * 32, 1) backward_kernel(BwdArgs a) {
           // the current cluster of its last step; each step's previous cluster
           // becomes the current one of the step before it
           fetch_state(&W.st[(cnt - 1) & 1][0][lane], gs + (cnt - 1) * (kStateF4 * kWarp));
-          HitRaw pv{};
-          if (i0 + cnt - 1 > 0) pv = load_hit(a, h0 + hd * (i0 + cnt - 2));
+          // (in later segments the reverse of the segment after this one left
+          // this cluster in pv)
+          if (s == nseg - 1 && i0 + cnt - 1 > 0) pv = load_hit(a, h0 + hd * (i0 + cnt - 2));
+          if (s > 0) {
+            seg_first = load_hit(a, h0 + hd * (i0 - kCkptEvery));
+            if (i0 - kCkptEvery > 0) seg_prev = load_hit(a, h0 + hd * (i0 - kCkptEvery - 1));
+          }
 #pragma unroll 1
           for (int kk = cnt - 1; kk >= 0; --kk) {
             const int i = i0 + kk;
