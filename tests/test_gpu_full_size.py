@@ -1,0 +1,86 @@
+"""The adjoint and the smoother on the full 400,000-track time frame, in the
+launch configuration the benchmark times (fast mode, 8-warp backward, length
+ordering), checked on a seeded sample of tracks (run on a GB300 with -m gpu).
+
+A track's cluster gradients, seed gradient and smoother outputs depend on that
+track alone, so the oracle computes them for the sample only; the alignment
+gradient sums every cluster, so it is checked against the per-key sums of the
+GPU's own cluster gradients."""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+import oracle  # noqa: E402
+from paper_2511_17018_gb300 import synth  # noqa: E402
+from paper_2511_17018_gb300 import tpcfit as tf  # noqa: E402
+from test_gpu_smooth import compare  # noqa: E402
+
+
+def _rel(a, b):
+    return float(np.linalg.norm(np.asarray(a, np.float64) - b) / np.linalg.norm(b))
+
+
+@pytest.fixture(scope="module")
+def full():
+    fr = synth.config2()
+    sample = np.sort(np.random.default_rng(78).choice(fr.n_tracks, 1500, replace=False))
+    return fr, sample
+
+
+def _hits_of(fr, tracks):
+    off = fr.offsets.astype(np.int64)
+    return np.concatenate([np.arange(off[i], off[i + 1]) for i in tracks])
+
+
+@pytest.mark.parametrize("det", [False, True], ids=["fast", "det"])
+def test_full_size_adjoint_sampled(full, det):
+    fr, sample = full
+    w = np.random.default_rng(79).uniform(0.5, 2.0, fr.n_tracks).astype(np.float32)
+    dev = tf.frame_to_device(fr)
+    f = tf.Fitter(fr.geometry, fr.bz, deterministic=det)
+    try:
+        f.set_backward_config(8)
+        f.set_record(True)
+        out = f.fit(dev)
+        gm = torch.empty((fr.n_hits, 2), device="cuda")
+        ga, gs = f.backward(dev, out, torch.from_numpy(w).cuda(), gm)
+        torch.cuda.synchronize()
+        gm, ga, gs = gm.cpu().numpy(), ga.cpu().numpy(), gs.cpu().numpy()
+        ndf = out["ndf"].cpu().numpy()
+        assert f.status()[0] == tf.OK
+    finally:
+        f.close()
+    sub = fr.subset(sample)
+    ref = oracle.grad(sub, weights=w[sample].astype(np.float64))
+    ok = ndf[sample] == ref["ndf"]
+    assert ok.mean() > 0.999
+    h = _hits_of(fr, sample)
+    hit_ok = np.repeat(ok, np.diff(sub.offsets))
+    assert _rel(gm[h][hit_ok], ref["grad_meas"][hit_ok]) < 5e-4
+    assert _rel(gs[:, sample][:, ok], ref["grad_seed"][:, ok]) < 5e-3
+    # 32M cluster gradients summed into 10,944 keys: FP32 sums (atomics in fast
+    # mode, fixed-order sums in deterministic mode) against FP64 ones
+    assert _rel(ga, oracle.align_grad_from_meas(fr, gm)) < 1e-4
+    # unfitted tracks contribute nothing
+    bad = np.flatnonzero(ndf <= 0)
+    if bad.size:
+        assert np.all(gm[_hits_of(fr, bad[:100])] == 0.0)
+
+
+def test_full_size_smoother_sampled(full):
+    fr, sample = full
+    dev = tf.frame_to_device(fr)
+    f = tf.Fitter(fr.geometry, fr.bz)
+    try:
+        f.set_record(True)
+        out = f.fit(dev)
+        sm = {k: v.cpu().numpy() for k, v in f.smooth(dev, out).items()}
+    finally:
+        f.close()
+    h = _hits_of(fr, sample)
+    got = {k: v[h] for k, v in sm.items()}
+    rep = compare(got, oracle.smooth(fr.subset(sample)))
+    assert rep["nan_agree"] > 0.999, rep
+    assert rep["resid_ok"] > 0.999 and rep["rcov_ok"] > 0.999 and rep["chi2_ok"] > 0.999, rep
