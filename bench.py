@@ -224,7 +224,7 @@ def e2e_run(fitter, fr, out, steps, tf, torch):
                pin["seeds"].numpy())
     for _ in range(2):
         tf.tpcfit_fit_host(fitter.h, *args_np, out=hnp)
-    n = max(3, min(50, steps // 10))
+    n = max(10, min(50, steps // 10))
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     for _ in range(n):
@@ -232,108 +232,72 @@ def e2e_run(fitter, fr, out, steps, tf, torch):
     return fr.n_tracks / ((time.perf_counter() - t0) / n)
 
 
-def e2e_fit_adjoint(fitter, fr, steps, tf, torch):
-    """Tracks/s of fit + adjoint through the public API from pinned host buffers:
-    each step copies the batch and dL/dchi2 to the device, fits with
-    checkpoints, runs the adjoint and copies chi2, ndf and both gradients back."""
+def _e2e_host_buffers(fr, torch):
+    """The batch and dL/dchi2 in pinned host memory, and two sets of pinned
+    host outputs (numpy views)."""
     n = fr.n_tracks
-    pin = {k: torch.from_numpy(np.ascontiguousarray(v)).pin_memory() for k, v in
-           (("y", fr.y), ("z", fr.z), ("rowsec", fr.rowsec.view(np.int16)), ("offsets", fr.offsets),
-            ("seeds", fr.seeds), ("g", np.full(n, 1.0 / n, np.float32)))}
-    d = {k: torch.empty_like(v, device="cuda") for k, v in pin.items()}
-    out = tf.empty_outputs(n)
-    ga = torch.empty(36 * 152 * 2, dtype=torch.float32, device="cuda")
-    gs = torch.empty((5, n), dtype=torch.float32, device="cuda")
-    host_out = {"chi2": torch.empty(n).pin_memory(), "ndf": torch.empty(n, dtype=torch.int32).pin_memory(),
-                "ga": torch.empty(36 * 152 * 2).pin_memory(), "gs": torch.empty((5, n)).pin_memory()}
+    pin = [torch.from_numpy(np.ascontiguousarray(a)).pin_memory() for a in
+           (fr.y, fr.z, fr.rowsec.view(np.int16), fr.offsets, fr.seeds, np.full(n, 1.0 / n, np.float32))]
+    y, z, rs, off, sd, g = (t.numpy() for t in pin)
+    args = (y, z, rs.view(np.uint16), off, sd, g)
+
+    def outputs():
+        t = {"chi2": torch.empty(n).pin_memory(), "ndf": torch.empty(n, dtype=torch.int32).pin_memory(),
+             "grad_align": torch.empty((36, 152, 2)).pin_memory(), "grad_seeds": torch.empty((5, n)).pin_memory()}
+        return t, {k: v.numpy() for k, v in t.items()}
+    outs = [outputs() for _ in range(2)]
+    h2d = sum(t.numel() * t.element_size() for t in pin)
+    d2h = sum(v.numel() * v.element_size() for v in outs[0][0].values())
+    return pin, args, outs, h2d, d2h
+
+
+def e2e_fit_adjoint(fitter, fr, steps, tf, torch):
+    """Tracks/s of fit + adjoint through the C-ABI host-buffer call
+    (tpcfit_fit_adjoint_host): each step copies the batch and dL/dchi2 from
+    pinned host memory, fits with checkpoints, runs the adjoint and copies chi2,
+    ndf and both gradients back; the host waits for each step before the next."""
+    _pin, args, outs, h2d, d2h = _e2e_host_buffers(fr, torch)
+    stream = torch.cuda.current_stream()
 
     def step():
-        for k in d:
-            d[k].copy_(pin[k], non_blocking=True)
-        fitter.fit(d, out)
-        tf.tpcfit_fit_backward(fitter.h, d["y"], d["z"], d["rowsec"], d["offsets"], out["ndf"], d["g"], ga, gs)
-        host_out["chi2"].copy_(out["chi2"], non_blocking=True)
-        host_out["ndf"].copy_(out["ndf"], non_blocking=True)
-        host_out["ga"].copy_(ga, non_blocking=True)
-        host_out["gs"].copy_(gs, non_blocking=True)
-        torch.cuda.current_stream().synchronize()
+        tf.tpcfit_fit_adjoint_host(fitter.h, *args, out=outs[0][1])
+        stream.synchronize()
 
     for _ in range(2):
         step()
-    m = max(3, min(30, steps // 10))
+    m = max(10, min(30, steps // 10))
     t0 = time.perf_counter()
     for _ in range(m):
         step()
     dt = (time.perf_counter() - t0) / m
-    h2d = sum(v.numel() * v.element_size() for v in pin.values())
-    d2h = sum(v.numel() * v.element_size() for v in host_out.values())
-    return n / dt, h2d, d2h
+    return fr.n_tracks / dt, h2d, d2h
 
 
 def e2e_fit_adjoint_pipelined(fitter, fr, steps, tf, torch):
-    """The same steps (per step: the batch and dL/dchi2 copied from pinned host
-    memory, fit with checkpoints, adjoint, chi2, ndf and both gradients copied
-    back and waited for by the host) with the inputs double-buffered: step k+1's
-    copies run on a copy stream while step k computes, as a caller streaming
-    batches through the device API would run them."""
-    n = fr.n_tracks
-    pin = {k: torch.from_numpy(np.ascontiguousarray(v)).pin_memory() for k, v in
-           (("y", fr.y), ("z", fr.z), ("rowsec", fr.rowsec.view(np.int16)), ("offsets", fr.offsets),
-            ("seeds", fr.seeds), ("g", np.full(n, 1.0 / n, np.float32)))}
-    bufs = [{k: torch.empty_like(v, device="cuda") for k, v in pin.items()} for _ in range(2)]
-    out = tf.empty_outputs(n)
-    ga = torch.empty(36 * 152 * 2, dtype=torch.float32, device="cuda")
-    gs = torch.empty((5, n), dtype=torch.float32, device="cuda")
-    host = [{"chi2": torch.empty(n).pin_memory(), "ndf": torch.empty(n, dtype=torch.int32).pin_memory(),
-             "ga": torch.empty(36 * 152 * 2).pin_memory(), "gs": torch.empty((5, n)).pin_memory()} for _ in range(2)]
-    comp = torch.cuda.current_stream()
-    copy = torch.cuda.Stream()
-    ev_in = [torch.cuda.Event() for _ in range(2)]
-    ev_free = [torch.cuda.Event() for _ in range(2)]
-    ev_out = [torch.cuda.Event() for _ in range(2)]
-
-    def enqueue_copy(j):
-        b = bufs[j % 2]
-        copy.wait_event(ev_free[j % 2])  # the step that last read this buffer has finished
-        with torch.cuda.stream(copy):
-            for k in b:
-                b[k].copy_(pin[k], non_blocking=True)
-        ev_in[j % 2].record(copy)
-
-    def enqueue_step(j):
-        b, ho = bufs[j % 2], host[j % 2]
-        comp.wait_event(ev_in[j % 2])
-        fitter.fit(b, out)
-        tf.tpcfit_fit_backward(fitter.h, b["y"], b["z"], b["rowsec"], b["offsets"], out["ndf"], b["g"], ga, gs)
-        ev_free[j % 2].record(comp)
-        ho["chi2"].copy_(out["chi2"], non_blocking=True)
-        ho["ndf"].copy_(out["ndf"], non_blocking=True)
-        ho["ga"].copy_(ga, non_blocking=True)
-        ho["gs"].copy_(gs, non_blocking=True)
-        ev_out[j % 2].record(comp)
+    """The same calls issued back to back: the library copies a call's inputs
+    on its own copy stream into one of two staging sets, so step k+1's copies
+    overlap step k's fit and adjoint; the host waits for every step's results
+    (step k-1's while step k runs) before reusing their buffers."""
+    _pin, args, outs, h2d, d2h = _e2e_host_buffers(fr, torch)
+    stream = torch.cuda.current_stream()
+    ev = [torch.cuda.Event() for _ in range(2)]
 
     def run(m):
-        enqueue_copy(0)
         for j in range(m):
-            if j + 1 < m:
-                enqueue_copy(j + 1)
             if j >= 2:
-                ev_out[j % 2].synchronize()  # the host has the results of step j - 2 before they are overwritten
-            enqueue_step(j)
+                ev[j % 2].synchronize()  # step j - 2's results were read before the buffers are reused
+            tf.tpcfit_fit_adjoint_host(fitter.h, *args, out=outs[j % 2][1])
+            ev[j % 2].record(stream)
             if j >= 1:
-                ev_out[(j - 1) % 2].synchronize()  # the host waits for step j - 1's results
-        ev_out[(m - 1) % 2].synchronize()
+                ev[(j - 1) % 2].synchronize()  # the host has step j - 1's results
+        ev[(m - 1) % 2].synchronize()
 
     run(3)
-    torch.cuda.synchronize()
-    m = max(4, min(30, steps // 10))
+    m = max(10, min(30, steps // 10))
     t0 = time.perf_counter()
     run(m)
     dt = (time.perf_counter() - t0) / m
-    torch.cuda.synchronize()
-    h2d = sum(v.numel() * v.element_size() for v in pin.values())
-    d2h = sum(v.numel() * v.element_size() for v in host[0].values())
-    return n / dt, h2d, d2h
+    return fr.n_tracks / dt, h2d, d2h
 
 
 def run_batched_frames(args, tf, torch, synth, flops, peak_tf):
@@ -593,8 +557,10 @@ def main():
             _, (v, e2e_plain["value"], v_serial) = combine_ranks(dist, torch, "cuda", 0.0,
                                                                  [v, e2e_plain["value"], v_serial])
         e2e = {"value": v, "unit": UNIT, "h2d_bytes_per_step": hb, "d2h_bytes_per_step": db,
-               "pipelining": "inputs double-buffered: step k+1's host-to-device copies overlap step k's compute; "
-                             "the host waits for every step's results",
+               "call": "tpcfit_fit_adjoint_host (C ABI, pinned host buffers), one call per step",
+               "pipelining": "calls issued back to back: step k+1's host-to-device copies (library copy stream, "
+                             "second staging set) overlap step k's fit and adjoint; the host waits for every "
+                             "step's results",
                "serial_value": v_serial}
 
     if rank != 0:

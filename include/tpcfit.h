@@ -264,6 +264,25 @@ tpcfit_status tpcfit_fit_backward(tpcfit_handle* h, const tpcfit_hits* hits, con
 tpcfit_status tpcfit_smooth(tpcfit_handle* h, const tpcfit_hits* hits, const int32_t* track_offsets, int32_t n_tracks,
                             const int32_t* ndf, float* resid, float* rcov, float* chi2, void* stream);
 
+/* Fit + adjoint with HOST buffers, for streams of batches.  Copies hits,
+ * offsets, seeds and grad_chi2 (host, as for tpcfit_fit and
+ * tpcfit_fit_backward) to the device on an internal copy stream, fits with
+ * recording on and runs the adjoint on `stream`, and copies back:
+ *   chi2_out [n_tracks], ndf_out [n_tracks], grad_align_out [36][152][2],
+ *   grad_seeds_out [5][n_tracks] (host).
+ * Returns once the work is enqueued: the outputs are valid when `stream` has
+ * passed this call (synchronise it, or an event recorded after the call), and
+ * the inputs must stay unchanged until then.  The handle keeps two device
+ * staging sets and uses them in turn, so the copies of the next call overlap
+ * this call's fit and adjoint (with pinned host memory).  It leaves the
+ * handle's recorded fit (for tpcfit_fit_backward and tpcfit_smooth) set to
+ * this batch.  n_tracks = 0 zeroes grad_align_out and returns.  EINVAL for
+ * missing pointers or n_hits above INT32_MAX. */
+tpcfit_status tpcfit_fit_adjoint_host(tpcfit_handle* h, const float* y, const float* z, const uint16_t* rowsec,
+                                      int64_t n_hits, const int32_t* track_offsets, int32_t n_tracks,
+                                      const float* seeds, const float* grad_chi2, float* chi2_out, int32_t* ndf_out,
+                                      float* grad_align_out, float* grad_seeds_out, void* stream);
+
 /* Fit with HOST buffers: copies hits, offsets and seeds to the device, fits and
  * copies the outputs back, all on `stream`, then synchronises the stream.
  * Same argument meaning as tpcfit_fit with every array in host memory

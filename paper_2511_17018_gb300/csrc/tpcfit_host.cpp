@@ -122,6 +122,14 @@ struct tpcfit_handle {
   // staging for tpcfit_fit_host
   unsigned char* d_stage = nullptr;
   size_t stage_cap = 0;
+  // tpcfit_fit_adjoint_host: two staging sets used in turn, their copy stream
+  // and events (inputs copied; the set's last reader finished)
+  unsigned char* d_pipe[2] = {nullptr, nullptr};
+  size_t pipe_cap[2] = {0, 0};
+  int pipe_slot = 0;
+  cudaStream_t pipe_copy = nullptr;
+  cudaEvent_t pipe_in[2] = {nullptr, nullptr};
+  cudaEvent_t pipe_free[2] = {nullptr, nullptr};
   // adjoint: checkpoints of the last recorded fit
   int record = 0;
   int bwd_warps = 8;
@@ -264,6 +272,12 @@ void tpcfit_destroy(tpcfit_handle* h) {
   if (h->d_sort_scratch) cudaFree(h->d_sort_scratch);
   if (h->d_perm) cudaFree(h->d_perm);
   if (h->d_stage) cudaFree(h->d_stage);
+  for (int i = 0; i < 2; ++i) {
+    if (h->d_pipe[i]) cudaFree(h->d_pipe[i]);
+    if (h->pipe_in[i]) cudaEventDestroy(h->pipe_in[i]);
+    if (h->pipe_free[i]) cudaEventDestroy(h->pipe_free[i]);
+  }
+  if (h->pipe_copy) cudaStreamDestroy(h->pipe_copy);
   if (h->d_ck) cudaFree(h->d_ck);
   if (h->d_ck_last) cudaFree(h->d_ck_last);
   if (h->d_gm) cudaFree(h->d_gm);
@@ -650,6 +664,82 @@ tpcfit_status tpcfit_fit_host(tpcfit_handle* h, const float* y, const float* z, 
   if (e == cudaSuccess) e = cudaMemcpyAsync(chi2_out, b + o_chi, 4 * N, cudaMemcpyDeviceToHost, s);
   if (e == cudaSuccess) e = cudaMemcpyAsync(ndf_out, b + o_ndf, 4 * N, cudaMemcpyDeviceToHost, s);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  return from_cuda(e);
+}
+
+tpcfit_status tpcfit_fit_adjoint_host(tpcfit_handle* h, const float* y, const float* z, const uint16_t* rowsec,
+                                      int64_t n_hits, const int32_t* track_offsets, int32_t n_tracks,
+                                      const float* seeds, const float* grad_chi2, float* chi2_out, int32_t* ndf_out,
+                                      float* grad_align_out, float* grad_seeds_out, void* stream) {
+  if (!h || n_tracks < 0 || n_hits < 0 || n_hits > INT32_MAX) return TPCFIT_EINVAL;
+  if (!grad_align_out) return TPCFIT_EINVAL;
+  if (n_tracks > 0 && (!track_offsets || !seeds || !grad_chi2 || !chi2_out || !ndf_out || !grad_seeds_out))
+    return TPCFIT_EINVAL;
+  if (n_hits > 0 && (!y || !z || !rowsec)) return TPCFIT_EINVAL;
+  cudaStream_t s = (cudaStream_t)stream;
+  cudaError_t e = cudaSuccess;
+  if (n_tracks == 0) {
+    std::memset(grad_align_out, 0, sizeof(float) * kAlignFloats);
+    return TPCFIT_OK;
+  }
+  const size_t N = (size_t)n_tracks, H = (size_t)n_hits;
+  auto up = [](size_t b) { return (b + 255) & ~(size_t)255; };
+  const size_t o_y = 0, o_z = o_y + up(4 * H), o_rs = o_z + up(4 * H), o_off = o_rs + up(2 * H),
+               o_seed = o_off + up(4 * (N + 1)), o_g = o_seed + up(20 * N), o_par = o_g + up(4 * N),
+               o_cov = o_par + up(20 * N), o_chi = o_cov + up(60 * N), o_ndf = o_chi + up(4 * N),
+               o_gs = o_ndf + up(4 * N), o_ga = o_gs + up(20 * N), total = o_ga + up(4 * (size_t)kAlignFloats);
+  if (!h->pipe_copy) {
+    e = cudaStreamCreateWithFlags(&h->pipe_copy, cudaStreamNonBlocking);
+    for (int i = 0; i < 2 && e == cudaSuccess; ++i) {
+      e = cudaEventCreateWithFlags(&h->pipe_in[i], cudaEventDisableTiming);
+      if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->pipe_free[i], cudaEventDisableTiming);
+    }
+    if (e != cudaSuccess) return from_cuda(e);
+  }
+  const int slot = h->pipe_slot;
+  if (total > h->pipe_cap[slot]) {
+    // the set may still be in use by an earlier call's work (its readback included)
+    e = cudaDeviceSynchronize();
+    if (e != cudaSuccess) return from_cuda(e);
+    if (h->d_pipe[slot]) cudaFree(h->d_pipe[slot]);
+    h->d_pipe[slot] = nullptr;
+    h->pipe_cap[slot] = 0;
+    e = cudaMalloc(&h->d_pipe[slot], total);
+    if (e != cudaSuccess) return from_cuda(e);
+    h->pipe_cap[slot] = total;
+  }
+  unsigned char* b = h->d_pipe[slot];
+  // inputs, on the copy stream, once the set's previous reader has finished
+  cudaStream_t c = h->pipe_copy;
+  e = cudaStreamWaitEvent(c, h->pipe_free[slot], 0);
+  if (e == cudaSuccess && H) e = cudaMemcpyAsync(b + o_y, y, 4 * H, cudaMemcpyHostToDevice, c);
+  if (e == cudaSuccess && H) e = cudaMemcpyAsync(b + o_z, z, 4 * H, cudaMemcpyHostToDevice, c);
+  if (e == cudaSuccess && H) e = cudaMemcpyAsync(b + o_rs, rowsec, 2 * H, cudaMemcpyHostToDevice, c);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(b + o_off, track_offsets, 4 * (N + 1), cudaMemcpyHostToDevice, c);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(b + o_seed, seeds, 20 * N, cudaMemcpyHostToDevice, c);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(b + o_g, grad_chi2, 4 * N, cudaMemcpyHostToDevice, c);
+  if (e == cudaSuccess) e = cudaEventRecord(h->pipe_in[slot], c);
+  // fit with checkpoints and adjoint on the caller's stream
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(s, h->pipe_in[slot], 0);
+  if (e != cudaSuccess) return from_cuda(e);
+  h->pipe_slot = slot ^ 1;
+  tpcfit_hits hh{(const float*)(b + o_y), (const float*)(b + o_z), (const uint16_t*)(b + o_rs), n_hits};
+  const int rec = h->record;
+  h->record = 1;
+  tpcfit_status st = tpcfit_fit(h, &hh, (const int32_t*)(b + o_off), n_tracks, (const float*)(b + o_seed),
+                                (float*)(b + o_par), (float*)(b + o_cov), (float*)(b + o_chi), (int32_t*)(b + o_ndf),
+                                stream);
+  h->record = rec;
+  if (st == TPCFIT_OK)
+    st = tpcfit_fit_backward(h, &hh, (const int32_t*)(b + o_off), n_tracks, (const int32_t*)(b + o_ndf),
+                             (const float*)(b + o_g), (float*)(b + o_ga), (float*)(b + o_gs), nullptr, stream);
+  if (st != TPCFIT_OK) return st;
+  e = cudaEventRecord(h->pipe_free[slot], s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(chi2_out, b + o_chi, 4 * N, cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(ndf_out, b + o_ndf, 4 * N, cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(grad_seeds_out, b + o_gs, 20 * N, cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(grad_align_out, b + o_ga, sizeof(float) * kAlignFloats, cudaMemcpyDeviceToHost, s);
   return from_cuda(e);
 }
 

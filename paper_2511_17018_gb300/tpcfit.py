@@ -54,6 +54,7 @@ def load():
         "tpcfit_reserve": (C.c_int, [vp, i64, i64]),
         "tpcfit_fit": (C.c_int, [vp, C.POINTER(_Hits), vp, i32, vp, vp, vp, vp, vp, vp]),
         "tpcfit_fit_host": (C.c_int, [vp, vp, vp, vp, i64, vp, i32, vp, vp, vp, vp, vp, vp]),
+        "tpcfit_fit_adjoint_host": (C.c_int, [vp, vp, vp, vp, i64, vp, i32, vp, vp, vp, vp, vp, vp, vp]),
         "tpcfit_get_status": (C.c_int, [vp, vp, C.POINTER(i32), C.POINTER(i64)]),
         "tpcfit_fit_noalloc": (C.c_int, [C.POINTER(_Geometry), C.c_double, vp, C.c_int, C.POINTER(_Hits), vp, i32, vp,
                                          vp, vp, vp, vp, vp]),
@@ -290,6 +291,36 @@ def tpcfit_fit_host(h, y, z, rowsec, offsets, seeds, stream=None, out=None):
                                 n, seeds.ctypes.data, out["params"].ctypes.data, out["cov"].ctypes.data,
                                 out["chi2"].ctypes.data, out["ndf"].ctypes.data, _stream(stream))
     _check(st, "tpcfit_fit_host")
+    return out
+
+
+def tpcfit_fit_adjoint_host(h, y, z, rowsec, offsets, seeds, grad_chi2, out=None, stream=None):
+    """Enqueue fit + adjoint from host arrays (pinned CPU tensors for overlap);
+    the host outputs are valid once `stream` has passed the call."""
+    def arr(a, dt):
+        if hasattr(a, "numpy"):
+            a = a.numpy()
+        a = np.asarray(a)
+        if a.dtype != dt or not a.flags["C_CONTIGUOUS"]:
+            raise TypeError(f"host array must be contiguous {dt}")
+        return a
+    y = arr(y, np.float32); z = arr(z, np.float32); rowsec = arr(rowsec, np.uint16)
+    offsets = arr(offsets, np.int32); seeds = arr(seeds, np.float32); grad_chi2 = arr(grad_chi2, np.float32)
+    n = offsets.shape[0] - 1
+    if out is None:
+        out = dict(chi2=np.empty(n, np.float32), ndf=np.empty(n, np.int32),
+                   grad_align=np.empty((36, 152, 2), np.float32), grad_seeds=np.empty((5, n), np.float32))
+    o = {}
+    for k, dt, size in (("chi2", np.float32, n), ("ndf", np.int32, n), ("grad_align", np.float32, 36 * 152 * 2),
+                        ("grad_seeds", np.float32, 5 * n)):
+        o[k] = arr(out[k], dt)
+        if o[k].size != size:
+            raise TypeError(f"{k}: {size} elements expected")
+    st = load().tpcfit_fit_adjoint_host(h, y.ctypes.data, z.ctypes.data, rowsec.ctypes.data, y.shape[0],
+                                        offsets.ctypes.data, n, seeds.ctypes.data, grad_chi2.ctypes.data,
+                                        o["chi2"].ctypes.data, o["ndf"].ctypes.data, o["grad_align"].ctypes.data,
+                                        o["grad_seeds"].ctypes.data, _stream(stream))
+    _check(st, "tpcfit_fit_adjoint_host")
     return out
 
 

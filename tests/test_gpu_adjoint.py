@@ -148,3 +148,39 @@ def test_failed_tracks_contribute_nothing():
         assert np.all(np.isfinite(ga.cpu().numpy()))
     finally:
         f.close()
+
+
+def test_fit_adjoint_host_pipelined_calls(case):
+    # the host-buffer entry point equals the device calls bit for bit
+    # (deterministic mode), and two calls issued back to back (the second's
+    # copies overlapping the first's work) each return their own batch's results
+    fr, d_true, w, _ = case
+    parts = [fr.subset(np.arange(0, 1500)), fr.subset(np.arange(1500, fr.n_tracks))]
+    f = tf.Fitter(fr.geometry, fr.bz, deterministic=True)
+    try:
+        f.set_alignment(torch.from_numpy(d_true).cuda())
+        want = []
+        for p in parts:
+            dev = tf.frame_to_device(p)
+            f.set_record(True)
+            out = f.fit(dev)
+            ga, gs = f.backward(dev, out, torch.from_numpy(w[:p.n_tracks]).cuda())
+            torch.cuda.synchronize()
+            want.append((out["chi2"].cpu().numpy(), out["ndf"].cpu().numpy(), ga.cpu().numpy(), gs.cpu().numpy()))
+        f.set_record(False)
+        pins = []
+        for p in parts:
+            pins.append([torch.from_numpy(np.ascontiguousarray(a)).pin_memory() for a in
+                         (p.y, p.z, p.rowsec.view(np.int16), p.offsets, p.seeds, w[:p.n_tracks])])
+        got = []
+        for p, pn in zip(parts, pins):
+            y, z, rs, off, sd, g = (t.numpy() for t in pn)
+            got.append(tf.tpcfit_fit_adjoint_host(f.h, y, z, rs.view(np.uint16), off, sd, g))
+        torch.cuda.synchronize()
+    finally:
+        f.close()
+    for (chi2, ndf, ga, gs), o in zip(want, got):
+        assert np.array_equal(o["ndf"], ndf)
+        assert np.array_equal(o["chi2"].view(np.int32), chi2.view(np.int32))
+        assert np.array_equal(o["grad_align"].view(np.int32), ga.view(np.int32))
+        assert np.array_equal(o["grad_seeds"].view(np.int32), gs.view(np.int32))
