@@ -284,10 +284,15 @@ tpcfit_status tpcfit_fit_adjoint_host(tpcfit_handle* h, const float* y, const fl
                                       float* grad_align_out, float* grad_seeds_out, void* stream);
 
 /* Fit with HOST buffers: copies hits, offsets and seeds to the device, fits and
- * copies the outputs back, all on `stream`, then synchronises the stream.
- * Same argument meaning as tpcfit_fit with every array in host memory
- * (pinned memory gives asynchronous copies).  Device staging buffers are owned
- * by the handle and grown as needed. */
+ * copies the outputs back, then synchronises `stream`.  Same argument meaning
+ * as tpcfit_fit with every array in host memory (pinned memory gives
+ * asynchronous copies).  The batch is streamed in chunks of about 196,608
+ * tracks (at most 8): a chunk is copied on the library's copy stream while the
+ * one before it is fitted on `stream`; results do not depend on the chunking.
+ * With recording on (tpcfit_set_record) the batch is one chunk, since the
+ * adjoint follows a single recorded fit.  EINVAL if the offsets at the chunk
+ * boundaries decrease or exceed n_hits.  Device staging buffers are owned by
+ * the handle and grown as needed. */
 tpcfit_status tpcfit_fit_host(tpcfit_handle* h, const float* y, const float* z, const uint16_t* rowsec,
                               int64_t n_hits, const int32_t* track_offsets, int32_t n_tracks, const float* seeds,
                               float* params_out, float* cov_out, float* chi2_out, int32_t* ndf_out, void* stream);

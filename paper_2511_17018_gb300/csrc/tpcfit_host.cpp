@@ -105,6 +105,13 @@ void forget_resident_constants() {
 
 using namespace tpcfit;
 
+// tpcfit_fit_host streams a batch in chunks of about this many tracks (at
+// most kHostChunksMax), copying one while the previous one is fitted.  A fit
+// takes at least the time of its longest tracks (about 0.44 ms for 152-row
+// tracks, whatever the batch size), so chunks stay large.
+constexpr size_t kHostChunkTracks = 196608;
+constexpr int kHostChunksMax = 8;
+
 struct tpcfit_handle {
   int device = 0;
   GeoConst geo{};
@@ -130,6 +137,8 @@ struct tpcfit_handle {
   cudaStream_t pipe_copy = nullptr;
   cudaEvent_t pipe_in[2] = {nullptr, nullptr};
   cudaEvent_t pipe_free[2] = {nullptr, nullptr};
+  // tpcfit_fit_host: one event per chunk copied
+  cudaEvent_t chunk_in[kHostChunksMax] = {};
   // adjoint: checkpoints of the last recorded fit
   int record = 0;
   int bwd_warps = 8;
@@ -187,6 +196,19 @@ tpcfit_status grow(T*& ptr, int64_t& cap, int64_t need) {
   if (e != cudaSuccess) return from_cuda(e);
   cap = need;
   return TPCFIT_OK;
+}
+
+// Lazily created copy stream and events of the host-buffer entry points.
+tpcfit_status ensure_pipe(tpcfit_handle* h) {
+  if (h->pipe_copy) return TPCFIT_OK;
+  cudaError_t e = cudaStreamCreateWithFlags(&h->pipe_copy, cudaStreamNonBlocking);
+  for (int i = 0; i < 2 && e == cudaSuccess; ++i) {
+    e = cudaEventCreateWithFlags(&h->pipe_in[i], cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->pipe_free[i], cudaEventDisableTiming);
+  }
+  for (int i = 0; i < kHostChunksMax && e == cudaSuccess; ++i)
+    e = cudaEventCreateWithFlags(&h->chunk_in[i], cudaEventDisableTiming);
+  return from_cuda(e);
 }
 
 tpcfit_status ensure_perm(tpcfit_handle* h, int64_t n) {
@@ -277,6 +299,8 @@ void tpcfit_destroy(tpcfit_handle* h) {
     if (h->pipe_in[i]) cudaEventDestroy(h->pipe_in[i]);
     if (h->pipe_free[i]) cudaEventDestroy(h->pipe_free[i]);
   }
+  for (int i = 0; i < kHostChunksMax; ++i)
+    if (h->chunk_in[i]) cudaEventDestroy(h->chunk_in[i]);
   if (h->pipe_copy) cudaStreamDestroy(h->pipe_copy);
   if (h->d_ck) cudaFree(h->d_ck);
   if (h->d_ck_last) cudaFree(h->d_ck_last);
@@ -633,38 +657,75 @@ tpcfit_status tpcfit_fit_host(tpcfit_handle* h, const float* y, const float* z, 
   cudaStream_t s = (cudaStream_t)stream;
   const size_t N = (size_t)n_tracks, H = (size_t)n_hits;
   auto up = [](size_t b) { return (b + 255) & ~(size_t)255; };
+  // hits and offsets at their own positions; seeds and outputs per chunk,
+  // [rows][chunk tracks] at the chunk's first track (rows x track offset)
   const size_t o_y = 0, o_z = o_y + up(4 * H), o_rs = o_z + up(4 * H), o_off = o_rs + up(2 * H),
                o_seed = o_off + up(4 * (N + 1)), o_par = o_seed + up(20 * N), o_cov = o_par + up(20 * N),
                o_chi = o_cov + up(60 * N), o_ndf = o_chi + up(4 * N), total = o_ndf + up(4 * N);
   if (total > h->stage_cap) {
+    cudaError_t e = cudaDeviceSynchronize();
+    if (e != cudaSuccess) return from_cuda(e);
     if (h->d_stage) cudaFree(h->d_stage);
     h->d_stage = nullptr;
     h->stage_cap = 0;
-    cudaError_t e = cudaMalloc(&h->d_stage, total);
+    e = cudaMalloc(&h->d_stage, total);
     if (e != cudaSuccess) return from_cuda(e);
     h->stage_cap = total;
   }
+  tpcfit_status st = ensure_pipe(h);
+  if (st != TPCFIT_OK) return st;
   unsigned char* b = h->d_stage;
-  cudaError_t e = cudaSuccess;
-  if (H) {
-    e = cudaMemcpyAsync(b + o_y, y, 4 * H, cudaMemcpyHostToDevice, s);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(b + o_z, z, 4 * H, cudaMemcpyHostToDevice, s);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(b + o_rs, rowsec, 2 * H, cudaMemcpyHostToDevice, s);
+  // chunks of about kHostChunkTracks tracks; one chunk while recording, since
+  // the adjoint follows a single recorded fit
+  int K = (int)((N + kHostChunkTracks - 1) / kHostChunkTracks);
+  if (K > kHostChunksMax) K = kHostChunksMax;
+  if (K < 1 || h->record) K = 1;
+  // the copies use the offsets at the chunk boundaries: they must be in order
+  // and within the hits (the kernels check every track's offsets)
+  for (int k = 0; k <= K; ++k) {
+    const int32_t o = track_offsets[N * (size_t)k / (size_t)K];
+    const int32_t prev = k ? track_offsets[N * (size_t)(k - 1) / (size_t)K] : 0;
+    if (o < prev || (int64_t)o > n_hits) return TPCFIT_EINVAL;
   }
-  if (e == cudaSuccess) e = cudaMemcpyAsync(b + o_off, track_offsets, 4 * (N + 1), cudaMemcpyHostToDevice, s);
-  if (e == cudaSuccess) e = cudaMemcpyAsync(b + o_seed, seeds, 20 * N, cudaMemcpyHostToDevice, s);
+  cudaStream_t c = h->pipe_copy;
+  cudaError_t e = cudaSuccess;
+  for (int k = 0; k < K && e == cudaSuccess; ++k) {
+    const size_t t0 = N * (size_t)k / (size_t)K, t1 = N * (size_t)(k + 1) / (size_t)K, n = t1 - t0;
+    const size_t h0 = (size_t)track_offsets[t0], h1 = (size_t)track_offsets[t1];
+    if (h1 > h0) {
+      e = cudaMemcpyAsync(b + o_y + 4 * h0, y + h0, 4 * (h1 - h0), cudaMemcpyHostToDevice, c);
+      if (e == cudaSuccess) e = cudaMemcpyAsync(b + o_z + 4 * h0, z + h0, 4 * (h1 - h0), cudaMemcpyHostToDevice, c);
+      if (e == cudaSuccess)
+        e = cudaMemcpyAsync(b + o_rs + 2 * h0, rowsec + h0, 2 * (h1 - h0), cudaMemcpyHostToDevice, c);
+    }
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(b + o_off + 4 * t0, track_offsets + t0, 4 * (n + 1), cudaMemcpyHostToDevice, c);
+    // seeds [5][N] on the host -> [5][n] for the chunk
+    if (e == cudaSuccess)
+      e = cudaMemcpy2DAsync(b + o_seed + 20 * t0, 4 * n, seeds + t0, 4 * N, 4 * n, 5, cudaMemcpyHostToDevice, c);
+    if (e == cudaSuccess) e = cudaEventRecord(h->chunk_in[k], c);
+  }
   if (e != cudaSuccess) return from_cuda(e);
   tpcfit_hits hh{(const float*)(b + o_y), (const float*)(b + o_z), (const uint16_t*)(b + o_rs), n_hits};
-  tpcfit_status st = tpcfit_fit(h, &hh, (const int32_t*)(b + o_off), n_tracks, (const float*)(b + o_seed),
-                                (float*)(b + o_par), (float*)(b + o_cov), (float*)(b + o_chi), (int32_t*)(b + o_ndf),
-                                stream);
-  if (st != TPCFIT_OK) return st;
-  e = cudaMemcpyAsync(params_out, b + o_par, 20 * N, cudaMemcpyDeviceToHost, s);
-  if (e == cudaSuccess) e = cudaMemcpyAsync(cov_out, b + o_cov, 60 * N, cudaMemcpyDeviceToHost, s);
-  if (e == cudaSuccess) e = cudaMemcpyAsync(chi2_out, b + o_chi, 4 * N, cudaMemcpyDeviceToHost, s);
-  if (e == cudaSuccess) e = cudaMemcpyAsync(ndf_out, b + o_ndf, 4 * N, cudaMemcpyDeviceToHost, s);
-  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
-  return from_cuda(e);
+  for (int k = 0; k < K; ++k) {
+    const size_t t0 = N * (size_t)k / (size_t)K, t1 = N * (size_t)(k + 1) / (size_t)K, n = t1 - t0;
+    e = cudaStreamWaitEvent(s, h->chunk_in[k], 0);
+    if (e != cudaSuccess) return from_cuda(e);
+    float* par = (float*)(b + o_par + 20 * t0);
+    float* cov = (float*)(b + o_cov + 60 * t0);
+    st = tpcfit_fit(h, &hh, (const int32_t*)(b + o_off + 4 * t0), (int32_t)n, (const float*)(b + o_seed + 20 * t0),
+                    par, cov, (float*)(b + o_chi) + t0, (int32_t*)(b + o_ndf) + t0, stream);
+    if (st != TPCFIT_OK) return st;
+    // [rows][n] -> the caller's [rows][N] at column t0
+    e = cudaMemcpy2DAsync(params_out + t0, 4 * N, par, 4 * n, 4 * n, 5, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaMemcpy2DAsync(cov_out + t0, 4 * N, cov, 4 * n, 4 * n, 15, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(chi2_out + t0, (float*)(b + o_chi) + t0, 4 * n, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(ndf_out + t0, (int32_t*)(b + o_ndf) + t0, 4 * n, cudaMemcpyDeviceToHost, s);
+    if (e != cudaSuccess) return from_cuda(e);
+  }
+  return from_cuda(cudaStreamSynchronize(s));
 }
 
 tpcfit_status tpcfit_fit_adjoint_host(tpcfit_handle* h, const float* y, const float* z, const uint16_t* rowsec,
@@ -688,13 +749,9 @@ tpcfit_status tpcfit_fit_adjoint_host(tpcfit_handle* h, const float* y, const fl
                o_seed = o_off + up(4 * (N + 1)), o_g = o_seed + up(20 * N), o_par = o_g + up(4 * N),
                o_cov = o_par + up(20 * N), o_chi = o_cov + up(60 * N), o_ndf = o_chi + up(4 * N),
                o_gs = o_ndf + up(4 * N), o_ga = o_gs + up(20 * N), total = o_ga + up(4 * (size_t)kAlignFloats);
-  if (!h->pipe_copy) {
-    e = cudaStreamCreateWithFlags(&h->pipe_copy, cudaStreamNonBlocking);
-    for (int i = 0; i < 2 && e == cudaSuccess; ++i) {
-      e = cudaEventCreateWithFlags(&h->pipe_in[i], cudaEventDisableTiming);
-      if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->pipe_free[i], cudaEventDisableTiming);
-    }
-    if (e != cudaSuccess) return from_cuda(e);
+  {
+    tpcfit_status sp = ensure_pipe(h);
+    if (sp != TPCFIT_OK) return sp;
   }
   const int slot = h->pipe_slot;
   if (total > h->pipe_cap[slot]) {

@@ -84,3 +84,19 @@ def test_full_size_smoother_sampled(full):
     rep = compare(got, oracle.smooth(fr.subset(sample)))
     assert rep["nan_agree"] > 0.999, rep
     assert rep["resid_ok"] > 0.999 and rep["rcov_ok"] > 0.999 and rep["chi2_ok"] > 0.999, rep
+
+
+@pytest.mark.parametrize("det", [False, True], ids=["fast", "det"])
+def test_host_buffer_fit_in_chunks_equals_device_fit(full, det):
+    # tpcfit_fit_host streams the 400k tracks in 3 chunks (copies of one chunk
+    # overlapping the fit of the one before); per-track results are those of
+    # the single device launch, bit for bit
+    fr, _ = full
+    f = tf.Fitter(fr.geometry, fr.bz, deterministic=det)
+    try:
+        ref = {k: v.cpu().numpy() for k, v in f.fit(tf.frame_to_device(fr)).items()}
+        got = tf.tpcfit_fit_host(f.h, fr.y, fr.z, fr.rowsec, fr.offsets, np.ascontiguousarray(fr.seeds))
+    finally:
+        f.close()
+    for k in ("params", "cov", "chi2", "ndf"):
+        assert np.array_equal(np.ascontiguousarray(got[k]).view(np.int32), np.ascontiguousarray(ref[k]).view(np.int32)), k
