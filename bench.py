@@ -114,10 +114,12 @@ def _traffic(kernel_key: str):
 
 
 def _source_sha() -> str:
+    """Hash of the kernel sources (.cu, .cuh and the headers they include); the
+    host-side .cpp files do not change what a kernel reads and writes."""
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_2511_17018_gb300", "csrc")
     for fn in sorted(os.listdir(csrc)):
-        if fn.endswith((".cu", ".cuh", ".h", ".cpp")):
+        if fn.endswith((".cu", ".cuh", ".h")):
             with open(os.path.join(csrc, fn), "rb") as f:
                 h.update(fn.encode())
                 h.update(f.read())
