@@ -66,4 +66,7 @@ def test_argument_errors_before_any_cuda_call(lib):
     assert lib.tpcfit_reserve(None, 10, 10) == tpcfit.EINVAL
     assert lib.tpcfit_fit(None, None, None, 0, None, None, None, None, None, None) == tpcfit.EINVAL
     assert lib.tpcfit_get_status(None, None, None, None) == tpcfit.EINVAL
+    assert lib.tpcfit_fit_host(None, None, None, None, 0, None, 1, None, None, None, None, None, None) == tpcfit.EINVAL
+    assert lib.tpcfit_fit_adjoint_host(None, None, None, None, 0, None, 1, None, None, None, None, None, None,
+                                       None) == tpcfit.EINVAL
     lib.tpcfit_destroy(None)
