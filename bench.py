@@ -167,7 +167,7 @@ def run_reference(args, rank: int, world: int):
         return
     from paper_2511_17018_gb300 import synth
     import oracle
-    fr = synth.config2(N_TRACKS)
+    fr = synth.time_frame(N_TRACKS)
     threads = oracle.default_threads()
     probe = fr.subset(np.arange(256))
     t0 = time.perf_counter()
@@ -303,11 +303,11 @@ def e2e_fit_adjoint_pipelined(fitter, fr, steps, tf, torch):
 
 
 def run_batched_frames(args, tf, torch, synth, flops, peak_tf):
-    """256 frames, track counts log-uniform on [1e3, 2e5] (about 15M tracks), one
+    """256 frames, track counts log-uniform on [1e3, 2e5] (8.99M tracks), one
     persistent launch replayed from a CUDA graph; launch shape from the autotuner."""
     from paper_2511_17018_gb300 import autotune
     from paper_2511_17018_gb300.frames import FrameBatch, GraphedFrameFit, fit_frames
-    pool, picks = synth.config4(pool_tracks=args.pool_tracks)
+    pool, picks = synth.batched_frames(pool_tracks=args.pool_tracks)
     batch = FrameBatch.from_pool(pool, picks)
     lengths = np.diff(batch.offsets.cpu().numpy().astype(np.int64))
     res = {"workload": "256 frames, tracks per frame log-uniform on [1e3, 2e5], drawn from a simulated pool of "

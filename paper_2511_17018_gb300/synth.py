@@ -363,26 +363,30 @@ def alignment_offsets(seed: int, sigma: float = 0.05) -> np.ndarray:
     return rng.normal(0.0, sigma, (N_SECTORS, N_ROWS, 2)).astype(np.float32)
 
 
-# --- the benchmark configurations -------------------------------------------------
+# --- the benchmark workloads -----------------------------------------------------
 
-def config1(n_tracks: int = 1000) -> Frame:
-    """Plain fit: natural lengths, one cluster per crossed row, sigma 0.1 cm."""
+def plain_frame(n_tracks: int = 1000) -> Frame:
+    """Plain-fit frame (1,000 tracks by default): natural lengths, one cluster
+    per crossed row, sigma 0.1 cm, no drops."""
     return generate(n_tracks, 1)
 
 
-def config2(n_tracks: int = 400_000) -> Frame:
-    """Time-frame-sized batch: 5% of hits dropped, lengths capped at U{10..152}."""
+def time_frame(n_tracks: int = 400_000) -> Frame:
+    """Time-frame-sized batch (400,000 tracks by default): 5% of hits dropped,
+    lengths capped at U{10..152}."""
     return generate(n_tracks, 2, drop_p=0.05, cap_lengths=True)
 
 
-def config3(n_tracks: int = 100_000) -> Frame:
-    """Adjoint workload: injected offsets N(0, 0.05 cm) on all 36 x 152 x 2 keys."""
+def adjoint_frame(n_tracks: int = 100_000) -> Frame:
+    """Adjoint workload (100,000 tracks by default): injected offsets
+    N(0, 0.05 cm) on all 36 x 152 x 2 keys."""
     d = alignment_offsets(3)
     return generate(n_tracks, 3, drop_p=0.05, cap_lengths=True, d_true=d)
 
 
-def config5(n_tracks: int = 2_000_000) -> Frame:
-    """Alignment-recovery workload: as the adjoint workload, more tracks."""
+def alignment_frame(n_tracks: int = 2_000_000) -> Frame:
+    """Alignment-recovery workload (2,000,000 tracks by default): as the
+    adjoint workload, more tracks."""
     d = alignment_offsets(5)
     return generate(n_tracks, 5, drop_p=0.05, cap_lengths=True, d_true=d)
 
@@ -393,10 +397,12 @@ def frame_sizes_batched(seed: int = 4, n_frames: int = 256, lo: int = 1000, hi: 
     return np.exp(rng.uniform(math.log(lo), math.log(hi), n_frames)).astype(np.int64)
 
 
-def config4(pool_tracks: int = 1_000_000, n_frames: int = 256, seed: int = 4):
-    """Batched uneven frames.  Tracks are drawn (seeded, with replacement) from a
-    simulated pool of ``pool_tracks`` distinct tracks with the configuration's
-    distributions; returns (pool Frame, per-frame track index arrays)."""
+def batched_frames(pool_tracks: int = 1_000_000, n_frames: int = 256, seed: int = 4):
+    """Batched uneven frames: ``n_frames`` frames with track counts log-uniform
+    on [1e3, 2e5] (256 frames: about 9.6M tracks on average, 8.99M for seed 4).
+    Tracks are drawn (seeded, with replacement) from a simulated pool of
+    ``pool_tracks`` distinct tracks with the time-frame batch's distributions;
+    returns (pool Frame, per-frame track index arrays)."""
     pool = generate(pool_tracks, seed, drop_p=0.05, cap_lengths=True)
     sizes = frame_sizes_batched(seed, n_frames)
     rng = _streams(seed + 1000, ["pick"])["pick"]

@@ -28,7 +28,7 @@ def oracle_mod():
 @pytest.fixture(scope="session")
 def frame_small(synth):
     """1,000 tracks, natural lengths (the plain-fit workload)."""
-    return synth.config1()
+    return synth.plain_frame()
 
 
 @pytest.fixture(scope="session")

@@ -40,7 +40,7 @@ def fitter():
 @pytest.fixture(scope="module")
 def frames():
     return {
-        "plain1000": synth.config1(),
+        "plain1000": synth.plain_frame(),
         "drop20k": synth.generate(20000, 2, drop_p=0.05, cap_lengths=True),
         "align5k": synth.generate(5000, 3, drop_p=0.05, cap_lengths=True, d_true=synth.alignment_offsets(3)),
     }
@@ -159,7 +159,7 @@ def test_host_buffer_entry_point_equals_device_entry_point(fitter, frames):
 def test_full_size_time_frame_sampled(fitter):
     # 400,000 tracks in one launch (the time-frame-sized batch); the oracle checks
     # a seeded sample of 3,000 tracks one by one
-    fr = synth.config2()
+    fr = synth.time_frame()
     dev = tf.frame_to_device(fr)
     rng = np.random.default_rng(77)
     sample = np.sort(rng.choice(fr.n_tracks, 3000, replace=False))

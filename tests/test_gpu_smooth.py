@@ -94,7 +94,7 @@ def test_smoother_flags_a_displaced_cluster():
 
 
 def test_smoother_needs_a_recorded_fit():
-    fr = synth.config1()
+    fr = synth.plain_frame()
     dev = tf.frame_to_device(fr)
     f = tf.Fitter(fr.geometry, fr.bz)
     try:
