@@ -3,7 +3,10 @@
 Each iteration uploads the current offset estimate to the fitter, fits every
 track with checkpoints, runs the adjoint of L = mean chi2 over fitted tracks
 and applies one Adam step (Kingma & Ba, 2015) to the offsets.  The iteration
-is captured in a CUDA graph once and replayed.
+is captured in a CUDA graph once and replayed.  The loop's state (offsets,
+Adam moments, step count) can be written to a file every few iterations and
+read back to resume; the file is replaced atomically, so an interrupted run
+leaves the previous checkpoint intact.
 
 Offsets that a helix absorbs cannot be recovered from chi2: per sector,
 dy_r = a + b X_r + c X_r^2 and dz_r = a' + b' X_r move every cluster of that
@@ -12,6 +15,8 @@ tan lambda) follow.  `recovery` therefore reports the RMS of the estimate's
 error both raw and after projecting out these five modes per sector.
 """
 from __future__ import annotations
+
+import os
 
 import numpy as np
 import torch
@@ -57,6 +62,39 @@ class AlignmentLoop:
         for x in (self.d, self.m, self.v, self.t):
             x.zero_()
 
+    # ---- checkpoint / resume
+    STATE_KEYS = ("d", "m", "v", "t")
+
+    def state_dict(self) -> dict:
+        """Offsets, Adam moments and step count (host copies) with the settings."""
+        sd = {k: getattr(self, k).detach().cpu().clone() for k in self.STATE_KEYS}
+        sd.update(lr=self.lr, betas=(self.b1, self.b2), eps=self.eps, n_tracks=self.n)
+        return sd
+
+    def load_state_dict(self, sd: dict):
+        """Copy a saved state into the loop's buffers in place (the captured
+        graph keeps reading the same device memory).  The settings must match."""
+        if (sd["lr"], tuple(sd["betas"]), sd["eps"]) != (self.lr, (self.b1, self.b2), self.eps):
+            raise ValueError("checkpoint was written with other Adam settings")
+        if sd["n_tracks"] != self.n:
+            raise ValueError("checkpoint was written for another track sample")
+        for k in self.STATE_KEYS:
+            dst = getattr(self, k)
+            src = sd[k]
+            if tuple(src.shape) != tuple(dst.shape):
+                raise ValueError(f"checkpoint entry {k} has shape {tuple(src.shape)}, expected {tuple(dst.shape)}")
+            dst.copy_(src.to(dst.device, dst.dtype))
+
+    def save(self, path: str):
+        save_state(path, self.state_dict())
+
+    def load(self, path: str):
+        self.load_state_dict(load_state(path))
+
+    @property
+    def iteration(self) -> int:
+        return int(self.t.item())
+
     def _iteration(self):
         tf.tpcfit_set_alignment(self.f.h, self.d)
         self.f.fit(self.dev, self.out)
@@ -82,12 +120,29 @@ class AlignmentLoop:
             self._iteration()
         return self.loss
 
-    def run(self, iters: int):
+    def run(self, iters: int, checkpoint: str | None = None, every: int = 0):
+        """`iters` iterations; with `checkpoint` and `every` > 0 the state is
+        saved to that file after every `every`-th iteration (counted from the
+        start of the whole run, resumed runs included) and after the last."""
         losses = []
-        for _ in range(iters):
+        start = self.iteration if checkpoint else 0
+        for i in range(iters):
             losses.append(self.step().clone())
+            if checkpoint and every > 0 and ((start + i + 1) % every == 0 or i == iters - 1):
+                self.save(checkpoint)
         torch.cuda.synchronize()
         return torch.stack(losses).cpu().numpy()
+
+
+def save_state(path: str, sd: dict):
+    """Write a loop state to `path` through a temporary file and a rename."""
+    tmp = f"{path}.tmp{os.getpid()}"
+    torch.save(sd, tmp)
+    os.replace(tmp, path)
+
+
+def load_state(path: str) -> dict:
+    return torch.load(path, map_location="cpu", weights_only=True)
 
 
 def weak_mode_basis(row_x):

@@ -48,3 +48,71 @@ def test_alignment_loop_recovers_offsets():
         assert np.allclose(l1, l2, rtol=1e-5)
     finally:
         f.close()
+
+
+def _bare_loop(n=10, lr=5e-3):
+    """An AlignmentLoop's state without a fitter (CPU tensors), for the file logic."""
+    torch = pytest.importorskip("torch")
+    from paper_2511_17018_gb300 import align
+    lp = align.AlignmentLoop.__new__(align.AlignmentLoop)
+    lp.n, lp.lr, lp.b1, lp.b2, lp.eps = n, lr, 0.9, 0.999, 1e-8
+    lp.d = torch.zeros(36 * 152 * 2)
+    lp.m = torch.zeros_like(lp.d)
+    lp.v = torch.zeros_like(lp.d)
+    lp.t = torch.zeros(())
+    return lp
+
+
+def test_checkpoint_round_trip_and_checks(tmp_path):
+    torch = pytest.importorskip("torch")
+    a = _bare_loop()
+    g = torch.Generator().manual_seed(3)
+    for x in (a.d, a.m, a.v):
+        x.copy_(torch.randn(x.shape, generator=g))
+    a.t.fill_(17.0)
+    path = str(tmp_path / "loop.pt")
+    a.save(path)
+    a.save(path)  # replaced in place
+    assert sorted(p.name for p in tmp_path.iterdir()) == ["loop.pt"]  # no temporary left behind
+    b = _bare_loop()
+    b.load(path)
+    for k in ("d", "m", "v", "t"):
+        assert torch.equal(getattr(a, k), getattr(b, k)), k
+    assert b.iteration == 17
+    with pytest.raises(ValueError):
+        _bare_loop(lr=1e-3).load(path)
+    with pytest.raises(ValueError):
+        _bare_loop(n=11).load(path)
+
+
+@pytest.mark.gpu
+def test_alignment_loop_resumes_bit_for_bit(tmp_path):
+    # deterministic mode: 3 iterations, checkpoint, 3 more; a fresh loop that
+    # reads the checkpoint and runs 3 iterations ends on the same offsets
+    torch = pytest.importorskip("torch")
+    from paper_2511_17018_gb300 import align
+    from paper_2511_17018_gb300 import tpcfit as tf
+    d_true = synth.alignment_offsets(5)
+    fr = synth.generate(6000, 56, drop_p=0.05, cap_lengths=True, d_true=d_true)
+    dev = tf.frame_to_device(fr)
+    path = str(tmp_path / "loop.pt")
+    f = tf.Fitter(fr.geometry, fr.bz, deterministic=True)
+    try:
+        loop = align.AlignmentLoop(f, dev, lr=5e-3)
+        loop.run(3, checkpoint=path, every=3)
+        tail = loop.run(3)
+        d_whole = loop.d.cpu().numpy()
+    finally:
+        f.close()
+    f = tf.Fitter(fr.geometry, fr.bz, deterministic=True)
+    try:
+        again = align.AlignmentLoop(f, dev, lr=5e-3)
+        again.load(path)
+        assert again.iteration == 3
+        tail2 = again.run(3)
+        d_resumed = again.d.cpu().numpy()
+    finally:
+        f.close()
+    assert np.array_equal(tail.view(np.int32), tail2.view(np.int32))
+    assert np.array_equal(d_whole.view(np.int32), d_resumed.view(np.int32))
+    assert np.abs(d_whole).max() > 0

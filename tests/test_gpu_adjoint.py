@@ -71,9 +71,15 @@ def test_deterministic_adjoint_is_bitwise_reproducible(case):
 
 def test_alignment_gradient_matches_fp64_finite_differences():
     # central differences of the FP64 oracle's weighted chi2 sum, step 1e-4 cm,
-    # on a 200-track subset, for 40 (sector, row, component) keys the subset uses
+    # on a 200-track subset of the 100,000-track adjoint workload (its first
+    # 200 tracks that the oracle fits), for 40 (sector, row, component) keys
+    # the subset uses
     d_true = synth.alignment_offsets(3)
-    fr = synth.generate(200, 33, drop_p=0.05, cap_lengths=True, d_true=d_true)
+    whole = synth.adjoint_frame()
+    head = whole.subset(np.arange(400))
+    fitted = np.flatnonzero(oracle.fit(head, "f64", align=d_true)["ndf"] > 0)[:200]
+    assert fitted.size == 200
+    fr = head.subset(fitted)
     w = np.ones(fr.n_tracks, np.float32)
     _, ga, _, ndf = _gpu_grad(fr, d_true, w, False)
     assert np.all(ndf > 0)
