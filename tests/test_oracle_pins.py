@@ -178,6 +178,20 @@ def test_noise_free_helix_returns_generating_parameters(oracle_mod, synth):
     assert r["chi2"].max() < 1e-16
 
 
+def test_three_point_seed_is_exact_on_noise_free_clusters(synth):
+    # The test inputs' seeds: a circle through the first, middle and last
+    # cluster (Menger curvature), the direction at the first cluster from the
+    # chord and the half angle, tan(lambda) from the arc.  On an exact helix
+    # (noise-free FP64 clusters, sector crossings included) the construction
+    # is exact, so it returns the generating state at the first cluster.
+    fr = synth.generate(500, 23, smear=0.0)
+    s = synth.three_point_seeds(fr, as_f64=True)
+    rs = fr.rowsec.astype(np.int64)
+    assert np.any((rs[fr.offsets[:-1]] & 63) != (rs[fr.offsets[1:] - 1] & 63))  # some tracks change sector
+    err = np.abs(s - fr.truth) / np.maximum(np.abs(fr.truth), 1e-3)
+    assert err.max() < 1e-9, err.max(axis=1)
+
+
 def test_noise_free_straight_tracks_give_zero_curvature(oracle_mod, synth):
     n = 200
     rng = np.random.default_rng(6)
