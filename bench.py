@@ -152,11 +152,23 @@ def cpu_baseline(frame, budget_s: float = 15.0):
     t1 = time.perf_counter()
     oracle.fit(psub, "f64", nthreads=threads)
     pdt = time.perf_counter() - t1
+    # the same two legs on one thread, on smaller samples (about 3 s in all)
+    one = frame.subset(np.arange(min(frame.n_tracks, 256)))
+    t2 = time.perf_counter()
+    _oracle_fit_adjoint(one, 1)
+    odt = time.perf_counter() - t2
+    one_plain = frame.subset(np.arange(min(frame.n_tracks, 20_000)))
+    t3 = time.perf_counter()
+    oracle.fit(one_plain, "f64", nthreads=1)
+    opdt = time.perf_counter() - t3
     return {"value": take / dt, "unit": UNIT, "cores": threads, "kind": "oracle",
             "sample": f"first {take} tracks of the batch: FP64 fit + forward-mode gradient, {threads} threads, "
                       f"{dt:.1f} s",
             "plain_fit": {"value": plain_take / pdt, "unit": UNIT,
-                          "sample": f"first {plain_take} tracks, FP64 fit only, {pdt:.2f} s"}}
+                          "sample": f"first {plain_take} tracks, FP64 fit only, {pdt:.2f} s"},
+            "one_thread": {"value": one.n_tracks / odt, "plain_fit": one_plain.n_tracks / opdt, "unit": UNIT,
+                           "sample": f"first {one.n_tracks} tracks (fit + gradient, {odt:.2f} s) and first "
+                                     f"{one_plain.n_tracks} tracks (FP64 fit only, {opdt:.2f} s), 1 thread"}}
 
 
 def run_reference(args, rank: int, world: int):

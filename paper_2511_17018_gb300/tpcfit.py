@@ -104,6 +104,16 @@ def _dev(t, dtype, name):
     return t.data_ptr()
 
 
+def _check_sizes(n, y, z, rowsec, seeds=None, params=None, cov=None, chi2=None, ndf=None):
+    """The C entry points see only pointers: array sizes are checked here."""
+    if z.numel() != y.numel() or rowsec.numel() != y.numel():
+        raise ValueError("y, z and rowsec must have the same length")
+    for name, t, per in (("seeds", seeds, 5), ("params", params, 5), ("cov", cov, 15), ("chi2", chi2, 1),
+                         ("ndf", ndf, 1)):
+        if t is not None and t.numel() != per * n:
+            raise ValueError(f"{name} has {t.numel()} elements, {per * n} expected for {n} tracks")
+
+
 def status_string(st: int) -> str:
     return load().tpcfit_status_string(int(st)).decode()
 
@@ -202,11 +212,7 @@ def tpcfit_fit(h, y, z, rowsec, offsets, seeds, params, cov, chi2, ndf, stream=N
     n = int(offsets.numel()) - 1
     hits = _Hits(_dev(y, torch.float32, "y"), _dev(z, torch.float32, "z"), _dev(rowsec, torch.int16, "rowsec"),
                  int(y.numel()))
-    if z.numel() != y.numel() or rowsec.numel() != y.numel():
-        raise ValueError("y, z and rowsec must have the same length")
-    if seeds.numel() != 5 * n or params.numel() != 5 * n or cov.numel() != 15 * n or chi2.numel() != n \
-            or ndf.numel() != n:
-        raise ValueError("seed / output sizes do not match the number of tracks")
+    _check_sizes(n, y, z, rowsec, seeds, params, cov, chi2, ndf)
     st = load().tpcfit_fit(h, C.byref(hits), _dev(offsets, torch.int32, "offsets"), n, _dev(seeds, torch.float32, "seeds"),
                            _dev(params, torch.float32, "params"), _dev(cov, torch.float32, "cov"),
                            _dev(chi2, torch.float32, "chi2"), _dev(ndf, torch.int32, "ndf"), _stream(stream))
@@ -225,6 +231,9 @@ def tpcfit_fit_frames(h, y, z, rowsec, offsets, frame_base, seeds, params, cov, 
     fr = None if frame_ready is None else _dev(frame_ready, torch.int32, "frame_ready")
     if fa is not None and frame_alignment.numel() != nf * 36 * 152 * 2:
         raise ValueError("frame_alignment must be [n_frames, 36, 152, 2]")
+    if fr is not None and frame_ready.numel() != nf:
+        raise ValueError("frame_ready must have one flag per frame")
+    _check_sizes(n, y, z, rowsec, seeds, params, cov, chi2, ndf)
     st = load().tpcfit_fit_frames(h, C.byref(hits), _dev(offsets, torch.int32, "offsets"), n,
                                   _dev(frame_base, torch.int64, "frame_base"), nf, fa, fr, int(wait_timeout_ns),
                                   _dev(seeds, torch.float32, "seeds"), _dev(params, torch.float32, "params"),
@@ -250,6 +259,9 @@ def tpcfit_fit_backward(h, y, z, rowsec, offsets, ndf, grad_chi2, grad_align, gr
                  int(y.numel()))
     if grad_align.numel() != 36 * 152 * 2 or grad_seeds.numel() != 5 * n or grad_chi2.numel() != n:
         raise ValueError("gradient sizes do not match")
+    if grad_meas is not None and grad_meas.numel() != 2 * int(y.numel()):
+        raise ValueError("grad_meas must have two elements per cluster")
+    _check_sizes(n, y, z, rowsec, ndf=ndf)
     gm = None if grad_meas is None else _dev(grad_meas, torch.float32, "grad_meas")
     st = load().tpcfit_fit_backward(h, C.byref(hits), _dev(offsets, torch.int32, "offsets"), n,
                                     _dev(ndf, torch.int32, "ndf"), _dev(grad_chi2, torch.float32, "grad_chi2"),
@@ -266,6 +278,7 @@ def tpcfit_smooth(h, y, z, rowsec, offsets, ndf, resid, rcov, chi2, stream=None)
     hits = _Hits(_dev(y, torch.float32, "y"), _dev(z, torch.float32, "z"), _dev(rowsec, torch.int16, "rowsec"), H)
     if resid.numel() != 2 * H or rcov.numel() != 3 * H or chi2.numel() != H:
         raise ValueError("smoother output sizes do not match the clusters")
+    _check_sizes(n, y, z, rowsec, ndf=ndf)
     st = load().tpcfit_smooth(h, C.byref(hits), _dev(offsets, torch.int32, "offsets"), n, _dev(ndf, torch.int32, "ndf"),
                               _dev(resid, torch.float32, "resid"), _dev(rcov, torch.float32, "rcov"),
                               _dev(chi2, torch.float32, "chi2"), _stream(stream))
@@ -338,6 +351,9 @@ def tpcfit_fit_noalloc(geometry, bz, alignment, deterministic, y, z, rowsec, off
     hits = _Hits(_dev(y, torch.float32, "y"), _dev(z, torch.float32, "z"), _dev(rowsec, torch.int16, "rowsec"),
                  int(y.numel()))
     al = None if alignment is None else _dev(alignment, torch.float32, "alignment")
+    if alignment is not None and alignment.numel() != 36 * 152 * 2:
+        raise ValueError("alignment must have 36*152*2 elements")
+    _check_sizes(n, y, z, rowsec, seeds, params, cov, chi2, ndf)
     st = load().tpcfit_fit_noalloc(C.byref(g), float(bz), al, int(bool(deterministic)), C.byref(hits),
                                    _dev(offsets, torch.int32, "offsets"), n, _dev(seeds, torch.float32, "seeds"),
                                    _dev(params, torch.float32, "params"), _dev(cov, torch.float32, "cov"),

@@ -148,6 +148,41 @@ def test_invalid_input_is_flagged_not_fatal(fitter):
     assert st == tf.EDEVICE and code == 1 and trk == fr.n_tracks - 1
 
 
+def test_binding_rejects_mismatched_sizes(fitter):
+    # the C entry points see only pointers; the binding checks every array's
+    # size against the track and cluster counts before it calls them
+    fr = synth.generate(50, 34)
+    dev = tf.frame_to_device(fr)
+    out = tf.empty_outputs(50)
+    short = tf.empty_outputs(49)
+    y, z, rs, off, seeds = dev["y"], dev["z"], dev["rowsec"], dev["offsets"], dev["seeds"]
+    with pytest.raises(ValueError):
+        tf.tpcfit_fit(fitter.h, y, z[:-1], rs, off, seeds, out["params"], out["cov"], out["chi2"], out["ndf"])
+    with pytest.raises(ValueError):
+        tf.tpcfit_fit(fitter.h, y, z, rs, off, seeds, out["params"], short["cov"], out["chi2"], out["ndf"])
+    with pytest.raises(ValueError):
+        tf.tpcfit_fit_noalloc(fr.geometry, fr.bz, None, 0, y, z, rs, off, seeds, out["params"], out["cov"],
+                              short["chi2"], out["ndf"])
+    base = torch.tensor([0, 50], dtype=torch.int64, device="cuda")
+    with pytest.raises(ValueError):
+        tf.tpcfit_fit_frames(fitter.h, y, z, rs, off, base, seeds[:, :49].contiguous(), out["params"], out["cov"],
+                             out["chi2"], out["ndf"])
+    with pytest.raises(ValueError):
+        tf.tpcfit_fit_frames(fitter.h, y, z, rs, off, base, seeds, out["params"], out["cov"], out["chi2"],
+                             out["ndf"], frame_ready=torch.zeros(2, dtype=torch.int32, device="cuda"))
+    g = torch.zeros(50, device="cuda")
+    with pytest.raises(ValueError):
+        tf.tpcfit_fit_backward(fitter.h, y, z, rs, off, out["ndf"], g, torch.empty(36 * 152 * 2, device="cuda"),
+                               torch.empty((5, 50), device="cuda"), grad_meas=torch.empty(y.numel(), device="cuda"))
+    with pytest.raises(ValueError):
+        tf.tpcfit_smooth(fitter.h, y, z, rs, off, short["ndf"], torch.empty((y.numel(), 2), device="cuda"),
+                         torch.empty((y.numel(), 3), device="cuda"), torch.empty(y.numel(), device="cuda"))
+    # nothing was enqueued: a correct call still works and the error word is clear
+    tf.tpcfit_fit(fitter.h, y, z, rs, off, seeds, out["params"], out["cov"], out["chi2"], out["ndf"])
+    assert np.all(_host(out)["ndf"] > 0)
+    assert fitter.status()[0] == tf.OK
+
+
 def test_host_buffer_entry_point_equals_device_entry_point(fitter, frames):
     fr = frames["drop20k"]
     fitter.set_mode(True)
