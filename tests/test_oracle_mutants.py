@@ -30,6 +30,14 @@ MUTANTS = {
                             "    for (int c = 0; c < 5; ++c) L[h][c] = a[c] * gamma;"),
     "dual_quotient_rule_sign": ("  for (int i = 0; i < g_nd; ++i) r.d[i] = (a.d[i] - r.v * b.d[i]) * ib;",
                                 "  for (int i = 0; i < g_nd; ++i) r.d[i] = (a.d[i] + r.v * b.d[i]) * ib;"),
+    "energy_loss_direction": ("  const T en = dir > 0 ? e - de : e + de;", "  const T en = dir > 0 ? e + de : e - de;"),
+    "highland_momentum_power": ("  const T th2 = (((S)(0.0136 * 0.0136) * ell) * g.x0_inv) * (e2 / (p2 * p2));",
+                                "  const T th2 = (((S)(0.0136 * 0.0136) * ell) * g.x0_inv) * (e2 / p2);"),
+    "field_map_dropped_z_term": ("    kappa = kappa * ((one + g.f_r * (xm * xm + ym * ym)) + g.f_z * (zm * zm));",
+                                 "    kappa = kappa * (one + g.f_r * (xm * xm + ym * ym));"),
+    "smoother_filtered_not_predicted": ("    precord(pass, to);\n    return F.update(g, p, chi2, m);",
+                                        "    const bool ok_ = F.update(g, p, chi2, m);\n    precord(pass, to);\n"
+                                        "    return ok_;"),
 }
 
 
@@ -165,6 +173,71 @@ def check_gradient_fd(synth):
     return abs(gr["grad_meas"][j, 0] - fd) < 1e-6 * max(1.0, abs(fd))
 
 
+def check_energy_loss_refit(synth):
+    from test_oracle_pins import _material_tracks
+    fr, _ = _material_tracks(synth, 12, 3, scatter=False, smear=0.0)
+    seeds = fr.seeds64.copy()
+    for _ in range(4):
+        r = oracle.fit(fr, "f64", exact_inputs=True, seeds=seeds)
+        if not np.all(r["ndf"] > 0):
+            return False
+        seeds = r["params"].copy()
+    return bool(np.abs(r["params"][:4] - fr.truth[:4]).max() < 1e-7 and
+                (np.abs(r["params"][4] - fr.truth[4]) / np.abs(fr.truth[4])).max() < 1e-7)
+
+
+def check_material_pulls(synth):
+    from test_oracle_pins import _material_tracks
+    fr, _ = _material_tracks(synth, 400, 1)
+    r = oracle.fit(fr, "f64")
+    ok = r["ndf"] > 0
+    C = oracle.unpack(r["cov"][:, ok])
+    sig = np.sqrt(np.stack([C[i, i] for i in range(5)]))
+    w = ((r["params"][:, ok] - fr.truth[:, ok]) / sig).std(axis=1)
+    return bool(np.all((w > 0.88) & (w < 1.12)))
+
+
+def check_field_map_refit(synth):
+    from test_oracle_pins import _field_tracks
+    fr, _ = _field_tracks(synth, 10, 3, smear=0.0)
+    seeds = fr.seeds64.copy()
+    for _ in range(4):
+        r = oracle.fit(fr, "f64", exact_inputs=True, seeds=seeds)
+        if not np.all(r["ndf"] > 0):
+            return False
+        seeds = r["params"].copy()
+    return bool(np.abs(r["params"][:4] - fr.truth[:4]).max() < 1e-6 and
+                (np.abs(r["params"][4] - fr.truth[4]) / np.abs(fr.truth[4])).max() < 3e-6)
+
+
+def check_smoother_leave_one_out(synth):
+    # the residual of each cluster of a short track against the dense weighted
+    # least-squares solve without that cluster (both passes' priors)
+    from conftest import truth_trajectory
+    from test_oracle_pins import _affine_chain, _short_tracks
+    fr, _ = _short_tracks(synth, 11, n=8)
+    ref = truth_trajectory(oracle, fr)
+    s = oracle.smooth(fr, ref=ref, exact_inputs=True)
+    r = oracle.fit(fr, "f64", ref=ref, trace=True, exact_inputs=True)
+    m = np.stack([fr.y64, fr.z64], axis=1)
+    H = np.zeros((2, 5)); H[0, 0] = 1; H[1, 1] = 1
+    for i in range(fr.n_tracks):
+        order, A, bb = _affine_chain(oracle, fr, ref, i, backward=False)
+        p_out = r["trace"][order[-1], 0, :5]
+        for k, h in enumerate(order):
+            N = np.eye(5) / 100.0 + A[-1].T @ A[-1] / 100.0
+            rhs = fr.seeds64[:, i] / 100.0 + A[-1].T @ (p_out - bb[-1]) / 100.0
+            for kk, j in enumerate(order):
+                if kk != k:
+                    HA = H @ A[kk]
+                    N += HA.T @ HA / 0.01
+                    rhs += HA.T @ (m[j] - H @ bb[kk]) / 0.01
+            xc = A[k] @ np.linalg.solve(N, rhs) + bb[k]
+            if not np.allclose(s["resid"][h], m[h] - xc[:2], rtol=1e-7, atol=1e-10):
+                return False
+    return True
+
+
 CASES = [
     ("propagation_sign", check_exact_helix),
     ("jacobian_dropped_factor", check_jacobian_fd),
@@ -173,6 +246,10 @@ CASES = [
     ("rotation_sign", check_round_trip),
     ("potter_wrong_factor", check_sqrt_vs_cov),
     ("dual_quotient_rule_sign", check_gradient_fd),
+    ("energy_loss_direction", check_energy_loss_refit),
+    ("highland_momentum_power", check_material_pulls),
+    ("field_map_dropped_z_term", check_field_map_refit),
+    ("smoother_filtered_not_predicted", check_smoother_leave_one_out),
 ]
 
 
