@@ -70,3 +70,43 @@ def test_argument_errors_before_any_cuda_call(lib):
     assert lib.tpcfit_fit_adjoint_host(None, None, None, None, 0, None, 1, None, None, None, None, None, None,
                                        None) == tpcfit.EINVAL
     lib.tpcfit_destroy(None)
+
+
+C_PROGRAM = r"""
+#include <stdio.h>
+#include <string.h>
+#include "tpcfit.h"
+
+int main(void) {
+  double rx[3] = {85.0, 84.0, 86.0};          /* not ascending: rejected */
+  tpcfit_geometry g = {36, 3, rx, 20.0, 250.0};
+  tpcfit_handle* h = NULL;
+  if (tpcfit_version() < 10000) return 1;
+  if (strcmp(tpcfit_status_string(TPCFIT_OK), "ok") != 0) return 2;
+  if (tpcfit_create(&g, 0.5, &h) != TPCFIT_EINVAL || h != NULL) return 3;
+  if (tpcfit_create(NULL, 0.5, &h) != TPCFIT_EINVAL) return 4;
+  if (tpcfit_set_mode(NULL, 1) != TPCFIT_EINVAL) return 5;
+  if (tpcfit_fit(NULL, NULL, NULL, 0, NULL, NULL, NULL, NULL, NULL, NULL) != TPCFIT_EINVAL) return 6;
+  tpcfit_destroy(NULL);
+  printf("c client ok\n");
+  return 0;
+}
+"""
+
+
+def test_header_compiles_as_c_and_links(lib, tmp_path):
+    # a plain C99 client: the header needs no C++ and no CUDA header, and the
+    # library links and answers without a GPU
+    import shutil
+    from paper_2511_17018_gb300 import tpcfit
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    src = tmp_path / "client.c"
+    src.write_text(C_PROGRAM)
+    exe = tmp_path / "client"
+    libdir = os.path.dirname(tpcfit.LIB_PATH)
+    subprocess.run([cc, "-std=c99", "-Wall", "-Wextra", "-Werror", "-pedantic", f"-I{os.path.join(ROOT, 'include')}",
+                    str(src), "-o", str(exe), f"-L{libdir}", "-ltpcfit", f"-Wl,-rpath,{libdir}"], check=True)
+    r = subprocess.run([str(exe)], capture_output=True, text=True)
+    assert r.returncode == 0 and "c client ok" in r.stdout, (r.returncode, r.stdout, r.stderr)
