@@ -35,6 +35,9 @@ MUTANTS = {
                                 "  const T th2 = (((S)(0.0136 * 0.0136) * ell) * g.x0_inv) * (e2 / p2);"),
     "field_map_dropped_z_term": ("    kappa = kappa * ((one + g.f_r * (xm * xm + ym * ym)) + g.f_z * (zm * zm));",
                                  "    kappa = kappa * (one + g.f_r * (xm * xm + ym * ym));"),
+    "side_change_as_sector_change": (
+        "        const bool rot = (hit_sec(h, from) % kNSectorsPerSide) != (hit_sec(h, to) % kNSectorsPerSide);",
+        "        const bool rot = hit_sec(h, from) != hit_sec(h, to);"),
     "smoother_filtered_not_predicted": ("    precord(pass, to);\n    return F.update(g, p, chi2, m);",
                                         "    const bool ok_ = F.update(g, p, chi2, m);\n    precord(pass, to);\n"
                                         "    return ok_;"),
@@ -238,6 +241,22 @@ def check_smoother_leave_one_out(synth):
     return True
 
 
+def check_side_change(synth):
+    # tracks crossing z = 0, fitted with their sector labels and with every
+    # label moved to the A side: the strict-FP32 fits agree bit for bit
+    fr = synth.generate(1500, 24, drop_p=0.05)
+    sec = fr.rowsec.astype(np.int64) & 63
+    off = fr.offsets.astype(np.int64)
+    cross = [i for i in range(fr.n_tracks)
+             if (sec[off[i]:off[i + 1]] >= 18).any() and (sec[off[i]:off[i + 1]] < 18).any()]
+    sub = fr.subset(np.array(cross))
+    a_side = sub.subset(np.arange(sub.n_tracks))
+    r = a_side.rowsec.astype(np.int64)
+    a_side.rowsec = (((r >> 6) << 6) | ((r & 63) % 18)).astype(np.uint16)
+    x, y = oracle.fit(sub, "f32"), oracle.fit(a_side, "f32")
+    return all(np.array_equal(x[k], y[k]) for k in ("params", "cov", "chi2", "ndf"))
+
+
 CASES = [
     ("propagation_sign", check_exact_helix),
     ("jacobian_dropped_factor", check_jacobian_fd),
@@ -250,6 +269,7 @@ CASES = [
     ("highland_momentum_power", check_material_pulls),
     ("field_map_dropped_z_term", check_field_map_refit),
     ("smoother_filtered_not_predicted", check_smoother_leave_one_out),
+    ("side_change_as_sector_change", check_side_change),
 ]
 
 

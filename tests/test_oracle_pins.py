@@ -192,6 +192,34 @@ def test_three_point_seed_is_exact_on_noise_free_clusters(synth):
     assert err.max() < 1e-9, err.max(axis=1)
 
 
+def test_crossing_z_zero_changes_only_the_sector_label(oracle_mod, synth):
+    # Sectors s and s + 18 share their azimuth: a track that crosses z = 0
+    # changes the side of its sector label but not its frame, so no rotation
+    # applies.  Without alignment offsets, labelling every cluster with its
+    # A-side sector leaves the fit unchanged, bit for bit, in both precisions;
+    # with offsets the label decides which offsets apply.
+    fr = synth.generate(3000, 24, drop_p=0.05)
+    rs = fr.rowsec.astype(np.int64)
+    sec = rs & 63
+    off = fr.offsets.astype(np.int64)
+    cross = np.array([(sec[off[i]:off[i + 1]] >= 18).any() and (sec[off[i]:off[i + 1]] < 18).any()
+                      for i in range(fr.n_tracks)])
+    assert cross.sum() >= 20
+    sub = fr.subset(np.flatnonzero(cross))
+    a_side = sub.subset(np.arange(sub.n_tracks))
+    r = a_side.rowsec.astype(np.int64)
+    a_side.rowsec = (((r >> 6) << 6) | ((r & 63) % 18)).astype(np.uint16)
+    for prec in ("f64", "f32"):
+        x, y = oracle_mod.fit(sub, prec), oracle_mod.fit(a_side, prec)
+        assert np.all(x["ndf"] > 0)
+        for k in ("params", "cov", "chi2", "ndf"):
+            assert np.array_equal(x[k], y[k]), (prec, k)
+    d = synth.alignment_offsets(7)
+    x = oracle_mod.fit(sub, "f64", align=d)
+    y = oracle_mod.fit(a_side, "f64", align=d)
+    assert not np.array_equal(x["chi2"], y["chi2"])
+
+
 def test_noise_free_straight_tracks_give_zero_curvature(oracle_mod, synth):
     n = 200
     rng = np.random.default_rng(6)
