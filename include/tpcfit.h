@@ -55,7 +55,7 @@ typedef struct {
   int32_t n_sectors;       /* must be 36 */
   int32_t n_rows;          /* 1..152 */
   const double* row_x;     /* host [n_rows]: local x of each pad-row plane, cm, ascending */
-  double sector_width_deg; /* 20 */
+  double sector_width_deg; /* must be 20: 18 sectors per side cover the circle */
   double z_max;            /* 250 cm (informational) */
 } tpcfit_geometry;
 

@@ -59,7 +59,8 @@ int registered_constant_modules() { return (int)registry().modules.size(); }
 // Build the per-time-frame constants on the host in FP64, rounded to FP32.
 bool build_geo(const tpcfit_geometry* g, double bz, GeoConst& out) {
   if (!g || !g->row_x || g->n_sectors != kNSectors || g->n_rows < 1 || g->n_rows > kMaxRows) return false;
-  if (!(g->sector_width_deg > 0.0) || !(g->sector_width_deg <= 90.0) || !std::isfinite(bz)) return false;
+  // 18 sectors per side must cover the circle (the rotation table wraps at 9 sector steps)
+  if (!(std::fabs(g->sector_width_deg * kNSide - 360.0) <= 1e-9) || !std::isfinite(bz)) return false;
   std::memset(&out, 0, sizeof(out));
   for (int r = 0; r < g->n_rows; ++r) {
     if (!std::isfinite(g->row_x[r]) || !(g->row_x[r] > 0.0)) return false;

@@ -60,6 +60,19 @@ def test_argument_errors_before_any_cuda_call(lib):
     assert lib.tpcfit_create(C.byref(g), 0.5, C.byref(h)) == tpcfit.EINVAL
     g = tpcfit._Geometry(35, 3, C.cast(rx, C.POINTER(C.c_double)), 20.0, 250.0)
     assert lib.tpcfit_create(C.byref(g), 0.5, C.byref(h)) == tpcfit.EINVAL
+    # the other geometry rules: 1..152 rows at positive ascending x, 20-degree
+    # sectors (18 per side cover the circle), a finite field
+    good = (C.c_double * 153)(*[85.0 + i for i in range(153)])
+    gp = C.cast(good, C.POINTER(C.c_double))
+    for n_rows, width, bz in ((0, 20.0, 0.5), (153, 20.0, 0.5), (152, 10.0, 0.5), (152, 20.5, 0.5),
+                              (152, 20.0, float("nan")), (152, 20.0, float("inf"))):
+        g = tpcfit._Geometry(36, n_rows, gp, width, 250.0)
+        assert lib.tpcfit_create(C.byref(g), bz, C.byref(h)) == tpcfit.EINVAL, (n_rows, width, bz)
+    neg = (C.c_double * 2)(-1.0, 85.0)
+    g = tpcfit._Geometry(36, 2, C.cast(neg, C.POINTER(C.c_double)), 20.0, 250.0)
+    assert lib.tpcfit_create(C.byref(g), 0.5, C.byref(h)) == tpcfit.EINVAL
+    assert lib.tpcfit_rtc_build(C.byref(tpcfit._Geometry(36, 152, gp, 10.0, 250.0)), 0.5, 0, 4, 24, 0, 0,
+                                None) == tpcfit.EINVAL
     # null handle everywhere
     assert lib.tpcfit_set_mode(None, 1) == tpcfit.EINVAL
     assert lib.tpcfit_set_config(None, 1, 4, 8, 1) == tpcfit.EINVAL
