@@ -35,9 +35,11 @@ def lib():
             f.restype = C.c_int
             f.argtypes = [C.POINTER(_Geo), C.c_double, C.c_int32, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp,
                           C.c_int32]
-        L.oracle_grad_f64.restype = C.c_int
-        L.oracle_grad_f64.argtypes = [C.POINTER(_Geo), C.c_double, C.c_int32, vp, vp, vp, vp, vp, vp, vp, vp, vp,
-                                      vp, vp, C.c_int32]
+        for name in ("oracle_grad_f64", "oracle_grad_f32"):
+            f = getattr(L, name)
+            f.restype = C.c_int
+            f.argtypes = [C.POINTER(_Geo), C.c_double, C.c_int32, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp,
+                          C.c_int32]
         L.oracle_step_f64.restype = C.c_int
         L.oracle_step_f64.argtypes = [C.POINTER(_Geo), C.c_double, vp, C.c_double, C.c_int32, C.c_int32, C.c_int32,
                                       vp, vp, vp]
@@ -49,6 +51,8 @@ def lib():
         L.oracle_asin_f64.argtypes = [C.c_double]
         L.oracle_asinc_f32.restype = C.c_float
         L.oracle_asinc_f32.argtypes = [C.c_float]
+        L.oracle_asinc_dual_f32.restype = C.c_float
+        L.oracle_asinc_dual_f32.argtypes = [C.c_float, C.POINTER(C.c_double)]
         L.oracle_guard_count.restype = C.c_longlong
         L.oracle_guard_reset.restype = None
         _lib = L
@@ -116,27 +120,34 @@ def fit(frame, precision: str = "f64", align=None, ref=None, trace: bool = False
     return dict(params=params, cov=cov, chi2=chi2, ndf=ndf, trace=tr)
 
 
-def grad(frame, weights=None, align=None, nthreads: int | None = None, exact_inputs: bool = False):
-    """FP64 forward-mode gradient of L = sum_i w_i chi2_i.
+def grad(frame, weights=None, align=None, nthreads: int | None = None, exact_inputs: bool = False,
+         precision: str = "f64"):
+    """Forward-mode gradient of L = sum_i w_i chi2_i.
 
+    precision 'f64': FP64 values (covariance form), the gradient reference.
+    precision 'f32': the strict-FP32 fit's own operation sequence (square-root
+    form, residual coordinates; chi2 and ndf bit for bit those of
+    ``fit(frame, 'f32')``) with its exact derivative carried in FP64 -- the
+    reference for an FP32 reverse-mode adjoint of that sequence.
     Returns dict(grad_meas[H,2] = dL/dm, grad_seed[5,n], chi2[n], ndf[n]).
     dL/d(alignment offset of key (sector,row,c)) = -sum of grad_meas over hits with that key.
     """
     L = lib()
     n = frame.n_tracks
     H = frame.n_hits
-    y = np.ascontiguousarray(frame.y64 if exact_inputs else frame.y, dtype=np.float64)
-    z = np.ascontiguousarray(frame.z64 if exact_inputs else frame.z, dtype=np.float64)
-    sd = np.ascontiguousarray(frame.seeds64 if exact_inputs else frame.seeds, dtype=np.float64)
+    dt = {"f64": np.float64, "f32": np.float32}[precision]
+    y = np.ascontiguousarray(frame.y64 if exact_inputs else frame.y, dtype=dt)
+    z = np.ascontiguousarray(frame.z64 if exact_inputs else frame.z, dtype=dt)
+    sd = np.ascontiguousarray(frame.seeds64 if exact_inputs else frame.seeds, dtype=dt)
     rs = np.ascontiguousarray(frame.rowsec, dtype=np.uint16)
     off = np.ascontiguousarray(frame.offsets, dtype=np.int32)
-    al = None if align is None else np.ascontiguousarray(align, dtype=np.float64).reshape(-1)
+    al = None if align is None else np.ascontiguousarray(align, dtype=dt).reshape(-1)
     w = None if weights is None else np.ascontiguousarray(weights, dtype=np.float64)
     gm = np.zeros((H, 2)); gs = np.zeros((5, n)); chi2 = np.empty(n); ndf = np.empty(n, np.int32)
     g, _keep = _geo(frame.geometry, getattr(frame, "material", None), getattr(frame, "field", None))
-    rc = L.oracle_grad_f64(C.byref(g), float(frame.bz), n, _ptr(off), _ptr(y), _ptr(z), _ptr(rs), _ptr(sd),
-                           _ptr(al), _ptr(w), _ptr(gm), _ptr(gs), _ptr(chi2), _ptr(ndf),
-                           nthreads or default_threads())
+    fn = L.oracle_grad_f64 if precision == "f64" else L.oracle_grad_f32
+    rc = fn(C.byref(g), float(frame.bz), n, _ptr(off), _ptr(y), _ptr(z), _ptr(rs), _ptr(sd), _ptr(al), _ptr(w),
+            _ptr(gm), _ptr(gs), _ptr(chi2), _ptr(ndf), nthreads or default_threads())
     if rc != 0:
         raise ValueError(f"oracle grad rejected its inputs (rc={rc})")
     return dict(grad_meas=gm, grad_seed=gs, chi2=chi2, ndf=ndf)
@@ -248,6 +259,13 @@ def asin_f64(u: float) -> float:
 
 def asinc_f32(u: float) -> float:
     return lib().oracle_asinc_f32(float(u))
+
+
+def asinc_dual_f32(u: float):
+    """(value, derivative) of the strict-FP32 asinc as its dual number carries them."""
+    d = C.c_double()
+    v = lib().oracle_asinc_dual_f32(float(u), C.byref(d))
+    return float(v), float(d.value)
 
 
 def guard_count() -> int:

@@ -51,25 +51,68 @@ constexpr int kMaxD = 2 * 152 + 5;  // forward-mode directions: 2 per hit + 5 se
 std::atomic<long long> g_guard_hits{0};
 
 // ------------------------------------------------------------------ dual numbers
+// Forward-mode derivatives: a value of type VT and g_nd FP64 directional
+// derivatives.  VT = double is the FP64 gradient reference.  VT = float
+// evaluates the strict-FP32 operation sequence itself (the values are bit for
+// bit those of the float instantiation) and carries the exact derivative of
+// that sequence, every rounding treated as the identity, in FP64: the
+// reference for a reverse-mode FP32 adjoint of the same sequence, free of the
+// rounding of the derivatives themselves.
 thread_local int g_nd = 0;
 
-struct Dual {
-  double v;
+template <class VT> struct DualT;
+template <class VT> DualT<VT> dual_add(const DualT<VT>& a, const DualT<VT>& b);
+template <class VT> DualT<VT> dual_sub(const DualT<VT>& a, const DualT<VT>& b);
+template <class VT> DualT<VT> dual_neg(const DualT<VT>& a);
+template <class VT> DualT<VT> dual_mul(const DualT<VT>& a, const DualT<VT>& b);
+template <class VT> DualT<VT> dual_div(const DualT<VT>& a, const DualT<VT>& b);
+
+template <class VT> struct DualT {
+  VT v;
   double d[kMaxD];
-  Dual() : v(0.0) { std::memset(d, 0, sizeof(double) * (size_t)g_nd); }
-  Dual(double x) : v(x) { std::memset(d, 0, sizeof(double) * (size_t)g_nd); }  // NOLINT
+  DualT() : v(0) { std::memset(d, 0, sizeof(double) * (size_t)g_nd); }
+  DualT(VT x) : v(x) { std::memset(d, 0, sizeof(double) * (size_t)g_nd); }  // NOLINT: constants enter implicitly
+  // hidden friends, so that a constant operand converts implicitly
+  friend DualT operator+(const DualT& a, const DualT& b) { return dual_add(a, b); }
+  friend DualT operator-(const DualT& a, const DualT& b) { return dual_sub(a, b); }
+  friend DualT operator-(const DualT& a) { return dual_neg(a); }
+  friend DualT operator*(const DualT& a, const DualT& b) { return dual_mul(a, b); }
+  friend DualT operator/(const DualT& a, const DualT& b) { return dual_div(a, b); }
 };
-inline Dual operator+(const Dual& a, const Dual& b) { Dual r(a.v + b.v); for (int i = 0; i < g_nd; ++i) r.d[i] = a.d[i] + b.d[i]; return r; }
-inline Dual operator-(const Dual& a, const Dual& b) { Dual r(a.v - b.v); for (int i = 0; i < g_nd; ++i) r.d[i] = a.d[i] - b.d[i]; return r; }
-inline Dual operator-(const Dual& a) { Dual r(-a.v); for (int i = 0; i < g_nd; ++i) r.d[i] = -a.d[i]; return r; }
-inline Dual operator*(const Dual& a, const Dual& b) { Dual r(a.v * b.v); for (int i = 0; i < g_nd; ++i) r.d[i] = a.d[i] * b.v + a.v * b.d[i]; return r; }
-inline Dual operator/(const Dual& a, const Dual& b) {
-  Dual r(a.v / b.v);
-  const double ib = 1.0 / b.v;
+template <class VT> DualT<VT> dual_add(const DualT<VT>& a, const DualT<VT>& b) {
+  DualT<VT> r(a.v + b.v);
+  for (int i = 0; i < g_nd; ++i) r.d[i] = a.d[i] + b.d[i];
+  return r;
+}
+template <class VT> DualT<VT> dual_sub(const DualT<VT>& a, const DualT<VT>& b) {
+  DualT<VT> r(a.v - b.v);
+  for (int i = 0; i < g_nd; ++i) r.d[i] = a.d[i] - b.d[i];
+  return r;
+}
+template <class VT> DualT<VT> dual_neg(const DualT<VT>& a) {
+  DualT<VT> r(-a.v);
+  for (int i = 0; i < g_nd; ++i) r.d[i] = -a.d[i];
+  return r;
+}
+template <class VT> DualT<VT> dual_mul(const DualT<VT>& a, const DualT<VT>& b) {
+  DualT<VT> r(a.v * b.v);
+  for (int i = 0; i < g_nd; ++i) r.d[i] = a.d[i] * (double)b.v + (double)a.v * b.d[i];
+  return r;
+}
+template <class VT> DualT<VT> dual_div(const DualT<VT>& a, const DualT<VT>& b) {
+  DualT<VT> r(a.v / b.v);
+  const double ib = 1.0 / (double)b.v;
   for (int i = 0; i < g_nd; ++i) r.d[i] = (a.d[i] - r.v * b.d[i]) * ib;
   return r;
 }
-inline Dual dsqrt(const Dual& a) { Dual r(std::sqrt(a.v)); const double h = 0.5 / r.v; for (int i = 0; i < g_nd; ++i) r.d[i] = a.d[i] * h; return r; }
+template <class VT> DualT<VT> dsqrt(const DualT<VT>& a) {
+  DualT<VT> r(std::sqrt(a.v));
+  const double h = 0.5 / (double)r.v;
+  for (int i = 0; i < g_nd; ++i) r.d[i] = a.d[i] * h;
+  return r;
+}
+using Dual = DualT<double>;
+using DualF = DualT<float>;
 
 // ------------------------------------------------------------------ scalar traits
 template <class T> struct Traits;
@@ -90,6 +133,12 @@ template <> struct Traits<Dual> {
   static double val(const Dual& x) { return x.v; }
   static Dual sqrt_(const Dual& x) { return dsqrt(x); }
   static constexpr double kLkSeries = 1e-5;
+};
+template <> struct Traits<DualF> {
+  using S = float;
+  static double val(const DualF& x) { return (double)x.v; }
+  static DualF sqrt_(const DualF& x) { return dsqrt(x); }
+  static constexpr double kLkSeries = 1e-2;
 };
 
 // ------------------------------------------------------------------ arcsin routines
@@ -168,6 +217,30 @@ inline Dual asinc_(const Dual& u) {
     fp = (x / std::sqrt(1.0 - x * x) - std::asin(x)) / (x * x);
   }
   Dual r(f);
+  for (int i = 0; i < g_nd; ++i) r.d[i] = u.d[i] * fp;
+  return r;
+}
+
+// The strict-FP32 asinc with the exact derivative of what it evaluates (in
+// FP64): the derivative of the float polynomial (coefficients as rounded) for
+// |u| <= 1/4, of asin(u)/u above, where the value comes from the FP64 island.
+inline DualF asinc_(const DualF& u) {
+  const float x = u.v;
+  const float f = asinc_(x);
+  const double xd = (double)x;
+  double fp;
+  if ((x < 0.0f ? -x : x) <= 0.25f) {
+    const double c[7] = {1.0, (double)(float)(1.0 / 6.0), (double)(float)(3.0 / 40.0), (double)(float)(5.0 / 112.0),
+                         (double)(float)(35.0 / 1152.0), (double)(float)(63.0 / 2816.0),
+                         (double)(float)(231.0 / 13312.0)};
+    const double q = xd * xd;
+    double acc = 6.0 * c[6];
+    for (int k = 5; k >= 1; --k) acc = acc * q + (double)k * c[k];
+    fp = 2.0 * xd * acc;
+  } else {
+    fp = (xd / std::sqrt((1.0 - xd) * (1.0 + xd)) - asin_f64(xd)) / (xd * xd);
+  }
+  DualF r(f);
   for (int i = 0; i < g_nd; ++i) r.d[i] = u.d[i] * fp;
   return r;
 }
@@ -673,7 +746,7 @@ FitResult fit_track(const Geo<typename Traits<T>::S>& g, const HitView<T>& h, co
   Filter<T, kSqrt> F;
   T x;
   T chi2(0.0);
-  constexpr bool kRes = std::is_same<T, float>::value;  // residual coordinates (see below)
+  constexpr bool kRes = std::is_same<typename Traits<T>::S, float>::value;  // residual coordinates (see below)
   T my(0.0), mz(0.0);                                    // measurement of the current cluster
   auto record = [&](int pass, int j) {
     if (!trace) return;
@@ -963,6 +1036,66 @@ int oracle_fit_f32(const OracleGeometry* geo, double bz, int32_t n_tracks, const
                               trace, nthreads);
 }
 
+}  // extern "C"
+
+namespace {
+// Forward-mode gradient of L = sum_i w_i chi2_i for one dual type: D = Dual
+// (FP64 values, covariance form) or DualF (strict-FP32 values, square-root form
+// and residual coordinates: the float fit's own operation sequence).
+template <class D, bool kSqrt, class VIn>
+int grad_all(const OracleGeometry* geo, double bz, int32_t n_tracks, const int32_t* off, const VIn* y, const VIn* z,
+             const uint16_t* rowsec, const VIn* seeds, const VIn* align, const double* w, double* grad_meas,
+             double* grad_seed, double* chi2, int32_t* ndf, int32_t nthreads) {
+  using S = typename Traits<D>::S;
+  if (check_inputs(geo, n_tracks, off)) return 1;
+  for (int32_t i = 0; i < n_tracks; ++i)
+    if (off[i + 1] - off[i] > 152) return 1;
+  Geo<S> g;
+  make_geo<S>(g, geo->row_x, geo->n_rows, geo->sector_width_deg, bz, geo->x0_cm, geo->dedx_gev_cm, geo->mass_gev,
+              geo->row_cm, geo->field_cr, geo->field_cz);
+#pragma omp parallel for schedule(dynamic, 4) num_threads(nthreads > 0 ? nthreads : 1)
+  for (int32_t i = 0; i < n_tracks; ++i) {
+    const int n = off[i + 1] - off[i];
+    g_nd = 2 * n + 5;
+    std::vector<D> yv(n), zv(n);
+    for (int j = 0; j < n; ++j) {
+      yv[j] = D(y[off[i] + j]);
+      yv[j].d[2 * j] = 1.0;
+      zv[j] = D(z[off[i] + j]);
+      zv[j].d[2 * j + 1] = 1.0;
+    }
+    D seed[5];
+    for (int c = 0; c < 5; ++c) {
+      seed[c] = D(seeds[(size_t)c * n_tracks + i]);
+      seed[c].d[2 * n + c] = 1.0;
+    }
+    // alignment enters as a constant shift (the same subtraction as the fit's
+    // measurement); the hit views index from 0
+    HitView<D> h{yv.data(), zv.data(), rowsec + off[i], nullptr, 0, n};
+    if (align) {
+      for (int j = 0; j < n; ++j) {
+        const int64_t key = ((int64_t)(rowsec[off[i] + j] & 63) * 152 + (rowsec[off[i] + j] >> 6)) * 2;
+        yv[j] = yv[j] - D(align[key]);
+        zv[j] = zv[j] - D(align[key + 1]);
+      }
+    }
+    D p[5], C[15], c2((S)0.0);
+    FitResult r = fit_track<D, kSqrt>(g, h, yv.data(), zv.data(), seed, nullptr, p, C, c2, nullptr);
+    const double wi = w ? w[i] : 1.0;
+    for (int j = 0; j < n; ++j) {
+      grad_meas[(size_t)(off[i] + j) * 2] = r.ok ? wi * c2.d[2 * j] : 0.0;
+      grad_meas[(size_t)(off[i] + j) * 2 + 1] = r.ok ? wi * c2.d[2 * j + 1] : 0.0;
+    }
+    for (int c = 0; c < 5; ++c) grad_seed[(size_t)c * n_tracks + i] = r.ok ? wi * c2.d[2 * n + c] : 0.0;
+    chi2[i] = r.ok ? (double)c2.v : NAN;
+    ndf[i] = r.ok ? 2 * r.n_used - 5 : -1;
+  }
+  return 0;
+}
+}  // namespace
+
+extern "C" {
+
 // Forward-mode FP64 gradient of L = sum_i w_i chi2_i.
 //   grad_meas[H][2] = dL/dm (m = measured y, z after alignment subtraction),
 //   grad_seed[5][n] = dL/dseed; chi2[n] and ndf[n] as in the fit.
@@ -971,50 +1104,21 @@ int oracle_grad_f64(const OracleGeometry* geo, double bz, int32_t n_tracks, cons
                     const double* z, const uint16_t* rowsec, const double* seeds, const double* align,
                     const double* w, double* grad_meas, double* grad_seed, double* chi2, int32_t* ndf,
                     int32_t nthreads) {
-  if (check_inputs(geo, n_tracks, off)) return 1;
-  for (int32_t i = 0; i < n_tracks; ++i)
-    if (off[i + 1] - off[i] > 152) return 1;
-  Geo<double> g;
-  make_geo<double>(g, geo->row_x, geo->n_rows, geo->sector_width_deg, bz, geo->x0_cm, geo->dedx_gev_cm, geo->mass_gev, geo->row_cm,
-               geo->field_cr, geo->field_cz);
-#pragma omp parallel for schedule(dynamic, 4) num_threads(nthreads > 0 ? nthreads : 1)
-  for (int32_t i = 0; i < n_tracks; ++i) {
-    const int n = off[i + 1] - off[i];
-    g_nd = 2 * n + 5;
-    std::vector<Dual> yv(n), zv(n), al;
-    for (int j = 0; j < n; ++j) {
-      yv[j] = Dual(y[off[i] + j]);
-      yv[j].d[2 * j] = 1.0;
-      zv[j] = Dual(z[off[i] + j]);
-      zv[j].d[2 * j + 1] = 1.0;
-    }
-    Dual seed[5];
-    for (int c = 0; c < 5; ++c) {
-      seed[c] = Dual(seeds[(size_t)c * n_tracks + i]);
-      seed[c].d[2 * n + c] = 1.0;
-    }
-    // alignment enters as a constant shift; the hit views index from 0
-    std::vector<Dual> alv;
-    HitView<Dual> h{yv.data(), zv.data(), rowsec + off[i], nullptr, 0, n};
-    if (align) {
-      for (int j = 0; j < n; ++j) {
-        const int64_t key = ((int64_t)(rowsec[off[i] + j] & 63) * 152 + (rowsec[off[i] + j] >> 6)) * 2;
-        yv[j] = yv[j] - Dual(align[key]);
-        zv[j] = zv[j] - Dual(align[key + 1]);
-      }
-    }
-    Dual p[5], C[15], c2(0.0);
-    FitResult r = fit_track<Dual, false>(g, h, yv.data(), zv.data(), seed, nullptr, p, C, c2, nullptr);
-    const double wi = w ? w[i] : 1.0;
-    for (int j = 0; j < n; ++j) {
-      grad_meas[(size_t)(off[i] + j) * 2] = r.ok ? wi * c2.d[2 * j] : 0.0;
-      grad_meas[(size_t)(off[i] + j) * 2 + 1] = r.ok ? wi * c2.d[2 * j + 1] : 0.0;
-    }
-    for (int c = 0; c < 5; ++c) grad_seed[(size_t)c * n_tracks + i] = r.ok ? wi * c2.d[2 * n + c] : 0.0;
-    chi2[i] = r.ok ? c2.v : NAN;
-    ndf[i] = r.ok ? 2 * r.n_used - 5 : -1;
-  }
-  return 0;
+  return grad_all<Dual, false, double>(geo, bz, n_tracks, off, y, z, rowsec, seeds, align, w, grad_meas, grad_seed,
+                                       chi2, ndf, nthreads);
+}
+
+// The gradient of the strict-FP32 fit itself: the same L with every value
+// computed by the float instantiation's operation sequence (chi2 and ndf are
+// bit for bit those of oracle_fit_f32) and its exact derivative carried in
+// FP64.  Inputs are float, as for oracle_fit_f32; outputs as for
+// oracle_grad_f64.  A reverse-mode FP32 adjoint of that sequence differs from it
+// only by the rounding of its own derivative arithmetic.
+int oracle_grad_f32(const OracleGeometry* geo, double bz, int32_t n_tracks, const int32_t* off, const float* y,
+                    const float* z, const uint16_t* rowsec, const float* seeds, const float* align, const double* w,
+                    double* grad_meas, double* grad_seed, double* chi2, int32_t* ndf, int32_t nthreads) {
+  return grad_all<DualF, true, float>(geo, bz, n_tracks, off, y, z, rowsec, seeds, align, w, grad_meas, grad_seed,
+                                      chi2, ndf, nthreads);
 }
 
 // One prediction step in FP64 (for Jacobian tests): state p_in at local x_in in
@@ -1061,6 +1165,15 @@ int oracle_transport_f64(double* C, const double* Jm) {
 
 double oracle_asin_f64(double u) { return asin_f64(u); }
 float oracle_asinc_f32(float u) { return asinc_(u); }
+// The strict-FP32 asinc with the derivative its dual carries (tests).
+float oracle_asinc_dual_f32(float u, double* deriv) {
+  g_nd = 1;
+  DualF x(u);
+  x.d[0] = 1.0;
+  const DualF r = asinc_(x);
+  *deriv = r.d[0];
+  return r.v;
+}
 
 long long oracle_guard_count(void) { return g_guard_hits.load(); }
 void oracle_guard_reset(void) { g_guard_hits.store(0); }

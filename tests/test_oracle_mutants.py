@@ -35,6 +35,8 @@ MUTANTS = {
                                 "  const T th2 = (((S)(0.0136 * 0.0136) * ell) * g.x0_inv) * (e2 / p2);"),
     "field_map_dropped_z_term": ("    kappa = kappa * ((one + g.f_r * (xm * xm + ym * ym)) + g.f_z * (zm * zm));",
                                  "    kappa = kappa * (one + g.f_r * (xm * xm + ym * ym));"),
+    "fp32_dual_asinc_derivative": ("    for (int k = 5; k >= 1; --k) acc = acc * q + (double)k * c[k];",
+                                   "    for (int k = 5; k >= 1; --k) acc = acc * q + c[k];"),
     "side_change_as_sector_change": (
         "        const bool rot = (hit_sec(h, from) % kNSectorsPerSide) != (hit_sec(h, to) % kNSectorsPerSide);",
         "        const bool rot = hit_sec(h, from) != hit_sec(h, to);"),
@@ -257,6 +259,16 @@ def check_side_change(synth):
     return all(np.array_equal(x[k], y[k]) for k in ("params", "cov", "chi2", "ndf"))
 
 
+def check_fp32_dual_asinc(synth):
+    for u in (0.05, -0.12, 0.2, 0.24):
+        _, d = oracle.asinc_dual_f32(u)
+        uf = float(np.float32(u))
+        exact = (uf / math.sqrt(1.0 - uf * uf) - math.asin(uf)) / (uf * uf)
+        if abs(d - exact) > 1e-7 * max(1.0, abs(exact)):
+            return False
+    return True
+
+
 CASES = [
     ("propagation_sign", check_exact_helix),
     ("jacobian_dropped_factor", check_jacobian_fd),
@@ -270,6 +282,7 @@ CASES = [
     ("field_map_dropped_z_term", check_field_map_refit),
     ("smoother_filtered_not_predicted", check_smoother_leave_one_out),
     ("side_change_as_sector_change", check_side_change),
+    ("fp32_dual_asinc_derivative", check_fp32_dual_asinc),
 ]
 
 

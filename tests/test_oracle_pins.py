@@ -713,3 +713,39 @@ def test_field_map_forms_and_strict_fp32(oracle_mod, synth):
     assert np.allclose(a["params"][:, ok], b["params"][:, ok], rtol=1e-8, atol=1e-10)
     rep = tolerance.compare_to_fp64(oracle_mod.fit(fr, "f32"), a)
     assert rep["ok"], rep
+
+
+def test_fp32_dual_asinc_derivative_matches_closed_form(oracle_mod):
+    # d/du asin(u)/u = (u / sqrt(1 - u^2) - asin(u)) / u^2; the FP32 dual takes
+    # the derivative of its polynomial for |u| <= 1/4 and of the FP64 island above
+    for u in np.concatenate([np.linspace(-0.9, 0.9, 181), [1e-3, -1e-3, 0.2499, 0.2501, 0.01]]):
+        v, d = oracle_mod.asinc_dual_f32(u)
+        uf = float(np.float32(u))
+        assert v == oracle_mod.asinc_f32(uf)
+        if abs(uf) < 1e-6:
+            continue
+        exact = (uf / np.sqrt(1.0 - uf * uf) - np.arcsin(uf)) / (uf * uf)
+        assert abs(d - exact) <= 1e-7 * max(1.0, abs(exact)), (u, d, exact)
+
+
+def test_fp32_dual_gradient_follows_the_strict_fp32_fit(oracle_mod, synth):
+    # the FP32-valued dual evaluates the strict-FP32 sequence itself: chi2 and
+    # ndf bit for bit those of the float fit; its derivative (carried in FP64)
+    # is that of the FP32 trajectory, so it sits within the FP32 forward's own
+    # rounding (a few 1e-5 in norm) of the FP64 gradient, not at 1e-9
+    d_true = synth.alignment_offsets(3)
+    fr = synth.generate(300, 3, drop_p=0.05, cap_lengths=True, d_true=d_true)
+    w = np.random.default_rng(5).uniform(0.5, 2.0, fr.n_tracks).astype(np.float32).astype(np.float64)
+    g32 = oracle_mod.grad(fr, weights=w, align=d_true, precision="f32")
+    g64 = oracle_mod.grad(fr, weights=w, align=d_true)
+    f32 = oracle_mod.fit(fr, "f32", align=d_true)
+    ok = f32["ndf"] > 0
+    assert ok.mean() > 0.99
+    assert np.array_equal(g32["ndf"], f32["ndf"])
+    assert np.array_equal(g32["chi2"][ok].astype(np.float32).view(np.int32), f32["chi2"][ok].view(np.int32))
+    a, b = g32["grad_meas"], g64["grad_meas"]
+    rel = np.linalg.norm(a - b) / np.linalg.norm(b)
+    assert 1e-6 < rel < 2e-4, rel
+    scale = np.maximum(np.abs(b), 1e-3 * np.abs(b).max())
+    assert np.quantile(np.abs(a - b) / scale, 0.99) < 2e-3
+    assert np.linalg.norm(g32["grad_seed"] - g64["grad_seed"]) < 3e-4 * np.linalg.norm(g64["grad_seed"])
