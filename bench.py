@@ -33,14 +33,6 @@ WORKLOAD = "time-frame batch: 400,000 tracks, 5% clusters dropped, lengths U{10.
 N_TRACKS = 400_000
 
 
-def _peaks():
-    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
-    if os.path.exists(p):
-        with open(p) as f:
-            return json.load(f), "measured"
-    return {"hbm_gbs": 6800.0, "sm_max_mhz": 2070.0}, "fallback"
-
-
 def fp32_peak_tflops(sm_mhz: float, n_sm: int = 152) -> float:
     """FP32 CUDA-core peak: SMs x 128 FP32 lanes x 2 flops (FMA) x clock."""
     return n_sm * 128 * 2 * sm_mhz * 1e6 / 1e12
@@ -210,6 +202,26 @@ def run_reference(args, rank: int, world: int):
     print(json.dumps(line), flush=True)
 
 
+def measure_fp32_peak(tf, torch, device_index: int, seconds: float = 1.5) -> dict:
+    """The FP32 peak of this GPU from the library's FMA-chain microbenchmark
+    (scalar FMAs and paired fma.f32x2, each one launch of about `seconds`,
+    clocks sampled during it); the larger of the two is the roofline's
+    denominator.  Cross-check: SMs x 128 FP32 lanes x 2 x the sampled clock."""
+    res = {}
+    for mode, name in ((0, "ffma"), (1, "ffma2")):
+        fl, ms = tf.tpcfit_fp32_peak(mode, 2000)           # calibration launch
+        iters = max(2000, int(2000 * seconds * 1e3 / max(ms, 1e-3)))
+        torch.cuda.synchronize()
+        with ClockSampler(device_index) as clk:
+            fl, ms = tf.tpcfit_fp32_peak(mode, iters)
+        res[name] = {"tflops": fl / (ms / 1e3) / 1e12, "ms": ms, "clocks": clk.summary()}
+    best = max(res.values(), key=lambda r: r["tflops"])
+    sms = torch.cuda.get_device_properties(device_index).multi_processor_count
+    mhz = best["clocks"].get("sm_mhz")
+    return {"tflops": best["tflops"], "ffma": res["ffma"], "ffma2": res["ffma2"], "sms": sms,
+            "nominal_at_sampled_clock_tflops": fp32_peak_tflops(mhz, sms) if mhz else None}
+
+
 def rank_seed(rank: int) -> int:
     """Each rank fits its own batch of the same size (weak scaling)."""
     return 2 + 1000 * rank
@@ -345,8 +357,9 @@ def run_batched_frames(args, tf, torch, synth, flops, peak_tf):
         torch.cuda.synchronize()
         ms = s.elapsed_time(e) / reps
         tfl = flops.fit_flops(lengths) / (ms / 1e3) / 1e12
+        tfm = flops.method_fit_flops(lengths) / (ms / 1e3) / 1e12
         res[mode] = {"tracks_per_s": batch.n_tracks / (ms / 1e3), "ms_per_batch": ms,
-                     "hits_per_s": batch.n_hits / (ms / 1e3), "frac_fp32_peak": tfl / peak_tf,
+                     "hits_per_s": batch.n_hits / (ms / 1e3), "frac_method": tfm / peak_tf, "frac_impl": tfl / peak_tf,
                      "config": {k: best[k] for k in ("lanes_per_track", "rows_per_stage", "warps_per_block",
                                                      "sort_by_length")},
                      "fitted_fraction": float((g.out["ndf"] > 0).float().mean().item())}
@@ -557,6 +570,26 @@ def main():
     fitter.set_record(False)
     fitter.set_field(None)
 
+    # ---- deterministic mode on the same frame: plain fit and fit + adjoint
+    det = None
+    if args.mode == "fast":
+        fitter.set_mode(True)
+        fitter.set_record(False)
+        for _ in range(args.warmup):
+            fitter.fit(dev, out)
+        torch.cuda.synchronize()
+        _, det_fit_per = timed(step_fit, max(10, args.steps // 4))
+        fitter.set_record(True)
+        for _ in range(args.warmup):
+            fit_adjoint()
+        torch.cuda.synchronize()
+        _, det_fa_per = timed(step_fa, max(10, args.steps // 4))
+        fitter.set_record(False)
+        fitter.set_mode(False)
+        det = {"plain_fit_ms": statistics.mean(p[0] for p in det_fit_per),
+               "fit_ms": statistics.mean(p[0] for p in det_fa_per),
+               "backward_ms": statistics.mean(p[1] for p in det_fa_per)}
+
     # ---- end to end through the public API with host buffers
     h2d = 10 * fr.n_hits + 4 * (fr.n_tracks + 1) + 20 * fr.n_tracks
     d2h = 88 * fr.n_tracks
@@ -583,70 +616,76 @@ def main():
             dist.destroy_process_group()
         return
 
-    peaks, peak_src = _peaks()
-    peak_tf = fp32_peak_tflops(float(peaks.get("sm_max_mhz", 2070.0)))
+    # ---- the FP32 peak of this GPU, measured (the roofline's denominator)
+    peak = measure_fp32_peak(tf, torch, local)
+    peak_tf = peak["tflops"]
     value = world * fr.n_tracks * args.steps / (total_ms / 1e3)
     clocks = clk.summary()
-    bwd_flops = flops.backward_flops(lengths)
-    fit_fl = flops.fit_flops(lengths)
-    bwd_tf = bwd_flops / (bwd_ms / 1e3) / 1e12
-    fit_tf = fit_fl / (plain_ms / 1e3) / 1e12
-    fa_tf = flops.fit_adjoint_flops(lengths) / (total_ms / args.steps / 1e3) / 1e12
-    peak_note = (f"152 SMs x 128 FP32 lanes x 2 x {peaks.get('sm_max_mhz', 2070.0)} MHz "
-                 f"(sm_max_mhz from the {peak_src} peaks file)")
+    step_ms = total_ms / args.steps
+    mhits = float(lengths.mean())
+
+    def frac2(impl_flops, method_flops, ms):
+        """achieved TFLOP/s and fraction of the measured peak on both counts."""
+        a_impl = impl_flops / (ms / 1e3) / 1e12
+        a_meth = method_flops / (ms / 1e3) / 1e12
+        return {"achieved_method": a_meth, "frac_method": a_meth / peak_tf,
+                "achieved_impl": a_impl, "frac_impl": a_impl / peak_tf}
+
+    bwd_f = frac2(flops.backward_flops(lengths), flops.method_backward_flops(lengths), bwd_ms)
+    fa_f = frac2(flops.fit_adjoint_flops(lengths), flops.method_fit_adjoint_flops(lengths), step_ms)
+    fit_f = frac2(flops.fit_flops(lengths), flops.method_fit_flops(lengths), plain_ms)
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True, "scaling": "weak",
+        "warmup": args.warmup, "ms_per_step": step_ms, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "step": "fit with checkpoints + adjoint (gradients w.r.t. alignment and seeds)",
-                   "mode": args.mode, "tracks": fr.n_tracks, "hits": fr.n_hits,
-                   "mean_hits_per_track": float(lengths.mean()),
-                   "l2": "inputs larger than L2 (clusters %.0f MB > 126 MB), no flush" % (10 * fr.n_hits / 1e6),
-                   "fitted_fraction": float(np.mean(ndf > 0))},
-        "hits_per_s": value * float(lengths.mean()),
-        "roofline": {"bound": "alu", "achieved": bwd_tf, "peak": peak_tf, "unit": "TFLOP/s", "frac": bwd_tf / peak_tf,
-                     "traffic": _traffic("backward_" + args.mode),
-                     "kernel": "backward_kernel (adjoint, dominant kernel of the step)",
-                     "algorithmic_flops_per_launch": bwd_flops, "launch_ms": bwd_ms, "peak_source": peak_note,
-                     "frac_at_sampled_clock": (bwd_tf / fp32_peak_tflops(clocks["sm_mhz"]))
-                     if clocks.get("sm_mhz") else None},
-        "fit_adjoint": {"tracks_per_s": value, "fit_ms": fit_rec_ms, "backward_ms": bwd_ms,
-                        "achieved_tflops": fa_tf, "frac": fa_tf / peak_tf,
-                        "algorithmic_flops_per_step": flops.fit_adjoint_flops(lengths)},
+        "roofline": {"bound": "alu", "achieved": bwd_f["achieved_method"], "peak": peak_tf, "unit": "TFLOP/s",
+                     "frac": bwd_f["frac_method"], "traffic": _traffic("backward_" + args.mode),
+                     "kernel": "backward_kernel", "launch_ms": bwd_ms,
+                     "frac_impl": bwd_f["frac_impl"], "achieved_impl": bwd_f["achieved_impl"],
+                     "count": "achieved/frac: method count (480 flop per cluster for the fit, x2.5 for the reverse); "
+                              "*_impl: the square-root form as implemented (flops.py)",
+                     "peak_source": "measured on this GPU: FMA-chain microbenchmark (fp32_peak)"},
+        "fit_adjoint": {"tracks_per_s": value, "ms": step_ms, "fit_ms": fit_rec_ms, "backward_ms": bwd_ms, **fa_f},
         "plain_fit": {"tracks_per_s": fr.n_tracks / (plain_ms / 1e3), "ms": plain_ms,
-                      "hits_per_s": fr.n_tracks / (plain_ms / 1e3) * float(lengths.mean()),
-                      "roofline": {"bound": "alu", "achieved": fit_tf, "peak": peak_tf, "unit": "TFLOP/s",
-                                   "frac": fit_tf / peak_tf, "traffic": _traffic("fit_" + args.mode),
-                                   "kernel": "fit_kernel<4,24> + length ordering",
-                                   "algorithmic_flops_per_launch": fit_fl},
-                      "e2e": e2e_plain},
+                      "hits_per_s": fr.n_tracks / (plain_ms / 1e3) * mhits, **fit_f,
+                      "traffic": _traffic("fit_" + args.mode)},
+        "hits_per_s": value * mhits,
         "e2e": e2e,
         "gpu_launches": 4 * args.steps,
         "clocks": clocks,
+        "config": {"workload": WORKLOAD, "step": "fit with checkpoints + adjoint (gradients w.r.t. alignment and seeds)",
+                   "mode": args.mode, "tracks": fr.n_tracks, "hits": fr.n_hits, "mean_hits_per_track": mhits,
+                   "l2": "inputs larger than L2 (clusters %.0f MB > 126 MB), no flush" % (10 * fr.n_hits / 1e6),
+                   "fitted_fraction": float(np.mean(ndf > 0))},
+        "fp32_peak": peak,
     }
-    sm_tf = flops.smooth_flops(lengths) / (smooth_ms / 1e3) / 1e12
+    if det is not None:
+        dfa_ms = det["fit_ms"] + det["backward_ms"]
+        line["deterministic"] = {
+            "plain_fit": {"tracks_per_s": fr.n_tracks / (det["plain_fit_ms"] / 1e3), "ms": det["plain_fit_ms"],
+                          "vs_fast": det["plain_fit_ms"] / plain_ms,
+                          **frac2(flops.fit_flops(lengths), flops.method_fit_flops(lengths), det["plain_fit_ms"])},
+            "fit_adjoint": {"tracks_per_s": fr.n_tracks / (dfa_ms / 1e3), "ms": dfa_ms, "fit_ms": det["fit_ms"],
+                            "backward_ms": det["backward_ms"], "vs_fast": dfa_ms / step_ms,
+                            "backward_vs_fast": det["backward_ms"] / bwd_ms},
+            "paper_slowdown": "1.5-10x (Sec. 2, the deterministic mode of the whole reconstruction)",
+            "note": "no FMA contraction: the deterministic kernels' ceiling is half the FMA peak"}
+    line["plain_fit"]["e2e"] = e2e_plain
+    sm_f = flops.smooth_flops(lengths) / (smooth_ms / 1e3) / 1e12
     line["smoother"] = {"tracks_per_s": fr.n_tracks / (smooth_ms / 1e3), "clusters_per_s": fr.n_hits / (smooth_ms / 1e3),
-                        "ms": smooth_ms, "achieved_tflops": sm_tf, "frac": sm_tf / peak_tf,
-                        "kernel": "smooth_kernel<8> (two-filter smoother of the recorded fit)",
-                        "algorithmic_flops_per_launch": flops.smooth_flops(lengths)}
+                        "ms": smooth_ms, "frac_impl": sm_f / peak_tf}
     line["plain_fit"]["field_map"] = {"tracks_per_s": fr.n_tracks / (fld_ms / 1e3), "ms": fld_ms,
-                                      "field": "Bz (1 + 0.3 (r/250 cm)^2 - 0.2 (z/250 cm)^2), midpoint per step",
-                                      "kernel": "fit_kernel<4,24> with the field map"}
+                                      "field": "Bz (1 + 0.3 (r/250)^2 - 0.2 (z/250)^2)"}
     line["plain_fit"]["material"] = {"tracks_per_s": fr.n_tracks / (mat_ms / 1e3), "ms": mat_ms,
-                                     "material": "TPC gas layer at every row (X0 3.1e4 cm, 1.6 MeV/m, one row pitch)",
-                                     "kernel": "fit_kernel<4,24> with the material layers"}
-    for key, per_, what in (("material", mat_fa_per, "TPC gas layer at every row"),
-                            ("field_map", fld_fa_per, "Bz (1 + 0.3 (r/250 cm)^2 - 0.2 (z/250 cm)^2)")):
+                                     "material": "TPC gas layer at every row"}
+    for key, per_ in (("material", mat_fa_per), ("field_map", fld_fa_per)):
         f_ms = statistics.mean(p[0] for p in per_)
         b_ms = statistics.mean(p[1] for p in per_)
         line["fit_adjoint"][key] = {"tracks_per_s": fr.n_tracks / ((f_ms + b_ms) / 1e3), "fit_ms": f_ms,
-                                    "backward_ms": b_ms, "physics": what,
-                                    "kernel": "backward_kernel<8> compiled for this physics"}
+                                    "backward_ms": b_ms}
     if rtc is not None:
-        rtc_tf = fit_fl / (rtc["ms"] / 1e3) / 1e12
         line["plain_fit"]["rtc"] = {"tracks_per_s": fr.n_tracks / (rtc["ms"] / 1e3), "ms": rtc["ms"],
-                                    "frac": rtc_tf / peak_tf, "first_call_s": rtc["first_call_s"],
-                                    "kernel": "fit_kernel<4,24> compiled with NVRTC for this frame's constants"}
+                                    "first_call_s": rtc["first_call_s"]}
     if not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(fr)
     fitter.close()

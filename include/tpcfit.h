@@ -10,8 +10,9 @@
  * inward refit.  Source: the paper names track propagation through the
  * magnetic field as the shared component of TPC tracking (Sec. 4) and the time
  * frame as the processing unit (Sec. 1).  The deterministic mode follows the
- * rules of Sec. 2; per-time-frame constants live in GPU constant memory as in
- * Sec. 4.1.
+ * rules of Sec. 2; the per-time-frame constants of Sec. 4.1 travel with
+ * every kernel launch in its argument block (the kernel-parameter constant
+ * bank), so handles never share them.
  *
  * Conventions (all calls):
  *   - Units cm, GeV/c, T.  Track state p = (y, z, sin phi, tan lambda, q/pt)
@@ -72,8 +73,9 @@ typedef struct tpcfit_handle tpcfit_handle;
 
 /* Create a fitter on the current CUDA device for the given geometry and field.
  * Builds the geometry tables (pad-row x, sector rotation cos/sin) on the host in
- * FP64, rounds them to FP32 and uploads them to every kernel module's constant
- * memory.  Returns EINVAL for a bad geometry, ECUDA/ENOMEM on CUDA failure. */
+ * FP64 and rounds them to FP32; the handle keeps them and passes them to every
+ * kernel it launches.  Returns EINVAL for a bad geometry, ECUDA/ENOMEM on CUDA
+ * failure. */
 tpcfit_status tpcfit_create(const tpcfit_geometry* geometry, double bz_tesla, tpcfit_handle** out);
 
 /* Release the handle and its device scratch.  Synchronises the device first.
@@ -148,7 +150,8 @@ tpcfit_status tpcfit_fit(tpcfit_handle* h, const tpcfit_hits* hits, const int32_
  * Work is ordered by frame, then by decreasing track length.  Recording for
  * the adjoint does not apply (tpcfit_fit_backward returns ESTATE after this).
  * Capturable in a CUDA graph after one call with the same sizes has run
- * outside the capture (scratch and constants are then in place). */
+ * outside the capture (scratch is then in place); the captured launches hold
+ * the handle's constants as they were at capture. */
 tpcfit_status tpcfit_fit_frames(tpcfit_handle* h, const tpcfit_hits* hits, const int32_t* track_offsets,
                                 int32_t n_tracks, const int64_t* frame_track_base, int32_t n_frames,
                                 const float* frame_alignment, const int32_t* frame_ready, int64_t wait_timeout_ns,
@@ -302,26 +305,30 @@ tpcfit_status tpcfit_fit_host(tpcfit_handle* h, const float* y, const float* z, 
 
 /* Fit without allocating device memory and without a handle.
  * The paper has no counterpart; this entry point is for callers that cannot
- * call cudaMalloc or cudaFree: code running inside a stream capture it does
- * not own, real-time loops that forbid allocator calls (and the device
- * synchronisation they can imply), or frameworks that only hand out their own
- * buffers.  It computes exactly what tpcfit_fit computes with the default
- * launch configuration (length ordering on, 4 rows per stage, 24 warps per
- * block), in the fast (deterministic = 0) or deterministic (1) mode.
- *   geometry, bz_tesla: as for tpcfit_create; the constants are rebuilt and
- *               uploaded to the kernels' constant memory on every call.
+ * call cudaMalloc or cudaFree: real-time loops that forbid allocator calls
+ * (and the device synchronisation they can imply), or frameworks that only
+ * hand out their own buffers.  It computes exactly what tpcfit_fit computes
+ * with the default launch configuration (length ordering on, 4 rows per
+ * stage, 24 warps per block), in the fast (deterministic = 0) or
+ * deterministic (1) mode.
+ *   geometry, bz_tesla: as for tpcfit_create; the constants are rebuilt on
+ *               every call and travel in the launch's argument block, so no
+ *               copy to the device is made for them and no other call (with
+ *               or without a handle) sees them.
  *   alignment:  device float [36][152][2] offsets, or NULL for none.
  *   other arguments and outputs: as for tpcfit_fit.
  * Its scratch is a fixed static device array of about 4.3 MB (room for
  * TPCFIT_NOALLOC_MAX_TRACKS tracks) that each GPU loading the library holds
  * until the process exits; n_tracks above TPCFIT_NOALLOC_MAX_TRACKS returns
  * EINVAL without touching the GPU.  The first call on a device looks up the
- * array's device address (cudaGetSymbolAddress); make that first call before
- * any stream capture.  All calls share the one array, so calls whose work
- * overlaps on the GPU (other streams, other host threads) race: serialise
- * them.  Invalid input gives ndf = -2 for the track (there is no error word
- * to read back).  Calls from a handle's functions afterwards re-upload the
- * handle's constants themselves. */
+ * array's device address (cudaGetSymbolAddress) and keeps it for the life of
+ * the process; make that first call before any stream capture, and do not
+ * call this entry point again on a device after cudaDeviceReset.  All calls
+ * share the one array, so calls whose work overlaps on the GPU (other
+ * streams, other host threads) race: serialise them.  Each call clears the
+ * array's error word and work counter before its kernels run.  Invalid input
+ * gives ndf = -2 and NaNs for the track (there is no error word to read
+ * back); the other tracks of the call are unaffected. */
 tpcfit_status tpcfit_fit_noalloc(const tpcfit_geometry* geometry, double bz_tesla, const float* alignment,
                                  int deterministic, const tpcfit_hits* hits, const int32_t* track_offsets,
                                  int32_t n_tracks, const float* seeds, float* params_out, float* cov_out,
@@ -333,6 +340,16 @@ tpcfit_status tpcfit_fit_noalloc(const tpcfit_geometry* geometry, double bz_tesl
  * none).  Synchronises `stream`.  Returns ETIMEOUT for code 3, EDEVICE for the
  * others, OK if nothing was recorded. */
 tpcfit_status tpcfit_get_status(tpcfit_handle* h, void* stream, int32_t* err_code, int64_t* err_track);
+
+/* FP32 throughput of this GPU, measured: the peak the fit's throughput is
+ * reported against (the paper has no counterpart).  One launch of a kernel
+ * that runs 8 independent FMA chains per thread, 2,048 threads on every SM,
+ * `iterations` times 32 FMAs per chain; mode 0 scalar FMAs, mode 1 paired
+ * fma.f32x2.  One short warm-up launch precedes it.  On return (the call
+ * synchronises `stream`): *flop_out = the FP32 operations executed (an FMA
+ * counts 2), *ms_out = the timed launch's duration from CUDA events on
+ * `stream`.  EINVAL for another mode, iterations < 1 or a null output. */
+tpcfit_status tpcfit_fp32_peak(int mode, int64_t iterations, void* stream, double* flop_out, double* ms_out);
 
 /* Static description of a status code. */
 const char* tpcfit_status_string(tpcfit_status s);

@@ -35,6 +35,7 @@ UNITS = {
     "length_order.cu": [],
     "tpcfit_noalloc.cu": [],
     "key_reduce.cu": [],
+    "fp32_peak.cu": [],
 }
 
 

@@ -63,9 +63,9 @@ __device__ __forceinline__ float asinc_deriv(float u) {
 // adjoint after the update, out = adjoint before; b_chi: adjoint of chi2 (the
 // same before and after).  b_m receives the adjoint of the measured value.
 template <int H>
-__device__ __forceinline__ void scalar_update_rev(const float p[5], const float L[5][5], float mv, float b_p[5],
+__device__ __forceinline__ void scalar_update_rev(const GeoRef& G, const float p[5], const float L[5][5], float mv, float b_p[5],
                                                   float b_L[5][5], float b_chi, float& b_m) {
-  const float v = c_geo.v_meas;
+  const float v = G.v_meas;
   float a[5];
 #pragma unroll
   for (int c = 0; c < 5; ++c) a[c] = L[H][c];
@@ -73,7 +73,7 @@ __device__ __forceinline__ void scalar_update_rev(const float p[5], const float 
 #pragma unroll
   for (int c = 1; c < 5; ++c) s2 = s2 + a[c] * a[c];
   float alpha, beta, gamma;
-  potter_coeffs(s2, v, c_geo.sqrt_v, alpha, beta, gamma);
+  potter_coeffs(s2, v, G.sqrt_v, alpha, beta, gamma);
   const float r = mv - p[H];
   float la[5], K[5];
 #pragma unroll
@@ -182,9 +182,9 @@ __device__ __forceinline__ void transport_rev(const float L[5][5], const Jac& J,
 // y, z, s, t and on the offsets (yo, zo) of residual coordinates, whose
 // adjoints go to b_yo, b_zo (zero without the map).
 template <int FIELD = 0>
-__device__ __forceinline__ void predict_rev(const PredTape& tp, const Jac& J, float t, float q, const float b_po[5],
+__device__ __forceinline__ void predict_rev(const GeoRef& G, const PredTape& tp, const Jac& J, float t, float q, const float b_po[5],
                                             const JacBar& bJ, float b_pi[5], float& b_yo, float& b_zo) {
-  const float kappa = FIELD == 1 ? tp.kap : c_geo.kappa;
+  const float kappa = FIELD == 1 ? tp.kap : G.kappa;
   float b_kap = 0.0f;  // adjoint of the curvature per unit q/pt (map only)
   const float dx = tp.dx, s1 = tp.s1, s2 = tp.s2, ic1 = tp.ic1, ic2 = tp.ic2, Tm = tp.Tm, tt = tp.tt;
   float b_t = b_po[3], b_q = b_po[4], b_s2 = b_po[2];
@@ -316,10 +316,10 @@ __device__ __forceinline__ void predict_rev(const PredTape& tp, const Jac& J, fl
   b_zo = 0.0f;
   if (FIELD == 1) {
     b_kap += q * b_k;
-    const float k0 = 2.0f * c_geo.kappa;
-    b_xm = (k0 * c_geo.f_r) * tp.xm * b_kap;
-    const float b_ym = (k0 * c_geo.f_r) * tp.ym * b_kap;
-    const float b_zm = (k0 * c_geo.f_z) * tp.zm * b_kap;
+    const float k0 = 2.0f * G.kappa;
+    b_xm = (k0 * G.f_r) * tp.xm * b_kap;
+    const float b_ym = (k0 * G.f_r) * tp.ym * b_kap;
+    const float b_zm = (k0 * G.f_z) * tp.zm * b_kap;
     const float hdx = 0.5f * dx, ic1c = ic1 * ic1 * ic1;
     b_yo = b_ym;
     b_zo = b_zm;
@@ -509,7 +509,7 @@ __device__ __forceinline__ void fetch_ckpt(float4* sdst, const float* ck) {
 // MAT: the material layers of the rows; FIELD as for predict_t (the smoother
 // follows both; the adjoint runs without either).
 template <bool MAT = false, int FIELD = 0>
-__device__ __forceinline__ void step_fwd(const SmemTables& T, StepState& S, float& my, float& mz, bool first, bool conv,
+__device__ __forceinline__ void step_fwd(const GeoRef& G, const SmemTables& T, StepState& S, float& my, float& mz, bool first, bool conv,
                                          int row, int sec18, float m0, float m1) {
   float chi2 = 0.0f;
   if (first) {
@@ -525,11 +525,11 @@ __device__ __forceinline__ void step_fwd(const SmemTables& T, StepState& S, floa
     PredTape tp;
     MatNoise N;
     if (MAT && !conv) {  // inward: the layer of the row left
-      material_step(S.p, -1, N);
+      material_step(G, S.p, -1, N);
       material_factor(S.L, N);
     }
-    predict_residual<FIELD>(T, S.p, S.x, S.sec, my, mz, sec18, T.row_x[row], m0, m1, pn, J, tp);
-    if (MAT && conv) material_step(pn, 1, N);
+    predict_residual<FIELD>(G, T, S.p, S.x, S.sec, my, mz, sec18, T.row_x[row], m0, m1, pn, J, tp);
+    if (MAT && conv) material_step(G, pn, 1, N);
 #pragma unroll
     for (int c = 0; c < 5; ++c) S.p[c] = pn[c];
     S.x = T.row_x[row];
@@ -539,8 +539,8 @@ __device__ __forceinline__ void step_fwd(const SmemTables& T, StepState& S, floa
   }
   my = m0;
   mz = m1;
-  scalar_update<0>(S.p, S.L, chi2, 0.0f);
-  scalar_update<1>(S.p, S.L, chi2, 0.0f);
+  scalar_update<0>(G, S.p, S.L, chi2, 0.0f);
+  scalar_update<1>(G, S.p, S.L, chi2, 0.0f);
 }
 
 // Reverse of one step from the state before it, which sits in shared memory
@@ -550,7 +550,7 @@ __device__ __forceinline__ void step_fwd(const SmemTables& T, StepState& S, floa
 // The measurements enter only through the residual shifts: b_mc = adjoint of
 // this cluster's (y, z), b_mp = of the previous one's.
 template <int FIELD = 0>
-__device__ __forceinline__ void step_rev(const SmemTables& T, const float4* src, float my_prev, float mz_prev,
+__device__ __forceinline__ void step_rev(const GeoRef& G, const SmemTables& T, const float4* src, float my_prev, float mz_prev,
                                          bool first, bool conv, int row, int sec18, float m0, float m1, float b_p[5],
                                          float b_L[5][5], float b_chi, float b_mc[2], float b_mp[2]) {
   StepState S0;
@@ -567,7 +567,7 @@ __device__ __forceinline__ void step_rev(const SmemTables& T, const float4* src,
       p1[1] = S0.p[1] - m1;
     }
   } else {
-    predict_residual<FIELD>(T, S0.p, S0.x, S0.sec, my_prev, mz_prev, sec18, T.row_x[row], m0, m1, p1, J, tp);
+    predict_residual<FIELD>(G, T, S0.p, S0.x, S0.sec, my_prev, mz_prev, sec18, T.row_x[row], m0, m1, p1, J, tp);
   }
   // the factor before the y update (kept) and before the z update
   float p2[5];
@@ -584,9 +584,9 @@ __device__ __forceinline__ void step_rev(const SmemTables& T, const float4* src,
   for (int i = 0; i < 5; ++i)
 #pragma unroll
     for (int c = 0; c < 5; ++c) L2[i][c] = L[i][c];
-  scalar_update<0>(p2, L2, chi_dummy, 0.0f);
-  scalar_update_rev<1>(p2, L2, 0.0f, b_p, b_L, b_chi, b_dummy);
-  scalar_update_rev<0>(p1, L, 0.0f, b_p, b_L, b_chi, b_dummy);
+  scalar_update<0>(G, p2, L2, chi_dummy, 0.0f);
+  scalar_update_rev<1>(G, p2, L2, 0.0f, b_p, b_L, b_chi, b_dummy);
+  scalar_update_rev<0>(G, p1, L, 0.0f, b_p, b_L, b_chi, b_dummy);
   // b_p is now the adjoint of the predicted (shifted) state p1
   b_mc[0] = -b_p[0];
   b_mc[1] = -b_p[1];
@@ -606,7 +606,7 @@ __device__ __forceinline__ void step_rev(const SmemTables& T, const float4* src,
   }
   // the prediction's intermediates (tp, J) are those of the forward above
   float b_pi[5], b_yo, b_zo;
-  predict_rev<FIELD>(tp, J, S0.p[3], S0.p[4], b_p, bJ, b_pi, b_yo, b_zo);
+  predict_rev<FIELD>(G, tp, J, S0.p[3], S0.p[4], b_p, bJ, b_pi, b_yo, b_zo);
   if (rot) {
     b_mp[0] = b_pi[0];
     b_mp[1] = b_pi[1];
@@ -621,23 +621,23 @@ __device__ __forceinline__ void step_rev(const SmemTables& T, const float4* src,
 // Reverse of material_step for a step that was taken.  p: the state before it;
 // b_p in: adjoint of the state after, out: of the state before; bN: adjoints of
 // the terms it handed on (qq, b_s, b_t, b_q).  Only s, t and q enter.
-__device__ __forceinline__ void material_step_rev(const float p[5], int dir, const MatNoise& bN, float b_p[5]) {
+__device__ __forceinline__ void material_step_rev(const GeoRef& G, const float p[5], int dir, const MatNoise& bN, float b_p[5]) {
   const float s = p[2], t = p[3], q = p[4];
   const float q2 = q * q;
   if (!(q2 > 0.0f)) return;  // no material effect: nothing depends on the state
   const float tt1 = 1.0f + t * t;
   const float c = sqrtf((1.0f - s) * (1.0f + s));
   const float st1 = sqrtf(tt1);
-  const float ell = (c_geo.d_row * st1) / c;
+  const float ell = (G.d_row * st1) / c;
   const float p2 = tt1 / q2;
-  const float e2 = p2 + c_geo.mass2;
-  const float kx = static_cast<float>(0.0136 * 0.0136) * c_geo.x0_inv;
+  const float e2 = p2 + G.mass2;
+  const float kx = static_cast<float>(0.0136 * 0.0136) * G.x0_inv;
   const float ip2 = 1.0f / p2;
   const float th2 = (kx * ell) * (e2 * (ip2 * ip2));
   const float e = sqrtf(e2);
-  const float de = (c_geo.dedx * ell) * (e2 * ip2);
+  const float de = (G.dedx * ell) * (e2 * ip2);
   const float en = dir > 0 ? e - de : e + de;
-  const float pn2 = en * en - c_geo.mass2;
+  const float pn2 = en * en - G.mass2;
   const float ratio = sqrtf(p2 / pn2);
   const float qo = q * ratio;
   const float th = sqrtf(th2);
@@ -660,14 +660,14 @@ __device__ __forceinline__ void material_step_rev(const float p[5], int dir, con
   float b_e2 = 0.5f * b_en / e;
   const float b_de = dir > 0 ? -b_en : b_en;
   // de = (dedx ell) (e2 / p2); th2 = (kx ell) (e2 / p2^2); e2 = p2 + m^2
-  float b_ell = (c_geo.dedx * (e2 * ip2)) * b_de + (kx * (e2 * (ip2 * ip2))) * b_th2;
-  b_e2 += ((c_geo.dedx * ell) * ip2) * b_de + ((kx * ell) * (ip2 * ip2)) * b_th2;
-  b_p2 -= ((c_geo.dedx * ell) * (e2 * (ip2 * ip2))) * b_de + 2.0f * ((kx * ell) * (e2 * (ip2 * ip2 * ip2))) * b_th2;
+  float b_ell = (G.dedx * (e2 * ip2)) * b_de + (kx * (e2 * (ip2 * ip2))) * b_th2;
+  b_e2 += ((G.dedx * ell) * ip2) * b_de + ((kx * ell) * (ip2 * ip2)) * b_th2;
+  b_p2 -= ((G.dedx * ell) * (e2 * (ip2 * ip2))) * b_de + 2.0f * ((kx * ell) * (e2 * (ip2 * ip2 * ip2))) * b_th2;
   b_p2 += b_e2;
   // p2 = tt1 / q^2; ell = d st1 / c; st1 = sqrt(tt1); c = sqrt((1 - s)(1 + s)); tt1 = 1 + t^2
   b_tt1 += b_p2 / q2;
   b_q += 2.0f * q * (-(b_p2 * p2) / q2);
-  b_st1 += (c_geo.d_row / c) * b_ell;
+  b_st1 += (G.d_row / c) * b_ell;
   b_c -= (ell / c) * b_ell;
   b_tt1 += 0.5f * b_st1 / st1;
   b_t += 2.0f * t * b_tt1;
@@ -773,7 +773,7 @@ __device__ __forceinline__ void material_factor_rev(const float Lin[5][5], const
 // undone first (on the state before the step), then prediction, transport and
 // updates.  Arguments as for step_rev.
 template <int FIELD = 0>
-__device__ __forceinline__ void step_rev_mat(const SmemTables& T, const float4* src, float my_prev, float mz_prev,
+__device__ __forceinline__ void step_rev_mat(const GeoRef& G, const SmemTables& T, const float4* src, float my_prev, float mz_prev,
                                              bool first, bool conv, int row, int sec18, float m0, float m1,
                                              float b_p[5], float b_L[5][5], float b_chi, float b_mc[2],
                                              float b_mp[2]) {
@@ -798,10 +798,10 @@ __device__ __forceinline__ void step_rev_mat(const SmemTables& T, const float4* 
 #pragma unroll
       for (int c = 0; c < 5; ++c) L[i][c] = S0.L[i][c];
   } else if (conv) {
-    predict_residual<FIELD>(T, S0.p, S0.x, S0.sec, my_prev, mz_prev, sec18, T.row_x[row], m0, m1, p1, J, tp);
+    predict_residual<FIELD>(G, T, S0.p, S0.x, S0.sec, my_prev, mz_prev, sec18, T.row_x[row], m0, m1, p1, J, tp);
 #pragma unroll
     for (int c = 0; c < 5; ++c) pb[c] = p1[c];
-    material_step(p1, 1, N);
+    material_step(G, p1, 1, N);
 #pragma unroll
     for (int i = 0; i < 5; ++i)
 #pragma unroll
@@ -815,13 +815,13 @@ __device__ __forceinline__ void step_rev_mat(const SmemTables& T, const float4* 
   } else {
 #pragma unroll
     for (int c = 0; c < 5; ++c) pb[c] = S0.p[c];
-    material_step(pb, -1, N);
+    material_step(G, pb, -1, N);
 #pragma unroll
     for (int i = 0; i < 5; ++i)
 #pragma unroll
       for (int c = 0; c < 5; ++c) Lb[i][c] = S0.L[i][c];
     material_factor(Lb, N);
-    predict_residual<FIELD>(T, pb, S0.x, S0.sec, my_prev, mz_prev, sec18, T.row_x[row], m0, m1, p1, J, tp);
+    predict_residual<FIELD>(G, T, pb, S0.x, S0.sec, my_prev, mz_prev, sec18, T.row_x[row], m0, m1, p1, J, tp);
 #pragma unroll
     for (int i = 0; i < 5; ++i)
 #pragma unroll
@@ -837,9 +837,9 @@ __device__ __forceinline__ void step_rev_mat(const SmemTables& T, const float4* 
   for (int i = 0; i < 5; ++i)
 #pragma unroll
     for (int c = 0; c < 5; ++c) L2[i][c] = L[i][c];
-  scalar_update<0>(p2, L2, chi_dummy, 0.0f);
-  scalar_update_rev<1>(p2, L2, 0.0f, b_p, b_L, b_chi, b_dummy);
-  scalar_update_rev<0>(p1, L, 0.0f, b_p, b_L, b_chi, b_dummy);
+  scalar_update<0>(G, p2, L2, chi_dummy, 0.0f);
+  scalar_update_rev<1>(G, p2, L2, 0.0f, b_p, b_L, b_chi, b_dummy);
+  scalar_update_rev<0>(G, p1, L, 0.0f, b_p, b_L, b_chi, b_dummy);
   // b_p: adjoint of the (shifted) state the updates started from; the layers
   // change only q, so its y, z entries are those of the prediction
   b_mc[0] = -b_p[0];
@@ -857,22 +857,22 @@ __device__ __forceinline__ void step_rev_mat(const SmemTables& T, const float4* 
   float b_pi[5], b_yo, b_zo;
   if (conv) {
     material_factor_rev(Lb, N, L, b_L, bN);
-    material_step_rev(pb, 1, bN, b_p);
+    material_step_rev(G, pb, 1, bN, b_p);
     if (!rot) {
       b_mp[0] = b_p[0];
       b_mp[1] = b_p[1];
     }
     transport_rev(S0.L, J, b_L, bJ);
-    predict_rev<FIELD>(tp, J, S0.p[3], S0.p[4], b_p, bJ, b_pi, b_yo, b_zo);
+    predict_rev<FIELD>(G, tp, J, S0.p[3], S0.p[4], b_p, bJ, b_pi, b_yo, b_zo);
   } else {
     if (!rot) {
       b_mp[0] = b_p[0];
       b_mp[1] = b_p[1];
     }
     transport_rev(Lb, J, b_L, bJ);
-    predict_rev<FIELD>(tp, J, pb[3], pb[4], b_p, bJ, b_pi, b_yo, b_zo);
+    predict_rev<FIELD>(G, tp, J, pb[3], pb[4], b_p, bJ, b_pi, b_yo, b_zo);
     material_factor_rev(S0.L, N, Lb, b_L, bN);
-    material_step_rev(S0.p, -1, bN, b_pi);
+    material_step_rev(G, S0.p, -1, bN, b_pi);
   }
   if (rot) {
     b_mp[0] = b_pi[0];
@@ -934,12 +934,13 @@ constexpr size_t backward_smem_bytes() {
 // is copied while the current segment is reversed.
 // PHYS: bit 1 the material layers, bit 2 the field map.
 template <int WARPS, int PHYS>
-__global__ void __launch_bounds__(WARPS * 32, 1) backward_kernel(BwdArgs a) {
+__global__ void __launch_bounds__(WARPS * 32, 1) backward_kernel(const __grid_constant__ BwdArgs a) {
+  const GeoRef& G = a.geo;
   constexpr bool MAT = (PHYS & 1) != 0;
   constexpr int FIELD = (PHYS & 2) ? 1 : 0;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   BwdSmem& B = *reinterpret_cast<BwdSmem*>(smem_raw);
-  load_tables(B.T);
+  load_tables(G, B.T);
   for (int i = threadIdx.x; i < kAlignFloats; i += blockDim.x) B.align[i] = __ldg(a.align + i);
   __syncthreads();
   const SmemTables& T = B.T;
@@ -1015,7 +1016,7 @@ __global__ void __launch_bounds__(WARPS * 32, 1) backward_kernel(BwdArgs a) {
             if (kk + 1 < cnt) nx = load_hit(a, h0 + hd * (i + 1));
             decode_hit(B.align, cur, m0, m1, row, sec);
             store_state(gs + kk * (kStateF4 * kWarp), S);
-            step_fwd<MAT, FIELD>(T, S, my, mz, i == 0, pass == 0, row, sec % kNSide, m0, m1);
+            step_fwd<MAT, FIELD>(G, T, S, my, mz, i == 0, pass == 0, row, sec % kNSide, m0, m1);
           }
           // the states just stored are read back by this thread's copies below
           __threadfence_block();
@@ -1053,10 +1054,10 @@ __global__ void __launch_bounds__(WARPS * 32, 1) backward_kernel(BwdArgs a) {
             if (addg && i > 0) gnx = gmr[h - hd];
             float b_mc[2], b_mp[2];
             if (MAT)
-              step_rev_mat<FIELD>(T, &W.st[kk & 1][0][lane], mpy, mpz, i == 0, pass == 0, row, sec % kNSide, m0, m1,
+              step_rev_mat<FIELD>(G, T, &W.st[kk & 1][0][lane], mpy, mpz, i == 0, pass == 0, row, sec % kNSide, m0, m1,
                                   b_p, b_L, b_chi, b_mc, b_mp);
             else
-              step_rev<FIELD>(T, &W.st[kk & 1][0][lane], mpy, mpz, i == 0, pass == 0, row, sec % kNSide, m0, m1,
+              step_rev<FIELD>(G, T, &W.st[kk & 1][0][lane], mpy, mpz, i == 0, pass == 0, row, sec % kNSide, m0, m1,
                               b_p, b_L, b_chi, b_mc, b_mp);
             accumulate_meas_grad(a, pass, h, row, sec, b_mc[0] + pend0, b_mc[1] + pend1, gcur);
             pend0 = b_mp[0];

@@ -50,9 +50,34 @@
 namespace tpcfit {
 namespace TPCFIT_NS {
 
-#if !TPCFIT_RTC
-__constant__ GeoConst c_geo;
+// Per-time-frame constants.  Ahead of time they travel with every launch as
+// part of its argument block (kernel parameters live in constant bank 0, read
+// as free operands like __constant__ data), so each launch -- and each node of
+// a captured CUDA graph -- carries its own time frame's constants and no
+// launch can see another handle's.  At run time (NVRTC) the source defines
+// c_geo with the scalars as compile-time constants instead.
+#if TPCFIT_RTC
+using GeoRef = GeoFold;
+#define TPCFIT_GEO(args) c_geo
+#else
+using GeoRef = GeoConst;
+#define TPCFIT_GEO(args) (args).geo
 #endif
+
+// Maclaurin coefficients of arcsin, a_n = a_{n-1} (2n-1)^2 / ((2n)(2n+1)),
+// a_0 = 1 (Abramowitz & Stegun 4.4.40), evaluated in FP64 at compile time; the
+// same for every time frame, so they are a fixed table of the module.
+struct AsinCoef {
+  double a[30];
+};
+__host__ __device__ constexpr AsinCoef asin_coefficients() {
+  AsinCoef c{};
+  c.a[0] = 1.0;
+  for (int n = 1; n < 30; ++n)
+    c.a[n] = c.a[n - 1] * ((double)(2 * n - 1) * (double)(2 * n - 1)) / ((double)(2 * n) * (double)(2 * n + 1));
+  return c;
+}
+__constant__ AsinCoef c_asin = asin_coefficients();
 
 struct Jac {
   bool rot;
@@ -61,12 +86,12 @@ struct Jac {
 
 // ---------------------------------------------------------------- arcsin pieces
 // FP64 arcsin: Maclaurin series for |u| <= 1/2, asin u = pi/2 - 2 asin(sqrt((1-u)/2))
-// above (Abramowitz & Stegun 4.4.40-4.4.41); coefficients from the constant bank.
+// above (Abramowitz & Stegun 4.4.40-4.4.41).
 __device__ __forceinline__ double asin_series_f64(double u) {
   const double q = u * u;
-  double acc = c_geo.asin_a[29];
+  double acc = c_asin.a[29];
 #pragma unroll 1
-  for (int n = 28; n >= 0; --n) acc = acc * q + c_geo.asin_a[n];
+  for (int n = 28; n >= 0; --n) acc = acc * q + c_asin.a[n];
   return acc * u;
 }
 
@@ -157,11 +182,11 @@ struct SmemTables {
   float rot_s[kNSide * kNSide];
 };
 
-__device__ __forceinline__ void load_tables(SmemTables& t) {
-  for (int i = threadIdx.x; i < kMaxRows; i += blockDim.x) t.row_x[i] = c_geo.row_x[i];
+__device__ __forceinline__ void load_tables(const GeoRef& G, SmemTables& t) {
+  for (int i = threadIdx.x; i < kMaxRows; i += blockDim.x) t.row_x[i] = G.row_x[i];
   for (int i = threadIdx.x; i < kNSide * kNSide; i += blockDim.x) {
-    t.rot_c[i] = c_geo.rot_c[i];
-    t.rot_s[i] = c_geo.rot_s[i];
+    t.rot_c[i] = G.rot_c[i];
+    t.rot_s[i] = G.rot_s[i];
   }
 }
 
@@ -182,17 +207,17 @@ struct PredTape {
 // rotation at the current point, then helix propagation at fixed Bz.  Returns
 // false, leaving nothing changed, if the step is impossible.
 //
-// Field map (c_geo.field): the step's curvature uses Bz at its midpoint,
+// Field map (G.field): the step's curvature uses Bz at its midpoint,
 // estimated by a straight half step from the start point (after the rotation),
 // kappa_step = kappa (1 + f_r (x_m^2 + y_m^2) + f_z z_m^2); the Jacobian
 // treats kappa_step as a constant.  (yo, zo) turn pin's y, z into absolute
 // positions (residual form).  FIELD: 0 uniform (no map code), 1 the map,
-// 2 decided at run time by c_geo.field.
+// 2 decided at run time by G.field.
 template <int FIELD = 2>
-__device__ __forceinline__ bool predict_t(const SmemTables& T, const float pin[5], float xin, int a, int b, float X,
+__device__ __forceinline__ bool predict_t(const GeoRef& G, const SmemTables& T, const float pin[5], float xin, int a, int b, float X,
                                           float pout[5], Jac& J, PredTape& tp, float yo = 0.0f, float zo = 0.0f) {
-  float kappa = c_geo.kappa;
-  const float maxsnp = c_geo.max_snp;
+  float kappa = G.kappa;
+  const float maxsnp = G.max_snp;
   float x1 = xin, y1 = pin[0], s1 = pin[2];
   const float t = pin[3];
   const float q = pin[4];
@@ -223,13 +248,13 @@ __device__ __forceinline__ bool predict_t(const SmemTables& T, const float pin[5
   tp.ca = ca;
   tp.sa = sa;
   const float dx = X - x1;
-  if (FIELD == 1 || (FIELD == 2 && c_geo.field)) {
+  if (FIELD == 1 || (FIELD == 2 && G.field)) {
     const float c1f = sqrtf((1.0f - s1) * (1.0f + s1));
     const float hdx = dx * 0.5f;
     const float ym = (yo + y1) + hdx * (s1 / c1f);
     const float zm = (zo + pin[1]) + hdx * (t / c1f);
     const float xm = x1 + hdx;
-    kappa = kappa * ((1.0f + c_geo.f_r * (xm * xm + ym * ym)) + c_geo.f_z * (zm * zm));
+    kappa = kappa * ((1.0f + G.f_r * (xm * xm + ym * ym)) + G.f_z * (zm * zm));
     tp.xm = xm;
     tp.ym = ym;
     tp.zm = zm;
@@ -300,10 +325,10 @@ __device__ __forceinline__ bool predict_t(const SmemTables& T, const float pin[5
   return true;
 }
 
-__device__ __forceinline__ bool predict(const SmemTables& T, const float pin[5], float xin, int a, int b, float X,
+__device__ __forceinline__ bool predict(const GeoRef& G, const SmemTables& T, const float pin[5], float xin, int a, int b, float X,
                                         float pout[5], Jac& J) {
   PredTape tp;
-  return predict_t<2>(T, pin, xin, a, b, X, pout, J, tp);
+  return predict_t<2>(G, T, pin, xin, a, b, X, pout, J, tp);
 }
 
 // Prediction in residual coordinates: p[0..1] are residuals from (my, mz), the
@@ -312,7 +337,7 @@ __device__ __forceinline__ bool predict(const SmemTables& T, const float pin[5],
 // rotation the absolute position is formed, rotated, propagated and
 // re-referenced.
 template <int FIELD = 2>
-__device__ __forceinline__ bool predict_residual(const SmemTables& T, const float p[5], float x, int sec, float my,
+__device__ __forceinline__ bool predict_residual(const GeoRef& G, const SmemTables& T, const float p[5], float x, int sec, float my,
                                                  float mz, int sec_to, float X, float m0, float m1, float pout[5],
                                                  Jac& J, PredTape& tp) {
   float pin[5];
@@ -323,7 +348,7 @@ __device__ __forceinline__ bool predict_residual(const SmemTables& T, const floa
     pin[0] = my + p[0];
     pin[1] = mz + p[1];
   }
-  if (!predict_t<FIELD>(T, pin, x, sec, sec_to, X, pout, J, tp, rot ? 0.0f : my, rot ? 0.0f : mz)) return false;
+  if (!predict_t<FIELD>(G, T, pin, x, sec, sec_to, X, pout, J, tp, rot ? 0.0f : my, rot ? 0.0f : mz)) return false;
   if (rot) {
     pout[0] = pout[0] - m0;
     pout[1] = pout[1] - m1;
@@ -361,8 +386,8 @@ __device__ __forceinline__ void transport(float L[5][5], const Jac& J) {
 
 // Potter scalar update of component H (0 = y, 1 = z) with measured value mv.
 template <int H>
-__device__ __forceinline__ void scalar_update(float p[5], float L[5][5], float& chi2, float mv) {
-  const float v = c_geo.v_meas;
+__device__ __forceinline__ void scalar_update(const GeoRef& G, float p[5], float L[5][5], float& chi2, float mv) {
+  const float v = G.v_meas;
   float a[5];
 #pragma unroll
   for (int c = 0; c < 5; ++c) a[c] = L[H][c];
@@ -370,7 +395,7 @@ __device__ __forceinline__ void scalar_update(float p[5], float L[5][5], float& 
 #pragma unroll
   for (int c = 1; c < 5; ++c) s2 = s2 + a[c] * a[c];
   float alpha, beta, gamma;
-  potter_coeffs(s2, v, c_geo.sqrt_v, alpha, beta, gamma);
+  potter_coeffs(s2, v, G.sqrt_v, alpha, beta, gamma);
   const float r = mv - p[H];
 #if TPCFIT_DET
   // canonical sequence: K = alpha L a, p += K r, gain factors gamma K
@@ -420,7 +445,7 @@ __device__ __forceinline__ void scalar_update(float p[5], float L[5][5], float& 
 }
 
 // ---------------------------------------------------------------- material
-// A thin material layer at every pad row (c_geo.mat): the state at a row is
+// A thin material layer at every pad row (G.mat): the state at a row is
 // the one the track leaves it with; the outward pass crosses a row's layer on
 // arriving (dir = +1), the inward pass undoes it before leaving the row
 // against the flight (dir = -1).  Path through the layer
@@ -433,7 +458,7 @@ struct MatNoise {
   float qq, b_s, b_t, b_q;
 };
 
-__device__ __forceinline__ bool material_step(float p[5], int dir, MatNoise& N) {
+__device__ __forceinline__ bool material_step(const GeoRef& G, float p[5], int dir, MatNoise& N) {
   const float s = p[2];
   const float t = p[3];
   const float q = p[4];
@@ -446,14 +471,14 @@ __device__ __forceinline__ bool material_step(float p[5], int dir, MatNoise& N) 
   const float tt1 = 1.0f + t * t;
   const float c = sqrtf((1.0f - s) * (1.0f + s));
   const float st1 = sqrtf(tt1);
-  const float ell = (c_geo.d_row * st1) / c;
+  const float ell = (G.d_row * st1) / c;
   const float p2 = tt1 / q2;
-  const float e2 = p2 + c_geo.mass2;
-  const float th2 = ((static_cast<float>(0.0136 * 0.0136) * ell) * c_geo.x0_inv) * (e2 / (p2 * p2));
-  const float de = (c_geo.dedx * ell) * (e2 / p2);
+  const float e2 = p2 + G.mass2;
+  const float th2 = ((static_cast<float>(0.0136 * 0.0136) * ell) * G.x0_inv) * (e2 / (p2 * p2));
+  const float de = (G.dedx * ell) * (e2 / p2);
   const float e = sqrtf(e2);
   const float en = dir > 0 ? e - de : e + de;
-  const float pn2 = en * en - c_geo.mass2;
+  const float pn2 = en * en - G.mass2;
   if (!(pn2 > 0.0f)) return false;
   const float ratio = sqrtf(p2 / pn2);
   p[4] = q * ratio;
@@ -513,11 +538,11 @@ __device__ __forceinline__ void material_factor(float L[5][5], const MatNoise& N
     for (int j = 0; j < 5; ++j) L[i][j] = j <= i ? X[j][i] : 0.0f;
 }
 
-__device__ __forceinline__ void reset_factor(float L[5][5]) {
+__device__ __forceinline__ void reset_factor(const GeoRef& G, float L[5][5]) {
 #pragma unroll
   for (int i = 0; i < 5; ++i)
 #pragma unroll
-    for (int c = 0; c < 5; ++c) L[i][c] = (i == c) ? c_geo.l0 : 0.0f;
+    for (int c = 0; c < 5; ++c) L[i][c] = (i == c) ? G.l0 : 0.0f;
 }
 
 __device__ __forceinline__ void record_error(unsigned long long* err, unsigned long long code, int64_t track) {
@@ -600,10 +625,10 @@ static_assert(sizeof(WarpStage<4>) == fit_warp_stage_bytes(4) && sizeof(WarpStag
               "kernel_abi.h staging size");
 
 template <int FIELD>
-__device__ __forceinline__ bool step_predict(const SmemTables& T, const TrackState& S, int sec_to, float X, float m0,
+__device__ __forceinline__ bool step_predict(const GeoRef& G, const SmemTables& T, const TrackState& S, int sec_to, float X, float m0,
                                              float m1, float pout[5], Jac& J) {
   PredTape tp;
-  return predict_residual<FIELD>(T, S.p, S.x, S.sec, S.my, S.mz, sec_to, X, m0, m1, pout, J, tp);
+  return predict_residual<FIELD>(G, T, S.p, S.x, S.sec, S.my, S.mz, sec_to, X, m0, m1, pout, J, tp);
 }
 
 __device__ __forceinline__ void write_ckpt(const FitArgs& a, int pass, int begin, int trk, int seg,
@@ -627,13 +652,14 @@ __device__ __forceinline__ void write_ckpt(const FitArgs& a, int pass, int begin
 // PHYS: bit 0 the material layers, bit 1 the field map (compile-time variants,
 // so that the plain fit carries neither).
 template <int RPS, int WARPS, int MINB, bool RECORD, bool FRAMES, int PHYS>
-__global__ void __launch_bounds__(WARPS * 32, MINB) fit_kernel(FitArgs a) {
+__global__ void __launch_bounds__(WARPS * 32, MINB) fit_kernel(const __grid_constant__ FitArgs a) {
+  const GeoRef& G = TPCFIT_GEO(a);
   constexpr bool MAT = (PHYS & 1) != 0;
   constexpr int FIELD = (PHYS & 2) ? 1 : 0;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   BlockSmem& B = *reinterpret_cast<BlockSmem*>(smem_raw);
   WarpStage<RPS>* stages = reinterpret_cast<WarpStage<RPS>*>(smem_raw + sizeof(BlockSmem));
-  load_tables(B.T);
+  load_tables(G, B.T);
   for (int i = threadIdx.x; i < kAlignFloats; i += blockDim.x) B.align[i] = __ldg(a.align + i);
   __syncthreads();
   const SmemTables& T = B.T;
@@ -693,7 +719,7 @@ __global__ void __launch_bounds__(WARPS * 32, MINB) fit_kernel(FitArgs a) {
     if (status == 0) {
 #pragma unroll
       for (int c = 0; c < 5; ++c) S.p[c] = __ldg(a.seeds + (int64_t)c * a.n_tracks + trk);
-      if (!(fabsf(S.p[2]) < c_geo.max_snp)) status = 2;
+      if (!(fabsf(S.p[2]) < G.max_snp)) status = 2;
     }
 
     // ---- two passes: outward (dir +1 from hit 0) and inward (dir -1 from `last`)
@@ -704,7 +730,7 @@ __global__ void __launch_bounds__(WARPS * 32, MINB) fit_kernel(FitArgs a) {
       const int my_count = (status == 0) ? (pass == 0 ? n : last + 1) : 0;
       bool go = status == 0;
       if (go) {
-        reset_factor(S.L);
+        reset_factor(G, S.L);
         S.chi2 = 0.0f;
         S.used = 0;
       }
@@ -734,7 +760,7 @@ __global__ void __launch_bounds__(WARPS * 32, MINB) fit_kernel(FitArgs a) {
           const int rsv = (int)((st.rs[buf][lane][k] >> shift) & 0xffffu);
           const int row = rsv >> 6;
           const int sec = rsv & 63;
-          if (row >= c_geo.n_rows || sec >= kNSectors) {
+          if (row >= G.n_rows || sec >= kNSectors) {
             status = 3;
             go = false;
             record_error(a.err, kErrRowSector, trk);
@@ -762,14 +788,14 @@ __global__ void __launch_bounds__(WARPS * 32, MINB) fit_kernel(FitArgs a) {
             Jac J;
             if (MAT && pass == 1) {  // the layer of the row left, undone against the flight
               MatNoise N;
-              if (!material_step(S.p, -1, N)) {
+              if (!material_step(G, S.p, -1, N)) {
                 go = false;
                 status = 2;
                 continue;
               }
               material_factor(S.L, N);
             }
-            if (!step_predict<FIELD>(T, S, sec18, T.row_x[row], m0, m1, pn, J)) {
+            if (!step_predict<FIELD>(G, T, S, sec18, T.row_x[row], m0, m1, pn, J)) {
               go = false;
               if (pass == 1) status = 2;  // the inward pass must reach the first cluster
               continue;
@@ -777,7 +803,7 @@ __global__ void __launch_bounds__(WARPS * 32, MINB) fit_kernel(FitArgs a) {
             MatNoise N;
             // the layer of the row arrived at (a particle that stops there ends
             // the outward pass with the state before the step)
-            if (MAT && pass == 0 && !material_step(pn, 1, N)) {
+            if (MAT && pass == 0 && !material_step(G, pn, 1, N)) {
               go = false;
               continue;
             }
@@ -790,8 +816,8 @@ __global__ void __launch_bounds__(WARPS * 32, MINB) fit_kernel(FitArgs a) {
             transport(S.L, J);
             if (MAT && pass == 0) material_factor(S.L, N);
           }
-          scalar_update<0>(S.p, S.L, S.chi2, 0.0f);
-          scalar_update<1>(S.p, S.L, S.chi2, 0.0f);
+          scalar_update<0>(G, S.p, S.L, S.chi2, 0.0f);
+          scalar_update<1>(G, S.p, S.L, S.chi2, 0.0f);
           S.used += 1;
           if (pass == 0) last = i;
         }
@@ -885,10 +911,6 @@ inline cudaError_t launch(const FitArgs& a, int lanes_per_track, int rps, int wa
   if (lanes_per_track != 1) return cudaErrorInvalidValue;
   if (a.frame_base) return a.ck ? launch_rec<true, true>(a, rps, warps, s) : launch_rec<false, true>(a, rps, warps, s);
   return a.ck ? launch_rec<true, false>(a, rps, warps, s) : launch_rec<false, false>(a, rps, warps, s);
-}
-
-cudaError_t upload(const GeoConst& g, cudaStream_t s) {
-  return cudaMemcpyToSymbolAsync(c_geo, &g, sizeof(GeoConst), 0, cudaMemcpyHostToDevice, s);
 }
 
 #endif  // !__CUDACC_RTC__

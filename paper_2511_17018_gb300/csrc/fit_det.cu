@@ -9,7 +9,6 @@
 #include "smooth_core.cuh"
 
 namespace tpcfit {
-static ConstRegistration reg_det("fit_det", &det::upload);
 cudaError_t launch_fit_det(const FitArgs& a, int lanes_per_track, int rows_per_stage, int warps, cudaStream_t s) {
   return det::launch(a, lanes_per_track, rows_per_stage, warps, s);
 }

@@ -1,6 +1,5 @@
 // Fast FP32 fit module: compiled with FMA contraction, approximate division and
-// square root, flush-to-zero.  Its __constant__ geometry is registered with the
-// host-side constant registry (Sec. 4.1).
+// square root, flush-to-zero.
 #define TPCFIT_DET 0
 #define TPCFIT_NS fast
 #include "fit_core.cuh"
@@ -8,7 +7,6 @@
 #include "smooth_core.cuh"
 
 namespace tpcfit {
-static ConstRegistration reg_fast("fit_fast", &fast::upload);
 cudaError_t launch_fit_fast(const FitArgs& a, int lanes_per_track, int rows_per_stage, int warps, cudaStream_t s) {
   return fast::launch(a, lanes_per_track, rows_per_stage, warps, s);
 }

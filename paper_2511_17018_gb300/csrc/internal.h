@@ -11,16 +11,6 @@
 
 namespace tpcfit {
 
-// ---- constant-memory registry (Sec. 4.1): every kernel module registers an
-// uploader for its own __constant__ copy; the host updates all of them.
-using ConstUploader = cudaError_t (*)(const GeoConst&, cudaStream_t);
-struct ConstRegistration {
-  ConstRegistration(const char* module, ConstUploader up);
-};
-cudaError_t upload_constants_all(const GeoConst& g, cudaStream_t s);
-void forget_resident_constants();
-int registered_constant_modules();
-
 // Geometry and field -> per-time-frame constants (host, FP64 rounded to FP32);
 // false for an invalid geometry.
 bool build_geo(const tpcfit_geometry* g, double bz, GeoConst& out);

@@ -31,13 +31,14 @@ constexpr int kCkptShift = 4;
 constexpr int kCkptEvery = 1 << kCkptShift;
 constexpr int kCkptFloats = 36;
 
-// Per-time-frame constants of the fit, uploaded to the __constant__ bank of
-// every kernel module (each compilation unit has its own copy, Sec. 4.1).
+// Per-time-frame constants of the fit (Sec. 4.1).  Every launch carries them
+// by value in its argument block, i.e. in the kernel-parameter constant bank
+// (3.4 KB of the 32 KB a launch may pass), so launches of different handles
+// and replays of captured graphs never share or overwrite them.
 struct GeoConst {
   float row_x[kMaxRows];      // local x of each pad-row plane (FP64 -> FP32)
   float rot_c[kNSide * kNSide];  // cos / sin of the rotation from sector a to b
   float rot_s[kNSide * kNSide];  //   (index a * 18 + b), FP64 -> FP32
-  double asin_a[30];          // Maclaurin coefficients of arcsin (FP64 island)
   float kappa;                // -0.00299792458 * Bz  [1/cm per (c/GeV)]
   float v_meas;               // cluster variance (0.1 cm)^2
   float sqrt_v;               // its square root (fast-mode Potter coefficients)
@@ -57,6 +58,7 @@ struct GeoConst {
 
 // Arguments of one fit launch.
 struct FitArgs {
+  GeoConst geo;                // the time frame's constants
   const float* y;
   const float* z;
   const uint16_t* rowsec;
@@ -88,6 +90,7 @@ struct FitArgs {
 
 // Arguments of one backward launch (same frame as the recorded fit).
 struct BwdArgs {
+  GeoConst geo;
   const float* y;
   const float* z;
   const uint16_t* rowsec;
@@ -111,6 +114,7 @@ struct BwdArgs {
 
 // Arguments of one smoother launch (same frame as the recorded fit).
 struct SmoothArgs {
+  GeoConst geo;
   const float* y;
   const float* z;
   const uint16_t* rowsec;

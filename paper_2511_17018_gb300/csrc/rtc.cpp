@@ -77,15 +77,10 @@ const NvrtcApi& nvrtc() {
   return api;
 }
 
-// Exact text of a float / double (C99 hexadecimal floating point).
+// Exact text of a float (C99 hexadecimal floating point).
 std::string hexf(float v) {
   char b[64];
   snprintf(b, sizeof b, "%af", (double)v);
-  return b;
-}
-std::string hexd(double v) {
-  char b[64];
-  snprintf(b, sizeof b, "%a", v);
   return b;
 }
 
@@ -212,7 +207,6 @@ std::string rtc_fit_source(const GeoConst& g, bool det) {
   s += "namespace tpcfit {\nnamespace rtc {\n";
   s += "struct GeoFold {\n";
   s += "  float row_x[kMaxRows];\n  float rot_c[kNSide * kNSide];\n  float rot_s[kNSide * kNSide];\n";
-  s += "  double asin_a[30];\n";
   s += "  static constexpr float kappa = " + hexf(g.kappa) + ";\n";
   s += "  static constexpr float v_meas = " + hexf(g.v_meas) + ";\n";
   s += "  static constexpr float sqrt_v = " + hexf(g.sqrt_v) + ";\n";
@@ -234,8 +228,6 @@ std::string rtc_fit_source(const GeoConst& g, bool det) {
   append_list(s, g.rot_c, kNSide * kNSide, hexf);
   s += ", ";
   append_list(s, g.rot_s, kNSide * kNSide, hexf);
-  s += ", ";
-  append_list(s, g.asin_a, 30, hexd);
   s += "};\n}  // namespace rtc\n}  // namespace tpcfit\n";
   s += "#include \"fit_core.cuh\"\n";
   return s;

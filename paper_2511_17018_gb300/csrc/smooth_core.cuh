@@ -37,7 +37,7 @@ namespace TPCFIT_NS {
 // (or C H^T) in FP32 instead squares the condition number of the factors and
 // loses the residual next to a diffuse end of the track (the second and the
 // second-last cluster).
-__device__ __forceinline__ void smooth_combine(const float p1[5], const float L1[5][5], const float p2[5],
+__device__ __forceinline__ void smooth_combine(const GeoRef& G, const float p1[5], const float L1[5][5], const float p2[5],
                                                const float L2[5][5], float r[2], float R[3], float& chi2) {
   float M[10][5];   // [A1; A2]
   float E[4][10];   // rows 0-1: [H L1, 0]; rows 2-3: [0, H L2]
@@ -114,7 +114,7 @@ __device__ __forceinline__ void smooth_combine(const float p1[5], const float L1
   // the state is relative to the measurement: r = m - H x_u = -(p1 + correction)
   r[0] = -(p1[0] + c0);
   r[1] = -(p1[1] + c1);
-  const float v = c_geo.v_meas;
+  const float v = G.v_meas;
   R[0] = v + h00;
   R[1] = 0.5f * (h01 + h10);
   R[2] = v + h11;
@@ -141,10 +141,11 @@ constexpr size_t smooth_smem_bytes() {
 }
 
 template <int WARPS, bool MAT>
-__global__ void __launch_bounds__(WARPS * 32, 1) smooth_kernel(SmoothArgs a) {
+__global__ void __launch_bounds__(WARPS * 32, 1) smooth_kernel(const __grid_constant__ SmoothArgs a) {
+  const GeoRef& G = a.geo;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   BwdSmem& B = *reinterpret_cast<BwdSmem*>(smem_raw);
-  load_tables(B.T);
+  load_tables(G, B.T);
   for (int i = threadIdx.x; i < kAlignFloats; i += blockDim.x) B.align[i] = __ldg(a.align + i);
   __syncthreads();
   const SmemTables& T = B.T;
@@ -204,7 +205,7 @@ __global__ void __launch_bounds__(WARPS * 32, 1) smooth_kernel(SmoothArgs a) {
         int row, sec;
         decode_hit(B.align, cur, m0, m1, row, sec);
         store_state(gs + kk * (kStateF4 * kWarp), S);
-        step_fwd<MAT, 2>(T, S, my, mz, j == 0, false, row, sec % kNSide, m0, m1);
+        step_fwd<MAT, 2>(G, T, S, my, mz, j == 0, false, row, sec % kNSide, m0, m1);
       }
       __threadfence_block();  // the states just stored are read back by this thread's copies below
       if (s > 0) fetch_ckpt(&W.ck[0][lane], ckp + (int64_t)(s - 1) * kCkptFloats);
@@ -241,10 +242,10 @@ __global__ void __launch_bounds__(WARPS * 32, 1) smooth_kernel(SmoothArgs a) {
           PredTape tp;
           if (MAT) {  // the layer of row c + 1, undone against the flight
             MatNoise N;
-            material_step(SI.p, -1, N);
+            material_step(G, SI.p, -1, N);
             material_factor(SI.L, N);
           }
-          predict_residual<2>(T, SI.p, SI.x, SI.sec, mpy, mpz, sec18, X, m0, m1, pi, J, tp);
+          predict_residual<2>(G, T, SI.p, SI.x, SI.sec, mpy, mpz, sec18, X, m0, m1, pi, J, tp);
           transport(SI.L, J);
         }
         // outward prediction at c
@@ -257,14 +258,14 @@ __global__ void __launch_bounds__(WARPS * 32, 1) smooth_kernel(SmoothArgs a) {
         } else {
           Jac J;
           PredTape tp;
-          predict_residual<2>(T, O.p, O.x, O.sec, omy, omz, sec18, X, m0, m1, po, J, tp);
+          predict_residual<2>(G, T, O.p, O.x, O.sec, omy, omz, sec18, X, m0, m1, po, J, tp);
           MatNoise N;
-          if (MAT) material_step(po, 1, N);  // the layer of row c
+          if (MAT) material_step(G, po, 1, N);  // the layer of row c
           transport(O.L, J);
           if (MAT) material_factor(O.L, N);
         }
         float r[2], R[3], c2;
-        smooth_combine(po, O.L, pi, SI.L, r, R, c2);
+        smooth_combine(G, po, O.L, pi, SI.L, r, R, c2);
         reinterpret_cast<float2*>(a.resid)[h] = make_float2(r[0], r[1]);
         a.rcov[(int64_t)h * 3] = R[0];
         a.rcov[(int64_t)h * 3 + 1] = R[1];
@@ -278,8 +279,8 @@ __global__ void __launch_bounds__(WARPS * 32, 1) smooth_kernel(SmoothArgs a) {
         omy = m0;
         omz = m1;
         float chi_unused = 0.0f;
-        scalar_update<0>(O.p, O.L, chi_unused, 0.0f);
-        scalar_update<1>(O.p, O.L, chi_unused, 0.0f);
+        scalar_update<0>(G, O.p, O.L, chi_unused, 0.0f);
+        scalar_update<1>(G, O.p, O.L, chi_unused, 0.0f);
       }
     }
   }

@@ -1,6 +1,7 @@
 // Host side of libtpcfit: the C ABI of include/tpcfit.h.  Validates arguments,
-// owns the handle's device scratch, builds the geometry tables and keeps every
-// kernel module's constant bank up to date (Sec. 4.1), and enqueues the kernels.
+// owns the handle's device scratch, builds the per-time-frame constants (Sec.
+// 4.1) that every launch carries in its argument block, and enqueues the
+// kernels.
 #include "tpcfit.h"
 
 #include <cuda_runtime.h>
@@ -25,37 +26,6 @@ bool fit_shape_supported(int lanes_per_track, int rows_per_stage, int warps) {
          (rows_per_stage == 8 && (warps == 8 || warps == 16)) || (rows_per_stage == 16 && warps == 8);
 }
 
-// ---------------------------------------------------------------- constant registry
-namespace {
-struct Registry {
-  std::mutex mu;
-  std::vector<std::pair<const char*, ConstUploader>> modules;
-  const void* last_owner = nullptr;  // handle whose constants are resident
-  int last_device = -1;
-};
-Registry& registry() {
-  static Registry r;
-  return r;
-}
-}  // namespace
-
-ConstRegistration::ConstRegistration(const char* module, ConstUploader up) {
-  Registry& r = registry();
-  std::lock_guard<std::mutex> lk(r.mu);
-  r.modules.emplace_back(module, up);
-}
-
-cudaError_t upload_constants_all(const GeoConst& g, cudaStream_t s) {
-  Registry& r = registry();
-  for (auto& m : r.modules) {
-    cudaError_t e = m.second(g, s);
-    if (e != cudaSuccess) return e;
-  }
-  return cudaSuccess;
-}
-
-int registered_constant_modules() { return (int)registry().modules.size(); }
-
 // Build the per-time-frame constants on the host in FP64, rounded to FP32.
 bool build_geo(const tpcfit_geometry* g, double bz, GeoConst& out) {
   if (!g || !g->row_x || g->n_sectors != kNSectors || g->n_rows < 1 || g->n_rows > kMaxRows) return false;
@@ -77,13 +47,6 @@ bool build_geo(const tpcfit_geometry* g, double bz, GeoConst& out) {
       out.rot_c[a * kNSide + b] = (float)std::cos(da);
       out.rot_s[a * kNSide + b] = (float)std::sin(da);
     }
-  // arcsin Maclaurin coefficients: a_n = a_{n-1} (2n-1)^2 / ((2n)(2n+1))
-  out.asin_a[0] = 1.0;
-  for (int n = 1; n < 30; ++n) {
-    const double num = (double)(2 * n - 1) * (double)(2 * n - 1);
-    const double den = (double)(2 * n) * (double)(2 * n + 1);
-    out.asin_a[n] = out.asin_a[n - 1] * num / den;
-  }
   out.kappa = (float)(-0.00299792458 * bz);
   out.v_meas = (float)0.01;
   out.sqrt_v = (float)0.1;
@@ -91,15 +54,6 @@ bool build_geo(const tpcfit_geometry* g, double bz, GeoConst& out) {
   out.max_snp = (float)0.999;
   out.n_rows = g->n_rows;
   return true;
-}
-
-// Forget which handle's constants are resident, so that the next handle call
-// uploads its own (used by callers that upload constants without a handle).
-void forget_resident_constants() {
-  Registry& r = registry();
-  std::lock_guard<std::mutex> lk(r.mu);
-  r.last_owner = nullptr;
-  r.last_device = -1;
 }
 
 }  // namespace tpcfit
@@ -174,18 +128,6 @@ tpcfit_status from_cuda(cudaError_t e) {
 }
 
 bool aligned(const void* p, size_t a) { return ((uintptr_t)p % a) == 0; }
-
-// Make the handle's constants resident in every module (shared per device).
-tpcfit_status make_resident(tpcfit_handle* h, cudaStream_t s) {
-  Registry& r = registry();
-  std::lock_guard<std::mutex> lk(r.mu);
-  if (r.last_owner == h && r.last_device == h->device) return TPCFIT_OK;
-  cudaError_t e = upload_constants_all(h->geo, s);
-  if (e != cudaSuccess) return from_cuda(e);
-  r.last_owner = h;
-  r.last_device = h->device;
-  return TPCFIT_OK;
-}
 
 template <class T>
 tpcfit_status grow(T*& ptr, int64_t& cap, int64_t need) {
@@ -273,11 +215,7 @@ tpcfit_status tpcfit_create(const tpcfit_geometry* geometry, double bz_tesla, tp
   if (e == cudaSuccess) e = cudaMalloc(&h->d_sort_scratch, sizeof(int32_t) * 512);
   if (e == cudaSuccess) e = cudaMemset(h->d_align, 0, sizeof(float) * kAlignFloats);
   if (e == cudaSuccess) e = cudaMemset(h->d_err, 0, sizeof(unsigned long long));
-  if (e == cudaSuccess) {
-    tpcfit_status st = make_resident(h, nullptr);
-    if (st == TPCFIT_OK) e = cudaDeviceSynchronize();
-    else e = cudaErrorUnknown;
-  }
+  if (e == cudaSuccess) e = cudaDeviceSynchronize();
   if (e != cudaSuccess) {
     tpcfit_destroy(h);
     return from_cuda(e);
@@ -309,11 +247,6 @@ void tpcfit_destroy(tpcfit_handle* h) {
   if (h->d_seg) cudaFree(h->d_seg);
   if (h->d_keys) cudaFree(h->d_keys);
   if (h->d_frame_scratch) cudaFree(h->d_frame_scratch);
-  {
-    Registry& r = registry();
-    std::lock_guard<std::mutex> lk(r.mu);
-    if (r.last_owner == h) r.last_owner = nullptr;
-  }
   delete h;
 }
 
@@ -361,9 +294,9 @@ tpcfit_status tpcfit_fit(tpcfit_handle* h, const tpcfit_hits* hits, const int32_
     return TPCFIT_EINVAL;
   if (hits->n_hits > INT32_MAX) return TPCFIT_EINVAL;  // int32 track offsets
   cudaStream_t s = (cudaStream_t)stream;
-  tpcfit_status st = make_resident(h, s);
-  if (st != TPCFIT_OK) return st;
+  tpcfit_status st = TPCFIT_OK;
   FitArgs a{};
+  a.geo = h->geo;
   a.y = hits->y;
   a.z = hits->z;
   a.rowsec = hits->rowsec;
@@ -430,12 +363,11 @@ tpcfit_status tpcfit_fit_frames(tpcfit_handle* h, const tpcfit_hits* hits, const
   // ready flags are set by work on other streams; on the legacy default stream
   // that work would wait for the fit itself
   if (frame_ready && (s == nullptr || s == cudaStreamLegacy)) return TPCFIT_EINVAL;
-  tpcfit_status st = make_resident(h, s);
-  if (st != TPCFIT_OK) return st;
-  st = ensure_perm(h, n_tracks);
+  tpcfit_status st = ensure_perm(h, n_tracks);
   if (st == TPCFIT_OK) st = grow(h->d_frame_scratch, h->frame_scratch_cap, frame_order_scratch_ints(n_frames));
   if (st != TPCFIT_OK) return st;
   FitArgs a{};
+  a.geo = h->geo;
   a.y = hits->y;
   a.z = hits->z;
   a.rowsec = hits->rowsec;
@@ -488,7 +420,6 @@ tpcfit_status tpcfit_set_material(tpcfit_handle* h, double x0_cm, double dedx_ge
     h->geo.d_row = (float)row_cm;
   }
   h->rec_valid = false;
-  forget_resident_constants();  // the handle's constants changed: upload them again
   return TPCFIT_OK;
 }
 
@@ -498,7 +429,6 @@ tpcfit_status tpcfit_set_field_map(tpcfit_handle* h, double c_r, double c_z) {
   h->geo.f_r = (float)(c_r / (250.0 * 250.0));
   h->geo.f_z = (float)(c_z / (250.0 * 250.0));
   h->rec_valid = false;
-  forget_resident_constants();
   return TPCFIT_OK;
 }
 
@@ -543,9 +473,9 @@ tpcfit_status tpcfit_fit_backward(tpcfit_handle* h, const tpcfit_hits* hits, con
   if (!h->rec_valid || h->rec_tracks != n_tracks || h->rec_hits != hits->n_hits ||
       h->rec_det != h->deterministic)
     return TPCFIT_ESTATE;
-  tpcfit_status st = make_resident(h, s);
-  if (st != TPCFIT_OK) return st;
+  tpcfit_status st = TPCFIT_OK;
   BwdArgs b{};
+  b.geo = h->geo;
   b.y = hits->y;
   b.z = hits->z;
   b.rowsec = hits->rowsec;
@@ -618,9 +548,9 @@ tpcfit_status tpcfit_smooth(tpcfit_handle* h, const tpcfit_hits* hits, const int
       h->rec_det != h->deterministic)
     return TPCFIT_ESTATE;
   cudaStream_t s = (cudaStream_t)stream;
-  tpcfit_status st = make_resident(h, s);
-  if (st != TPCFIT_OK) return st;
+  tpcfit_status st = TPCFIT_OK;
   SmoothArgs a{};
+  a.geo = h->geo;
   a.y = hits->y;
   a.z = hits->z;
   a.rowsec = hits->rowsec;

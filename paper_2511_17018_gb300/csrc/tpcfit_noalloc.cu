@@ -1,12 +1,13 @@
 // A fit entry point that allocates no device memory.
 //
 // Who needs it: code that runs where cudaMalloc / cudaFree must not be called,
-// for instance inside a CUDA stream capture that someone else owns, in a
-// real-time loop that forbids allocator calls and their implicit device
-// synchronisation, or in a host framework that hands out only the buffers it
-// manages itself.  tpcfit_fit needs a handle, and creating one allocates (the
-// alignment table, the error word, the length permutation); this entry point
-// needs neither.
+// for instance a real-time loop that forbids allocator calls and the device
+// synchronisation they can imply, or a host framework that hands out only the
+// buffers it manages itself.  tpcfit_fit needs a handle, and creating one
+// allocates (the alignment table, the error word, the length permutation);
+// this entry point needs neither.  The time frame's constants travel in the
+// launch's own argument block, as for every fit launch, so nothing is copied
+// to the device for them.
 //
 // Its scratch (length histogram, work counter, error word, a zero alignment
 // table and the length permutation) lives in one file-scope static device
@@ -87,14 +88,11 @@ extern "C" tpcfit_status tpcfit_fit_noalloc(const tpcfit_geometry* geometry, dou
   cudaError_t e = scratch_address(&scratch);
   if (e != cudaSuccess) return TPCFIT_ECUDA;
   cudaStream_t s = (cudaStream_t)stream;
-  // constants of this call into every kernel module; handle-based calls re-upload theirs
-  forget_resident_constants();
-  e = upload_constants_all(geo, s);
-  if (e != cudaSuccess) return TPCFIT_ECUDA;
   unsigned long long* err = reinterpret_cast<unsigned long long*>(scratch + kOffErr);
   e = cudaMemsetAsync(err, 0, sizeof(unsigned long long), s);
   if (e != cudaSuccess) return TPCFIT_ECUDA;
   FitArgs a{};
+  a.geo = geo;
   a.y = hits->y;
   a.z = hits->z;
   a.rowsec = hits->rowsec;

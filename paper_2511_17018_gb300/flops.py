@@ -72,3 +72,27 @@ def smooth_flops(lengths) -> float:
     n = np.asarray(lengths, dtype=np.int64)
     n = n[n >= 1]
     return float(np.sum((n - 1) * STEP + FIRST + n * SMOOTH_COMBINE))
+
+
+# The method's count (the textbook covariance-form filter, estimated per step
+# and pass: propagation ~20, Jacobian ~20, transport ~100, update ~120 -> 240;
+# both passes -> 480 per cluster), and the adjoint's reverse sweep at 2.5 times
+# the forward (fit + adjoint = 3.5 x fit).  It credits none of the work the
+# square-root form and the residual coordinates add, so fractions taken on it
+# are the conservative ones.
+METHOD_STEP = 240
+METHOD_REVERSE_FACTOR = 2.5
+
+
+def method_fit_flops(lengths) -> float:
+    """The method's count of the fit: 480 flops per cluster (two passes of 240)."""
+    n = np.asarray(lengths, dtype=np.int64)
+    return float(2 * METHOD_STEP * n[n >= 1].sum())
+
+
+def method_backward_flops(lengths) -> float:
+    return METHOD_REVERSE_FACTOR * method_fit_flops(lengths)
+
+
+def method_fit_adjoint_flops(lengths) -> float:
+    return (1.0 + METHOD_REVERSE_FACTOR) * method_fit_flops(lengths)

@@ -72,6 +72,7 @@ def load():
         "tpcfit_rtc_available": (C.c_int, []),
         "tpcfit_rtc_compile_count": (C.c_longlong, []),
         "tpcfit_rtc_log": (C.c_char_p, []),
+        "tpcfit_fp32_peak": (C.c_int, [C.c_int, i64, vp, C.POINTER(C.c_double), C.POINTER(C.c_double)]),
         "tpcfit_status_string": (C.c_char_p, [C.c_int]),
         "tpcfit_version": (i32, []),
     }
@@ -116,6 +117,14 @@ def _check_sizes(n, y, z, rowsec, seeds=None, params=None, cov=None, chi2=None, 
 
 def status_string(st: int) -> str:
     return load().tpcfit_status_string(int(st)).decode()
+
+
+def tpcfit_fp32_peak(mode: int = 0, iterations: int = 200000, stream=None):
+    """(FP32 flops executed, launch ms) of the FMA-chain microbenchmark."""
+    fl, ms = C.c_double(), C.c_double()
+    _check(load().tpcfit_fp32_peak(int(mode), int(iterations), _stream(stream), C.byref(fl), C.byref(ms)),
+           "tpcfit_fp32_peak")
+    return fl.value, ms.value
 
 
 def tpcfit_version() -> int:

@@ -1,10 +1,19 @@
-"""The hand-written adjoint against the oracle's FP64 forward-mode gradient and
-FP64 central finite differences (run on a GB300 with -m gpu).
+"""The hand-written adjoint against the oracle's forward-mode gradients and
+FP64 central finite differences (run on a GB300 with -m gpu).  Gradients are
+compared element by element: |g - g_ref| <= tol * max(|g_ref|, 1e-3 max|g_ref|)
+(tolerance.gradient_errors).
 
-The FP32 gradient cannot be closer to the FP64 one than the FP32 forward is to
-the FP64 forward: cluster positions up to ~40 cm carry ~4e-6 cm of rounding
-against residuals of ~0.1 cm, i.e. ~5e-5 of the gradient per step.  The bounds
-below (5e-4 in relative norm) are a few times that floor."""
+Two references.  (1) The gradient of the strict-FP32 fit itself (oracle
+precision 'f32': the same FP32 operation sequence as the deterministic kernels,
+its derivative carried exactly in FP64).  The deterministic adjoint runs on
+that very trajectory, so the two differ only by the FP32 rounding of the
+reverse sweep's own arithmetic: DET_ELEM = 1e-5 per element, the gradient
+accuracy asked of the method.  (2) The FP64 gradient.  No FP32 gradient can be
+closer to it than the FP32 forward is to the FP64 forward -- cluster positions
+carry ~4e-6 cm of rounding against ~0.1 cm residuals, and that shifts the
+FP32 trajectory's own exact gradient by ~5e-5 in norm and up to ~1e-2 in the
+worst elements (measured on the CPU for the strict-FP32 sequence) -- so
+FP32_ELEM bounds that floor, and the norm stays at 5e-4."""
 import numpy as np
 import pytest
 
@@ -12,15 +21,21 @@ torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
 import oracle  # noqa: E402
-from paper_2511_17018_gb300 import synth  # noqa: E402
+from paper_2511_17018_gb300 import synth, tolerance  # noqa: E402
 from paper_2511_17018_gb300 import tpcfit as tf  # noqa: E402
 from paper_2511_17018_gb300.autograd import fit_chi2  # noqa: E402
 
 REL = 5e-4
+DET_ELEM = 1e-5
+FP32_ELEM = 3e-2
 
 
 def rel(a, b):
     return float(np.linalg.norm(np.asarray(a, np.float64) - b) / np.linalg.norm(b))
+
+
+def _elem(got, ref):
+    return tolerance.gradient_errors(got, ref)
 
 
 @pytest.fixture(scope="module")
@@ -29,6 +44,7 @@ def case():
     fr = synth.generate(3000, 3, drop_p=0.05, cap_lengths=True, d_true=d_true)
     w = np.random.default_rng(5).uniform(0.5, 2.0, fr.n_tracks).astype(np.float32)
     ref = oracle.grad(fr, weights=w.astype(np.float64), align=d_true)
+    ref["f32"] = oracle.grad(fr, weights=w.astype(np.float64), align=d_true, precision="f32")
     return fr, d_true, w, ref
 
 
@@ -51,13 +67,27 @@ def _gpu_grad(fr, d_true, w, det, rps=4, warps=24, srt=True, bwd=12):
 
 @pytest.mark.parametrize("det", [False, True])
 def test_adjoint_matches_forward_mode_oracle(case, det):
+    # against the FP64 gradient: per element within the FP32 forward's floor
     fr, d_true, w, ref = case
     gm, ga, gs, ndf = _gpu_grad(fr, d_true, w, det)
     assert np.array_equal(ndf, ref["ndf"])
-    assert rel(gm, ref["grad_meas"]) < REL
-    assert rel(ga, oracle.align_grad_from_meas(fr, ref["grad_meas"])) < REL
-    assert rel(gs, ref["grad_seed"]) < 10 * REL   # the seed gradient is ~1e-5 of the cluster gradient
-    assert np.abs(gs - ref["grad_seed"]).max() < 1e-5 * np.abs(ref["grad_meas"]).max()
+    ga_ref = oracle.align_grad_from_meas(fr, ref["grad_meas"])
+    for name, got, want in (("meas", gm, ref["grad_meas"]), ("align", ga, ga_ref), ("seeds", gs, ref["grad_seed"])):
+        e = _elem(got, want)
+        assert e["max"] < FP32_ELEM and e["norm"] < (10 * REL if name == "seeds" else REL), (name, e)
+
+
+def test_deterministic_adjoint_matches_the_fp32_sequence_gradient(case):
+    # the deterministic adjoint runs on the strict-FP32 trajectory: against that
+    # trajectory's exact gradient it must agree per element to 1e-5
+    fr, d_true, w, ref = case
+    r32 = ref["f32"]
+    gm, ga, gs, ndf = _gpu_grad(fr, d_true, w, True)
+    assert np.array_equal(ndf, r32["ndf"])
+    ga_ref = oracle.align_grad_from_meas(fr, r32["grad_meas"])
+    for name, got, want in (("meas", gm, r32["grad_meas"]), ("align", ga, ga_ref), ("seeds", gs, r32["grad_seed"])):
+        e = _elem(got, want)
+        assert e["max"] <= DET_ELEM, (name, e)
 
 
 def test_deterministic_adjoint_is_bitwise_reproducible(case):
@@ -98,7 +128,10 @@ def test_alignment_gradient_matches_fp64_finite_differences():
             lm = np.nansum(oracle.fit(fr, "f64", align=dm.reshape(36, 152, 2))["chi2"])
             fd.append((lp - lm) / (2 * h))
             got.append(ga.reshape(-1, 2)[k, c])
-    assert rel(got, np.array(fd)) < REL
+    fd = np.array(fd)
+    assert rel(got, fd) < REL
+    # per component against the largest: the FP32 forward's floor (~5e-5 of each element)
+    assert np.abs(np.array(got) - fd).max() <= 2e-4 * np.abs(fd).max()
 
 
 def test_autograd_function_and_masking(case):
@@ -112,8 +145,10 @@ def test_autograd_function_and_masking(case):
         ok = ndf > 0
         loss = (chi2[ok] * torch.from_numpy(w).cuda()[ok]).sum()
         loss.backward()
-        assert rel(align.grad.cpu().numpy(), oracle.align_grad_from_meas(fr, ref["grad_meas"])) < REL
-        assert rel(seeds.grad.cpu().numpy(), ref["grad_seed"]) < 10 * REL
+        ea = _elem(align.grad.cpu().numpy(), oracle.align_grad_from_meas(fr, ref["grad_meas"]))
+        es = _elem(seeds.grad.cpu().numpy(), ref["grad_seed"])
+        assert ea["max"] < FP32_ELEM and ea["norm"] < REL, ea
+        assert es["max"] < FP32_ELEM and es["norm"] < 10 * REL, es
     finally:
         f.close()
 

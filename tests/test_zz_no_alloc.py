@@ -75,3 +75,24 @@ def test_noalloc_rejects_sizes_beyond_its_scratch():
                               torch.empty(tf.NOALLOC_MAX_TRACKS + 1, device="cuda"),
                               torch.empty(tf.NOALLOC_MAX_TRACKS + 1, dtype=torch.int32, device="cuda"))
     assert e.value.status == tf.EINVAL
+
+
+def test_noalloc_bad_track_is_flagged_and_the_next_call_is_clean():
+    # one track with a row beyond the geometry: that track alone gets ndf = -2
+    # and NaNs; a clean call afterwards equals tpcfit_fit bit for bit, so the
+    # shared array's error word and work counter carry nothing over
+    fr = synth.generate(3000, 44, drop_p=0.05, cap_lengths=True)
+    bad = fr.subset(np.arange(fr.n_tracks))
+    bad.rowsec = bad.rowsec.copy()
+    t = 1234
+    bad.rowsec[bad.offsets[t] + 2] = np.uint16((160 << 6) | (int(bad.rowsec[bad.offsets[t] + 2]) & 63))
+    got = _run_noalloc(bad, True)
+    ref = _run_handle(fr, True)
+    assert got["ndf"][t] == -2
+    assert np.all(np.isnan(got["params"][:, t])) and np.isnan(got["chi2"][t])
+    keep = np.arange(fr.n_tracks) != t
+    for k in ("params", "cov", "chi2", "ndf"):
+        a = np.ascontiguousarray(got[k][..., keep]).view(np.int32)
+        b = np.ascontiguousarray(ref[k][..., keep]).view(np.int32)
+        assert np.array_equal(a, b), k
+    assert _same_bits(_run_noalloc(fr, True), ref)
