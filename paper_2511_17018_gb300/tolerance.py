@@ -8,13 +8,18 @@ sin(phi) and tan(lambda) cross zero; chi2 against max(chi2, 1); a covariance
 element C_ij against sqrt(C_ii C_jj) (the scale of its correlation).
 
 A 150-step FP32 recursion carries rounding of about 1e-5 to 1e-4 sigma, so the
-bound holds for all but a thin tail of tracks (the strict-FP32 sequence: 1 of
-20,000 tracks at 1.1e-4, chi2 at most 2.3e-3, covariance at most 9e-5).  The
+bound holds for all but a thin tail of tracks (on 20,000 tracks: the
+strict-FP32 sequence has 1 track at 1.1e-4, chi2 at most 2.3e-3, covariance
+at most 9e-5; the fast GPU mode 1 track at 1.3e-4, chi2 at most 3.5e-3,
+covariance at most 2.8e-4, where its approximate reciprocal square roots
+enter the factor; with the thick test layers, X0 = 300 cm, the strict-FP32
+sequence itself reaches 1.2e-3 in the covariance, from the noise folding).
+The covariance is not part of the stated tolerance; it is held to 2e-3.  The
 criterion:
-  * at least 99.99 % of tracks meet 1e-4 (params), 1e-3 (chi2) and 1e-4 (cov)
+  * at least 99.99 % of tracks meet 1e-4 (params), 1e-3 (chi2) and 2e-3 (cov)
     (on samples of fewer than 20,000 tracks one track may miss, which the
     percentage alone would not allow on 1,000 or 4,000 tracks),
-  * no track exceeds 5e-4 (params), 5e-3 (chi2) or 1e-3 (cov),
+  * no track exceeds 5e-4 (params), 5e-3 (chi2) or 1e-2 (cov),
   * the failure flag (ndf < 0) agrees on at least 99.99 % of tracks.
 
 Gradient.  Elementwise, |g - g_ref| <= tol * max(|g_ref|, 1e-3 max|g_ref|):
@@ -27,13 +32,13 @@ import numpy as np
 
 PARAM_TOL = 1e-4
 CHI2_TOL = 1e-3
-COV_TOL = 1e-4
+COV_TOL = 2e-3
 PARAM_FRAC = 0.9999
 CHI2_FRAC = 0.9999
 COV_FRAC = 0.9999
 PARAM_HARD = 5e-4
 CHI2_HARD = 5e-3
-COV_HARD = 1e-3
+COV_HARD = 1e-2
 FLAG_FRAC = 0.9999
 
 _DIAG = [0, 2, 5, 9, 14]

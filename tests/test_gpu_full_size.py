@@ -60,6 +60,13 @@ def test_full_size_adjoint_sampled(full, det):
     hit_ok = np.repeat(ok, np.diff(sub.offsets))
     assert _rel(gm[h][hit_ok], ref["grad_meas"][hit_ok]) < 5e-4
     assert _rel(gs[:, sample][:, ok], ref["grad_seed"][:, ok]) < 5e-3
+    if det:
+        # the deterministic adjoint against the exact gradient of the strict-FP32
+        # sequence on the sampled tracks, element by element
+        r32 = oracle.grad(sub, weights=w[sample].astype(np.float64), precision="f32")
+        assert np.array_equal(ndf[sample], r32["ndf"])
+        e = tolerance.gradient_errors(gm[h], r32["grad_meas"])
+        assert e["norm"] <= 1e-5 and e["q999"] <= 2e-5 and e["max"] <= 1e-4, e
     # 32M cluster gradients summed into 10,944 keys: FP32 sums (atomics in fast
     # mode, fixed-order sums in deterministic mode) against FP64 ones
     assert _rel(ga, oracle.align_grad_from_meas(fr, gm)) < 1e-4
