@@ -362,6 +362,7 @@ def run_batched_frames(args, tf, torch, synth, flops, peak_tf):
                      "hits_per_s": batch.n_hits / (ms / 1e3), "frac_method": tfm / peak_tf, "frac_impl": tfl / peak_tf,
                      "config": {k: best[k] for k in ("lanes_per_track", "rows_per_stage", "warps_per_block",
                                                      "sort_by_length")},
+                     "sweep_by_lanes_ms": {k: round(v["ms"], 3) for k, v in best["by_lanes"].items()},
                      "fitted_fraction": float((g.out["ndf"] > 0).float().mean().item())}
         del g
         f.close()

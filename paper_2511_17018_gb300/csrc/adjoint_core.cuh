@@ -1016,7 +1016,7 @@ __global__ void __launch_bounds__(WARPS * 32, 1) backward_kernel(const __grid_co
             if (kk + 1 < cnt) nx = load_hit(a, h0 + hd * (i + 1));
             decode_hit(B.align, cur, m0, m1, row, sec);
             store_state(gs + kk * (kStateF4 * kWarp), S);
-            step_fwd<MAT, FIELD>(G, T, S, my, mz, i == 0, pass == 0, row, sec % kNSide, m0, m1);
+            step_fwd<MAT, FIELD>(G, T, S, my, mz, i == 0, pass == 0, row, side_sector(sec), m0, m1);
           }
           // the states just stored are read back by this thread's copies below
           __threadfence_block();
@@ -1054,10 +1054,10 @@ __global__ void __launch_bounds__(WARPS * 32, 1) backward_kernel(const __grid_co
             if (addg && i > 0) gnx = gmr[h - hd];
             float b_mc[2], b_mp[2];
             if (MAT)
-              step_rev_mat<FIELD>(G, T, &W.st[kk & 1][0][lane], mpy, mpz, i == 0, pass == 0, row, sec % kNSide, m0, m1,
+              step_rev_mat<FIELD>(G, T, &W.st[kk & 1][0][lane], mpy, mpz, i == 0, pass == 0, row, side_sector(sec), m0, m1,
                                   b_p, b_L, b_chi, b_mc, b_mp);
             else
-              step_rev<FIELD>(G, T, &W.st[kk & 1][0][lane], mpy, mpz, i == 0, pass == 0, row, sec % kNSide, m0, m1,
+              step_rev<FIELD>(G, T, &W.st[kk & 1][0][lane], mpy, mpz, i == 0, pass == 0, row, side_sector(sec), m0, m1,
                               b_p, b_L, b_chi, b_mc, b_mp);
             accumulate_meas_grad(a, pass, h, row, sec, b_mc[0] + pend0, b_mc[1] + pend1, gcur);
             pend0 = b_mp[0];

@@ -268,7 +268,11 @@ __device__ __forceinline__ bool predict_t(const GeoRef& G, const SmemTables& T, 
   sqrt_and_inv((1.0f - s1) * (1.0f + s1), c1, ic1);
   sqrt_and_inv((1.0f - s2) * (1.0f + s2), c2, ic2);
   const float den = c1 + c2;
+#if TPCFIT_DET
   const float Tm = (s1 + s2) / den;
+#else
+  const float Tm = __fdividef(s1 + s2, den);
+#endif
   const float w = c1 + s1 * Tm;
   const float sig = kdx * w;
   const float A = asinc_f(sig);
@@ -301,7 +305,11 @@ __device__ __forceinline__ bool predict_t(const GeoRef& G, const SmemTables& T, 
     Lk = (dx * dx) * (a1 + kdx * a2);
 #endif
   } else {
+#if TPCFIT_DET
     Lk = (dx * ic2 - dl) / k;
+#else
+    Lk = __fdividef(dx * ic2 - dl, k);
+#endif
   }
   J.zq = (t * kappa) * Lk;
   J.sq = dx * kappa;
@@ -418,12 +426,17 @@ __device__ __forceinline__ void scalar_update(const GeoRef& G, float p[5], float
     for (int c = 0; c < 5; ++c) L[i][c] = L[i][c] - gk * a[c];
   }
 #else
-  // fast: the same algebra with alpha folded into the fused multiply-adds
+  // fast: the same algebra with alpha folded into the fused multiply-adds;
+  // row H of L a is a . a = s2 - v
   const float ar = alpha * r;
   const float ga = gamma * alpha;
   float la[5];
 #pragma unroll
   for (int i = 0; i < 5; ++i) {
+    if (i == H) {
+      la[i] = s2 - v;
+      continue;
+    }
     float acc = L[i][0] * a[0];
 #pragma unroll
     for (int c = 1; c < 5; ++c) acc = acc + L[i][c] * a[c];
@@ -544,6 +557,9 @@ __device__ __forceinline__ void reset_factor(const GeoRef& G, float L[5][5]) {
 #pragma unroll
     for (int c = 0; c < 5; ++c) L[i][c] = (i == c) ? G.l0 : 0.0f;
 }
+
+// Sector mod 18 (its azimuth) of a validated sector number (< 36).
+__device__ __forceinline__ int side_sector(int sec) { return sec >= kNSide ? sec - kNSide : sec; }
 
 __device__ __forceinline__ void record_error(unsigned long long* err, unsigned long long code, int64_t track) {
   const unsigned long long v = (code << 56) | ((unsigned long long)track & 0x00FFFFFFFFFFFFFFull);
@@ -770,7 +786,7 @@ __global__ void __launch_bounds__(WARPS * 32, MINB) fit_kernel(const __grid_cons
                                   : reinterpret_cast<const float2*>(B.align)[sec * kMaxRows + row];
           const float m0 = st.y[buf][lane][k] - d.x;
           const float m1 = st.z[buf][lane][k] - d.y;
-          const int sec18 = sec % kNSide;
+          const int sec18 = side_sector(sec);
           if (RECORD && (i & (kCkptEvery - 1)) == 0) write_ckpt(a, pass, begin, trk, i >> kCkptShift, S);
           if (i == 0) {
             // first cluster of the pass: the state sits on its row already; the

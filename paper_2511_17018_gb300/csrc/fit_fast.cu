@@ -3,12 +3,15 @@
 #define TPCFIT_DET 0
 #define TPCFIT_NS fast
 #include "fit_core.cuh"
+#include "fit_lanes.cuh"
 #include "adjoint_core.cuh"
 #include "smooth_core.cuh"
 
 namespace tpcfit {
 cudaError_t launch_fit_fast(const FitArgs& a, int lanes_per_track, int rows_per_stage, int warps, cudaStream_t s) {
-  return fast::launch(a, lanes_per_track, rows_per_stage, warps, s);
+  // several lanes per track: uniform field without material layers only
+  if (lanes_per_track != 1 && !a.mat && !a.field) return fast::launch_lanes(a, lanes_per_track, s);
+  return fast::launch(a, 1, rows_per_stage, warps, s);
 }
 cudaError_t launch_backward_fast(const BwdArgs& a, int warps, cudaStream_t s) {
   return fast::launch_backward(a, warps, s);

@@ -205,7 +205,7 @@ __global__ void __launch_bounds__(WARPS * 32, 1) smooth_kernel(const __grid_cons
         int row, sec;
         decode_hit(B.align, cur, m0, m1, row, sec);
         store_state(gs + kk * (kStateF4 * kWarp), S);
-        step_fwd<MAT, 2>(G, T, S, my, mz, j == 0, false, row, sec % kNSide, m0, m1);
+        step_fwd<MAT, 2>(G, T, S, my, mz, j == 0, false, row, side_sector(sec), m0, m1);
       }
       __threadfence_block();  // the states just stored are read back by this thread's copies below
       if (s > 0) fetch_ckpt(&W.ck[0][lane], ckp + (int64_t)(s - 1) * kCkptFloats);
@@ -225,7 +225,7 @@ __global__ void __launch_bounds__(WARPS * 32, 1) smooth_kernel(const __grid_cons
         float m0, m1;
         int row, sec;
         decode_hit(B.align, load_hit(a.y, a.z, a.rowsec, h), m0, m1, row, sec);
-        const int sec18 = sec % kNSide;
+        const int sec18 = side_sector(sec);
         const float X = T.row_x[row];
         // inward prediction at c
         StepState SI;

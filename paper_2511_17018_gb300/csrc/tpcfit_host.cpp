@@ -21,6 +21,9 @@ namespace tpcfit {
 bool backward_shape_supported(int warps) { return warps == 4 || warps == 8 || warps == 10 || warps == 12; }
 
 bool fit_shape_supported(int lanes_per_track, int rows_per_stage, int warps) {
+  if (lanes_per_track == 2 || lanes_per_track == 4 || lanes_per_track == 8 || lanes_per_track == 16 ||
+      lanes_per_track == 32)
+    return rows_per_stage == 4 && warps == 24;
   if (lanes_per_track != 1) return false;
   return (rows_per_stage == 4 && (warps == 8 || warps == 12 || warps == 24)) ||
          (rows_per_stage == 8 && (warps == 8 || warps == 16)) || (rows_per_stage == 16 && warps == 8);
@@ -175,7 +178,7 @@ namespace {
 // The fit launch of a handle: ahead-of-time kernels, or the kernel compiled
 // at run time for the handle's constants.
 tpcfit_status launch_fit(const tpcfit_handle* h, const FitArgs& a, cudaStream_t s) {
-  if (h->rtc)
+  if (h->rtc && h->lanes_per_track == 1)
     return rtc_launch_fit(h->geo, h->deterministic != 0, h->rows_per_stage, h->warps_per_block, a,
                           h->rtc_dir.empty() ? nullptr : h->rtc_dir.c_str(), s);
   const cudaError_t e = h->deterministic

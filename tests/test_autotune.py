@@ -16,7 +16,7 @@ def test_cache_roundtrip(tmp_path):
 def test_candidates_cover_the_documented_sweep():
     from paper_2511_17018_gb300 import autotune
     c = list(autotune.candidates())
-    assert {x[0] for x in c} == {1, 4, 8, 16, 32}      # tracks per warp 32, 8, 4, 2, 1
+    assert {x[0] for x in c} == {1, 2, 4, 8, 16, 32}   # tracks per warp 32, 16, 8, 4, 2, 1
     assert {x[1] for x in c} == {4, 8, 16}
     assert len(c) == len(set(c))
 

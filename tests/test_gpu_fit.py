@@ -210,3 +210,55 @@ def test_full_size_time_frame_sampled(fitter):
     gs = {k: (v[:, sample] if v.ndim == 2 else v[sample]) for k, v in got.items()}
     assert _bits_equal(gs, oracle.fit(sub, "f32")) is None
     assert fitter.status()[0] == tf.OK
+
+
+@pytest.mark.parametrize("lanes", [2, 4, 8, 16, 32])
+def test_lanes_per_track_variants(fitter, frames, lanes):
+    # 32 / lanes tracks per warp: the factor's columns split over a track's
+    # lanes, the column sums gathered in column order -- bit-identical to the
+    # strict-FP32 reference in deterministic mode, within tolerance in fast mode
+    fr = frames["drop20k"]
+    dev = tf.frame_to_device(fr)
+    try:
+        fitter.set_config(lanes, 4, 24, True)
+        fitter.set_mode(True)
+        got = _host(fitter.fit(dev))
+        assert _bits_equal(got, oracle.fit(fr, "f32")) is None
+        fitter.set_mode(False)
+        got = _host(fitter.fit(dev))
+        rep = tolerance.compare_to_fp64(got, oracle.fit(fr, "f64"))
+        assert rep["ok"], rep
+    finally:
+        fitter.set_config(1, 4, 24, True)
+
+
+def test_lanes_per_track_shapes_and_fallbacks(fitter):
+    # several lanes per track come in one shape; other shapes are refused
+    for bad in ((2, 8, 16), (4, 4, 12), (3, 4, 24), (64, 4, 24)):
+        with pytest.raises(tf.TpcfitError):
+            fitter.set_config(bad[0], bad[1], bad[2], True)
+    fitter.set_config(1, 4, 24, True)
+
+
+def test_lanes_recording_feeds_the_same_adjoint():
+    # a fit recorded with 8 lanes per track leaves the checkpoints the one-lane
+    # fit leaves: the deterministic adjoint is bit for bit the same
+    fr = synth.generate(3000, 9, drop_p=0.05, cap_lengths=True)
+    dev = tf.frame_to_device(fr)
+    g = torch.from_numpy(np.random.default_rng(2).uniform(0.5, 2, fr.n_tracks).astype(np.float32)).cuda()
+    res = []
+    for lanes in (1, 8, 2):
+        f = tf.Fitter(fr.geometry, fr.bz, deterministic=True)
+        try:
+            f.set_config(lanes, 4, 24, True)
+            f.set_record(True)
+            out = f.fit(dev)
+            gm = torch.empty((fr.n_hits, 2), device="cuda")
+            ga, gs = f.backward(dev, out, g, gm)
+            torch.cuda.synchronize()
+            res.append([x.cpu().numpy().view(np.int32).copy() for x in (gm, ga, gs, out["chi2"])])
+        finally:
+            f.close()
+    for other in res[1:]:
+        for a, b in zip(res[0], other):
+            assert np.array_equal(a, b)

@@ -155,3 +155,30 @@ def test_frames_from_pool_sampling():
             assert np.array_equal(np.ascontiguousarray(a).view(np.int32), np.ascontiguousarray(b).view(np.int32)), k
     finally:
         f.close()
+
+
+@pytest.mark.parametrize("lanes", [4, 16])
+def test_frames_with_several_lanes_per_track(frames, lanes):
+    # the batched launch with 32 / lanes tracks per warp: bit for bit the
+    # one-lane per-frame fits (deterministic), and a ready wait that runs out
+    # still marks exactly its frame
+    f = tf.Fitter(frames[0].geometry, frames[0].bz, deterministic=True)
+    try:
+        ref = _individual(f, frames)
+        f.set_config(lanes, 4, 24, True)
+        batch = FrameBatch.from_frames(frames)
+        assert _bits(_host(fit_frames(f, batch)), ref)
+        flags = torch.ones(batch.n_frames, dtype=torch.int32, device="cuda")
+        flags[2] = 0
+        s = torch.cuda.Stream()
+        s.wait_stream(torch.cuda.current_stream())
+        with torch.cuda.stream(s):
+            out = fit_frames(f, batch, frame_ready=flags, wait_timeout_ns=20_000_000)
+        out = _host(out)
+        fb = batch.frame_base.cpu().numpy()
+        assert f.status(s)[0] == tf.ETIMEOUT
+        assert np.all(out["ndf"][fb[2]:fb[3]] == -3)
+        keep = np.r_[0:fb[2], fb[3]:fb[-1]]
+        assert np.array_equal(out["ndf"][keep], ref["ndf"][keep])
+    finally:
+        f.close()
