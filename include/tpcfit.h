@@ -216,7 +216,7 @@ const char* tpcfit_rtc_log(void);
 
 /* Record checkpoints for the adjoint (record = 1) or not (0, default).  With
  * recording on, tpcfit_fit also stores the filter state before every 16th step
- * of both passes (about 9 floats per cluster, handle-owned, grown as needed) so
+ * of both passes (about 8 floats per cluster, handle-owned, grown as needed) so
  * that tpcfit_fit_backward can follow.  Any tpcfit_fit call replaces the
  * recording. */
 tpcfit_status tpcfit_set_record(tpcfit_handle* h, int record);

@@ -20,7 +20,7 @@ class _Geo(C.Structure):
     _fields_ = [("row_x", C.POINTER(C.c_double)), ("n_rows", C.c_int32), ("n_sectors", C.c_int32),
                 ("sector_width_deg", C.c_double), ("x0_cm", C.c_double), ("dedx_gev_cm", C.c_double),
                 ("mass_gev", C.c_double), ("row_cm", C.c_double), ("field_cr", C.c_double),
-                ("field_cz", C.c_double)]
+                ("field_cz", C.c_double), ("inward_inflate", C.c_double)]
 
 
 def lib():
@@ -63,16 +63,17 @@ def _ptr(a):
     return None if a is None else a.ctypes.data
 
 
-def _geo(geometry, material=None, field=None):
+def _geo(geometry, material=None, field=None, inward_inflate=0.0):
     """ctypes geometry; material: object with x0_cm, dedx_gev_cm, mass_gev, row_cm (None: none);
-    field: object with c_r, c_z of the field map (None: uniform)."""
+    field: object with c_r, c_z of the field map (None: uniform); inward_inflate:
+    the test-only informative restart of the inward pass (0: C reset to C0)."""
     rx = np.ascontiguousarray(geometry.row_x, dtype=np.float64)
     m = material
     g = _Geo(rx.ctypes.data_as(C.POINTER(C.c_double)), rx.shape[0], geometry.n_sectors,
              float(geometry.sector_width_deg), float(m.x0_cm) if m is not None else 0.0,
              float(m.dedx_gev_cm) if m is not None else 0.0, float(m.mass_gev) if m is not None else 0.0,
              float(m.row_cm) if m is not None else 0.0, float(field.c_r) if field is not None else 0.0,
-             float(field.c_z) if field is not None else 0.0)
+             float(field.c_z) if field is not None else 0.0, float(inward_inflate))
     return g, rx
 
 
@@ -81,13 +82,15 @@ def default_threads() -> int:
 
 
 def fit(frame, precision: str = "f64", align=None, ref=None, trace: bool = False, exact_inputs: bool = False,
-        nthreads: int | None = None, seeds=None):
+        nthreads: int | None = None, seeds=None, inward_inflate: float = 0.0):
     """Run the oracle fit on a ``synth.Frame``.
 
     precision: 'f64' (FP64 reference, covariance form), 'f32' (strict FP32
     reference, square-root form), 'sqrt_f64' (square-root form in FP64) or
     'cov_f32' (covariance form in strict FP32).
     exact_inputs: feed the FP64 copies of hits / seeds (noise-free tests).
+    inward_inflate > 0: test-only reading of the inward restart, from
+    inward_inflate * C_out instead of C0 (0: the product reading).
     Returns dict(params[5,n], cov[15,n], chi2[n], ndf[n], trace[H,2,22] or None).
     """
     L = lib()
@@ -110,7 +113,7 @@ def fit(frame, precision: str = "f64", align=None, ref=None, trace: bool = False
     params = np.empty((5, n), dt); cov = np.empty((15, n), dt); chi2 = np.empty(n, dt)
     ndf = np.empty(n, np.int32)
     tr = np.empty((H, 2, 22), np.float64) if trace else None
-    g, _keep = _geo(frame.geometry, getattr(frame, "material", None), getattr(frame, "field", None))
+    g, _keep = _geo(frame.geometry, getattr(frame, "material", None), getattr(frame, "field", None), inward_inflate)
     fn = {"f64": L.oracle_fit_f64, "f32": L.oracle_fit_f32, "sqrt_f64": L.oracle_fit_sqrt_f64,
           "cov_f32": L.oracle_fit_cov_f32}[precision]
     rc = fn(C.byref(g), float(frame.bz), n, _ptr(off), _ptr(y), _ptr(z), _ptr(rs), _ptr(sd), _ptr(al), _ptr(rf),

@@ -263,6 +263,7 @@ template <class S> struct Geo {
   // field map Bz(r, z) = Bz0 (1 + c_r (r / 250)^2 + c_z (z / 250)^2) (off when field = false)
   bool field;
   S f_r, f_z;  // c_r / 250^2, c_z / 250^2 [1/cm^2]
+  double inflate;  // inward restart from inflate * C_out (0: reset to C0)
 };
 
 // Rotation angle from sector a to b: m = (b - a) mod 18 taken in [-8, 9],
@@ -293,6 +294,7 @@ template <class S> void make_geo(Geo<S>& g, const double* row_x, int n_rows, dou
   g.field = c_r != 0.0 || c_z != 0.0;
   g.f_r = (S)(c_r / (250.0 * 250.0));
   g.f_z = (S)(c_z / (250.0 * 250.0));
+  g.inflate = 0.0;
 }
 
 // packed index of (i, j), i >= j
@@ -527,6 +529,7 @@ template <class T> struct Filter<T, false> {
   }
   void transport_(const Jac<T>& J) { transport<T>(C, J); }
   void cov(T out[15]) const { for (int e = 0; e < 15; ++e) out[e] = C[e]; }
+  void scale(double k) { for (int e = 0; e < 15; ++e) C[e] = C[e] * T((S)k); }
   // C <- D C D + B B^T, D = diag(1, 1, 1, 1, qq)
   void material_(const Noise<T>& N) {
     for (int j = 0; j < 4; ++j) C[P(4, j)] = C[P(4, j)] * N.qq;
@@ -600,6 +603,11 @@ template <class T> struct Filter<T, true> {
     const S l0 = (S)std::sqrt((double)g.c0);
     for (int i = 0; i < 5; ++i)
       for (int c = 0; c < 5; ++c) L[i][c] = T(i == c ? l0 : (S)0.0);
+  }
+  void scale(double k) {
+    const S r = (S)std::sqrt(k);
+    for (int i = 0; i < 5; ++i)
+      for (int c = 0; c < 5; ++c) L[i][c] = L[i][c] * T(r);
   }
   // L <- J L: only rows y, z, s change (rows t, q of J are identity).
   void transport_(const Jac<T>& J) {
@@ -884,7 +892,8 @@ FitResult fit_track(const Geo<typename Traits<T>::S>& g, const HitView<T>& h, co
     record(0, j);
   }
   // ---- inward refit
-  F.init(g);
+  if (g.inflate > 0.0) F.scale(g.inflate);  // test-only reading: an informative restart
+  else F.init(g);
   chi2 = T((S)0.0);
   int used = 0;
   {
@@ -928,6 +937,11 @@ struct OracleGeometry {
   double row_cm;       // thickness of the material layer at each pad row (normal incidence)
   double field_cr;     // field map Bz(r, z) = Bz0 (1 + field_cr (r/250)^2 + field_cz (z/250)^2)
   double field_cz;
+  // Test-only alternative reading of the inward restart (0: the product
+  // reading, C reset to C0): the inward pass starts from the outward result
+  // with C = inward_inflate * C_out, an informative prior instead of the
+  // diffuse one.  It exists to show where the EKF's pull excess comes from.
+  double inward_inflate;
 };
 
 int check_inputs(const OracleGeometry* geo, int32_t n_tracks, const int32_t* off) {
@@ -948,6 +962,7 @@ int fit_all(const OracleGeometry* geo, double bz, int32_t n_tracks, const int32_
   Geo<S> g;
   make_geo<S>(g, geo->row_x, geo->n_rows, geo->sector_width_deg, bz, geo->x0_cm, geo->dedx_gev_cm, geo->mass_gev, geo->row_cm,
                geo->field_cr, geo->field_cz);
+  g.inflate = geo->inward_inflate;
   if ((g.mat || g.field) && ref) return 1;  // the linearised filter has neither material nor a field map
   const T nan = T((S)NAN);
 #pragma omp parallel for schedule(dynamic, 64) num_threads(nthreads > 0 ? nthreads : 1)

@@ -8,7 +8,7 @@
 // and dL/dseed_i.  The outward pass feeds the inward one through its final
 // state (the covariance is reset, the outward chi2 is not part of L).
 //
-// Checkpoints: the forward writes the filter state (p, L, x, sector, chi2)
+// Checkpoints: the forward writes the filter state (p, L, x, sector)
 // before every kCkptEvery-th step of each pass.  The backward walks the
 // segments of a track in reverse: it recomputes a segment's steps from its
 // checkpoint into a per-warp segment store, then reverses the steps one by one
@@ -493,7 +493,7 @@ __device__ __forceinline__ void fetch_state(float4* sdst, const float4* gsrc) {
   cp_async_commit();
 }
 
-// A checkpoint (36 contiguous floats, 16-byte aligned; its first 32 are the
+// A checkpoint (32 contiguous floats, 16-byte aligned: the
 // state) into a lane-interleaved shared slot, as one commit group.
 __device__ __forceinline__ void fetch_ckpt(float4* sdst, const float* ck) {
   const float4* g = reinterpret_cast<const float4*>(ck);

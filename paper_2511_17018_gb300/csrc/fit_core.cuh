@@ -650,7 +650,7 @@ __device__ __forceinline__ bool step_predict(const GeoRef& G, const SmemTables& 
 __device__ __forceinline__ void write_ckpt(const FitArgs& a, int pass, int begin, int trk, int seg,
                                            const TrackState& S) {
   float4* dst = reinterpret_cast<float4*>(a.ck + ((int64_t)pass * a.ck_slots + (begin >> kCkptShift) + trk + seg) * kCkptFloats);
-  float v[36];
+  float v[kCkptFloats];
 #pragma unroll
   for (int c = 0; c < 5; ++c) v[c] = S.p[c];
 #pragma unroll
@@ -659,10 +659,8 @@ __device__ __forceinline__ void write_ckpt(const FitArgs& a, int pass, int begin
     for (int c = 0; c < 5; ++c) v[5 + 5 * i + c] = S.L[i][c];
   v[30] = S.x;
   v[31] = __int_as_float(S.sec);
-  v[32] = S.chi2;
-  v[33] = v[34] = v[35] = 0.0f;
 #pragma unroll
-  for (int j = 0; j < 9; ++j) dst[j] = make_float4(v[4 * j], v[4 * j + 1], v[4 * j + 2], v[4 * j + 3]);
+  for (int j = 0; j < kCkptFloats / 4; ++j) dst[j] = make_float4(v[4 * j], v[4 * j + 1], v[4 * j + 2], v[4 * j + 3]);
 }
 
 // PHYS: bit 0 the material layers, bit 1 the field map (compile-time variants,

@@ -337,8 +337,6 @@ __global__ void __launch_bounds__(WARPS * 32, 1) fit_kernel_lanes(const __grid_c
               for (int c = 0; c < 5; ++c) dst[c] = p[c];
               dst[30] = x;
               dst[31] = __int_as_float(sec_cur);
-              dst[32] = chi2;
-              dst[33] = dst[34] = dst[35] = 0.0f;
             }
           }
           bool ok = step;

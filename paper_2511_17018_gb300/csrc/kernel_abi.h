@@ -26,10 +26,12 @@ constexpr int kMaxRows = 152;
 constexpr int kAlignFloats = kNSectors * kMaxRows * 2;
 constexpr int kWarp = 32;
 // The adjoint's checkpoints: the filter state before every kCkptEvery-th step
-// of each pass, kCkptFloats floats each (p 5, L 25, x, sector bits, chi2, 3 pad).
+// of each pass, kCkptFloats floats each (p 5, L 25, x, sector bits: what the
+// recomputation starts from; chi2 is not needed, since only the inward pass's
+// total enters the objective and its adjoint is a constant).
 constexpr int kCkptShift = 4;
 constexpr int kCkptEvery = 1 << kCkptShift;
-constexpr int kCkptFloats = 36;
+constexpr int kCkptFloats = 32;
 
 // Per-time-frame constants of the fit (Sec. 4.1).  Every launch carries them
 // by value in its argument block, i.e. in the kernel-parameter constant bank
@@ -75,7 +77,7 @@ struct FitArgs {
   unsigned long long* err;     // error word: code << 56 | track
   unsigned int* work;          // work-item counter (zeroed by the launcher)
   // checkpoint recording for the adjoint (null = off)
-  float* ck;                   // [2][ck_slots][36] filter state before every kCkptEvery-th step of each pass
+  float* ck;                   // [2][ck_slots][32] filter state before every kCkptEvery-th step of each pass
   int32_t* ck_last;            // [n_tracks] index of the last cluster of the outward pass
   int64_t ck_slots;            // slots per pass: n_hits / kCkptEvery + n_tracks + 1
   // several time frames in one launch (frame_base = null: one frame)
