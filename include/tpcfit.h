@@ -221,11 +221,11 @@ const char* tpcfit_rtc_log(void);
  * recording. */
 tpcfit_status tpcfit_set_record(tpcfit_handle* h, int record);
 
-/* Launch configuration of the adjoint: warps per block (4, 8 or 12; default
- * 8).  Each resident warp owns a segment store in device memory (the handle
- * allocates it on the first backward) and 12 KB of shared memory that holds the
- * states it copies ahead.  Results do not depend on it.  EINVAL for other
- * values. */
+/* Launch configuration of the adjoint's reverse: warps per block (4, 8, 10 or
+ * 12; default 8).  Each resident warp owns 8-12 KB of shared memory that holds
+ * the states it copies ahead (and, in fast mode without material, a segment
+ * store in device memory that the handle allocates on the first backward).
+ * Results do not depend on it.  EINVAL for other values. */
 tpcfit_status tpcfit_set_backward_config(tpcfit_handle* h, int warps_per_block);
 
 /* Adjoint of the recorded fit: gradients of L = sum_i grad_chi2[i] * chi2_i.
@@ -238,11 +238,16 @@ tpcfit_status tpcfit_set_backward_config(tpcfit_handle* h, int warps_per_block);
  *   grad_align: float [36][152][2], dL/d(dy, dz) of the alignment offsets;
  *   grad_seeds: float [5][n_tracks], dL/dseed;
  *   grad_meas:  float [n_hits][2], dL/d(measured y, z) per cluster, or NULL.
- * The backward recomputes each 16-step segment from its checkpoint into a
- * per-warp segment store and runs the hand-written reverse of every step,
- * copying the state before each step into shared memory one step ahead.  It
- * follows the field map and the material layers (tpcfit_set_field_map,
- * tpcfit_set_material).  Fast mode accumulates grad_align with
+ * The backward recomputes each 16-step segment from its checkpoint and runs
+ * the hand-written reverse of every step, copying the state before each step
+ * into shared memory one step ahead.  Fast mode without material layers
+ * recomputes into a per-warp segment store in the same kernel; the
+ * deterministic mode and the material layers replay the segments in a kernel
+ * of their own onto a tape of every step's state (about 40 MB per 1,000
+ * tracks, handle-owned, grown as needed) and reverse from it.  It follows the
+ * field map and the material layers (tpcfit_set_field_map,
+ * tpcfit_set_material).  Tracks of more than 152 clusters get no gradient in
+ * the taped cases.  Fast mode accumulates grad_align with
  * atomics; deterministic mode writes per-cluster gradients, sorts the clusters
  * by (sector, row) with a stable radix sort and sums each key in a fixed order,
  * so grad_align is bitwise reproducible.  Tracks with ndf <= 0 contribute 0. */

@@ -1081,6 +1081,232 @@ __global__ void __launch_bounds__(WARPS * 32, 1) backward_kernel(const __grid_co
   }
 }
 
+// ---------------------------------------------------------------- the tape
+// The backward in two kernels.  recompute_kernel replays every 16-step
+// segment of both passes from its checkpoint (the fit's own arithmetic, at the
+// fit's occupancy) and writes the state before each step to a tape in device
+// memory.  tape_reverse_kernel then reverses the steps of each pass from the
+// last, copying each state from the tape into shared memory one step ahead;
+// it holds the reverse step's registers but does no forward work.
+// Tape layout: [pass][32-track work item][step][float4 j][lane], kTapeSteps
+// steps per work item, so that a warp's store or copy of float4 j of one step
+// moves 512 contiguous bytes.  Both kernels map processing slot k to work
+// item k / 32 and lane k % 32.  A track of more than kTapeSteps clusters (no
+// valid track has more than one per pad row) gets no gradient.
+constexpr int kTapeSteps = kMaxRows;
+
+__host__ __device__ constexpr int64_t tape_float4s(int64_t n_tracks) {
+  return 2 * ((n_tracks + kWarp - 1) / kWarp) * (int64_t)kTapeSteps * kStateF4 * kWarp;
+}
+
+// Float4 0 of step 0 of (pass, work item), offset by the lane.
+__device__ __forceinline__ int64_t tape_base(int pass, int64_t chunk, int64_t n_chunks, int lane) {
+  return (((int64_t)pass * n_chunks + chunk) * kTapeSteps) * (kStateF4 * kWarp) + lane;
+}
+
+constexpr int kRecomputeWarps = 24;
+
+template <int PHYS>
+__global__ void __launch_bounds__(kRecomputeWarps * 32, 1) recompute_kernel(const __grid_constant__ BwdArgs a) {
+  const GeoRef& G = a.geo;
+  constexpr bool MAT = (PHYS & 1) != 0;
+  constexpr int FIELD = (PHYS & 2) ? 1 : 0;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  BwdSmem& B = *reinterpret_cast<BwdSmem*>(smem_raw);
+  load_tables(G, B.T);
+  for (int i = threadIdx.x; i < kAlignFloats; i += blockDim.x) B.align[i] = __ldg(a.align + i);
+  __syncthreads();
+  const SmemTables& T = B.T;
+  const int lane = threadIdx.x & 31;
+  const int64_t n_chunks = ((int64_t)a.n_tracks + kWarp - 1) / kWarp;
+#pragma unroll 1
+  for (;;) {
+    int64_t chunk = 0;
+    if (lane == 0) chunk = (int64_t)atomicAdd(a.work, 1u);
+    chunk = __shfl_sync(0xffffffffu, chunk, 0);
+    if (chunk >= n_chunks) break;
+    const int64_t slot = chunk * kWarp + lane;
+    if (slot >= a.n_tracks) continue;
+    const int32_t trk = a.perm ? a.perm[slot] : (int32_t)slot;
+    if (a.ndf[trk] <= 0) continue;
+    const int begin = a.off[trk];
+    const int last = a.ck_last[trk];
+    const int steps = last + 1;
+    if (steps > kTapeSteps) continue;
+    const int nseg = (steps + kCkptEvery - 1) / kCkptEvery;
+#pragma unroll 1
+    for (int pass = 0; pass < 2; ++pass) {
+      const int h0 = pass == 0 ? begin : begin + last;
+      const int hd = pass == 0 ? 1 : -1;
+      const float* ckp = a.ck + ((int64_t)pass * a.ck_slots + (begin >> kCkptShift) + trk) * kCkptFloats;
+      float4* const tp = a.tape + tape_base(pass, chunk, n_chunks, lane);
+#pragma unroll 1
+      for (int s = 0; s < nseg; ++s) {
+        const int i0 = s * kCkptEvery;
+        const int cnt = min(kCkptEvery, steps - i0);
+        StepState S;
+        load_ckpt(ckp + (int64_t)s * kCkptFloats, S);
+        float my = 0.0f, mz = 0.0f;
+        if (i0 > 0) {
+          int row, sec;
+          decode_hit(B.align, load_hit(a, h0 + hd * (i0 - 1)), my, mz, row, sec);
+        }
+        HitRaw nx = load_hit(a, h0 + hd * i0);
+#pragma unroll 1
+        for (int kk = 0; kk < cnt; ++kk) {
+          const int i = i0 + kk;
+          const HitRaw cur = nx;
+          if (kk + 1 < cnt) nx = load_hit(a, h0 + hd * (i + 1));
+          float m0, m1;
+          int row, sec;
+          decode_hit(B.align, cur, m0, m1, row, sec);
+          store_state(tp + (int64_t)i * (kStateF4 * kWarp), S);
+          step_fwd<MAT, FIELD>(G, T, S, my, mz, i == 0, pass == 0, row, side_sector(sec), m0, m1);
+        }
+      }
+    }
+  }
+}
+
+// The reverse of both passes from the tape (inward pass first); the same
+// reverse steps, cluster loads and gradient accumulation as backward_kernel.
+template <int WARPS, int PHYS>
+__global__ void __launch_bounds__(WARPS * 32, 1) tape_reverse_kernel(const __grid_constant__ BwdArgs a) {
+  const GeoRef& G = a.geo;
+  constexpr bool MAT = (PHYS & 1) != 0;
+  constexpr int FIELD = (PHYS & 2) ? 1 : 0;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  BwdSmem& B = *reinterpret_cast<BwdSmem*>(smem_raw);
+  load_tables(G, B.T);
+  for (int i = threadIdx.x; i < kAlignFloats; i += blockDim.x) B.align[i] = __ldg(a.align + i);
+  __syncthreads();
+  const SmemTables& T = B.T;
+  const int lane = threadIdx.x & 31;
+  const int warp = threadIdx.x >> 5;
+  float4 (*const st)[kStateF4][kWarp] =
+      reinterpret_cast<float4 (*)[kStateF4][kWarp]>(smem_raw + sizeof(BwdSmem)) + 2 * warp;
+  const int64_t n_chunks = ((int64_t)a.n_tracks + kWarp - 1) / kWarp;
+  const int64_t N = a.n_tracks;
+#pragma unroll 1
+  for (;;) {
+    int64_t chunk = 0;
+    if (lane == 0) chunk = (int64_t)atomicAdd(a.work, 1u);
+    chunk = __shfl_sync(0xffffffffu, chunk, 0);
+    if (chunk >= n_chunks) break;
+    const int64_t slot = chunk * kWarp + lane;
+    if (slot >= N) continue;
+    const int32_t trk = a.perm ? a.perm[slot] : (int32_t)slot;
+    const float g = __ldg(a.grad_chi2 + trk);
+    const bool fitted = a.ndf[trk] > 0;
+    float b_p[5] = {0.0f, 0.0f, 0.0f, 0.0f, 0.0f};
+    const int begin = fitted ? a.off[trk] : 0;
+    const int last = fitted ? a.ck_last[trk] : 0;
+    if (fitted && last + 1 <= kTapeSteps) {
+      float b_L[5][5];
+#pragma unroll 1
+      for (int pass = 1; pass >= 0; --pass) {
+#pragma unroll
+        for (int i = 0; i < 5; ++i)
+#pragma unroll
+          for (int c = 0; c < 5; ++c) b_L[i][c] = 0.0f;
+        const float b_chi = pass == 1 ? g : 0.0f;
+        const int steps = last + 1;
+        const int h0 = pass == 0 ? begin : begin + last;
+        const int hd = pass == 0 ? 1 : -1;
+        const float4* const tp = a.tape + tape_base(pass, chunk, n_chunks, lane);
+        float pend0 = 0.0f, pend1 = 0.0f;  // gradient owed to the measurement of the step before
+        const float2* const gmr = reinterpret_cast<const float2*>(a.grad_meas);
+        const bool addg = pass == 0 && gmr != nullptr;
+        float2 gnx = addg ? gmr[h0 + hd * (steps - 1)] : make_float2(0.0f, 0.0f);
+        fetch_state(&st[(steps - 1) & 1][0][lane], tp + (int64_t)(steps - 1) * (kStateF4 * kWarp));
+        float m0, m1;
+        int row, sec;
+        decode_hit(B.align, load_hit(a, h0 + hd * (steps - 1)), m0, m1, row, sec);
+        HitRaw pv{};
+        if (steps > 1) pv = load_hit(a, h0 + hd * (steps - 2));
+#pragma unroll 1
+        for (int i = steps - 1; i >= 0; --i) {
+          const int h = h0 + hd * i;
+          if (i > 0) {
+            fetch_state(&st[(i - 1) & 1][0][lane], tp + (int64_t)(i - 1) * (kStateF4 * kWarp));
+            cp_async_wait<1>();
+          } else {
+            cp_async_wait<0>();
+          }
+          float mpy = 0.0f, mpz = 0.0f;
+          int prow = 0, psec = 0;
+          if (i > 0) {
+            const HitRaw pc = pv;
+            if (i > 1) pv = load_hit(a, h - 2 * hd);
+            decode_hit(B.align, pc, mpy, mpz, prow, psec);
+          }
+          const float2 gcur = gnx;
+          if (addg && i > 0) gnx = gmr[h - hd];
+          float b_mc[2], b_mp[2];
+          if (MAT)
+            step_rev_mat<FIELD>(G, T, &st[i & 1][0][lane], mpy, mpz, i == 0, pass == 0, row, side_sector(sec), m0,
+                                m1, b_p, b_L, b_chi, b_mc, b_mp);
+          else
+            step_rev<FIELD>(G, T, &st[i & 1][0][lane], mpy, mpz, i == 0, pass == 0, row, side_sector(sec), m0, m1,
+                            b_p, b_L, b_chi, b_mc, b_mp);
+          accumulate_meas_grad(a, pass, h, row, sec, b_mc[0] + pend0, b_mc[1] + pend1, gcur);
+          pend0 = b_mp[0];
+          pend1 = b_mp[1];
+          m0 = mpy;
+          m1 = mpz;
+          row = prow;
+          sec = psec;
+        }
+        // the inward pass starts from the outward result with the factor reset:
+        // b_p carries over, b_L does not
+      }
+    } else if (a.grad_meas) {
+      const int b = a.off[trk];
+      const int end = a.off[trk + 1];
+      for (int h = b; h < end; ++h) reinterpret_cast<float2*>(a.grad_meas)[h] = make_float2(0.0f, 0.0f);
+    }
+#pragma unroll
+    for (int c = 0; c < 5; ++c) a.grad_seeds[(int64_t)c * N + trk] = b_p[c];
+  }
+}
+
+template <int WARPS>
+constexpr size_t tape_reverse_smem_bytes() {
+  return sizeof(BwdSmem) + (size_t)WARPS * 2 * kStateF4 * kWarp * sizeof(float4);
+}
+
+// Persistent launch of a kernel with `warps` warps per block and `smem` bytes
+// of shared memory (the grid cached per kernel).
+template <class K>
+cudaError_t launch_persistent(K kernel, int& cached, int warps, size_t smem, const BwdArgs& a, cudaStream_t s) {
+  if (cached == 0) {
+    cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    int dev = 0, sms = 0, per_sm = 0;
+    e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, warps * 32, smem);
+    if (e != cudaSuccess) return e;
+    if (per_sm < 1) return cudaErrorInvalidConfiguration;
+    cached = sms * per_sm;
+  }
+  const int64_t chunks = ((int64_t)a.n_tracks + kWarp - 1) / kWarp;
+  const int64_t need = (chunks + warps - 1) / warps;
+  const int blocks = (int)(need < cached ? need : cached);
+  cudaError_t e = cudaMemsetAsync(a.work, 0, sizeof(unsigned int), s);
+  if (e != cudaSuccess) return e;
+  kernel<<<blocks, warps * 32, smem, s>>>(a);
+  return cudaGetLastError();
+}
+
+template <int WARPS, int PHYS>
+cudaError_t launch_tape_backward_cfg(const BwdArgs& a, cudaStream_t s) {
+  static int g_rec = 0, g_rev = 0;
+  cudaError_t e = launch_persistent(recompute_kernel<PHYS>, g_rec, kRecomputeWarps, sizeof(BwdSmem), a, s);
+  if (e != cudaSuccess) return e;
+  return launch_persistent(tape_reverse_kernel<WARPS, PHYS>, g_rev, WARPS, tape_reverse_smem_bytes<WARPS>(), a, s);
+}
+
 // Persistent grid of the backward (blocks resident at once over all SMs).
 template <int WARPS, int PHYS>
 cudaError_t backward_grid(int& grid) {
@@ -1135,9 +1361,7 @@ inline int backward_warps(int warps, int phys) { return phys ? 8 : warps; }
 inline cudaError_t backward_store(int warps, int phys, int64_t& float4s) {
   switch (phys) {
     case 0: break;
-    case 1: return backward_store_cfg<8, 1>(float4s);
     case 2: return backward_store_cfg<8, 2>(float4s);
-    case 3: return backward_store_cfg<8, 3>(float4s);
     default: return cudaErrorInvalidValue;
   }
   switch (warps) {
@@ -1149,13 +1373,43 @@ inline cudaError_t backward_store(int warps, int phys, int64_t& float4s) {
   }
 }
 
-inline cudaError_t launch_backward(const BwdArgs& a, int warps, cudaStream_t s) {
-  if (a.n_tracks <= 0) return cudaSuccess;
+// The deterministic backward always, and the fast one with material layers,
+// replay the segments onto the tape (recompute_kernel + tape_reverse_kernel);
+// the fast backward without material recomputes into the segment store
+// (backward_kernel).
+inline cudaError_t launch_tape_backward(const BwdArgs& a, int warps, cudaStream_t s) {
   switch (a.phys) {
     case 0: break;
-    case 1: return launch_backward_cfg<8, 1>(a, s);
+    case 1: return launch_tape_backward_cfg<8, 1>(a, s);
+#if TPCFIT_DET
+    case 2: return launch_tape_backward_cfg<8, 2>(a, s);
+#endif
+    case 3: return launch_tape_backward_cfg<8, 3>(a, s);
+    default: return cudaErrorInvalidValue;
+  }
+#if TPCFIT_DET
+  switch (warps) {
+    case 4: return launch_tape_backward_cfg<4, 0>(a, s);
+    case 8: return launch_tape_backward_cfg<8, 0>(a, s);
+    case 10: return launch_tape_backward_cfg<10, 0>(a, s);
+    case 12: return launch_tape_backward_cfg<12, 0>(a, s);
+    default: return cudaErrorInvalidValue;
+  }
+#else
+  (void)warps;
+  return cudaErrorInvalidValue;
+#endif
+}
+
+inline cudaError_t launch_backward(const BwdArgs& a, int warps, cudaStream_t s) {
+  if (a.n_tracks <= 0) return cudaSuccess;
+  if (a.tape) return launch_tape_backward(a, warps, s);
+#if TPCFIT_DET
+  return cudaErrorInvalidValue;
+#else
+  switch (a.phys) {
+    case 0: break;
     case 2: return launch_backward_cfg<8, 2>(a, s);
-    case 3: return launch_backward_cfg<8, 3>(a, s);
     default: return cudaErrorInvalidValue;
   }
   switch (warps) {
@@ -1165,6 +1419,7 @@ inline cudaError_t launch_backward(const BwdArgs& a, int warps, cudaStream_t s) 
     case 12: return launch_backward_cfg<12, 0>(a, s);
     default: return cudaErrorInvalidValue;
   }
+#endif
 }
 
 }  // namespace TPCFIT_NS

@@ -18,9 +18,6 @@ cudaError_t launch_fit_det(const FitArgs& a, int lanes_per_track, int rows_per_s
 cudaError_t launch_backward_det(const BwdArgs& a, int warps, cudaStream_t s) {
   return det::launch_backward(a, warps, s);
 }
-cudaError_t backward_store_det(int warps, int phys, int64_t& float4s) {
-  return det::backward_store(warps, phys, float4s);
-}
 cudaError_t launch_smooth_det(const SmoothArgs& a, cudaStream_t s) { return det::launch_smooth(a, s); }
 cudaError_t smooth_store_det(int64_t& float4s) { return det::smooth_store(float4s); }
 }  // namespace tpcfit

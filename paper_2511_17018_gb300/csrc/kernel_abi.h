@@ -111,6 +111,7 @@ struct BwdArgs {
   float* grad_align_atomic;    // [36][152][2] accumulated with atomics, or null
   unsigned int* work;
   float4* seg;                 // segment store: [resident warps][kCkptEvery][8][32] float4
+  float4* tape;                // or the tape: [2][n_hits][8] float4, the state before every step (null: segment store)
   int32_t phys;                // physics of the recorded fit: bit 1 material layers, bit 2 the field map
 };
 
