@@ -512,6 +512,20 @@ def main():
     _, sm_per = timed(step_smooth, max(5, args.steps // 4))
     smooth_ms = statistics.mean(p[0] for p in sm_per)
     del sm
+    # the smoothed state and covariance at every cluster
+    ss = dict(state=torch.empty((fr.n_hits, 5), device="cuda"), cov=torch.empty((fr.n_hits, 15), device="cuda"))
+
+    def step_states(mid):
+        tf.tpcfit_smooth_states(fitter.h, dev["y"], dev["z"], dev["rowsec"], dev["offsets"], out["ndf"],
+                                ss["state"], ss["cov"])
+        mid.record(stream)
+
+    for _ in range(args.warmup):
+        step_states(torch.cuda.Event())
+    torch.cuda.synchronize()
+    _, ss_per = timed(step_states, max(5, args.steps // 4))
+    states_ms = statistics.mean(p[0] for p in ss_per)
+    del ss
 
     # ---- the plain fit (no checkpoints)
     fitter.set_record(False)
@@ -674,7 +688,8 @@ def main():
     line["plain_fit"]["e2e"] = e2e_plain
     sm_f = flops.smooth_flops(lengths) / (smooth_ms / 1e3) / 1e12
     line["smoother"] = {"tracks_per_s": fr.n_tracks / (smooth_ms / 1e3), "clusters_per_s": fr.n_hits / (smooth_ms / 1e3),
-                        "ms": smooth_ms, "frac_impl": sm_f / peak_tf}
+                        "ms": smooth_ms, "frac_impl": sm_f / peak_tf,
+                        "states": {"ms": states_ms, "clusters_per_s": fr.n_hits / (states_ms / 1e3)}}
     line["plain_fit"]["field_map"] = {"tracks_per_s": fr.n_tracks / (fld_ms / 1e3), "ms": fld_ms,
                                       "field": "Bz (1 + 0.3 (r/250)^2 - 0.2 (z/250)^2)"}
     line["plain_fit"]["material"] = {"tracks_per_s": fr.n_tracks / (mat_ms / 1e3), "ms": mat_ms,

@@ -272,6 +272,22 @@ tpcfit_status tpcfit_fit_backward(tpcfit_handle* h, const tpcfit_hits* hits, con
 tpcfit_status tpcfit_smooth(tpcfit_handle* h, const tpcfit_hits* hits, const int32_t* track_offsets, int32_t n_tracks,
                             const int32_t* ndf, float* resid, float* rcov, float* chi2, void* stream);
 
+/* Smoothed states of the recorded fit: for every cluster, the estimate of the
+ * track state at that cluster from all the clusters of its track -- the
+ * two-filter form of the smoother (Fraser & Potter), the outward pass's
+ * filtered state at the cluster combined with the inward prediction there.
+ * Inputs as for tpcfit_smooth (the last tpcfit_fit on this handle, with
+ * recording on, same mode; otherwise ESTATE).  Outputs (device, overwritten):
+ *   state:     float [n_hits][5], (y, z, sin phi, tan lambda, q/pt) at the
+ *              cluster's pad row, in its sector's frame, y and z absolute;
+ *   state_cov: float [n_hits][15], its covariance (packed lower-triangular).
+ * NaN for the clusters of tracks with ndf <= 0 and for clusters the outward
+ * pass did not reach.  Uses the handle's segment store: calls on one handle
+ * must not overlap. */
+tpcfit_status tpcfit_smooth_states(tpcfit_handle* h, const tpcfit_hits* hits, const int32_t* track_offsets,
+                                   int32_t n_tracks, const int32_t* ndf, float* state, float* state_cov,
+                                   void* stream);
+
 /* Fit + adjoint with HOST buffers, for streams of batches.  Copies hits,
  * offsets, seeds and grad_chi2 (host, as for tpcfit_fit and
  * tpcfit_fit_backward) to the device on an internal copy stream, fits with

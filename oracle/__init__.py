@@ -218,6 +218,54 @@ def smooth(frame, align=None, ref=None, exact_inputs: bool = False, seeds=None, 
     return dict(resid=resid, rcov=rcov, chi2=c2, ndf=ndf)
 
 
+def smooth_states(frame, align=None, ref=None, exact_inputs: bool = False, seeds=None, nthreads: int | None = None):
+    """Smoothed state at every cluster from all clusters of its track (FP64,
+    two-filter form, Fraser & Potter 1969): the information-weighted mean of
+    the outward pass's filtered state at the cluster (seed prior and clusters
+    0..c) and the inward pass's prediction there (the inward prior and clusters
+    c+1..last):
+        C_s = (C_out^-1 + C_in^-1)^-1,   x_s = C_s (C_out^-1 x_out + C_in^-1 x_in).
+    Positions are absolute, in the cluster's sector frame at its pad row.
+    NaN for the clusters of unfitted tracks and for clusters the outward pass
+    did not reach.  Returns dict(state[H,5], state_cov[H,15] (packed), ndf[n]).
+    """
+    L = lib()
+    n = frame.n_tracks
+    H = frame.n_hits
+    y = np.ascontiguousarray(frame.y64 if exact_inputs else frame.y, dtype=np.float64)
+    z = np.ascontiguousarray(frame.z64 if exact_inputs else frame.z, dtype=np.float64)
+    sd = frame.seeds64 if exact_inputs else frame.seeds
+    sd = np.ascontiguousarray(sd if seeds is None else seeds, dtype=np.float64)
+    rs = np.ascontiguousarray(frame.rowsec, dtype=np.uint16)
+    off = np.ascontiguousarray(frame.offsets, dtype=np.int32)
+    al = None if align is None else np.ascontiguousarray(align, dtype=np.float64).reshape(-1)
+    rf = None if ref is None else np.ascontiguousarray(ref, dtype=np.float64)
+    params = np.empty((5, n)); cov = np.empty((15, n)); chi2 = np.empty(n); ndf = np.empty(n, np.int32)
+    pt = np.empty((H, 2, 20))
+    g, _keep = _geo(frame.geometry, getattr(frame, "material", None), getattr(frame, "field", None))
+    rc = L.oracle_fit_pred_f64(C.byref(g), float(frame.bz), n, _ptr(off), _ptr(y), _ptr(z), _ptr(rs), _ptr(sd),
+                               _ptr(al), _ptr(rf), _ptr(params), _ptr(cov), _ptr(chi2), _ptr(ndf), _ptr(pt),
+                               nthreads or default_threads())
+    if rc != 0:
+        raise ValueError(f"oracle fit rejected its inputs (rc={rc})")
+    tr = fit(frame, "f64", align=align, ref=ref, trace=True, exact_inputs=exact_inputs, nthreads=nthreads,
+             seeds=seeds)["trace"]
+    fitted = np.repeat(ndf > 0, np.diff(off))
+    ok = fitted & np.all(np.isfinite(tr[:, 0, :20]), axis=1) & np.all(np.isfinite(pt[:, 1]), axis=1)
+    state = np.full((H, 5), np.nan)
+    scov = np.full((H, 15), np.nan)
+    if ok.any():
+        x1, x2 = tr[ok, 0, :5], pt[ok, 1, :5]
+        C1 = np.moveaxis(unpack(tr[ok, 0, 5:20].T), -1, 0)
+        C2 = np.moveaxis(unpack(pt[ok, 1, 5:].T), -1, 0)
+        I1, I2 = np.linalg.inv(C1), np.linalg.inv(C2)
+        Cs = np.linalg.inv(I1 + I2)
+        xs = np.einsum("nij,nj->ni", Cs, np.einsum("nij,nj->ni", I1, x1) + np.einsum("nij,nj->ni", I2, x2))
+        state[ok] = xs
+        scov[ok] = pack(np.moveaxis(Cs, 0, -1)).T
+    return dict(state=state, state_cov=scov, ndf=ndf)
+
+
 def align_grad_from_meas(frame, grad_meas):
     """dL/d(offsets) [36,152,2] from dL/dm (m = raw - offset)."""
     rs = frame.rowsec.astype(np.int64)

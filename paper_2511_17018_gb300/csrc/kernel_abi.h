@@ -133,6 +133,8 @@ struct SmoothArgs {
   float* resid;                // [n_hits][2] m - H x_u
   float* rcov;                 // [n_hits][3] R00, R10, R11 of V + H C_u H^T
   float* chi2;                 // [n_hits] r^T R^-1 r
+  float* state;                // [n_hits][5] smoothed state from all clusters, or null
+  float* state_cov;            // [n_hits][15] its covariance (packed)
   unsigned int* work;
   float4* seg;                 // segment store, as for the adjoint
   int32_t mat;                 // material layers on (the recorded fit had them)

@@ -122,14 +122,108 @@ __device__ __forceinline__ void smooth_combine(const GeoRef& G, const float p1[5
   chi2 = (R[2] * r[0] * r[0] - 2.0f * R[1] * r[0] * r[1] + R[0] * r[1] * r[1]) / det;
 }
 
+// Smoothed state from all clusters at one cluster: the same square-root
+// combination, of the outward pass's filtered state there (p1, L1) with the
+// inward prediction (p2, L2), but with the five rows of [L1, 0] and of
+// [0, L2] carried through the reflectors: W1 = [L1, 0] Q, W2 = [0, L2] Q,
+//   x_s = p1 + W1 u,  C_s = W1 W2^T (symmetrised),  u = R^-T (p2 - p1).
+__device__ __forceinline__ void smooth_state(const float p1[5], const float L1[5][5], const float p2[5],
+                                             const float L2[5][5], float xs[5], float Cs[15]) {
+  float M[10][5];   // [A1; A2]
+  float E[10][10];  // rows 0-4: [L1, 0]; rows 5-9: [0, L2]
+#pragma unroll
+  for (int q = 0; q < 5; ++q)
+#pragma unroll
+    for (int i = 0; i < 5; ++i) {
+      M[q][i] = L1[i][q];
+      M[5 + q][i] = L2[i][q];
+    }
+#pragma unroll
+  for (int h = 0; h < 5; ++h)
+#pragma unroll
+    for (int q = 0; q < 5; ++q) {
+      E[h][q] = L1[h][q];
+      E[h][5 + q] = 0.0f;
+      E[5 + h][q] = 0.0f;
+      E[5 + h][5 + q] = L2[h][q];
+    }
+#pragma unroll
+  for (int k = 0; k < 5; ++k) {
+    float nrm2 = M[k][k] * M[k][k];
+#pragma unroll
+    for (int q = k + 1; q < 10; ++q) nrm2 = nrm2 + M[q][k] * M[q][k];
+    float nrm, inrm;
+    sqrt_and_inv(nrm2, nrm, inrm);
+    const float alpha = M[k][k] > 0.0f ? -nrm : nrm;
+    const float v0 = M[k][k] - alpha;
+    const float g = 1.0f / (alpha * v0);
+#pragma unroll
+    for (int j = k + 1; j < 5; ++j) {
+      float t = v0 * M[k][j];
+#pragma unroll
+      for (int q = k + 1; q < 10; ++q) t = t + M[q][k] * M[q][j];
+      t = t * g;
+      M[k][j] = M[k][j] + t * v0;
+#pragma unroll
+      for (int q = k + 1; q < 10; ++q) M[q][j] = M[q][j] + t * M[q][k];
+    }
+#pragma unroll
+    for (int e = 0; e < 10; ++e) {
+      float t = E[e][k] * v0;
+#pragma unroll
+      for (int q = k + 1; q < 10; ++q) t = t + E[e][q] * M[q][k];
+      t = t * g;
+      E[e][k] = E[e][k] + t * v0;
+#pragma unroll
+      for (int q = k + 1; q < 10; ++q) E[e][q] = E[e][q] + t * M[q][k];
+    }
+    M[k][k] = alpha;
+  }
+  float u[5];
+#pragma unroll
+  for (int i = 0; i < 5; ++i) {
+    float e = p2[i] - p1[i];
+#pragma unroll
+    for (int q = 0; q < i; ++q) e = e - M[q][i] * u[q];
+    u[i] = e / M[i][i];
+  }
+#pragma unroll
+  for (int i = 0; i < 5; ++i) {
+    float acc = E[i][0] * u[0];
+#pragma unroll
+    for (int q = 1; q < 5; ++q) acc = acc + E[i][q] * u[q];
+    xs[i] = p1[i] + acc;
+  }
+  int e = 0;
+#pragma unroll
+  for (int i = 0; i < 5; ++i)
+#pragma unroll
+    for (int j = 0; j <= i; ++j) {
+      float a12 = E[i][0] * E[5 + j][0];
+      float a21 = E[j][0] * E[5 + i][0];
+#pragma unroll
+      for (int q = 1; q < 5; ++q) {
+        a12 = a12 + E[i][q] * E[5 + j][q];
+        a21 = a21 + E[j][q] * E[5 + i][q];
+      }
+      Cs[e++] = 0.5f * (a12 + a21);
+    }
+}
+
 __device__ __forceinline__ void write_nan_clusters(const SmoothArgs& a, int h0, int h1) {
   const float qnan = __int_as_float(0x7fc00000);
   for (int h = h0; h < h1; ++h) {
-    reinterpret_cast<float2*>(a.resid)[h] = make_float2(qnan, qnan);
-    a.rcov[(int64_t)h * 3] = qnan;
-    a.rcov[(int64_t)h * 3 + 1] = qnan;
-    a.rcov[(int64_t)h * 3 + 2] = qnan;
-    a.chi2[h] = qnan;
+    if (a.resid) {
+      reinterpret_cast<float2*>(a.resid)[h] = make_float2(qnan, qnan);
+      a.rcov[(int64_t)h * 3] = qnan;
+      a.rcov[(int64_t)h * 3 + 1] = qnan;
+      a.rcov[(int64_t)h * 3 + 2] = qnan;
+      a.chi2[h] = qnan;
+    }
+    if (a.state) {
+      for (int q = 0; q < 5; ++q) a.state[(int64_t)h * 5 + q] = qnan;
+      for (int q = 0; q < 15; ++q) a.state_cov[(int64_t)h * 15 + q] = qnan;
+    }
   }
 }
 
@@ -140,7 +234,9 @@ constexpr size_t smooth_smem_bytes() {
   return sizeof(BwdSmem) + WARPS * sizeof(BwdWarpBufs);
 }
 
-template <int WARPS, bool MAT>
+// STATES: the smoothed state and its covariance at every cluster as well
+// (a.state, a.state_cov); without it the kernel carries none of that code.
+template <int WARPS, bool MAT, bool STATES>
 __global__ void __launch_bounds__(WARPS * 32, 1) smooth_kernel(const __grid_constant__ SmoothArgs a) {
   const GeoRef& G = a.geo;
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -264,13 +360,15 @@ __global__ void __launch_bounds__(WARPS * 32, 1) smooth_kernel(const __grid_cons
           transport(O.L, J);
           if (MAT) material_factor(O.L, N);
         }
-        float r[2], R[3], c2;
-        smooth_combine(G, po, O.L, pi, SI.L, r, R, c2);
-        reinterpret_cast<float2*>(a.resid)[h] = make_float2(r[0], r[1]);
-        a.rcov[(int64_t)h * 3] = R[0];
-        a.rcov[(int64_t)h * 3 + 1] = R[1];
-        a.rcov[(int64_t)h * 3 + 2] = R[2];
-        a.chi2[h] = c2;
+        if (a.resid) {
+          float r[2], R[3], c2;
+          smooth_combine(G, po, O.L, pi, SI.L, r, R, c2);
+          reinterpret_cast<float2*>(a.resid)[h] = make_float2(r[0], r[1]);
+          a.rcov[(int64_t)h * 3] = R[0];
+          a.rcov[(int64_t)h * 3 + 1] = R[1];
+          a.rcov[(int64_t)h * 3 + 2] = R[2];
+          a.chi2[h] = c2;
+        }
         // the outward filter takes cluster c
 #pragma unroll
         for (int q = 0; q < 5; ++q) O.p[q] = po[q];
@@ -281,25 +379,35 @@ __global__ void __launch_bounds__(WARPS * 32, 1) smooth_kernel(const __grid_cons
         float chi_unused = 0.0f;
         scalar_update<0>(G, O.p, O.L, chi_unused, 0.0f);
         scalar_update<1>(G, O.p, O.L, chi_unused, 0.0f);
+        if (STATES) {  // the outward filtered state at c with the inward prediction
+          float xs[5], Cs[15];
+          smooth_state(O.p, O.L, pi, SI.L, xs, Cs);
+          xs[0] = xs[0] + m0;  // residual coordinates back to positions
+          xs[1] = xs[1] + m1;
+#pragma unroll
+          for (int q = 0; q < 5; ++q) a.state[(int64_t)h * 5 + q] = xs[q];
+#pragma unroll
+          for (int q = 0; q < 15; ++q) a.state_cov[(int64_t)h * 15 + q] = Cs[q];
+        }
       }
     }
   }
 }
 
 #ifndef __CUDACC_RTC__
-template <int WARPS, bool MAT>
+template <int WARPS, bool MAT, bool STATES>
 cudaError_t smooth_grid(int& grid) {
   static int cached = 0;
   if (cached == 0) {
     const size_t smem = smooth_smem_bytes<WARPS>();
     cudaError_t e =
-        cudaFuncSetAttribute(smooth_kernel<WARPS, MAT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        cudaFuncSetAttribute(smooth_kernel<WARPS, MAT, STATES>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     int dev = 0, sms = 0, per_sm = 0;
     e = cudaGetDevice(&dev);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     if (e == cudaSuccess)
-      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, smooth_kernel<WARPS, MAT>, WARPS * 32, smem);
+      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, smooth_kernel<WARPS, MAT, STATES>, WARPS * 32, smem);
     if (e != cudaSuccess) return e;
     if (per_sm < 1) return cudaErrorInvalidConfiguration;
     cached = sms * per_sm;
@@ -312,30 +420,35 @@ constexpr int kSmoothWarps = 8;
 
 // Segment store (float4 count) the smoother needs (the larger of its variants).
 inline cudaError_t smooth_store(int64_t& float4s) {
-  int g0 = 0, g1 = 0;
-  cudaError_t e = smooth_grid<kSmoothWarps, false>(g0);
-  if (e == cudaSuccess) e = smooth_grid<kSmoothWarps, true>(g1);
-  float4s = (int64_t)(g0 > g1 ? g0 : g1) * kSmoothWarps * kCkptEvery * kStateF4 * kWarp;
+  int g[4] = {0, 0, 0, 0};
+  cudaError_t e = smooth_grid<kSmoothWarps, false, false>(g[0]);
+  if (e == cudaSuccess) e = smooth_grid<kSmoothWarps, true, false>(g[1]);
+  if (e == cudaSuccess) e = smooth_grid<kSmoothWarps, false, true>(g[2]);
+  if (e == cudaSuccess) e = smooth_grid<kSmoothWarps, true, true>(g[3]);
+  int gm = 0;
+  for (int i = 0; i < 4; ++i) gm = g[i] > gm ? g[i] : gm;
+  float4s = (int64_t)gm * kSmoothWarps * kCkptEvery * kStateF4 * kWarp;
   return e;
 }
 
-template <bool MAT>
+template <bool MAT, bool STATES>
 cudaError_t launch_smooth_cfg(const SmoothArgs& a, cudaStream_t s) {
   int grid = 0;
-  cudaError_t e = smooth_grid<kSmoothWarps, MAT>(grid);
+  cudaError_t e = smooth_grid<kSmoothWarps, MAT, STATES>(grid);
   if (e != cudaSuccess) return e;
   const int64_t chunks = ((int64_t)a.n_tracks + kWarp - 1) / kWarp;
   const int64_t need = (chunks + kSmoothWarps - 1) / kSmoothWarps;
   const int blocks = (int)(need < grid ? need : grid);
   e = cudaMemsetAsync(a.work, 0, sizeof(unsigned int), s);
   if (e != cudaSuccess) return e;
-  smooth_kernel<kSmoothWarps, MAT><<<blocks, kSmoothWarps * 32, smooth_smem_bytes<kSmoothWarps>(), s>>>(a);
+  smooth_kernel<kSmoothWarps, MAT, STATES><<<blocks, kSmoothWarps * 32, smooth_smem_bytes<kSmoothWarps>(), s>>>(a);
   return cudaGetLastError();
 }
 
 inline cudaError_t launch_smooth(const SmoothArgs& a, cudaStream_t s) {
   if (a.n_tracks <= 0) return cudaSuccess;
-  return a.mat ? launch_smooth_cfg<true>(a, s) : launch_smooth_cfg<false>(a, s);
+  if (a.state) return a.mat ? launch_smooth_cfg<true, true>(a, s) : launch_smooth_cfg<false, true>(a, s);
+  return a.mat ? launch_smooth_cfg<true, false>(a, s) : launch_smooth_cfg<false, false>(a, s);
 }
 #endif
 

@@ -554,13 +554,19 @@ tpcfit_status tpcfit_fit_backward(tpcfit_handle* h, const tpcfit_hits* hits, con
   return from_cuda(e);
 }
 
-tpcfit_status tpcfit_smooth(tpcfit_handle* h, const tpcfit_hits* hits, const int32_t* track_offsets, int32_t n_tracks,
-                            const int32_t* ndf, float* resid, float* rcov, float* chi2, void* stream) {
+namespace {
+// The smoother of the recorded fit: the leave-one-out outputs (resid, rcov,
+// chi2) and / or the smoothed states (state, state_cov); null pointers skip.
+tpcfit_status run_smooth(tpcfit_handle* h, const tpcfit_hits* hits, const int32_t* track_offsets, int32_t n_tracks,
+                         const int32_t* ndf, float* resid, float* rcov, float* chi2, float* state, float* state_cov,
+                         void* stream) {
   if (!h || !hits || n_tracks < 0 || hits->n_hits < 0) return TPCFIT_EINVAL;
   if (n_tracks == 0) return TPCFIT_OK;
-  if (!track_offsets || !ndf || !resid || !rcov || !chi2) return TPCFIT_EINVAL;
+  if (!track_offsets || !ndf) return TPCFIT_EINVAL;
   if (hits->n_hits > 0 && (!hits->y || !hits->z || !hits->rowsec)) return TPCFIT_EINVAL;
-  if (!aligned(resid, 8) || !aligned(rcov, 4) || !aligned(chi2, 4) || !aligned(ndf, 4)) return TPCFIT_EINVAL;
+  if (!aligned(ndf, 4) || (resid && (!aligned(resid, 8) || !aligned(rcov, 4) || !aligned(chi2, 4))) ||
+      (state && (!aligned(state, 4) || !aligned(state_cov, 4))))
+    return TPCFIT_EINVAL;
   if (!h->rec_valid || h->rec_tracks != n_tracks || h->rec_hits != hits->n_hits ||
       h->rec_det != h->deterministic)
     return TPCFIT_ESTATE;
@@ -583,6 +589,8 @@ tpcfit_status tpcfit_smooth(tpcfit_handle* h, const tpcfit_hits* hits, const int
   a.resid = resid;
   a.rcov = rcov;
   a.chi2 = chi2;
+  a.state = state;
+  a.state_cov = state_cov;
   a.work = h->d_work;
   a.mat = h->geo.mat;
   int64_t need = 0;
@@ -593,6 +601,20 @@ tpcfit_status tpcfit_smooth(tpcfit_handle* h, const tpcfit_hits* hits, const int
   a.seg = h->d_seg;
   e = h->deterministic ? launch_smooth_det(a, s) : launch_smooth_fast(a, s);
   return from_cuda(e);
+}
+}  // namespace
+
+tpcfit_status tpcfit_smooth(tpcfit_handle* h, const tpcfit_hits* hits, const int32_t* track_offsets, int32_t n_tracks,
+                            const int32_t* ndf, float* resid, float* rcov, float* chi2, void* stream) {
+  if (n_tracks > 0 && (!resid || !rcov || !chi2)) return TPCFIT_EINVAL;
+  return run_smooth(h, hits, track_offsets, n_tracks, ndf, resid, rcov, chi2, nullptr, nullptr, stream);
+}
+
+tpcfit_status tpcfit_smooth_states(tpcfit_handle* h, const tpcfit_hits* hits, const int32_t* track_offsets,
+                                   int32_t n_tracks, const int32_t* ndf, float* state, float* state_cov,
+                                   void* stream) {
+  if (n_tracks > 0 && (!state || !state_cov)) return TPCFIT_EINVAL;
+  return run_smooth(h, hits, track_offsets, n_tracks, ndf, nullptr, nullptr, nullptr, state, state_cov, stream);
 }
 
 tpcfit_status tpcfit_fit_host(tpcfit_handle* h, const float* y, const float* z, const uint16_t* rowsec,

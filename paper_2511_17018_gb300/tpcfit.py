@@ -64,6 +64,7 @@ def load():
                                         vp]),
         "tpcfit_fit_backward": (C.c_int, [vp, C.POINTER(_Hits), vp, i32, vp, vp, vp, vp, vp, vp]),
         "tpcfit_smooth": (C.c_int, [vp, C.POINTER(_Hits), vp, i32, vp, vp, vp, vp, vp]),
+        "tpcfit_smooth_states": (C.c_int, [vp, C.POINTER(_Hits), vp, i32, vp, vp, vp, vp]),
         "tpcfit_set_material": (C.c_int, [vp, C.c_double, C.c_double, C.c_double, C.c_double]),
         "tpcfit_set_field_map": (C.c_int, [vp, C.c_double, C.c_double]),
         "tpcfit_set_rtc": (C.c_int, [vp, C.c_int, C.c_char_p]),
@@ -294,6 +295,21 @@ def tpcfit_smooth(h, y, z, rowsec, offsets, ndf, resid, rcov, chi2, stream=None)
     _check(st, "tpcfit_smooth")
 
 
+def tpcfit_smooth_states(h, y, z, rowsec, offsets, ndf, state, state_cov, stream=None) -> None:
+    """Enqueue the smoothed states of the last recorded fit (device tensors; see include/tpcfit.h)."""
+    import torch
+    n = int(offsets.numel()) - 1
+    H = int(y.numel())
+    hits = _Hits(_dev(y, torch.float32, "y"), _dev(z, torch.float32, "z"), _dev(rowsec, torch.int16, "rowsec"), H)
+    if state.numel() != 5 * H or state_cov.numel() != 15 * H:
+        raise ValueError("smoothed-state output sizes do not match the clusters")
+    _check_sizes(n, y, z, rowsec, ndf=ndf)
+    st = load().tpcfit_smooth_states(h, C.byref(hits), _dev(offsets, torch.int32, "offsets"), n,
+                                     _dev(ndf, torch.int32, "ndf"), _dev(state, torch.float32, "state"),
+                                     _dev(state_cov, torch.float32, "state_cov"), _stream(stream))
+    _check(st, "tpcfit_smooth_states")
+
+
 def tpcfit_fit_host(h, y, z, rowsec, offsets, seeds, stream=None, out=None):
     """Fit from host arrays (numpy or pinned CPU tensors); returns host outputs."""
     def arr(a, dt):
@@ -469,6 +485,17 @@ class Fitter:
                    chi2=torch.empty(H, dtype=torch.float32, device=d))
         tpcfit_smooth(self.h, dev["y"], dev["z"], dev["rowsec"], dev["offsets"], out["ndf"], res["resid"], res["rcov"],
                       res["chi2"], stream)
+        return res
+
+    def smooth_states(self, dev: dict, out: dict, stream=None) -> dict:
+        """Smoothed state and covariance at every cluster of the last recorded fit."""
+        import torch
+        H = int(dev["y"].numel())
+        d = dev["y"].device
+        res = dict(state=torch.empty((H, 5), dtype=torch.float32, device=d),
+                   state_cov=torch.empty((H, 15), dtype=torch.float32, device=d))
+        tpcfit_smooth_states(self.h, dev["y"], dev["z"], dev["rowsec"], dev["offsets"], out["ndf"], res["state"],
+                             res["state_cov"], stream)
         return res
 
     def backward(self, dev: dict, out: dict, grad_chi2, grad_meas=None, stream=None):

@@ -4,7 +4,9 @@ Per cluster the leave-one-out residual, its covariance and chi2 agree with the
 oracle's information-form combination within the FP32 tolerance below (the
 same FP32-vs-FP64 rounding argument as for the fit: residuals of ~0.1 cm
 carried through ~150 steps); the deterministic mode repeats bit for bit; a
-displaced cluster is flagged."""
+displaced cluster is flagged.  The smoothed state and covariance at every
+cluster agree with the oracle's two-filter combination, and at the first
+cluster equal the kernel's own fit output combined with the seed prior."""
 import numpy as np
 import pytest
 
@@ -104,3 +106,97 @@ def test_smoother_needs_a_recorded_fit():
         assert e.value.status == tf.ESTATE
     finally:
         f.close()
+
+
+def _states(fr, det, align=None, material=None):
+    dev = tf.frame_to_device(fr)
+    f = tf.Fitter(fr.geometry, fr.bz, deterministic=det)
+    try:
+        f.set_material(material)
+        if align is not None:
+            f.set_alignment(torch.from_numpy(align).cuda())
+        f.set_record(True)
+        out = f.fit(dev)
+        sm = f.smooth_states(dev, out)
+        again = f.smooth_states(dev, out)
+        torch.cuda.synchronize()
+        return ({k: v.cpu().numpy() for k, v in sm.items()}, {k: v.cpu().numpy() for k, v in again.items()})
+    finally:
+        f.close()
+
+
+def compare_states(got, ref):
+    """Smoothed states relative to max(|x_i|, sqrt(C_ii)) of the FP64 result
+    (the reading of the fit's tolerance: y, z, sin phi and tan lambda cross
+    zero), their covariances relative to sqrt(C_ii C_jj); NaN patterns must
+    agree on all but a few clusters."""
+    okr, okg = np.all(np.isfinite(ref["state"]), axis=1), np.all(np.isfinite(got["state"]), axis=1)
+    both = okr & okg
+    C = ref["state_cov"][both]
+    sig = np.sqrt(C[:, [0, 2, 5, 9, 14]])
+    x = ref["state"][both]
+    ds = (np.abs(got["state"][both] - x) / np.maximum(np.abs(x), sig)).max(axis=1)
+    pk = [(i, j) for i in range(5) for j in range(i + 1)]
+    den = np.stack([sig[:, i] * sig[:, j] for i, j in pk], axis=1)
+    dc = (np.abs(got["state_cov"][both] - C) / den).max(axis=1)
+    return dict(nan_agree=float(np.mean(okr == okg)), n=int(both.sum()), state_ok=float(np.mean(ds < 1e-4)),
+                state_max=float(ds.max()), cov_ok=float(np.mean(dc < 1e-3)), cov_max=float(dc.max()))
+
+
+@pytest.mark.parametrize("det", [False, True])
+def test_smoothed_states_match_fp64_oracle(det):
+    # the state at every cluster from all clusters of its track, against the
+    # oracle's information-form combination of the outward filtered state and
+    # the inward prediction; the deterministic mode repeats bit for bit
+    d = synth.alignment_offsets(3)
+    fr = synth.generate(8000, 13, drop_p=0.05, cap_lengths=True, d_true=d)
+    got, again = _states(fr, det, align=d)
+    ref = oracle.smooth_states(fr, align=d)
+    rep = compare_states(got, ref)
+    print(rep)
+    assert rep["nan_agree"] > 0.9999 and rep["n"] > 0.99 * fr.n_hits, rep
+    assert rep["state_ok"] > 0.999 and rep["cov_ok"] > 0.98, rep
+    assert rep["state_max"] < 5e-3 and rep["cov_max"] < 0.1, rep
+    if det:
+        for k in got:
+            assert np.array_equal(got[k].view(np.int32), again[k].view(np.int32))
+
+
+def test_smoothed_states_with_material():
+    fr = synth.generate(4000, 14, drop_p=0.05, cap_lengths=True)
+    fr.material = synth.TPC_GAS
+    got, _ = _states(fr, False, material=synth.TPC_GAS)
+    rep = compare_states(got, oracle.smooth_states(fr))
+    print(rep)
+    assert rep["nan_agree"] > 0.9999 and rep["state_ok"] > 0.999 and rep["cov_ok"] > 0.98, rep
+
+
+def test_smoothed_state_at_the_first_cluster_is_the_fit_with_the_seed_prior():
+    # at the first cluster the smoothed state holds every cluster and the
+    # outward pass's seed prior (seed, 100 I): the kernel's own fit output
+    # combined with that prior in information form, up to FP32 rounding
+    fr = synth.generate(2000, 15, drop_p=0.05, cap_lengths=True)
+    dev = tf.frame_to_device(fr)
+    f = tf.Fitter(fr.geometry, fr.bz)
+    try:
+        f.set_record(True)
+        out = f.fit(dev)
+        sm = f.smooth_states(dev, out)
+        torch.cuda.synchronize()
+        st = sm["state"].cpu().numpy().astype(np.float64)
+        params = out["params"].cpu().numpy().astype(np.float64)
+        cov = out["cov"].cpu().numpy().astype(np.float64)
+        ndf = out["ndf"].cpu().numpy()
+    finally:
+        f.close()
+    ok = ndf > 0
+    assert ok.mean() > 0.95
+    first = fr.offsets[:-1][ok]
+    If = np.linalg.inv(np.moveaxis(oracle.unpack(cov[:, ok]), -1, 0))
+    Cs = np.linalg.inv(If + np.eye(5) / 100.0)
+    xs = np.einsum("nij,nj->ni", Cs, np.einsum("nij,nj->ni", If, params[:, ok].T)
+                   + fr.seeds[:, ok].T.astype(np.float64) / 100.0)
+    sig = np.sqrt(np.einsum("nii->ni", Cs))
+    d = np.abs(st[first] - xs) / np.maximum(np.abs(xs), sig)
+    print(np.nanquantile(d, 0.999), np.nanmax(d))
+    assert np.quantile(d, 0.999) < 1e-4 and np.max(d) < 1e-3, (np.quantile(d, 0.999), np.max(d))

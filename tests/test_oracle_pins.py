@@ -324,6 +324,62 @@ def test_smoother_equals_leave_one_out_least_squares(oracle_mod, synth):
     assert checked == lens.sum()
 
 
+def test_smoothed_states_equal_least_squares(oracle_mod, synth):
+    # Linearised about the exact trajectory: the smoothed state at every
+    # cluster (all clusters of the track, both passes' priors) equals the
+    # dense weighted least-squares solve mapped to that cluster, and its
+    # covariance the solve's covariance mapped there.
+    fr, lens = _short_tracks(synth, 12)
+    ref = truth_trajectory(oracle_mod, fr)
+    s = oracle_mod.smooth_states(fr, ref=ref, exact_inputs=True)
+    r = oracle_mod.fit(fr, "f64", ref=ref, trace=True, exact_inputs=True)
+    m = np.stack([fr.y64, fr.z64], axis=1)
+    H = np.zeros((2, 5)); H[0, 0] = 1; H[1, 1] = 1
+    checked = 0
+    for i in range(fr.n_tracks):
+        order, A, bb = _affine_chain(oracle_mod, fr, ref, i, backward=False)
+        p_out = r["trace"][order[-1], 0, :5]
+        N = np.eye(5) / 100.0 + A[-1].T @ A[-1] / 100.0
+        rhs = fr.seeds64[:, i] / 100.0 + A[-1].T @ (p_out - bb[-1]) / 100.0
+        for kk, j in enumerate(order):
+            HA = H @ A[kk]
+            N += HA.T @ HA / 0.01
+            rhs += HA.T @ (m[j] - H @ bb[kk]) / 0.01
+        x0 = np.linalg.solve(N, rhs)
+        P = np.linalg.inv(N)
+        for k, h in enumerate(order):
+            xc = A[k] @ x0 + bb[k]
+            Pc = A[k] @ P @ A[k].T
+            assert np.allclose(s["state"][h], xc, rtol=1e-8, atol=1e-10)
+            assert np.allclose(oracle_mod.unpack(s["state_cov"][h]), Pc, rtol=1e-7, atol=1e-14)
+            checked += 1
+    assert checked == lens.sum()
+
+
+def test_smoothed_state_at_the_first_cluster_is_the_fit_with_the_seed_prior(oracle_mod, synth):
+    # At the first cluster the outward pass holds only the seed prior (seed,
+    # c0 I) and that cluster; the inward pass's prediction there holds every
+    # other cluster, so with the linear (y, z) measurement the smoothed state
+    # is the inward refit's output combined, in information form, with the
+    # seed prior — on the real, non-linearised fit of full-length tracks.
+    fr = synth.generate(400, 15, drop_p=0.05, cap_lengths=True)
+    s = oracle_mod.smooth_states(fr)
+    r = oracle_mod.fit(fr, "f64")
+    ok = r["ndf"] > 0
+    assert ok.mean() > 0.95
+    first = fr.offsets[:-1][ok]
+    If = np.linalg.inv(np.moveaxis(oracle_mod.unpack(r["cov"][:, ok]), -1, 0))
+    Cs = np.linalg.inv(If + np.eye(5) / 100.0)
+    xs = np.einsum("nij,nj->ni", Cs, np.einsum("nij,nj->ni", If, r["params"][:, ok].T) + fr.seeds[:, ok].T / 100.0)
+    sig = np.sqrt(np.einsum("nii->ni", Cs))
+    assert np.max(np.abs(s["state"][first] - xs) / np.maximum(np.abs(xs), sig)) < 1e-7
+    Cg = np.moveaxis(oracle_mod.unpack(s["state_cov"][first].T), -1, 0)
+    assert np.max(np.abs(Cg - Cs) / np.sqrt(np.einsum("nii->ni", Cs)[:, :, None] * np.einsum("nii->ni", Cs)[:, None, :])) < 1e-7
+    # the seed prior matters for the short, poorly measured tracks only
+    moved = np.abs(xs - r["params"][:, ok].T) / sig
+    assert np.median(moved) < 1e-2
+
+
 def test_smoother_flags_a_displaced_cluster(oracle_mod, synth):
     # a cluster moved by 1 cm (10 sigma) stands out: the largest chi2 of its
     # track, far beyond the 2-dof tail; the rest follow the 2-dof distribution
@@ -779,3 +835,21 @@ def test_fp32_dual_gradient_follows_the_strict_fp32_fit(oracle_mod, synth):
     scale = np.maximum(np.abs(b), 1e-3 * np.abs(b).max())
     assert np.quantile(np.abs(a - b) / scale, 0.99) < 2e-3
     assert np.linalg.norm(g32["grad_seed"] - g64["grad_seed"]) < 3e-4 * np.linalg.norm(g64["grad_seed"])
+
+
+@pytest.mark.parametrize("phys", ["field", "gas", "field+gas"])
+def test_fp32_dual_follows_the_strict_fp32_fit_with_physics(oracle_mod, synth, phys):
+    # the FP32-valued dual through the field map and the material layers: its
+    # chi2 is bit for bit the strict-FP32 fit's, its gradient within the FP32
+    # floor of the FP64 gradient
+    fr = synth.generate(60, 31, drop_p=0.05, cap_lengths=True)
+    fr.field = synth.FieldMap(0.3, -0.2) if "field" in phys else None
+    fr.material = synth.TPC_GAS if "gas" in phys else None
+    g32 = oracle_mod.grad(fr, precision="f32")
+    g64 = oracle_mod.grad(fr)
+    f32 = oracle_mod.fit(fr, "f32")
+    ok = f32["ndf"] > 0
+    assert ok.all() and np.array_equal(g32["ndf"], f32["ndf"])
+    assert np.array_equal(g32["chi2"][ok].astype(np.float32).view(np.int32), f32["chi2"][ok].view(np.int32))
+    a, b = g32["grad_meas"], g64["grad_meas"]
+    assert np.linalg.norm(a - b) / np.linalg.norm(b) < 3e-4
