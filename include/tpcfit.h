@@ -228,6 +228,17 @@ tpcfit_status tpcfit_set_record(tpcfit_handle* h, int record);
  * Results do not depend on it.  EINVAL for other values. */
 tpcfit_status tpcfit_set_backward_config(tpcfit_handle* h, int warps_per_block);
 
+/* Factor of the covariance that the fast backward without material layers
+ * recomputes its segments in: 1 = U-D (C = U D U^T, U unit upper triangular,
+ * Bierman's measurement updates; default), 0 = the fit's square-root factor
+ * (C = L L^T, Potter's updates).  Both give the gradient of the same fit; they
+ * differ in FP32 rounding and speed (U-D: 15 factor entries instead of 25, 6
+ * float4 per stored state instead of 8).  The paper prescribes no factor for
+ * the adjoint; this is an implementation choice.  The deterministic mode and
+ * the material layers always take the square-root factor.  EINVAL for other
+ * values. */
+tpcfit_status tpcfit_set_backward_form(tpcfit_handle* h, int form);
+
 /* Adjoint of the recorded fit: gradients of L = sum_i grad_chi2[i] * chi2_i.
  * Inputs must be those of the last tpcfit_fit on this handle, which must have
  * run with recording on and in the same mode (otherwise ESTATE):
@@ -241,7 +252,8 @@ tpcfit_status tpcfit_set_backward_config(tpcfit_handle* h, int warps_per_block);
  * The backward recomputes each 16-step segment from its checkpoint and runs
  * the hand-written reverse of every step, copying the state before each step
  * into shared memory one step ahead.  Fast mode without material layers
- * recomputes into a per-warp segment store in the same kernel; the
+ * recomputes into a per-warp segment store in the same kernel, in the factor
+ * form tpcfit_set_backward_form chose; the
  * deterministic mode and the material layers replay the segments in a kernel
  * of their own onto a tape of every step's state (about 40 MB per 1,000
  * tracks, handle-owned, grown as needed) and reverse from it.  It follows the

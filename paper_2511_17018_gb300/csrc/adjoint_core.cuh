@@ -485,11 +485,12 @@ __device__ __forceinline__ void cp_async16(void* smem_dst, const void* gmem_src)
   asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(d), "l"(gmem_src) : "memory");
 }
 
-// One lane's state: 8 float4 from a lane-interleaved global slot into its
+// One lane's state: F4 float4 from a lane-interleaved global slot into its
 // lane-interleaved shared slot, as one commit group.
+template <int F4 = kStateF4>
 __device__ __forceinline__ void fetch_state(float4* sdst, const float4* gsrc) {
 #pragma unroll
-  for (int j = 0; j < kStateF4; ++j) cp_async16(sdst + j * kWarp, gsrc + j * kWarp);
+  for (int j = 0; j < F4; ++j) cp_async16(sdst + j * kWarp, gsrc + j * kWarp);
   cp_async_commit();
 }
 
@@ -885,6 +886,14 @@ __device__ __forceinline__ void step_rev_mat(const GeoRef& G, const SmemTables& 
   for (int c = 0; c < 5; ++c) b_p[c] = b_pi[c];
 }
 
+}  // namespace TPCFIT_NS
+}  // namespace tpcfit
+
+#include "ud_core.cuh"
+
+namespace tpcfit {
+namespace TPCFIT_NS {
+
 // Fire-and-forget global float add (no value returned, nothing to wait for).
 __device__ __forceinline__ void red_add(float* p, float v) {
   asm volatile("red.global.add.f32 [%0], %1;\n" ::"l"(__cvta_generic_to_global(p)), "f"(v) : "memory");
@@ -932,12 +941,17 @@ constexpr size_t backward_smem_bytes() {
 // first, each state copied into shared memory asynchronously one step ahead.
 // Clusters are loaded one step ahead as well; the next segment's checkpoint
 // is copied while the current segment is reversed.
-// PHYS: bit 1 the material layers, bit 2 the field map.
-template <int WARPS, int PHYS>
+// PHYS: bit 1 the material layers, bit 2 the field map.  FORM: the factor the
+// segments are recomputed in, 0 the fit's square-root factor L, 1 U-D (no
+// material layers; the checkpoint's L is converted where a segment starts).
+template <int WARPS, int PHYS, int FORM = 0>
 __global__ void __launch_bounds__(WARPS * 32, 1) backward_kernel(const __grid_constant__ BwdArgs a) {
   const GeoRef& G = a.geo;
   constexpr bool MAT = (PHYS & 1) != 0;
   constexpr int FIELD = (PHYS & 2) ? 1 : 0;
+  static_assert(FORM == 0 || !MAT, "the U-D backward runs without material layers");
+  constexpr int F4 = FORM ? kUDStateF4 : kStateF4;
+  using State = typename std::conditional<FORM == 1, UDState, StepState>::type;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   BwdSmem& B = *reinterpret_cast<BwdSmem*>(smem_raw);
   load_tables(G, B.T);
@@ -948,7 +962,7 @@ __global__ void __launch_bounds__(WARPS * 32, 1) backward_kernel(const __grid_co
   const int warp = threadIdx.x >> 5;
   BwdWarpBufs& W = reinterpret_cast<BwdWarpBufs*>(smem_raw + sizeof(BwdSmem))[warp];
   // this warp's segment store: [step kk][float4 j][lane]
-  float4* const gs = a.seg + ((int64_t)blockIdx.x * WARPS + warp) * (kCkptEvery * kStateF4 * kWarp) + lane;
+  float4* const gs = a.seg + ((int64_t)blockIdx.x * WARPS + warp) * (kCkptEvery * F4 * kWarp) + lane;
   const int64_t n_chunks = ((int64_t)a.n_tracks + kWarp - 1) / kWarp;
   const int64_t N = a.n_tracks;
 #pragma unroll 1
@@ -966,13 +980,18 @@ __global__ void __launch_bounds__(WARPS * 32, 1) backward_kernel(const __grid_co
     if (fitted) {
       const int begin = a.off[trk];
       const int last = a.ck_last[trk];
-      float b_L[5][5];
+      float b_L[5][5];         // FORM 0: adjoint of the square-root factor
+      float b_u[10], b_d[5];   // FORM 1: adjoint of the U-D factor
 #pragma unroll 1
       for (int pass = 1; pass >= 0; --pass) {
 #pragma unroll
         for (int i = 0; i < 5; ++i)
 #pragma unroll
           for (int c = 0; c < 5; ++c) b_L[i][c] = 0.0f;
+#pragma unroll
+        for (int e = 0; e < 10; ++e) b_u[e] = 0.0f;
+#pragma unroll
+        for (int c = 0; c < 5; ++c) b_d[c] = 0.0f;
         const float b_chi = pass == 1 ? g : 0.0f;
         const int steps = last + 1;
         const int nseg = (steps + kCkptEvery - 1) / kCkptEvery;
@@ -997,7 +1016,7 @@ __global__ void __launch_bounds__(WARPS * 32, 1) backward_kernel(const __grid_co
         for (int s = nseg - 1; s >= 0; --s) {
           const int i0 = s * kCkptEvery;
           const int cnt = min(kCkptEvery, steps - i0);
-          StepState S;
+          State S;
           float my = 0.0f, mz = 0.0f;
           HitRaw nx = seg_first;
           if (i0 > 0) {
@@ -1005,7 +1024,13 @@ __global__ void __launch_bounds__(WARPS * 32, 1) backward_kernel(const __grid_co
             decode_hit(B.align, seg_prev, my, mz, row, sec);
           }
           cp_async_wait<0>();
-          read_state(&W.ck[0][lane], S);
+          if constexpr (FORM == 1) {
+            StepState C;
+            read_state(&W.ck[0][lane], C);
+            ud_state_from(C, S);
+          } else {
+            read_state(&W.ck[0][lane], S);
+          }
           // level 1: the segment, storing the state before each step
           float m0 = 0.0f, m1 = 0.0f;
           int row = 0, sec = 0;
@@ -1015,8 +1040,11 @@ __global__ void __launch_bounds__(WARPS * 32, 1) backward_kernel(const __grid_co
             const HitRaw cur = nx;
             if (kk + 1 < cnt) nx = load_hit(a, h0 + hd * (i + 1));
             decode_hit(B.align, cur, m0, m1, row, sec);
-            store_state(gs + kk * (kStateF4 * kWarp), S);
-            step_fwd<MAT, FIELD>(G, T, S, my, mz, i == 0, pass == 0, row, side_sector(sec), m0, m1);
+            store_state(gs + kk * (F4 * kWarp), S);
+            if constexpr (FORM == 1)
+              step_fwd_ud<FIELD>(G, T, S, my, mz, i == 0, pass == 0, row, side_sector(sec), m0, m1);
+            else
+              step_fwd<MAT, FIELD>(G, T, S, my, mz, i == 0, pass == 0, row, side_sector(sec), m0, m1);
           }
           // the states just stored are read back by this thread's copies below
           __threadfence_block();
@@ -1025,7 +1053,7 @@ __global__ void __launch_bounds__(WARPS * 32, 1) backward_kernel(const __grid_co
           // reverse; (m0, m1, row, sec) hold the segment's last cluster, which is
           // the current cluster of its last step; each step's previous cluster
           // becomes the current one of the step before it
-          fetch_state(&W.st[(cnt - 1) & 1][0][lane], gs + (cnt - 1) * (kStateF4 * kWarp));
+          fetch_state<F4>(&W.st[(cnt - 1) & 1][0][lane], gs + (cnt - 1) * (F4 * kWarp));
           // (in later segments the reverse of the segment after this one left
           // this cluster in pv)
           if (s == nseg - 1 && i0 + cnt - 1 > 0) pv = load_hit(a, h0 + hd * (i0 + cnt - 2));
@@ -1038,7 +1066,7 @@ __global__ void __launch_bounds__(WARPS * 32, 1) backward_kernel(const __grid_co
             const int i = i0 + kk;
             const int h = h0 + hd * i;
             if (kk > 0) {
-              fetch_state(&W.st[(kk - 1) & 1][0][lane], gs + (kk - 1) * (kStateF4 * kWarp));
+              fetch_state<F4>(&W.st[(kk - 1) & 1][0][lane], gs + (kk - 1) * (F4 * kWarp));
               cp_async_wait<1>();
             } else {
               cp_async_wait<0>();
@@ -1053,7 +1081,10 @@ __global__ void __launch_bounds__(WARPS * 32, 1) backward_kernel(const __grid_co
             const float2 gcur = gnx;
             if (addg && i > 0) gnx = gmr[h - hd];
             float b_mc[2], b_mp[2];
-            if (MAT)
+            if constexpr (FORM == 1)
+              step_rev_ud<FIELD>(G, T, &W.st[kk & 1][0][lane], mpy, mpz, i == 0, pass == 0, row, side_sector(sec), m0,
+                                 m1, b_p, b_u, b_d, b_chi, b_mc, b_mp);
+            else if (MAT)
               step_rev_mat<FIELD>(G, T, &W.st[kk & 1][0][lane], mpy, mpz, i == 0, pass == 0, row, side_sector(sec), m0, m1,
                                   b_p, b_L, b_chi, b_mc, b_mp);
             else
@@ -1202,13 +1233,18 @@ __global__ void __launch_bounds__(WARPS * 32, 1) tape_reverse_kernel(const __gri
     const int begin = fitted ? a.off[trk] : 0;
     const int last = fitted ? a.ck_last[trk] : 0;
     if (fitted && last + 1 <= kTapeSteps) {
-      float b_L[5][5];
+      float b_L[5][5];         // FORM 0: adjoint of the square-root factor
+      float b_u[10], b_d[5];   // FORM 1: adjoint of the U-D factor
 #pragma unroll 1
       for (int pass = 1; pass >= 0; --pass) {
 #pragma unroll
         for (int i = 0; i < 5; ++i)
 #pragma unroll
           for (int c = 0; c < 5; ++c) b_L[i][c] = 0.0f;
+#pragma unroll
+        for (int e = 0; e < 10; ++e) b_u[e] = 0.0f;
+#pragma unroll
+        for (int c = 0; c < 5; ++c) b_d[c] = 0.0f;
         const float b_chi = pass == 1 ? g : 0.0f;
         const int steps = last + 1;
         const int h0 = pass == 0 ? begin : begin + last;
@@ -1308,20 +1344,20 @@ cudaError_t launch_tape_backward_cfg(const BwdArgs& a, cudaStream_t s) {
 }
 
 // Persistent grid of the backward (blocks resident at once over all SMs).
-template <int WARPS, int PHYS>
+template <int WARPS, int PHYS, int FORM>
 cudaError_t backward_grid(int& grid) {
   static int cached = 0;
   if (cached == 0) {
     constexpr int kThreads = WARPS * 32;
     const size_t smem = backward_smem_bytes<WARPS>();
-    cudaError_t e =
-        cudaFuncSetAttribute(backward_kernel<WARPS, PHYS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e = cudaFuncSetAttribute(backward_kernel<WARPS, PHYS, FORM>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     int dev = 0, sms = 0, per_sm = 0;
     e = cudaGetDevice(&dev);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     if (e == cudaSuccess)
-      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, backward_kernel<WARPS, PHYS>, kThreads, smem);
+      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, backward_kernel<WARPS, PHYS, FORM>, kThreads, smem);
     if (e != cudaSuccess) return e;
     if (per_sm < 1) return cudaErrorInvalidConfiguration;
     cached = sms * per_sm;
@@ -1330,25 +1366,25 @@ cudaError_t backward_grid(int& grid) {
   return cudaSuccess;
 }
 
-template <int WARPS, int PHYS>
+template <int WARPS, int PHYS, int FORM>
 cudaError_t backward_store_cfg(int64_t& float4s) {
   int grid = 0;
-  cudaError_t e = backward_grid<WARPS, PHYS>(grid);
-  float4s = (int64_t)grid * WARPS * kCkptEvery * kStateF4 * kWarp;
+  cudaError_t e = backward_grid<WARPS, PHYS, FORM>(grid);
+  float4s = (int64_t)grid * WARPS * kCkptEvery * (FORM ? kUDStateF4 : kStateF4) * kWarp;
   return e;
 }
 
-template <int WARPS, int PHYS>
+template <int WARPS, int PHYS, int FORM>
 cudaError_t launch_backward_cfg(const BwdArgs& a, cudaStream_t s) {
   int grid = 0;
-  cudaError_t e = backward_grid<WARPS, PHYS>(grid);
+  cudaError_t e = backward_grid<WARPS, PHYS, FORM>(grid);
   if (e != cudaSuccess) return e;
   const int64_t chunks = ((int64_t)a.n_tracks + kWarp - 1) / kWarp;
   const int64_t need = (chunks + WARPS - 1) / WARPS;
   const int blocks = (int)(need < grid ? need : grid);
   e = cudaMemsetAsync(a.work, 0, sizeof(unsigned int), s);
   if (e != cudaSuccess) return e;
-  backward_kernel<WARPS, PHYS><<<blocks, WARPS * 32, backward_smem_bytes<WARPS>(), s>>>(a);
+  backward_kernel<WARPS, PHYS, FORM><<<blocks, WARPS * 32, backward_smem_bytes<WARPS>(), s>>>(a);
   return cudaGetLastError();
 }
 
@@ -1356,21 +1392,48 @@ cudaError_t launch_backward_cfg(const BwdArgs& a, cudaStream_t s) {
 // field without material; the other physics run in the 8-warp shape only.
 inline int backward_warps(int warps, int phys) { return phys ? 8 : warps; }
 
-// Segment store (float4 count) the backward needs for `warps` warps per block
-// and the physics bits phys (1: material layers, 2: the field map).
-inline cudaError_t backward_store(int warps, int phys, int64_t& float4s) {
+// One-kernel fast backward (no material layers): FORM 0 or 1 in every
+// compiled block shape, uniform field (PHYS 0) or the field map (PHYS 2, 8
+// warps).
+template <int FORM>
+cudaError_t backward_store_form(int warps, int phys, int64_t& float4s) {
   switch (phys) {
     case 0: break;
-    case 2: return backward_store_cfg<8, 2>(float4s);
+    case 2: return backward_store_cfg<8, 2, FORM>(float4s);
     default: return cudaErrorInvalidValue;
   }
   switch (warps) {
-    case 4: return backward_store_cfg<4, 0>(float4s);
-    case 8: return backward_store_cfg<8, 0>(float4s);
-    case 10: return backward_store_cfg<10, 0>(float4s);
-    case 12: return backward_store_cfg<12, 0>(float4s);
+    case 4: return backward_store_cfg<4, 0, FORM>(float4s);
+    case 8: return backward_store_cfg<8, 0, FORM>(float4s);
+    case 10: return backward_store_cfg<10, 0, FORM>(float4s);
+    case 12: return backward_store_cfg<12, 0, FORM>(float4s);
     default: return cudaErrorInvalidValue;
   }
+}
+
+template <int FORM>
+cudaError_t launch_backward_form(const BwdArgs& a, int warps, cudaStream_t s) {
+  switch (a.phys) {
+    case 0: break;
+    case 2: return launch_backward_cfg<8, 2, FORM>(a, s);
+    default: return cudaErrorInvalidValue;
+  }
+  switch (warps) {
+    case 4: return launch_backward_cfg<4, 0, FORM>(a, s);
+    case 8: return launch_backward_cfg<8, 0, FORM>(a, s);
+    case 10: return launch_backward_cfg<10, 0, FORM>(a, s);
+    case 12: return launch_backward_cfg<12, 0, FORM>(a, s);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+// Segment store (float4 count) the backward needs for `warps` warps per block,
+// the physics bits phys (1: material layers, 2: the field map) and the factor
+// form (0: square root, 1: U-D).
+inline cudaError_t backward_store(int warps, int phys, int form, int64_t& float4s) {
+  if (form == 1) return backward_store_form<1>(warps, phys, float4s);
+  if (form == 0) return backward_store_form<0>(warps, phys, float4s);
+  return cudaErrorInvalidValue;
 }
 
 // The deterministic backward always, and the fast one with material layers,
@@ -1407,18 +1470,9 @@ inline cudaError_t launch_backward(const BwdArgs& a, int warps, cudaStream_t s) 
 #if TPCFIT_DET
   return cudaErrorInvalidValue;
 #else
-  switch (a.phys) {
-    case 0: break;
-    case 2: return launch_backward_cfg<8, 2>(a, s);
-    default: return cudaErrorInvalidValue;
-  }
-  switch (warps) {
-    case 4: return launch_backward_cfg<4, 0>(a, s);
-    case 8: return launch_backward_cfg<8, 0>(a, s);
-    case 10: return launch_backward_cfg<10, 0>(a, s);
-    case 12: return launch_backward_cfg<12, 0>(a, s);
-    default: return cudaErrorInvalidValue;
-  }
+  if (a.form == 1) return launch_backward_form<1>(a, warps, s);
+  if (a.form == 0) return launch_backward_form<0>(a, warps, s);
+  return cudaErrorInvalidValue;
 #endif
 }
 

@@ -16,8 +16,8 @@ cudaError_t launch_fit_fast(const FitArgs& a, int lanes_per_track, int rows_per_
 cudaError_t launch_backward_fast(const BwdArgs& a, int warps, cudaStream_t s) {
   return fast::launch_backward(a, warps, s);
 }
-cudaError_t backward_store_fast(int warps, int phys, int64_t& float4s) {
-  return fast::backward_store(warps, phys, float4s);
+cudaError_t backward_store_fast(int warps, int phys, int form, int64_t& float4s) {
+  return fast::backward_store(warps, phys, form, float4s);
 }
 int64_t backward_tape_float4s(int64_t n_tracks) { return fast::tape_float4s(n_tracks); }
 cudaError_t launch_smooth_fast(const SmoothArgs& a, cudaStream_t s) { return fast::launch_smooth(a, s); }

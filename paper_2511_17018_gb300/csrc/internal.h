@@ -21,8 +21,9 @@ cudaError_t launch_fit_det(const FitArgs& a, int lanes_per_track, int rows_per_s
 cudaError_t launch_backward_fast(const BwdArgs& a, int warps, cudaStream_t s);
 cudaError_t launch_backward_det(const BwdArgs& a, int warps, cudaStream_t s);
 // float4 elements of the segment store a fast backward launch without material
-// with `warps` and the physics bits phys needs
-cudaError_t backward_store_fast(int warps, int phys, int64_t& float4s);
+// with `warps`, the physics bits phys and the factor form (0 square root, 1 U-D)
+// needs
+cudaError_t backward_store_fast(int warps, int phys, int form, int64_t& float4s);
 // float4 elements of the backward's tape for n_tracks tracks
 int64_t backward_tape_float4s(int64_t n_tracks);
 // the two-filter smoother of a recorded fit, and its segment store (float4s)

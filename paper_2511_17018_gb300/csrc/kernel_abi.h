@@ -113,6 +113,7 @@ struct BwdArgs {
   float4* seg;                 // segment store: [resident warps][kCkptEvery][8][32] float4
   float4* tape;                // or the tape: [2][n_hits][8] float4, the state before every step (null: segment store)
   int32_t phys;                // physics of the recorded fit: bit 1 material layers, bit 2 the field map
+  int32_t form;                // factor the fast one-kernel backward recomputes in: 0 square root (L), 1 U-D
 };
 
 // Arguments of one smoother launch (same frame as the recorded fit).

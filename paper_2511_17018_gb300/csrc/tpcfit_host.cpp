@@ -100,6 +100,7 @@ struct tpcfit_handle {
   // adjoint: checkpoints of the last recorded fit
   int record = 0;
   int bwd_warps = 8;
+  int bwd_form = 1;            // factor of the fast one-kernel backward: 1 U-D, 0 square root
   int rtc = 0;                 // fit kernels compiled at run time (Sec. 5)
   std::string rtc_dir;         // their on-disk cache, or empty
   float* d_ck = nullptr;
@@ -409,6 +410,12 @@ tpcfit_status tpcfit_set_backward_config(tpcfit_handle* h, int warps_per_block) 
   return TPCFIT_OK;
 }
 
+tpcfit_status tpcfit_set_backward_form(tpcfit_handle* h, int form) {
+  if (!h || (form != 0 && form != 1)) return TPCFIT_EINVAL;
+  h->bwd_form = form;
+  return TPCFIT_OK;
+}
+
 tpcfit_status tpcfit_set_material(tpcfit_handle* h, double x0_cm, double dedx_gev_cm, double mass_gev,
                                   double row_cm) {
   if (!h) return TPCFIT_EINVAL;
@@ -510,10 +517,11 @@ tpcfit_status tpcfit_fit_backward(tpcfit_handle* h, const tpcfit_hits* hits, con
     b.tape = h->d_tape;
   } else {
     // otherwise one kernel recomputes each segment into a per-warp segment
-    // store that stays in L2 until the reverse reads it back (4.7 ms against
-    // 5.6 ms with the tape)
+    // store that stays in L2 until the reverse reads it back (square-root
+    // factor: 4.7 ms against 5.6 ms with the tape)
     int64_t need = 0;
-    e = backward_store_fast(h->bwd_warps, b.phys, need);
+    b.form = h->bwd_form;
+    e = backward_store_fast(h->bwd_warps, b.phys, b.form, need);
     if (e != cudaSuccess) return from_cuda(e);
     st = grow(h->d_seg, h->seg_cap, need);
     if (st != TPCFIT_OK) return st;
