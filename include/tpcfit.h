@@ -228,14 +228,31 @@ tpcfit_status tpcfit_set_record(tpcfit_handle* h, int record);
  * Results do not depend on it.  EINVAL for other values. */
 tpcfit_status tpcfit_set_backward_config(tpcfit_handle* h, int warps_per_block);
 
+/* Factor of the covariance that the fast fit without material layers carries:
+ * 1 = U-D (C = U D U^T, Bierman's measurement updates, modified weighted
+ * Gram-Schmidt at sector rotations; default), 0 = the square-root factor
+ * (C = L L^T, Potter's updates).  Both compute the same extended Kalman filter
+ * and differ in FP32 rounding and speed; the deterministic mode and the
+ * material layers always take the square-root factor (its strict-FP32
+ * sequence is the deterministic mode's reference).  The recording keeps the
+ * factor of the form the fit ran in; the smoother and the backward read
+ * either.  The paper prescribes no factorisation; this is an implementation
+ * choice.  Replaces the recording.
+ * EINVAL for other values. */
+tpcfit_status tpcfit_set_fit_form(tpcfit_handle* h, int form);
+
 /* Factor of the covariance that the fast backward without material layers
  * recomputes its segments in: 1 = U-D (C = U D U^T, U unit upper triangular,
- * Bierman's measurement updates; default), 0 = the fit's square-root factor
+ * Bierman's measurement updates; default), 0 = the square-root factor
  * (C = L L^T, Potter's updates).  Both give the gradient of the same fit; they
  * differ in FP32 rounding and speed (U-D: 15 factor entries instead of 25, 6
- * float4 per stored state instead of 8).  The paper prescribes no factor for
- * the adjoint; this is an implementation choice.  The deterministic mode and
- * the material layers always take the square-root factor.  EINVAL for other
+ * float4 per stored state instead of 8).  The square-root reverse needs a
+ * recording made in the square-root form (tpcfit_set_fit_form 0, or one lane
+ * per track not in effect): its adjoint crosses segment boundaries only if the
+ * recomputed factor is the recorded one; after a U-D fit tpcfit_fit_backward
+ * answers ESTATE in that form.  The paper prescribes no factor for the
+ * adjoint; this is an implementation choice.  The deterministic mode and the
+ * material layers always take the square-root factor.  EINVAL for other
  * values. */
 tpcfit_status tpcfit_set_backward_form(tpcfit_handle* h, int form);
 

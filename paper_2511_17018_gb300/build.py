@@ -40,7 +40,7 @@ UNITS = {
 
 
 # Device sources the library carries for run-time compilation (Sec. 5).
-RTC_SOURCES = ("kernel_abi.h", "device_util.cuh", "fit_core.cuh")
+RTC_SOURCES = ("kernel_abi.h", "device_util.cuh", "fit_core.cuh", "ud_filter.cuh")
 RTC_EMBED = os.path.join(BUILD, "rtc_sources.cpp")
 
 

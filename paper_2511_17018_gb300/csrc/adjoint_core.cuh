@@ -382,6 +382,20 @@ __device__ __forceinline__ void load_ckpt(const float* src, StepState& S) {
   S.sec = __float_as_int(v[31]);
 }
 
+// A checkpoint of the U-D fit, loaded as if it held L (u in rows 0-1, d in
+// row 2): turned into the square-root factor L = U sqrt(D), upper triangular.
+__device__ __forceinline__ void sqrt_from_ud_ckpt(StepState& S) {
+  float u[10], sd[5];
+#pragma unroll
+  for (int e = 0; e < 10; ++e) u[e] = S.L[e / 5][e % 5];
+#pragma unroll
+  for (int c = 0; c < 5; ++c) sd[c] = sqrtf(S.L[2][c]);
+#pragma unroll
+  for (int i = 0; i < 5; ++i)
+#pragma unroll
+    for (int c = 0; c < 5; ++c) S.L[i][c] = c < i ? 0.0f : (c == i ? sd[c] : u[4 * i - (i * (i - 1)) / 2 + (c - i - 1)] * sd[c]);
+}
+
 // One cluster as stored (y, z, packed row/sector), loaded ahead of its use.
 struct HitRaw {
   float y, z;
@@ -1027,7 +1041,7 @@ __global__ void __launch_bounds__(WARPS * 32, 1) backward_kernel(const __grid_co
           if constexpr (FORM == 1) {
             StepState C;
             read_state(&W.ck[0][lane], C);
-            ud_state_from(C, S);
+            ud_state_from(C, a.ck_form == 1, S);
           } else {
             read_state(&W.ck[0][lane], S);
           }
@@ -1177,6 +1191,7 @@ __global__ void __launch_bounds__(kRecomputeWarps * 32, 1) recompute_kernel(cons
         const int cnt = min(kCkptEvery, steps - i0);
         StepState S;
         load_ckpt(ckp + (int64_t)s * kCkptFloats, S);
+        if (a.ck_form == 1) sqrt_from_ud_ckpt(S);
         float my = 0.0f, mz = 0.0f;
         if (i0 > 0) {
           int row, sec;

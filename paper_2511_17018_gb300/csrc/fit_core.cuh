@@ -457,6 +457,14 @@ __device__ __forceinline__ void scalar_update(const GeoRef& G, float p[5], float
   for (int c = 0; c < 5; ++c) L[H][c] = a[c] * beta;
 }
 
+}  // namespace TPCFIT_NS
+}  // namespace tpcfit
+
+#include "ud_filter.cuh"
+
+namespace tpcfit {
+namespace TPCFIT_NS {
+
 // ---------------------------------------------------------------- material
 // A thin material layer at every pad row (G.mat): the state at a row is
 // the one the track leaves it with; the outward pass crosses a row's layer on
@@ -572,7 +580,9 @@ __device__ __forceinline__ void record_error(unsigned long long* err, unsigned l
 // current cluster: p[0] = y - my, p[1] = z - mz.
 struct TrackState {
   float p[5];
-  float L[5][5];
+  float L[5][5];   // square-root factor (C = L L^T), or
+  float u[10];     // the U-D factor (C = U D U^T), by the kernel's FORM
+  float d[5];
   float x;
   float chi2;
   float my, mz;
@@ -647,16 +657,29 @@ __device__ __forceinline__ bool step_predict(const GeoRef& G, const SmemTables& 
   return predict_residual<FIELD>(G, T, S.p, S.x, S.sec, S.my, S.mz, sec_to, X, m0, m1, pout, J, tp);
 }
 
+// Checkpoint: the state and its covariance factor (32 floats: p, the factor,
+// x, sector).  The square-root form writes L row by row in floats 5..29; the
+// U-D form writes u (10) in floats 5..14, d (5) in 15..19 and zeros after.
+template <int FORM>
 __device__ __forceinline__ void write_ckpt(const FitArgs& a, int pass, int begin, int trk, int seg,
                                            const TrackState& S) {
   float4* dst = reinterpret_cast<float4*>(a.ck + ((int64_t)pass * a.ck_slots + (begin >> kCkptShift) + trk + seg) * kCkptFloats);
   float v[kCkptFloats];
 #pragma unroll
   for (int c = 0; c < 5; ++c) v[c] = S.p[c];
+  if (FORM == 1) {
 #pragma unroll
-  for (int i = 0; i < 5; ++i)
+    for (int e = 0; e < 10; ++e) v[5 + e] = S.u[e];
 #pragma unroll
-    for (int c = 0; c < 5; ++c) v[5 + 5 * i + c] = S.L[i][c];
+    for (int c = 0; c < 5; ++c) v[15 + c] = S.d[c];
+#pragma unroll
+    for (int e = 20; e < 30; ++e) v[e] = 0.0f;
+  } else {
+#pragma unroll
+    for (int i = 0; i < 5; ++i)
+#pragma unroll
+      for (int c = 0; c < 5; ++c) v[5 + 5 * i + c] = S.L[i][c];
+  }
   v[30] = S.x;
   v[31] = __int_as_float(S.sec);
 #pragma unroll
@@ -664,12 +687,15 @@ __device__ __forceinline__ void write_ckpt(const FitArgs& a, int pass, int begin
 }
 
 // PHYS: bit 0 the material layers, bit 1 the field map (compile-time variants,
-// so that the plain fit carries neither).
-template <int RPS, int WARPS, int MINB, bool RECORD, bool FRAMES, int PHYS>
+// so that the plain fit carries neither).  FORM: the covariance's factor, 0
+// the square-root factor with Potter's updates (the canonical sequence of the
+// deterministic mode), 1 U-D with Bierman's (fast mode, no material layers).
+template <int RPS, int WARPS, int MINB, bool RECORD, bool FRAMES, int PHYS, int FORM = 0>
 __global__ void __launch_bounds__(WARPS * 32, MINB) fit_kernel(const __grid_constant__ FitArgs a) {
   const GeoRef& G = TPCFIT_GEO(a);
   constexpr bool MAT = (PHYS & 1) != 0;
   constexpr int FIELD = (PHYS & 2) ? 1 : 0;
+  static_assert(FORM == 0 || (!MAT && !TPCFIT_DET), "the U-D fit: fast mode without material layers");
   extern __shared__ __align__(16) unsigned char smem_raw[];
   BlockSmem& B = *reinterpret_cast<BlockSmem*>(smem_raw);
   WarpStage<RPS>* stages = reinterpret_cast<WarpStage<RPS>*>(smem_raw + sizeof(BlockSmem));
@@ -744,7 +770,14 @@ __global__ void __launch_bounds__(WARPS * 32, MINB) fit_kernel(const __grid_cons
       const int my_count = (status == 0) ? (pass == 0 ? n : last + 1) : 0;
       bool go = status == 0;
       if (go) {
-        reset_factor(G, S.L);
+        if (FORM == 1) {
+#pragma unroll
+          for (int e = 0; e < 10; ++e) S.u[e] = 0.0f;
+#pragma unroll
+          for (int c = 0; c < 5; ++c) S.d[c] = G.l0 * G.l0;
+        } else {
+          reset_factor(G, S.L);
+        }
         S.chi2 = 0.0f;
         S.used = 0;
       }
@@ -785,7 +818,7 @@ __global__ void __launch_bounds__(WARPS * 32, MINB) fit_kernel(const __grid_cons
           const float m0 = st.y[buf][lane][k] - d.x;
           const float m1 = st.z[buf][lane][k] - d.y;
           const int sec18 = side_sector(sec);
-          if (RECORD && (i & (kCkptEvery - 1)) == 0) write_ckpt(a, pass, begin, trk, i >> kCkptShift, S);
+          if (RECORD && (i & (kCkptEvery - 1)) == 0) write_ckpt<FORM>(a, pass, begin, trk, i >> kCkptShift, S);
           if (i == 0) {
             // first cluster of the pass: the state sits on its row already; the
             // outward pass turns the seed's (y, z) into residuals
@@ -827,11 +860,23 @@ __global__ void __launch_bounds__(WARPS * 32, MINB) fit_kernel(const __grid_cons
             S.sec = sec18;
             S.my = m0;
             S.mz = m1;
-            transport(S.L, J);
+            if (FORM == 1) {
+              if (J.rot)
+                rotate_ud(S.u, S.d, J);
+              else
+                transport_ud(S.u, J);
+            } else {
+              transport(S.L, J);
+            }
             if (MAT && pass == 0) material_factor(S.L, N);
           }
-          scalar_update<0>(G, S.p, S.L, S.chi2, 0.0f);
-          scalar_update<1>(G, S.p, S.L, S.chi2, 0.0f);
+          if (FORM == 1) {
+            bierman_update<0>(S.p, S.u, S.d, S.chi2, G.v_meas);
+            bierman_update<1>(S.p, S.u, S.d, S.chi2, G.v_meas);
+          } else {
+            scalar_update<0>(G, S.p, S.L, S.chi2, 0.0f);
+            scalar_update<1>(G, S.p, S.L, S.chi2, 0.0f);
+          }
           S.used += 1;
           if (pass == 0) last = i;
         }
@@ -854,9 +899,16 @@ __global__ void __launch_bounds__(WARPS * 32, MINB) fit_kernel(const __grid_cons
       for (int i = 0; i < 5; ++i)
 #pragma unroll
         for (int j = 0; j <= i; ++j) {
-          float acc = S.L[i][0] * S.L[j][0];
+          float acc;
+          if (FORM == 1) {  // C_ij = sum over k >= i of u_ik d_k u_jk (j <= i, u_kk = 1)
+            acc = (j == i ? 1.0f : S.u[ui(j, i)]) * S.d[i];
 #pragma unroll
-          for (int c = 1; c < 5; ++c) acc = acc + S.L[i][c] * S.L[j][c];
+            for (int k = i + 1; k < 5; ++k) acc = acc + (S.u[ui(i, k)] * S.d[k]) * S.u[ui(j, k)];
+          } else {
+            acc = S.L[i][0] * S.L[j][0];
+#pragma unroll
+            for (int c = 1; c < 5; ++c) acc = acc + S.L[i][c] * S.L[j][c];
+          }
           a.cov[(int64_t)e * N + trk] = acc;
           ++e;
         }
@@ -875,20 +927,19 @@ __global__ void __launch_bounds__(WARPS * 32, MINB) fit_kernel(const __grid_cons
 }
 
 #ifndef __CUDACC_RTC__
-template <int RPS, int WARPS, int MINB, bool RECORD, bool FRAMES, int PHYS>
+template <int RPS, int WARPS, int MINB, bool RECORD, bool FRAMES, int PHYS, int FORM>
 cudaError_t launch_cfg(const FitArgs& a, cudaStream_t s) {
   constexpr int kThreads = WARPS * 32;
   const size_t smem = sizeof(BlockSmem) + WARPS * sizeof(WarpStage<RPS>);
+  auto kernel = fit_kernel<RPS, WARPS, MINB, RECORD, FRAMES, PHYS, FORM>;
   static int grid = 0;
   if (grid == 0) {
-    cudaError_t e =
-        cudaFuncSetAttribute(fit_kernel<RPS, WARPS, MINB, RECORD, FRAMES, PHYS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     int dev = 0, sms = 0, per_sm = 0;
     e = cudaGetDevice(&dev);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    if (e == cudaSuccess)
-      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fit_kernel<RPS, WARPS, MINB, RECORD, FRAMES, PHYS>, kThreads, smem);
+    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, kThreads, smem);
     if (e != cudaSuccess) return e;
     if (per_sm < 1) return cudaErrorInvalidConfiguration;
     grid = sms * per_sm;
@@ -898,33 +949,48 @@ cudaError_t launch_cfg(const FitArgs& a, cudaStream_t s) {
   const int blocks = (int)(need < grid ? need : grid);
   cudaError_t e = cudaMemsetAsync(a.work, 0, sizeof(unsigned int), s);
   if (e != cudaSuccess) return e;
-  fit_kernel<RPS, WARPS, MINB, RECORD, FRAMES, PHYS><<<blocks, kThreads, smem, s>>>(a);
+  kernel<<<blocks, kThreads, smem, s>>>(a);
   return cudaGetLastError();
 }
 
 // Supported (rows per stage, warps per block) shapes; the shared-memory budget
 // (alignment table + double buffer) decides how many blocks fit on an SM.
 // With material or a field map the fit runs at (4, 24).
-template <bool RECORD, bool FRAMES>
+template <bool RECORD, bool FRAMES, int FORM>
 inline cudaError_t launch_rec(const FitArgs& a, int rps, int warps, cudaStream_t s) {
   const int phys = (a.mat ? 1 : 0) | (a.field ? 2 : 0);
-  if (phys == 1) return launch_cfg<4, 24, fit_min_blocks(4, 24), RECORD, FRAMES, 1>(a, s);
-  if (phys == 2) return launch_cfg<4, 24, fit_min_blocks(4, 24), RECORD, FRAMES, 2>(a, s);
-  if (phys == 3) return launch_cfg<4, 24, fit_min_blocks(4, 24), RECORD, FRAMES, 3>(a, s);
-  if (rps == 4 && warps == 8) return launch_cfg<4, 8, fit_min_blocks(4, 8), RECORD, FRAMES, 0>(a, s);
-  if (rps == 4 && warps == 12) return launch_cfg<4, 12, fit_min_blocks(4, 12), RECORD, FRAMES, 0>(a, s);
-  if (rps == 4 && warps == 24) return launch_cfg<4, 24, fit_min_blocks(4, 24), RECORD, FRAMES, 0>(a, s);
-  if (rps == 8 && warps == 8) return launch_cfg<8, 8, fit_min_blocks(8, 8), RECORD, FRAMES, 0>(a, s);
-  if (rps == 8 && warps == 16) return launch_cfg<8, 16, fit_min_blocks(8, 16), RECORD, FRAMES, 0>(a, s);
-  if (rps == 16 && warps == 8) return launch_cfg<16, 8, fit_min_blocks(16, 8), RECORD, FRAMES, 0>(a, s);
+  if (FORM == 0) {
+    if (phys == 1) return launch_cfg<4, 24, fit_min_blocks(4, 24), RECORD, FRAMES, 1, 0>(a, s);
+    if (phys == 3) return launch_cfg<4, 24, fit_min_blocks(4, 24), RECORD, FRAMES, 3, 0>(a, s);
+  } else if (phys & 1) {
+    return cudaErrorInvalidValue;
+  }
+  if (phys == 2) return launch_cfg<4, 24, fit_min_blocks(4, 24), RECORD, FRAMES, 2, FORM>(a, s);
+  if (rps == 4 && warps == 8) return launch_cfg<4, 8, fit_min_blocks(4, 8), RECORD, FRAMES, 0, FORM>(a, s);
+  if (rps == 4 && warps == 12) return launch_cfg<4, 12, fit_min_blocks(4, 12), RECORD, FRAMES, 0, FORM>(a, s);
+  if (rps == 4 && warps == 24) return launch_cfg<4, 24, fit_min_blocks(4, 24), RECORD, FRAMES, 0, FORM>(a, s);
+  if (rps == 8 && warps == 8) return launch_cfg<8, 8, fit_min_blocks(8, 8), RECORD, FRAMES, 0, FORM>(a, s);
+  if (rps == 8 && warps == 16) return launch_cfg<8, 16, fit_min_blocks(8, 16), RECORD, FRAMES, 0, FORM>(a, s);
+  if (rps == 16 && warps == 8) return launch_cfg<16, 8, fit_min_blocks(16, 8), RECORD, FRAMES, 0, FORM>(a, s);
   return cudaErrorInvalidValue;
 }
 
+template <int FORM>
+inline cudaError_t launch_form(const FitArgs& a, int rps, int warps, cudaStream_t s) {
+  if (a.frame_base)
+    return a.ck ? launch_rec<true, true, FORM>(a, rps, warps, s) : launch_rec<false, true, FORM>(a, rps, warps, s);
+  return a.ck ? launch_rec<true, false, FORM>(a, rps, warps, s) : launch_rec<false, false, FORM>(a, rps, warps, s);
+}
+
+// One lane per track.  FORM 1 (U-D) in fast mode without material layers,
+// otherwise the square-root factor.
 inline cudaError_t launch(const FitArgs& a, int lanes_per_track, int rps, int warps, cudaStream_t s) {
   if (a.n_tracks <= 0) return cudaSuccess;
   if (lanes_per_track != 1) return cudaErrorInvalidValue;
-  if (a.frame_base) return a.ck ? launch_rec<true, true>(a, rps, warps, s) : launch_rec<false, true>(a, rps, warps, s);
-  return a.ck ? launch_rec<true, false>(a, rps, warps, s) : launch_rec<false, false>(a, rps, warps, s);
+#if !TPCFIT_DET
+  if (a.form == 1 && !a.mat) return launch_form<1>(a, rps, warps, s);
+#endif
+  return launch_form<0>(a, rps, warps, s);
 }
 
 #endif  // !__CUDACC_RTC__

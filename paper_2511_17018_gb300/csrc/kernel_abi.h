@@ -88,6 +88,7 @@ struct FitArgs {
   int64_t wait_ns;             // bound of a ready-flag wait
   int32_t mat;                 // material layers on (selects the kernel variant that crosses them)
   int32_t field;               // field map on (selects the kernel variant that follows it)
+  int32_t form;                // factor of the covariance: 0 square root (L), 1 U-D (fast mode without material)
 };
 
 // Arguments of one backward launch (same frame as the recorded fit).
@@ -114,6 +115,7 @@ struct BwdArgs {
   float4* tape;                // or the tape: [2][n_hits][8] float4, the state before every step (null: segment store)
   int32_t phys;                // physics of the recorded fit: bit 1 material layers, bit 2 the field map
   int32_t form;                // factor the fast one-kernel backward recomputes in: 0 square root (L), 1 U-D
+  int32_t ck_form;             // factor the checkpoints hold: 0 L, 1 U-D (u, d)
 };
 
 // Arguments of one smoother launch (same frame as the recorded fit).
@@ -138,6 +140,7 @@ struct SmoothArgs {
   float* state_cov;            // [n_hits][15] its covariance (packed)
   unsigned int* work;
   float4* seg;                 // segment store, as for the adjoint
+  int32_t ck_form;             // factor the checkpoints hold: 0 L, 1 U-D (u, d)
   int32_t mat;                 // material layers on (the recorded fit had them)
 };
 

@@ -240,12 +240,13 @@ struct Variant {
   std::string src, expr, key;
 };
 
-Variant variant(const GeoConst& g, bool det, int rps, int warps, bool record, bool frames) {
+Variant variant(const GeoConst& g, bool det, int rps, int warps, bool record, bool frames, int form) {
   Variant v;
   v.src = rtc_fit_source(g, det);
   v.expr = "tpcfit::rtc::fit_kernel<" + std::to_string(rps) + ", " + std::to_string(warps) + ", " +
            std::to_string(fit_min_blocks(rps, warps)) + ", " + (record ? "true" : "false") + ", " +
-           (frames ? "true" : "false") + ", " + std::to_string((g.mat ? 1 : 0) | (g.field ? 2 : 0)) + ">";
+           (frames ? "true" : "false") + ", " + std::to_string((g.mat ? 1 : 0) | (g.field ? 2 : 0)) + ", " +
+           std::to_string(form) + ">";
   std::string opt;
   for (const std::string& x : options(det)) opt += x + " ";
   char keyb[32];
@@ -280,7 +281,8 @@ tpcfit_status cubin_of(const Variant& v, bool det, const char* cache_dir, std::v
 
 tpcfit_status rtc_build(const GeoConst& g, bool det, int rps, int warps, bool record, bool frames,
                         const char* cache_dir) {
-  const Variant v = variant(g, det, rps, warps, record, frames);
+  // the library's default factor: U-D in fast mode without material layers
+  const Variant v = variant(g, det, rps, warps, record, frames, (!det && !g.mat) ? 1 : 0);
   std::vector<char> cubin;
   std::string lowered;
   return cubin_of(v, det, cache_dir, cubin, lowered);
@@ -289,7 +291,8 @@ tpcfit_status rtc_build(const GeoConst& g, bool det, int rps, int warps, bool re
 tpcfit_status rtc_launch_fit(const GeoConst& g, bool det, int rps, int warps, const FitArgs& a, const char* cache_dir,
                              cudaStream_t s) {
   if (a.n_tracks <= 0) return TPCFIT_OK;
-  const Variant v = variant(g, det, rps, warps, a.ck != nullptr, a.frame_base != nullptr);
+  const Variant v = variant(g, det, rps, warps, a.ck != nullptr, a.frame_base != nullptr,
+                            (!det && !g.mat && a.form == 1) ? 1 : 0);
   const std::string& key = v.key;
   Compiled* c = nullptr;
   {

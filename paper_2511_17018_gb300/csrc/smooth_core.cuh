@@ -271,6 +271,7 @@ __global__ void __launch_bounds__(WARPS * 32, 1) smooth_kernel(const __grid_cons
     // outward filter: from its first checkpoint (the seed, factor L0)
     StepState O;
     load_ckpt(a.ck + slot0 * kCkptFloats, O);
+    if (a.ck_form == 1) sqrt_from_ud_ckpt(O);
     float omy = 0.0f, omz = 0.0f;  // measurement O's residuals refer to (none for the seed)
     // inward segments, last first: inward step j is cluster last - j
     const int steps = last + 1;
@@ -291,6 +292,7 @@ __global__ void __launch_bounds__(WARPS * 32, 1) smooth_kernel(const __grid_cons
       }
       cp_async_wait<0>();
       read_state(&W.ck[0][lane], S);
+      if (a.ck_form == 1) sqrt_from_ud_ckpt(S);
       // level 1: the inward segment, storing the state before each step
 #pragma unroll 1
       for (int kk = 0; kk < cnt; ++kk) {

@@ -101,6 +101,7 @@ struct tpcfit_handle {
   int record = 0;
   int bwd_warps = 8;
   int bwd_form = 1;            // factor of the fast one-kernel backward: 1 U-D, 0 square root
+  int fit_form = 1;            // factor of the fast fit without material: 1 U-D, 0 square root
   int rtc = 0;                 // fit kernels compiled at run time (Sec. 5)
   std::string rtc_dir;         // their on-disk cache, or empty
   float* d_ck = nullptr;
@@ -111,6 +112,7 @@ struct tpcfit_handle {
   bool rec_valid = false;
   int64_t rec_tracks = 0, rec_hits = 0;
   int rec_det = 0;
+  int rec_form = 0;            // factor the recorded fit carried (1: U-D, its checkpoints hold U sqrt(D))
   // adjoint scratch: per-cluster gradients and the key sort
   float4* d_seg = nullptr;     // the segment store of the backward (fast mode) and the smoother
   int64_t seg_cap = 0;         // float4 elements
@@ -304,6 +306,7 @@ tpcfit_status tpcfit_fit(tpcfit_handle* h, const tpcfit_hits* hits, const int32_
   tpcfit_status st = TPCFIT_OK;
   FitArgs a{};
   a.geo = h->geo;
+  a.form = (!h->deterministic && !h->geo.mat) ? h->fit_form : 0;
   a.y = hits->y;
   a.z = hits->z;
   a.rowsec = hits->rowsec;
@@ -346,6 +349,7 @@ tpcfit_status tpcfit_fit(tpcfit_handle* h, const tpcfit_hits* hits, const int32_
     h->rec_tracks = n_tracks;
     h->rec_hits = hits->n_hits;
     h->rec_det = h->deterministic;
+    h->rec_form = (a.form == 1 && h->lanes_per_track == 1) ? 1 : 0;  // several lanes per track: square root
   }
   return TPCFIT_OK;
 }
@@ -375,6 +379,7 @@ tpcfit_status tpcfit_fit_frames(tpcfit_handle* h, const tpcfit_hits* hits, const
   if (st != TPCFIT_OK) return st;
   FitArgs a{};
   a.geo = h->geo;
+  a.form = (!h->deterministic && !h->geo.mat) ? h->fit_form : 0;
   a.y = hits->y;
   a.z = hits->z;
   a.rowsec = hits->rowsec;
@@ -407,6 +412,13 @@ tpcfit_status tpcfit_fit_frames(tpcfit_handle* h, const tpcfit_hits* hits, const
 tpcfit_status tpcfit_set_backward_config(tpcfit_handle* h, int warps_per_block) {
   if (!h || !backward_shape_supported(warps_per_block)) return TPCFIT_EINVAL;
   h->bwd_warps = warps_per_block;
+  return TPCFIT_OK;
+}
+
+tpcfit_status tpcfit_set_fit_form(tpcfit_handle* h, int form) {
+  if (!h || (form != 0 && form != 1)) return TPCFIT_EINVAL;
+  h->fit_form = form;
+  h->rec_valid = false;
   return TPCFIT_OK;
 }
 
@@ -505,6 +517,7 @@ tpcfit_status tpcfit_fit_backward(tpcfit_handle* h, const tpcfit_hits* hits, con
   b.grad_seeds = grad_seeds;
   b.work = h->d_work;
   b.phys = (h->geo.mat ? 1 : 0) | (h->geo.field ? 2 : 0);
+  b.ck_form = h->rec_form;
   cudaError_t e = cudaSuccess;
   if (h->deterministic || h->geo.mat) {
     // where the forward step is expensive (no FMA; the material folding) the
@@ -520,6 +533,11 @@ tpcfit_status tpcfit_fit_backward(tpcfit_handle* h, const tpcfit_hits* hits, con
     // store that stays in L2 until the reverse reads it back (square-root
     // factor: 4.7 ms against 5.6 ms with the tape)
     int64_t need = 0;
+    // the square-root reverse hands each segment's factor adjoint to the
+    // segment before it, which holds only if its recomputation reproduces the
+    // recorded factor: after a U-D fit only the U-D reverse applies (the U-D
+    // factorisation of a covariance is unique)
+    if (h->bwd_form == 0 && h->rec_form == 1) return TPCFIT_ESTATE;
     b.form = h->bwd_form;
     e = backward_store_fast(h->bwd_warps, b.phys, b.form, need);
     if (e != cudaSuccess) return from_cuda(e);
@@ -601,6 +619,7 @@ tpcfit_status run_smooth(tpcfit_handle* h, const tpcfit_hits* hits, const int32_
   a.state_cov = state_cov;
   a.work = h->d_work;
   a.mat = h->geo.mat;
+  a.ck_form = h->rec_form;
   int64_t need = 0;
   cudaError_t e = h->deterministic ? smooth_store_det(need) : smooth_store_fast(need);
   if (e != cudaSuccess) return from_cuda(e);

@@ -93,6 +93,7 @@ extern "C" tpcfit_status tpcfit_fit_noalloc(const tpcfit_geometry* geometry, dou
   if (e != cudaSuccess) return TPCFIT_ECUDA;
   FitArgs a{};
   a.geo = geo;
+  a.form = deterministic ? 0 : 1;  // the library's default factor
   a.y = hits->y;
   a.z = hits->z;
   a.rowsec = hits->rowsec;

@@ -61,6 +61,7 @@ def load():
         "tpcfit_set_record": (C.c_int, [vp, C.c_int]),
         "tpcfit_set_backward_config": (C.c_int, [vp, C.c_int]),
         "tpcfit_set_backward_form": (C.c_int, [vp, C.c_int]),
+        "tpcfit_set_fit_form": (C.c_int, [vp, C.c_int]),
         "tpcfit_fit_frames": (C.c_int, [vp, C.POINTER(_Hits), vp, i32, vp, i32, vp, vp, i64, vp, vp, vp, vp, vp,
                                         vp]),
         "tpcfit_fit_backward": (C.c_int, [vp, C.POINTER(_Hits), vp, i32, vp, vp, vp, vp, vp, vp]),
@@ -255,6 +256,10 @@ def tpcfit_fit_frames(h, y, z, rowsec, offsets, frame_base, seeds, params, cov, 
 
 def tpcfit_set_backward_config(h, warps_per_block: int = 8) -> None:
     _check(load().tpcfit_set_backward_config(h, int(warps_per_block)), "tpcfit_set_backward_config")
+
+
+def tpcfit_set_fit_form(h, form: int = 1) -> None:
+    _check(load().tpcfit_set_fit_form(h, int(form)), "tpcfit_set_fit_form")
 
 
 def tpcfit_set_backward_form(h, form: int = 1) -> None:
@@ -476,6 +481,10 @@ class Fitter:
 
     def set_backward_config(self, warps_per_block: int = 8):
         tpcfit_set_backward_config(self.h, warps_per_block)
+
+    def set_fit_form(self, form: int = 1):
+        """Factor of the fast fit without material: 1 U-D (default), 0 square root."""
+        tpcfit_set_fit_form(self.h, form)
 
     def set_backward_form(self, form: int = 1):
         """Factor of the fast backward's recomputation: 1 U-D (default), 0 square root."""

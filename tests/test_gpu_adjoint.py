@@ -55,12 +55,13 @@ def case():
     return fr, d_true, w, ref
 
 
-def _gpu_grad(fr, d_true, w, det, rps=4, warps=24, srt=True, bwd=12, form=1):
+def _gpu_grad(fr, d_true, w, det, rps=4, warps=24, srt=True, bwd=12, form=1, fit_form=1):
     dev = tf.frame_to_device(fr)
     f = tf.Fitter(fr.geometry, fr.bz, deterministic=det, rows_per_stage=rps, warps_per_block=warps,
                   sort_by_length=srt)
     f.set_backward_config(bwd)
     f.set_backward_form(form)
+    f.set_fit_form(fit_form)
     try:
         f.set_alignment(torch.from_numpy(d_true).cuda())
         f.set_record(True)
@@ -77,7 +78,7 @@ def _gpu_grad(fr, d_true, w, det, rps=4, warps=24, srt=True, bwd=12, form=1):
 def test_adjoint_matches_forward_mode_oracle(case, det, form):
     # against the FP64 gradient: per element within the FP32 forward's floor
     fr, d_true, w, ref = case
-    gm, ga, gs, ndf = _gpu_grad(fr, d_true, w, det, form=form)
+    gm, ga, gs, ndf = _gpu_grad(fr, d_true, w, det, form=form, fit_form=form)
     assert np.array_equal(ndf, ref["ndf"])
     ga_ref = oracle.align_grad_from_meas(fr, ref["grad_meas"])
     for name, got, want in (("meas", gm, ref["grad_meas"]), ("align", ga, ga_ref), ("seeds", gs, ref["grad_seed"])):
@@ -88,12 +89,12 @@ def test_adjoint_matches_forward_mode_oracle(case, det, form):
 
 def test_fast_adjoint_factor_forms_agree(case):
     # the U-D and the square-root recomputation differentiate the same recorded
-    # fast fit: they differ by the FP32 rounding of the reverse sweeps only, in
-    # every compiled block shape
+    # fast fit (square-root form): they differ by the FP32 rounding of the
+    # reverse sweeps only, in every compiled block shape
     fr, d_true, w, _ = case
-    base = _gpu_grad(fr, d_true, w, False, form=0)
+    base = _gpu_grad(fr, d_true, w, False, form=0, fit_form=0)
     for bwd in (4, 8, 10, 12):
-        got = _gpu_grad(fr, d_true, w, False, bwd=bwd, form=1)
+        got = _gpu_grad(fr, d_true, w, False, bwd=bwd, form=1, fit_form=0)
         for name, a, b in zip(("meas", "align", "seeds"), got[:3], base[:3]):
             e = _elem(a, b)
             print(bwd, name, e)
@@ -176,6 +177,26 @@ def test_autograd_function_and_masking(case):
         es = _elem(seeds.grad.cpu().numpy(), ref["grad_seed"])
         assert ea["max"] < FP32_ELEM and ea["norm"] < REL, ea
         assert es["max"] < FP32_ELEM and es["norm"] < 10 * REL, es
+    finally:
+        f.close()
+
+
+def test_square_root_reverse_refuses_a_u_d_recording():
+    fr = synth.generate(200, 36)
+    dev = tf.frame_to_device(fr)
+    f = tf.Fitter(fr.geometry, fr.bz)
+    try:
+        f.set_record(True)
+        f.set_fit_form(1)
+        out = f.fit(dev)
+        f.set_backward_form(0)
+        with pytest.raises(tf.TpcfitError) as e:
+            f.backward(dev, out, torch.ones(fr.n_tracks, device="cuda"))
+        assert e.value.status == tf.ESTATE
+        f.set_backward_form(1)
+        ga, gs = f.backward(dev, out, torch.ones(fr.n_tracks, device="cuda"))
+        torch.cuda.synchronize()
+        assert np.all(np.isfinite(ga.cpu().numpy()))
     finally:
         f.close()
 

@@ -47,15 +47,35 @@ def frames():
 
 
 @pytest.mark.parametrize("name", ["plain1000", "drop20k"])
-def test_fast_mode_matches_fp64_oracle(fitter, frames, name):
+@pytest.mark.parametrize("form", [1, 0], ids=["ud", "sqrt"])
+def test_fast_mode_matches_fp64_oracle(fitter, frames, name, form):
+    # both factor forms of the fast fit (U-D, square root) against FP64
     fr = frames[name]
     fitter.set_mode(False)
     fitter.set_config(1, 4, 24, True)
-    got = _host(fitter.fit(tf.frame_to_device(fr)))
+    fitter.set_fit_form(form)
+    try:
+        got = _host(fitter.fit(tf.frame_to_device(fr)))
+    finally:
+        fitter.set_fit_form(1)
     ref = oracle.fit(fr, "f64")
     rep = tolerance.compare_to_fp64(got, ref)
+    print(form, rep)
     assert rep["ok"], rep
     assert np.array_equal(got["ndf"], ref["ndf"])
+
+
+@pytest.mark.parametrize("shape", [(4, 8), (4, 12), (8, 8), (8, 16), (16, 8)])
+def test_fast_u_d_fit_in_every_shape(fitter, frames, shape):
+    fr = frames["drop20k"]
+    fitter.set_mode(False)
+    try:
+        fitter.set_config(1, shape[0], shape[1], shape[0] != 8)
+        got = _host(fitter.fit(tf.frame_to_device(fr)))
+    finally:
+        fitter.set_config(1, 4, 24, True)
+    rep = tolerance.compare_to_fp64(got, oracle.fit(fr, "f64"))
+    assert rep["ok"], (shape, rep)
 
 
 @pytest.mark.parametrize("name", ["plain1000", "drop20k"])
