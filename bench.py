@@ -356,7 +356,9 @@ def run_batched_frames(args, tf, torch, synth, flops, peak_tf):
         e.record()
         torch.cuda.synchronize()
         ms = s.elapsed_time(e) / reps
-        tfl = flops.fit_flops(lengths) / (ms / 1e3) / 1e12
+        # the U-D fit in fast mode with one lane per track, else the square-root form
+        form = 1 if (mode == "fast" and best["lanes_per_track"] == 1) else 0
+        tfl = flops.fit_flops(lengths, form) / (ms / 1e3) / 1e12
         tfm = flops.method_fit_flops(lengths) / (ms / 1e3) / 1e12
         res[mode] = {"tracks_per_s": batch.n_tracks / (ms / 1e3), "ms_per_batch": ms,
                      "hits_per_s": batch.n_hits / (ms / 1e3), "frac_method": tfm / peak_tf, "frac_impl": tfl / peak_tf,
@@ -605,6 +607,28 @@ def main():
                "fit_ms": statistics.mean(p[0] for p in det_fa_per),
                "backward_ms": statistics.mean(p[1] for p in det_fa_per)}
 
+    # ---- the square-root factor (Potter's updates) in place of U-D in fast mode
+    sqrt_form = None
+    if args.mode == "fast":
+        fitter.set_fit_form(0)
+        fitter.set_backward_form(0)
+        fitter.set_record(False)
+        for _ in range(args.warmup):
+            fitter.fit(dev, out)
+        torch.cuda.synchronize()
+        _, sq_fit_per = timed(step_fit, max(10, args.steps // 4))
+        fitter.set_record(True)
+        for _ in range(args.warmup):
+            fit_adjoint()
+        torch.cuda.synchronize()
+        _, sq_fa_per = timed(step_fa, max(10, args.steps // 4))
+        fitter.set_record(False)
+        fitter.set_fit_form(1)
+        fitter.set_backward_form(1)
+        sqrt_form = {"plain_fit_ms": statistics.mean(p[0] for p in sq_fit_per),
+                     "fit_ms": statistics.mean(p[0] for p in sq_fa_per),
+                     "backward_ms": statistics.mean(p[1] for p in sq_fa_per)}
+
     # ---- end to end through the public API with host buffers
     h2d = 10 * fr.n_hits + 4 * (fr.n_tracks + 1) + 20 * fr.n_tracks
     d2h = 88 * fr.n_tracks
@@ -646,9 +670,10 @@ def main():
         return {"achieved_method": a_meth, "frac_method": a_meth / peak_tf,
                 "achieved_impl": a_impl, "frac_impl": a_impl / peak_tf}
 
-    bwd_f = frac2(flops.backward_flops(lengths), flops.method_backward_flops(lengths), bwd_ms)
-    fa_f = frac2(flops.fit_adjoint_flops(lengths), flops.method_fit_adjoint_flops(lengths), step_ms)
-    fit_f = frac2(flops.fit_flops(lengths), flops.method_fit_flops(lengths), plain_ms)
+    form = 1 if args.mode == "fast" else 0  # the factor the kernels run in: U-D fast, square root deterministic
+    bwd_f = frac2(flops.backward_flops(lengths, form), flops.method_backward_flops(lengths), bwd_ms)
+    fa_f = frac2(flops.fit_adjoint_flops(lengths, form), flops.method_fit_adjoint_flops(lengths), step_ms)
+    fit_f = frac2(flops.fit_flops(lengths, form), flops.method_fit_flops(lengths), plain_ms)
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": step_ms, "higher_is_better": True, "scaling": "weak",
@@ -658,7 +683,7 @@ def main():
                      "kernel": "backward_kernel", "launch_ms": bwd_ms,
                      "frac_impl": bwd_f["frac_impl"], "achieved_impl": bwd_f["achieved_impl"],
                      "count": "achieved/frac: method count (480 flop per cluster for the fit, x2.5 for the reverse); "
-                              "*_impl: the square-root form as implemented (flops.py)",
+                              "*_impl: the form as implemented (flops.py; fast mode: U-D)",
                      "peak_source": "measured on this GPU: FMA-chain microbenchmark (fp32_peak)"},
         "fit_adjoint": {"tracks_per_s": value, "ms": step_ms, "fit_ms": fit_rec_ms, "backward_ms": bwd_ms, **fa_f},
         "plain_fit": {"tracks_per_s": fr.n_tracks / (plain_ms / 1e3), "ms": plain_ms,
@@ -685,6 +710,16 @@ def main():
                             "backward_vs_fast": det["backward_ms"] / bwd_ms},
             "paper_slowdown": "1.5-10x (Sec. 2, the deterministic mode of the whole reconstruction)",
             "note": "no FMA contraction: the deterministic kernels' ceiling is half the FMA peak"}
+    if sqrt_form is not None:
+        sq_fa = sqrt_form["fit_ms"] + sqrt_form["backward_ms"]
+        line["square_root_form"] = {
+            "plain_fit": {"ms": sqrt_form["plain_fit_ms"], "vs_u_d": sqrt_form["plain_fit_ms"] / plain_ms,
+                          **frac2(flops.fit_flops(lengths, 0), flops.method_fit_flops(lengths),
+                                  sqrt_form["plain_fit_ms"])},
+            "fit_adjoint": {"tracks_per_s": fr.n_tracks / (sq_fa / 1e3), "ms": sq_fa, "fit_ms": sqrt_form["fit_ms"],
+                            "backward_ms": sqrt_form["backward_ms"], "vs_u_d": sq_fa / step_ms},
+            "note": "fast mode with the square-root factor and Potter's updates (the deterministic mode's "
+                    "sequence) in place of U-D and Bierman's"}
     line["plain_fit"]["e2e"] = e2e_plain
     sm_f = flops.smooth_flops(lengths) / (smooth_ms / 1e3) / 1e12
     line["smoother"] = {"tracks_per_s": fr.n_tracks / (smooth_ms / 1e3), "clusters_per_s": fr.n_hits / (smooth_ms / 1e3),

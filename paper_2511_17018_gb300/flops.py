@@ -2,11 +2,14 @@
 
 Counted from the formula list of one step as the kernels evaluate it: every
 add, subtract and multiply is one operation (a fused multiply-add counts as
-two), every division and square root one.  A step = rotation-free prediction
-(79, with the d(path)/dk series that single-row steps use) + square-root
-transport L <- J L (60) + two Potter scalar updates (2 x 128) + the alignment
-subtraction (2).  The first cluster of a pass has no prediction or transport.
-The output covariance C = L L^T costs 135 per track.
+two), every division, reciprocal and square root one.  Square-root form: a
+step = rotation-free prediction (79, with the d(path)/dk series that
+single-row steps use) + transport L <- J L (60) + two Potter scalar updates
+(2 x 128) + the alignment subtraction (2).  U-D form: the same prediction +
+transport U <- J U (16) + Bierman's updates of y (85) and z (75) + 2.  The
+first cluster of a pass has no prediction or transport.  The output
+covariance costs 135 per track from L, 75 from U and D.  form: 0 square
+root, 1 U-D.
 """
 from __future__ import annotations
 
@@ -19,13 +22,19 @@ MEAS = 2
 STEP = PREDICT + TRANSPORT + 2 * SCALAR_UPDATE + MEAS          # 397
 FIRST = 2 * SCALAR_UPDATE + MEAS                               # 258
 OUTPUT = 135
+UD_TRANSPORT = 16
+UD_UPDATE = (85, 75)
+UD_STEP = PREDICT + UD_TRANSPORT + sum(UD_UPDATE) + MEAS       # 257
+UD_FIRST = sum(UD_UPDATE) + MEAS                               # 162
+UD_OUTPUT = 75
 
 
-def fit_flops(lengths) -> float:
+def fit_flops(lengths, form: int = 0) -> float:
     """Algorithmic flops of fitting tracks with the given cluster counts (both passes)."""
     n = np.asarray(lengths, dtype=np.int64)
     n = n[n >= 1]
-    return float(np.sum(2 * ((n - 1) * STEP + FIRST) + OUTPUT))
+    step, first, out = (UD_STEP, UD_FIRST, UD_OUTPUT) if form == 1 else (STEP, FIRST, OUTPUT)
+    return float(np.sum(2 * ((n - 1) * step + first) + out))
 
 
 def fit_bytes(lengths) -> float:
@@ -37,25 +46,32 @@ def fit_bytes(lengths) -> float:
 
 # Reverse sweep (adjoint), counted from the formula list of the hand-written
 # reverse of each forward piece: a Potter scalar update (268), the transport
-# L <- J L (120) and the prediction with its Jacobian (150).  Recomputation of
-# forward values (checkpoint segments, per-step intermediates) is overhead and
-# is not counted.
+# L <- J L (120) and the prediction with its Jacobian (150); in U-D form
+# Bierman's updates of y (272) and z (243, their partial gain sums recomputed
+# in the forward's order included) and the transport U <- J U (26).
+# Recomputation of forward values (checkpoint segments, per-step
+# intermediates) is overhead and is not counted.
 REV_SCALAR_UPDATE = 268
 REV_TRANSPORT = 120
 REV_PREDICT = 150
 REV_STEP = REV_PREDICT + REV_TRANSPORT + 2 * REV_SCALAR_UPDATE   # 806
 REV_FIRST = 2 * REV_SCALAR_UPDATE                                 # 536
+UD_REV_UPDATE = (272, 243)
+UD_REV_TRANSPORT = 26
+UD_REV_STEP = REV_PREDICT + UD_REV_TRANSPORT + sum(UD_REV_UPDATE)  # 691
+UD_REV_FIRST = sum(UD_REV_UPDATE)                                   # 515
 
 
-def backward_flops(lengths) -> float:
+def backward_flops(lengths, form: int = 0) -> float:
     """Algorithmic flops of the reverse sweep over both passes."""
     n = np.asarray(lengths, dtype=np.int64)
     n = n[n >= 1]
-    return float(np.sum(2 * ((n - 1) * REV_STEP + REV_FIRST)))
+    step, first = (UD_REV_STEP, UD_REV_FIRST) if form == 1 else (REV_STEP, REV_FIRST)
+    return float(np.sum(2 * ((n - 1) * step + first)))
 
 
-def fit_adjoint_flops(lengths) -> float:
-    return fit_flops(lengths) + backward_flops(lengths)
+def fit_adjoint_flops(lengths, form: int = 0) -> float:
+    return fit_flops(lengths, form) + backward_flops(lengths, form)
 
 
 # Two-filter smoother, per cluster: the outward filter it runs (a fit step,
