@@ -8,7 +8,7 @@ single-row steps use) + transport L <- J L (60) + two Potter scalar updates
 (2 x 128) + the alignment subtraction (2).  U-D form: the same prediction +
 transport U <- J U (16) + Bierman's updates of y (85) and z (75) + 2.  The
 first cluster of a pass has no prediction or transport.  The output
-covariance costs 135 per track from L, 75 from U and D.  form: 0 square
+covariance costs 135 per track from L, 70 from U and D.  form: 0 square
 root, 1 U-D.
 """
 from __future__ import annotations
@@ -26,7 +26,7 @@ UD_TRANSPORT = 16
 UD_UPDATE = (85, 75)
 UD_STEP = PREDICT + UD_TRANSPORT + sum(UD_UPDATE) + MEAS       # 257
 UD_FIRST = sum(UD_UPDATE) + MEAS                               # 162
-UD_OUTPUT = 75
+UD_OUTPUT = 70
 
 
 def fit_flops(lengths, form: int = 0) -> float:
@@ -47,8 +47,8 @@ def fit_bytes(lengths) -> float:
 # Reverse sweep (adjoint), counted from the formula list of the hand-written
 # reverse of each forward piece: a Potter scalar update (268), the transport
 # L <- J L (120) and the prediction with its Jacobian (150); in U-D form
-# Bierman's updates of y (272) and z (243, their partial gain sums recomputed
-# in the forward's order included) and the transport U <- J U (26).
+# Bierman's updates of y (260) and z (226, their partial gain sums recomputed
+# in the forward's order included) and the transport U <- J U (20).
 # Recomputation of forward values (checkpoint segments, per-step
 # intermediates) is overhead and is not counted.
 REV_SCALAR_UPDATE = 268
@@ -56,10 +56,10 @@ REV_TRANSPORT = 120
 REV_PREDICT = 150
 REV_STEP = REV_PREDICT + REV_TRANSPORT + 2 * REV_SCALAR_UPDATE   # 806
 REV_FIRST = 2 * REV_SCALAR_UPDATE                                 # 536
-UD_REV_UPDATE = (272, 243)
-UD_REV_TRANSPORT = 26
-UD_REV_STEP = REV_PREDICT + UD_REV_TRANSPORT + sum(UD_REV_UPDATE)  # 691
-UD_REV_FIRST = sum(UD_REV_UPDATE)                                   # 515
+UD_REV_UPDATE = (260, 226)
+UD_REV_TRANSPORT = 20
+UD_REV_STEP = REV_PREDICT + UD_REV_TRANSPORT + sum(UD_REV_UPDATE)  # 656
+UD_REV_FIRST = sum(UD_REV_UPDATE)                                   # 486
 
 
 def backward_flops(lengths, form: int = 0) -> float:

@@ -35,6 +35,7 @@ class N:
     __rmul__ = __mul__
     def __truediv__(self, o): return self._op(self.v / N._v(o))
     def __rtruediv__(self, o): return self._op(N._v(o) / self.v)
+    def __neg__(self): return N(-self.v)   # a sign flip folds into the operation that uses it
 
 
 def sqrt(x):
@@ -141,6 +142,173 @@ def covariance_output():
                 acc = acc + L[i][c] * L[j][c]
 
 
+def _ud(seed=0.1):
+    u = [[N(seed * (i + 2 * j + 1)) if j > i else None for j in range(5)] for i in range(5)]
+    d = [N(1.0 + 0.1 * j) for j in range(5)]
+    return u, d
+
+
+def transport_ud():
+    """U <- J U without rotation (J unit upper triangular): the seven entries that change."""
+    u, _ = _ud()
+    ys, yq, zs, zt, zq, sq = (N(0.2) for _ in range(6))
+    u[0][4] = (u[0][4] + ys * u[2][4]) + yq
+    u[0][3] = u[0][3] + ys * u[2][3]
+    u[0][2] = u[0][2] + ys
+    u[1][4] = ((u[1][4] + zs * u[2][4]) + zt * u[3][4]) + zq
+    u[1][3] = (u[1][3] + zs * u[2][3]) + zt
+    u[1][2] = u[1][2] + zs
+    u[2][4] = u[2][4] + sq
+
+
+def bierman_update(H):
+    """Bierman's scalar update of component H in residual coordinates (measured value 0)."""
+    u, d = _ud()
+    p = [N(0.3) for _ in range(5)]
+    v, chi2 = N(0.01), N(0.0)
+    K = [None] * 5
+    ap, iap = v, None
+    for j in range(H, 5):
+        f = None if j == H else u[H][j]
+        g = d[j] if j == H else d[j] * f
+        a = ap + g if j == H else ap + f * g
+        ia = 1.0 / a
+        if j > H:
+            lam = -(f * iap)
+            for i in range(j):
+                uo = u[i][j]
+                u[i][j] = uo + lam * K[i]
+                K[i] = K[i] + g * uo
+        else:
+            for i in range(j):
+                K[i] = g * u[i][j]
+        d[j] = d[j] * (ap * ia)
+        K[j] = g
+        ap, iap = a, ia
+    r = -p[H]
+    q = r * iap
+    for i in range(5):
+        p[i] = p[i] + K[i] * q
+    chi2 = chi2 + r * q
+
+
+def covariance_output_ud():
+    """C = U D U^T, lower triangle: C_ij = sum over k >= i of u_ik d_k u_jk (u_kk = 1)."""
+    u, d = _ud()
+    for i in range(5):
+        for j in range(i + 1):
+            acc = d[i] if j == i else u[j][i] * d[i]
+            for k in range(i + 1, 5):
+                acc = acc + (u[i][k] * d[k]) * u[j][k]
+
+
+def transport_ud_rev():
+    """Reverse of transport_ud: the Jacobian's adjoint (started at zero) and the factor's."""
+    u, _ = _ud()
+    b = {k: N(0.3) for k in ("02", "03", "04", "12", "13", "14", "24")}
+    ys, zs, zt = N(0.2), N(0.2), N(0.2)
+    bJ_ys = (b["02"] + u[2][3] * b["03"]) + u[2][4] * b["04"]
+    bJ_zs = (b["12"] + u[2][3] * b["13"]) + u[2][4] * b["14"]
+    bJ_zt = b["13"] + u[3][4] * b["14"]
+    bu23, bu24, bu34 = N(0.1), N(0.1), N(0.1)
+    bu23 = bu23 + (ys * b["03"] + zs * b["13"])
+    bu24 = bu24 + (ys * b["04"] + zs * b["14"])
+    bu34 = bu34 + zt * b["14"]
+
+
+def bierman_update_rev(H):
+    """Reverse of bierman_update<H> with the partial gain sums recomputed in the
+    forward's order; operations whose results are unused where j = H are left out."""
+    u, d = _ud()
+    bu = [[N(0.2) if j > i else None for j in range(5)] for i in range(5)]
+    bd = [N(0.2) for _ in range(5)]
+    bp = [N(0.2) for _ in range(5)]
+    p = [N(0.3) for _ in range(5)]
+    v, bchi = N(0.01), N(1.0)
+    gv = [None if j < H else (d[j] if j == H else d[j] * u[H][j]) for j in range(5)]
+    al, ial = [None] * 5, [None] * 5
+    ap = v
+    for j in range(H, 5):
+        al[j] = ap + gv[j] if j == H else ap + u[H][j] * gv[j]
+        ial[j] = 1.0 / al[j]
+        ap = al[j]
+
+    def k_before(i, j):
+        acc = gv[i]
+        for k in range(max(i + 1, H), j):
+            acc = u[i][k] * gv[k] if acc is None else acc + u[i][k] * gv[k]
+        return acc
+
+    K = [k_before(i, 5) for i in range(5)]
+    r = -p[H]
+    q = r * ial[4]
+    bK = [q * bp[i] for i in range(5)]
+    bqo = r * bchi
+    for i in range(5):
+        if i != H:
+            bqo = bqo + K[i] * bp[i]
+    bq = bqo + K[H] * bp[H]
+    ba = -(ial[4] * ial[4]) * (r * bq)
+    bp[H] = (v * ial[4]) * bp[H] - (q * bchi + ial[4] * bqo)
+    for j in range(4, H - 1, -1):
+        g = gv[j]
+        bg = bK[j]
+        if j > H:
+            f = u[H][j]
+            iapj = ial[j - 1]
+            lam = -(f * iapj)
+            blam = None
+            for i in range(j - 1, -1, -1):
+                uo = u[i][j]
+                kb = k_before(i, j)
+                bv = bu[i][j]
+                bg = bg + uo * bK[i] if bK[i] is not None else bg
+                blam = kb * bv if blam is None else blam + kb * bv
+                if kb is None:
+                    pass
+                bu[i][j] = bv + g * bK[i] if bK[i] is not None else bv
+                bK[i] = lam * bv if bK[i] is None else bK[i] + lam * bv
+            bf = -(blam * iapj)
+            bap = -(lam * blam) * iapj
+            rho = al[j - 1] * ial[j]
+            bdn = bd[j]
+            bap = bap + (d[j] * bdn) * ial[j]
+            ba = ba - ((d[j] * rho) * bdn) * ial[j]
+            bdj = bdn * rho
+            bap = bap + ba
+            bf = bf + g * ba
+            bg = bg + f * ba
+            bdj = bdj + f * bg
+            bf = bf + d[j] * bg
+            bd[j] = bdj
+            bu[H][j] = bu[H][j] + bf
+            ba = bap
+        else:
+            for i in range(j - 1, -1, -1):
+                uo = u[i][j]
+                bg = bg + uo * bK[i]
+                bu[i][j] = bu[i][j] + g * bK[i]
+            rho = v * ial[j]
+            bdn = bd[j]
+            ba = ba - ((d[j] * rho) * bdn) * ial[j]
+            bdj = bdn * rho
+            bg = bg + ba
+            bd[j] = bdj + bg
+
+
+@pytest.mark.parametrize("fn,const", [(transport_ud, flops.UD_TRANSPORT),
+                                      (lambda: bierman_update(0), flops.UD_UPDATE[0]),
+                                      (lambda: bierman_update(1), flops.UD_UPDATE[1]),
+                                      (covariance_output_ud, flops.UD_OUTPUT),
+                                      (transport_ud_rev, flops.UD_REV_TRANSPORT),
+                                      (lambda: bierman_update_rev(0), flops.UD_REV_UPDATE[0]),
+                                      (lambda: bierman_update_rev(1), flops.UD_REV_UPDATE[1])],
+                         ids=["transport_ud", "bierman_y", "bierman_z", "covariance_output_ud",
+                              "transport_ud_rev", "bierman_rev_y", "bierman_rev_z"])
+def test_u_d_piece_counts(fn, const):
+    assert count(fn) == const
+
+
 @pytest.mark.parametrize("fn,const", [(prediction, flops.PREDICT), (transport, flops.TRANSPORT),
                                       (scalar_update, flops.SCALAR_UPDATE), (alignment, flops.MEAS),
                                       (covariance_output, flops.OUTPUT)],
@@ -154,3 +322,5 @@ def test_step_totals():
     assert flops.FIRST == 2 * flops.SCALAR_UPDATE + flops.MEAS
     # a track of n clusters: both passes of n - 1 full steps and one first step, and the output
     assert flops.fit_flops([10, 1, 0]) == 2 * (9 * 397 + 258) + 135 + 2 * 258 + 135
+    assert flops.UD_STEP == flops.PREDICT + flops.UD_TRANSPORT + sum(flops.UD_UPDATE) + flops.MEAS
+    assert flops.fit_flops([10], form=1) == 2 * (9 * flops.UD_STEP + flops.UD_FIRST) + flops.UD_OUTPUT
