@@ -1096,8 +1096,8 @@ __global__ void __launch_bounds__(WARPS * 32, 1) backward_kernel(const __grid_co
             if (addg && i > 0) gnx = gmr[h - hd];
             float b_mc[2], b_mp[2];
             if constexpr (FORM == 1)
-              step_rev_ud<FIELD>(G, T, &W.st[kk & 1][0][lane], mpy, mpz, i == 0, pass == 0, row, side_sector(sec), m0,
-                                 m1, b_p, b_u, b_d, b_chi, b_mc, b_mp);
+              step_rev_ud<FIELD>(G, T, &W.st[kk & 1][0][lane], mpy, mpz, T.row_x[prow], side_sector(psec), i == 0,
+                                 pass == 0, row, side_sector(sec), m0, m1, b_p, b_u, b_d, b_chi, b_mc, b_mp);
             else if (MAT)
               step_rev_mat<FIELD>(G, T, &W.st[kk & 1][0][lane], mpy, mpz, i == 0, pass == 0, row, side_sector(sec), m0, m1,
                                   b_p, b_L, b_chi, b_mc, b_mp);

@@ -26,9 +26,11 @@ struct UDState {
   int sec;
 };
 
-// States between checkpoints in U-D form: 6 float4 (p 5, u 10, d 5, x, sector
-// bits, 2 unused), lane-interleaved like the square-root states.
-constexpr int kUDStateF4 = 6;
+// States between checkpoints in U-D form: 5 float4 (p 5, u 10, d 5),
+// lane-interleaved like the square-root states.  x and the sector of a stored
+// state are those of the cluster before the step, which the reverse decodes
+// anyway, so they are not stored.
+constexpr int kUDStateF4 = 5;
 
 // (U, D) of C = L L^T: the rows of L orthogonalised last first with unit
 // weights, d_k = |w_k|^2, u_ik = (w_i . w_k) / d_k, w_i -= u_ik w_k.
@@ -274,24 +276,20 @@ __device__ __forceinline__ void bierman_update_rev(const float p[5], const float
 
 // ---------------------------------------------------------------- one step in U-D form
 __device__ __forceinline__ void store_state(float4* dst, const UDState& S) {
-  float v[24];
+  float v[20];
 #pragma unroll
   for (int c = 0; c < 5; ++c) v[c] = S.p[c];
 #pragma unroll
   for (int e = 0; e < 10; ++e) v[5 + e] = S.u[e];
 #pragma unroll
   for (int c = 0; c < 5; ++c) v[15 + c] = S.d[c];
-  v[20] = S.x;
-  v[21] = __int_as_float(S.sec);
-  v[22] = 0.0f;
-  v[23] = 0.0f;
 #pragma unroll
   for (int j = 0; j < kUDStateF4; ++j) dst[j * kWarp] = make_float4(v[4 * j], v[4 * j + 1], v[4 * j + 2], v[4 * j + 3]);
 }
 
 template <bool VOLATILE>
 __device__ __forceinline__ void read_state_ud(const float4* src, UDState& S) {
-  float v[24];
+  float v[20];
 #pragma unroll
   for (int j = 0; j < kUDStateF4; ++j) {
     const float4 f = VOLATILE ? lds_volatile(src + j * kWarp) : src[j * kWarp];
@@ -306,8 +304,6 @@ __device__ __forceinline__ void read_state_ud(const float4* src, UDState& S) {
   for (int e = 0; e < 10; ++e) S.u[e] = v[5 + e];
 #pragma unroll
   for (int c = 0; c < 5; ++c) S.d[c] = v[15 + c];
-  S.x = v[20];
-  S.sec = __float_as_int(v[21]);
 }
 
 // A segment's first state from the fit's checkpoint, loaded as a StepState:
@@ -364,14 +360,17 @@ __device__ __forceinline__ void step_fwd_ud(const GeoRef& G, const SmemTables& T
 }
 
 // Reverse of one step in U-D form; the arguments as for step_rev, with the
-// factor's adjoint (b_u, b_d) in place of b_L.
+// factor's adjoint (b_u, b_d) in place of b_L, and x_prev, sec_prev (the
+// previous cluster's row position and sector mod 18: the state's frame).
 template <int FIELD = 0>
 __device__ __forceinline__ void step_rev_ud(const GeoRef& G, const SmemTables& T, const float4* src, float my_prev,
-                                            float mz_prev, bool first, bool conv, int row, int sec18, float m0,
-                                            float m1, float b_p[5], float b_u[10], float b_d[5], float b_chi,
-                                            float b_mc[2], float b_mp[2]) {
+                                            float mz_prev, float x_prev, int sec_prev, bool first, bool conv, int row,
+                                            int sec18, float m0, float m1, float b_p[5], float b_u[10], float b_d[5],
+                                            float b_chi, float b_mc[2], float b_mp[2]) {
   UDState S0;
   read_state_ud<false>(src, S0);
+  S0.x = x_prev;
+  S0.sec = sec_prev;
   float p1[5];
   Jac J;
   PredTape tp;
