@@ -334,8 +334,9 @@ def run_batched_frames(args, tf, torch, synth, flops, peak_tf):
     pool, picks = synth.batched_frames(pool_tracks=args.pool_tracks)
     batch = FrameBatch.from_pool(pool, picks)
     lengths = np.diff(batch.offsets.cpu().numpy().astype(np.int64))
-    res = {"workload": "256 frames, tracks per frame log-uniform on [1e3, 2e5], drawn from a simulated pool of "
-                       f"{pool.n_tracks} tracks (5% drop, lengths U{{10..152}})",
+    res = {"workload": "256 frames, tracks per frame log-uniform on [1e3, 2e5], drawn (seeded, with replacement) "
+                       f"from a simulated pool of {pool.n_tracks} tracks (5% drop, lengths U{{10..152}}): frames "
+                       "repeat pool tracks, so they are not independent simulations",
            "frames": batch.n_frames, "tracks": batch.n_tracks, "hits": batch.n_hits}
     for mode in ("fast", "det"):
         f = tf.Fitter(pool.geometry, pool.bz, deterministic=(mode == "det"))
