@@ -1062,8 +1062,12 @@ __global__ void __launch_bounds__(WARPS * 32, 1) backward_kernel(const __grid_co
           }
           // the states just stored are read back by this thread's copies below
           __threadfence_block();
-          // the next segment's checkpoint travels while this one is reversed
-          if (s > 0) fetch_ckpt(&W.ck[0][lane], ckp + (int64_t)(s - 1) * kCkptFloats);
+          // the next segment's checkpoint travels while this one is reversed.
+          // Copy groups complete in order, so it is committed after the
+          // loop's first state copy: the first reverse step then waits only
+          // for its own state (a one-step segment commits it here)
+          const bool ck_next = s > 0;
+          if (ck_next && cnt == 1) fetch_ckpt(&W.ck[0][lane], ckp + (int64_t)(s - 1) * kCkptFloats);
           // reverse; (m0, m1, row, sec) hold the segment's last cluster, which is
           // the current cluster of its last step; each step's previous cluster
           // becomes the current one of the step before it
@@ -1081,7 +1085,12 @@ __global__ void __launch_bounds__(WARPS * 32, 1) backward_kernel(const __grid_co
             const int h = h0 + hd * i;
             if (kk > 0) {
               fetch_state<F4>(&W.st[(kk - 1) & 1][0][lane], gs + (kk - 1) * (F4 * kWarp));
-              cp_async_wait<1>();
+              if (ck_next && kk == cnt - 1) {
+                fetch_ckpt(&W.ck[0][lane], ckp + (int64_t)(s - 1) * kCkptFloats);
+                cp_async_wait<2>();
+              } else {
+                cp_async_wait<1>();
+              }
             } else {
               cp_async_wait<0>();
             }
