@@ -181,6 +181,23 @@ def test_autograd_function_and_masking(case):
         f.close()
 
 
+def test_factor_form_setters_reject_other_values():
+    fr = synth.generate(20, 37)
+    f = tf.Fitter(fr.geometry, fr.bz)
+    try:
+        for bad in (-1, 2):
+            with pytest.raises(tf.TpcfitError) as e:
+                f.set_fit_form(bad)
+            assert e.value.status == tf.EINVAL
+            with pytest.raises(tf.TpcfitError) as e:
+                f.set_backward_form(bad)
+            assert e.value.status == tf.EINVAL
+        f.set_fit_form(0)
+        f.set_backward_form(0)
+    finally:
+        f.close()
+
+
 def test_square_root_reverse_refuses_a_u_d_recording():
     fr = synth.generate(200, 36)
     dev = tf.frame_to_device(fr)
