@@ -939,14 +939,18 @@ struct BwdSmem {
   SmemTables T;
   float align[kAlignFloats];
 };
-struct BwdWarpBufs {
-  float4 st[2][kStateF4][kWarp];
+// F4: float4 per stored state (kStateF4 for the square-root form, kUDStateF4
+// for U-D); the checkpoint buffer always holds kStateF4.
+template <int F4 = kStateF4>
+struct BwdWarpBufsT {
+  float4 st[2][F4][kWarp];
   float4 ck[kStateF4][kWarp];
 };
+using BwdWarpBufs = BwdWarpBufsT<>;
 
-template <int WARPS>
+template <int WARPS, int FORM = 0>
 constexpr size_t backward_smem_bytes() {
-  return sizeof(BwdSmem) + WARPS * sizeof(BwdWarpBufs);
+  return sizeof(BwdSmem) + WARPS * sizeof(BwdWarpBufsT<FORM ? kUDStateF4 : kStateF4>);
 }
 
 // Per track, per pass (inward reversed first), segment by segment from the
@@ -974,7 +978,7 @@ __global__ void __launch_bounds__(WARPS * 32, 1) backward_kernel(const __grid_co
   const SmemTables& T = B.T;
   const int lane = threadIdx.x & 31;
   const int warp = threadIdx.x >> 5;
-  BwdWarpBufs& W = reinterpret_cast<BwdWarpBufs*>(smem_raw + sizeof(BwdSmem))[warp];
+  BwdWarpBufsT<F4>& W = reinterpret_cast<BwdWarpBufsT<F4>*>(smem_raw + sizeof(BwdSmem))[warp];
   // this warp's segment store: [step kk][float4 j][lane]
   float4* const gs = a.seg + ((int64_t)blockIdx.x * WARPS + warp) * (kCkptEvery * F4 * kWarp) + lane;
   const int64_t n_chunks = ((int64_t)a.n_tracks + kWarp - 1) / kWarp;
@@ -1373,7 +1377,7 @@ cudaError_t backward_grid(int& grid) {
   static int cached = 0;
   if (cached == 0) {
     constexpr int kThreads = WARPS * 32;
-    const size_t smem = backward_smem_bytes<WARPS>();
+    const size_t smem = backward_smem_bytes<WARPS, FORM>();
     cudaError_t e = cudaFuncSetAttribute(backward_kernel<WARPS, PHYS, FORM>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
@@ -1408,7 +1412,7 @@ cudaError_t launch_backward_cfg(const BwdArgs& a, cudaStream_t s) {
   const int blocks = (int)(need < grid ? need : grid);
   e = cudaMemsetAsync(a.work, 0, sizeof(unsigned int), s);
   if (e != cudaSuccess) return e;
-  backward_kernel<WARPS, PHYS, FORM><<<blocks, WARPS * 32, backward_smem_bytes<WARPS>(), s>>>(a);
+  backward_kernel<WARPS, PHYS, FORM><<<blocks, WARPS * 32, backward_smem_bytes<WARPS, FORM>(), s>>>(a);
   return cudaGetLastError();
 }
 
