@@ -258,7 +258,9 @@ tpcfit_status tpcfit_set_backward_form(tpcfit_handle* h, int form);
 
 /* Adjoint of the recorded fit: gradients of L = sum_i grad_chi2[i] * chi2_i.
  * Inputs must be those of the last tpcfit_fit on this handle, which must have
- * run with recording on and in the same mode (otherwise ESTATE):
+ * run with recording on and in the same mode, and, for the square-root
+ * reverse (tpcfit_set_backward_form 0), in the square-root form (otherwise
+ * ESTATE):
  *   hits, track_offsets, n_tracks: as for tpcfit_fit;
  *   ndf:        device int32 [n_tracks], the ndf output of that fit;
  *   grad_chi2:  device float [n_tracks], dL/dchi2_i.
