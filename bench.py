@@ -514,7 +514,23 @@ def main():
     torch.cuda.synchronize()
     _, sm_per = timed(step_smooth, max(5, args.steps // 4))
     smooth_ms = statistics.mean(p[0] for p in sm_per)
-    del sm
+    # outlier rejection on the smoother's chi2 (2-dof cut 16): kept clusters copied, new offsets
+    rj = dict(y=torch.empty(fr.n_hits, device="cuda"), z=torch.empty(fr.n_hits, device="cuda"),
+              rs=torch.empty(fr.n_hits, dtype=torch.int16, device="cuda"),
+              off=torch.empty(fr.n_tracks + 1, dtype=torch.int32, device="cuda"))
+
+    def step_reject(mid):
+        tf.tpcfit_reject_outliers(fitter.h, dev["y"], dev["z"], dev["rowsec"], dev["offsets"], sm["chi2"], 16.0,
+                                  rj["y"], rj["z"], rj["rs"], rj["off"])
+        mid.record(stream)
+
+    for _ in range(args.warmup):
+        step_reject(torch.cuda.Event())
+    torch.cuda.synchronize()
+    _, rj_per = timed(step_reject, max(5, args.steps // 4))
+    reject_ms = statistics.mean(p[0] for p in rj_per)
+    reject_kept = int(rj["off"][-1].item())
+    del sm, rj
     # the smoothed state and covariance at every cluster
     ss = dict(state=torch.empty((fr.n_hits, 5), device="cuda"), cov=torch.empty((fr.n_hits, 15), device="cuda"))
 
@@ -725,7 +741,10 @@ def main():
     sm_f = flops.smooth_flops(lengths) / (smooth_ms / 1e3) / 1e12
     line["smoother"] = {"tracks_per_s": fr.n_tracks / (smooth_ms / 1e3), "clusters_per_s": fr.n_hits / (smooth_ms / 1e3),
                         "ms": smooth_ms, "frac_impl": sm_f / peak_tf,
-                        "states": {"ms": states_ms, "clusters_per_s": fr.n_hits / (states_ms / 1e3)}}
+                        "states": {"ms": states_ms, "clusters_per_s": fr.n_hits / (states_ms / 1e3)},
+                        "reject": {"ms": reject_ms, "clusters_per_s": fr.n_hits / (reject_ms / 1e3),
+                                   "cut": 16.0, "kept_fraction": reject_kept / fr.n_hits,
+                                   "bytes_per_cluster": 24, "achieved_gbs": 24 * fr.n_hits / (reject_ms / 1e3) / 1e9}}
     line["plain_fit"]["field_map"] = {"tracks_per_s": fr.n_tracks / (fld_ms / 1e3), "ms": fld_ms,
                                       "field": "Bz (1 + 0.3 (r/250)^2 - 0.2 (z/250)^2)"}
     line["plain_fit"]["material"] = {"tracks_per_s": fr.n_tracks / (mat_ms / 1e3), "ms": mat_ms,

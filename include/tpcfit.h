@@ -319,6 +319,29 @@ tpcfit_status tpcfit_smooth_states(tpcfit_handle* h, const tpcfit_hits* hits, co
                                    int32_t n_tracks, const int32_t* ndf, float* state, float* state_cov,
                                    void* stream);
 
+/* Outlier rejection (the cluster-to-track association the smoother's chi2
+ * tests; Sec. 2 keeps that relation's order deterministic): the clusters
+ * whose leave-one-out chi2 from tpcfit_smooth is above chi2_cut are dropped
+ * from their tracks, all others are copied, in their order, into
+ * (y_out, z_out, rowsec_out).  offsets_out [n_tracks + 1] receives the new
+ * track offsets; its last element is the number of clusters kept.  A cluster
+ * whose chi2 is NaN (an unfitted track, a cluster the fit did not reach) is
+ * kept.  The seeds stay as they were: a track whose first cluster is dropped
+ * starts its refit from its old seed at the new first cluster's row, which the
+ * diffuse start (100 cm^2, 100 in the angles and q/pt) makes immaterial for
+ * all but the shortest tracks.  Inputs: the hits and offsets of the smoothed
+ * fit (device) and its per-cluster chi2 (device float [n_hits]).  Outputs:
+ * device arrays of n_hits elements (at most that many are written) and
+ * offsets_out; they must not overlap the inputs.  Tracks whose offsets are
+ * out of order or outside the arrays keep no cluster; tracks whose ranges
+ * overlap give unspecified contents, and nothing is written beyond n_hits
+ * elements.  Deterministic: the
+ * result does not depend on the launch.  EINVAL for a negative or NaN cut,
+ * missing or misaligned pointers, n_hits > INT32_MAX. */
+tpcfit_status tpcfit_reject_outliers(tpcfit_handle* h, const tpcfit_hits* hits, const int32_t* track_offsets,
+                                     int32_t n_tracks, const float* chi2, float chi2_cut, float* y_out, float* z_out,
+                                     uint16_t* rowsec_out, int32_t* offsets_out, void* stream);
+
 /* Fit + adjoint with HOST buffers, for streams of batches.  Copies hits,
  * offsets, seeds and grad_chi2 (host, as for tpcfit_fit and
  * tpcfit_fit_backward) to the device on an internal copy stream, fits with

@@ -36,6 +36,7 @@ UNITS = {
     "tpcfit_noalloc.cu": [],
     "key_reduce.cu": [],
     "fp32_peak.cu": [],
+    "reject.cu": [],
 }
 
 

@@ -62,6 +62,13 @@ tpcfit_status rtc_launch_fit(const GeoConst& g, bool det, int rps, int warps, co
 int64_t frame_order_scratch_ints(int32_t n_frames);
 cudaError_t launch_frame_length_order(const int32_t* off, int32_t n_tracks, const int64_t* frame_base,
                                       int32_t n_frames, int32_t* perm, int32_t* scratch, cudaStream_t s);
+// Outlier rejection (reject.cu): the clusters with chi2 > cut dropped, the
+// others copied in order; off_out [n_tracks + 1] receives the new offsets.
+// scratch: reject_scratch_ints(n_tracks) ints.
+int64_t reject_scratch_ints(int32_t n_tracks);
+cudaError_t launch_reject(const int32_t* off, int32_t n_tracks, const float* y, const float* z, const uint16_t* rowsec,
+                          int64_t n_hits, const float* chi2, float cut, float* y_out, float* z_out,
+                          uint16_t* rowsec_out, int32_t* off_out, int32_t* scratch, cudaStream_t s);
 // Exclusive prefix sum of n ints in place (key_reduce.cu); tmp: scan_tmp_ints(n) ints.
 int64_t scan_tmp_ints(int64_t n);
 cudaError_t launch_scan_exclusive(int* v, int n, int* tmp, cudaStream_t s);

@@ -123,6 +123,8 @@ struct tpcfit_handle {
   unsigned char* d_keys = nullptr;
   size_t keys_cap = 0;
   // batched frames: ordering scratch
+  int32_t* d_reject = nullptr;  // scan scratch of the outlier rejection
+  int64_t reject_cap = 0;       // ints
   int32_t* d_frame_scratch = nullptr;
   int64_t frame_scratch_cap = 0;
 };
@@ -256,6 +258,7 @@ void tpcfit_destroy(tpcfit_handle* h) {
   if (h->d_tape) cudaFree(h->d_tape);
   if (h->d_keys) cudaFree(h->d_keys);
   if (h->d_frame_scratch) cudaFree(h->d_frame_scratch);
+  if (h->d_reject) cudaFree(h->d_reject);
   delete h;
 }
 
@@ -413,6 +416,23 @@ tpcfit_status tpcfit_set_backward_config(tpcfit_handle* h, int warps_per_block) 
   if (!h || !backward_shape_supported(warps_per_block)) return TPCFIT_EINVAL;
   h->bwd_warps = warps_per_block;
   return TPCFIT_OK;
+}
+
+tpcfit_status tpcfit_reject_outliers(tpcfit_handle* h, const tpcfit_hits* hits, const int32_t* track_offsets,
+                                     int32_t n_tracks, const float* chi2, float chi2_cut, float* y_out, float* z_out,
+                                     uint16_t* rowsec_out, int32_t* offsets_out, void* stream) {
+  if (!h || !hits || n_tracks < 0 || hits->n_hits < 0 || hits->n_hits > INT32_MAX || !offsets_out) return TPCFIT_EINVAL;
+  if (!(chi2_cut >= 0.0f) || !aligned(offsets_out, 4)) return TPCFIT_EINVAL;  // a NaN cut is refused too
+  if (n_tracks > 0 && (!track_offsets || !aligned(track_offsets, 4))) return TPCFIT_EINVAL;
+  if (hits->n_hits > 0) {
+    if (!hits->y || !hits->z || !hits->rowsec || !chi2 || !y_out || !z_out || !rowsec_out) return TPCFIT_EINVAL;
+    if (!aligned(chi2, 4) || !aligned(y_out, 4) || !aligned(z_out, 4) || !aligned(rowsec_out, 2)) return TPCFIT_EINVAL;
+  }
+  tpcfit_status st = grow(h->d_reject, h->reject_cap, reject_scratch_ints(n_tracks));
+  if (st != TPCFIT_OK) return st;
+  return from_cuda(launch_reject(track_offsets, n_tracks, hits->y, hits->z, hits->rowsec, hits->n_hits, chi2,
+                                 chi2_cut, y_out, z_out, rowsec_out, offsets_out, h->d_reject,
+                                 (cudaStream_t)stream));
 }
 
 tpcfit_status tpcfit_set_fit_form(tpcfit_handle* h, int form) {

@@ -62,6 +62,7 @@ def load():
         "tpcfit_set_backward_config": (C.c_int, [vp, C.c_int]),
         "tpcfit_set_backward_form": (C.c_int, [vp, C.c_int]),
         "tpcfit_set_fit_form": (C.c_int, [vp, C.c_int]),
+        "tpcfit_reject_outliers": (C.c_int, [vp, C.POINTER(_Hits), vp, C.c_int32, vp, C.c_float, vp, vp, vp, vp, vp]),
         "tpcfit_fit_frames": (C.c_int, [vp, C.POINTER(_Hits), vp, i32, vp, i32, vp, vp, i64, vp, vp, vp, vp, vp,
                                         vp]),
         "tpcfit_fit_backward": (C.c_int, [vp, C.POINTER(_Hits), vp, i32, vp, vp, vp, vp, vp, vp]),
@@ -305,6 +306,29 @@ def tpcfit_smooth(h, y, z, rowsec, offsets, ndf, resid, rcov, chi2, stream=None)
     _check(st, "tpcfit_smooth")
 
 
+def tpcfit_reject_outliers(h, y, z, rowsec, offsets, chi2, chi2_cut, y_out, z_out, rowsec_out, offsets_out,
+                           stream=None) -> None:
+    """Enqueue the outlier rejection: the clusters with chi2 above chi2_cut dropped (device tensors; see
+    include/tpcfit.h)."""
+    import torch
+    n = int(offsets.numel()) - 1
+    H = int(y.numel())
+    hits = _Hits(_dev(y, torch.float32, "y"), _dev(z, torch.float32, "z"), _dev(rowsec, torch.int16, "rowsec"), H)
+    _check_sizes(n, y, z, rowsec)
+    if chi2.numel() != H:
+        raise ValueError("chi2 must have one value per cluster")
+    if y_out.numel() < H or z_out.numel() < H or rowsec_out.numel() < H:
+        raise ValueError("the outputs must hold as many clusters as the input")
+    if offsets_out.numel() != n + 1:
+        raise ValueError("offsets_out must have n_tracks + 1 elements")
+    st = load().tpcfit_reject_outliers(h, C.byref(hits), _dev(offsets, torch.int32, "offsets"), n,
+                                       _dev(chi2, torch.float32, "chi2"), C.c_float(float(chi2_cut)),
+                                       _dev(y_out, torch.float32, "y_out"), _dev(z_out, torch.float32, "z_out"),
+                                       _dev(rowsec_out, torch.int16, "rowsec_out"),
+                                       _dev(offsets_out, torch.int32, "offsets_out"), _stream(stream))
+    _check(st, "tpcfit_reject_outliers")
+
+
 def tpcfit_smooth_states(h, y, z, rowsec, offsets, ndf, state, state_cov, stream=None) -> None:
     """Enqueue the smoothed states of the last recorded fit (device tensors; see include/tpcfit.h)."""
     import torch
@@ -504,6 +528,24 @@ class Fitter:
         tpcfit_smooth(self.h, dev["y"], dev["z"], dev["rowsec"], dev["offsets"], out["ndf"], res["resid"], res["rcov"],
                       res["chi2"], stream)
         return res
+
+    def reject_outliers(self, dev: dict, chi2, chi2_cut: float, stream=None) -> dict:
+        """A copy of the device frame without the clusters whose leave-one-out chi2 (from smooth) is above
+        chi2_cut; the seeds are kept.  Waits for the kept count to size the arrays."""
+        import torch
+        H = int(dev["y"].numel())
+        n = int(dev["offsets"].numel()) - 1
+        d = dev["y"].device
+        y = torch.empty(H, dtype=torch.float32, device=d)
+        z = torch.empty(H, dtype=torch.float32, device=d)
+        rs = torch.empty(H, dtype=torch.int16, device=d)
+        off = torch.empty(n + 1, dtype=torch.int32, device=d)
+        tpcfit_reject_outliers(self.h, dev["y"], dev["z"], dev["rowsec"], dev["offsets"], chi2, chi2_cut, y, z, rs, off,
+                               stream)
+        if stream is not None:
+            stream.synchronize()
+        kept = int(off[-1].item())
+        return dict(y=y[:kept], z=z[:kept], rowsec=rs[:kept], offsets=off, seeds=dev["seeds"])
 
     def smooth_states(self, dev: dict, out: dict, stream=None) -> dict:
         """Smoothed state and covariance at every cluster of the last recorded fit."""
