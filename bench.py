@@ -440,7 +440,7 @@ def main():
     lengths = fr.lengths()
     dev = tf.frame_to_device(fr)
     fitter = tf.Fitter(fr.geometry, fr.bz, deterministic=(args.mode == "det"))
-    if args.bwd_warps:
+    if args.bwd_warps is not None:
         fitter.set_backward_config(args.bwd_warps)
     tf.tpcfit_reserve(fitter.h, fr.n_tracks, fr.n_hits)
     out = tf.empty_outputs(fr.n_tracks)
