@@ -500,6 +500,33 @@ def main():
     fit_rec_ms = statistics.mean(p[0] for p in per)
     bwd_ms = statistics.mean(p[1] for p in per)
 
+    # ---- end to end through the public API with host buffers, on the same
+    # handle right after the device-timed step
+    h2d = 10 * fr.n_hits + 4 * (fr.n_tracks + 1) + 20 * fr.n_tracks
+    d2h = 88 * fr.n_tracks
+    e2e = e2e_plain = None
+    if not args.no_e2e:
+        fitter.set_record(False)
+        e2e_plain = {"value": e2e_run(fitter, fr, out, args.steps, tf, torch), "unit": UNIT,
+                     "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h}
+        fitter.set_record(True)
+        v_serial, _, _ = e2e_fit_adjoint(fitter, fr, args.steps, tf, torch)
+        v, hb, db = e2e_fit_adjoint_pipelined(fitter, fr, args.steps, tf, torch)
+        if world > 1:  # whole job: every rank streams its own batch; the slowest rank sets the pace
+            _, (v, e2e_plain["value"], v_serial) = combine_ranks(dist, torch, "cuda", 0.0,
+                                                                 [v, e2e_plain["value"], v_serial])
+        e2e = {"value": v, "unit": UNIT, "h2d_bytes_per_step": hb, "d2h_bytes_per_step": db,
+               "call": "tpcfit_fit_adjoint_host (C ABI, pinned host buffers), one call per step",
+               "pipelining": "calls issued back to back: step k+1's host-to-device copies (library copy stream, "
+                             "second staging set) overlap step k's fit and adjoint; the host waits for every "
+                             "step's results",
+               "serial_value": v_serial}
+
+    # the smoother below reads the recording of the device-buffer fit
+    fitter.set_record(True)
+    fitter.fit(dev, out)
+    torch.cuda.synchronize()
+
     # ---- the two-filter smoother of the recorded fit (per-cluster outlier test)
     sm = dict(resid=torch.empty((fr.n_hits, 2), device="cuda"), rcov=torch.empty((fr.n_hits, 3), device="cuda"),
               chi2=torch.empty(fr.n_hits, device="cuda"))
@@ -645,26 +672,6 @@ def main():
         sqrt_form = {"plain_fit_ms": statistics.mean(p[0] for p in sq_fit_per),
                      "fit_ms": statistics.mean(p[0] for p in sq_fa_per),
                      "backward_ms": statistics.mean(p[1] for p in sq_fa_per)}
-
-    # ---- end to end through the public API with host buffers
-    h2d = 10 * fr.n_hits + 4 * (fr.n_tracks + 1) + 20 * fr.n_tracks
-    d2h = 88 * fr.n_tracks
-    e2e = e2e_plain = None
-    if not args.no_e2e:
-        e2e_plain = {"value": e2e_run(fitter, fr, out, args.steps, tf, torch), "unit": UNIT,
-                     "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h}
-        fitter.set_record(True)
-        v_serial, _, _ = e2e_fit_adjoint(fitter, fr, args.steps, tf, torch)
-        v, hb, db = e2e_fit_adjoint_pipelined(fitter, fr, args.steps, tf, torch)
-        if world > 1:  # whole job: every rank streams its own batch; the slowest rank sets the pace
-            _, (v, e2e_plain["value"], v_serial) = combine_ranks(dist, torch, "cuda", 0.0,
-                                                                 [v, e2e_plain["value"], v_serial])
-        e2e = {"value": v, "unit": UNIT, "h2d_bytes_per_step": hb, "d2h_bytes_per_step": db,
-               "call": "tpcfit_fit_adjoint_host (C ABI, pinned host buffers), one call per step",
-               "pipelining": "calls issued back to back: step k+1's host-to-device copies (library copy stream, "
-                             "second staging set) overlap step k's fit and adjoint; the host waits for every "
-                             "step's results",
-               "serial_value": v_serial}
 
     if rank != 0:
         fitter.close()
