@@ -256,6 +256,21 @@ tpcfit_status tpcfit_set_fit_form(tpcfit_handle* h, int form);
  * values. */
 tpcfit_status tpcfit_set_backward_form(tpcfit_handle* h, int form);
 
+/* How the deterministic mode sums the per-cluster gradients into grad_align
+ * (Sec. 2 asks for results that do not depend on the order of parallel work):
+ *   0 (default): each cluster gradient is rounded once to a 64-bit
+ *     fixed-point integer with the unit 2^-S, S fixed per call by the largest
+ *     finite |gradient| and the cluster count so that no sum can overflow;
+ *     integer addition does not depend on its order, and each key's sum is
+ *     rounded once to FP32 (NaN where a cluster gradient is not finite);
+ *   1: the clusters are sorted by (sector, row) with a stable radix sort and
+ *     each key is summed in FP32 in a fixed order.
+ * Both give the same bits in every run and launch shape; 0 is the closer to
+ * the exact sum (its only rounding: 2^-S per cluster, at most about 1e-11 of
+ * the largest gradient at 400,000 tracks, and the final FP32 rounding) and
+ * the faster.  Fast mode is not affected.  EINVAL for other values. */
+tpcfit_status tpcfit_set_det_reduction(tpcfit_handle* h, int method);
+
 /* Adjoint of the recorded fit: gradients of L = sum_i grad_chi2[i] * chi2_i.
  * Inputs must be those of the last tpcfit_fit on this handle, which must have
  * run with recording on and in the same mode, and, for the square-root
@@ -279,9 +294,9 @@ tpcfit_status tpcfit_set_backward_form(tpcfit_handle* h, int form);
  * field map and the material layers (tpcfit_set_field_map,
  * tpcfit_set_material).  Tracks of more than 152 clusters get no gradient in
  * the taped cases.  Fast mode accumulates grad_align with
- * atomics; deterministic mode writes per-cluster gradients, sorts the clusters
- * by (sector, row) with a stable radix sort and sums each key in a fixed order,
- * so grad_align is bitwise reproducible.  Tracks with ndf <= 0 contribute 0. */
+ * atomics; deterministic mode writes per-cluster gradients and reduces them
+ * per (sector, row) so that grad_align is bitwise reproducible, by the method
+ * tpcfit_set_det_reduction chose.  Tracks with ndf <= 0 contribute 0. */
 tpcfit_status tpcfit_fit_backward(tpcfit_handle* h, const tpcfit_hits* hits, const int32_t* track_offsets,
                                   int32_t n_tracks, const int32_t* ndf, const float* grad_chi2, float* grad_align,
                                   float* grad_seeds, float* grad_meas, void* stream);

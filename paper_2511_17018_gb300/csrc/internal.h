@@ -40,6 +40,11 @@ cudaError_t launch_key_sort(const uint16_t* rowsec, int64_t n_hits, int n_rows, 
                             int** key_start_out, cudaStream_t s);
 cudaError_t launch_key_reduce(const float* grad_meas, const int* sorted, const int* key_start, float* grad_align,
                               cudaStream_t s);
+// The order-independent alternative: fixed-point integer sums per key (the
+// deterministic mode's default); scratch of key_fixed_scratch_bytes().
+size_t key_fixed_scratch_bytes();
+cudaError_t launch_key_fixed_reduce(const float* grad_meas, const uint16_t* rowsec, int64_t n_hits, int n_rows,
+                                    void* scratch, float* grad_align, cudaStream_t s);
 // true if (lanes_per_track, rows_per_stage, warps) is a compiled launch shape
 bool fit_shape_supported(int lanes_per_track, int rows_per_stage, int warps);
 

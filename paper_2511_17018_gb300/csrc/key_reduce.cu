@@ -9,6 +9,16 @@
 // 2. key_reduce: one warp per key sums its clusters' gradients in sorted order:
 //    lane l takes every 32nd element starting at l, then a fixed shuffle tree.
 // The order of every floating-point addition is a function of the input only.
+//
+// The default reduction is order-independent instead (key_fixed_*): every
+// per-cluster gradient is rounded once to a 64-bit fixed-point integer whose
+// unit is a power of two, 2^-S, fixed by the largest finite |gradient| of the
+// call and by the number of clusters, so that no sum can overflow; integer
+// addition is associative, so the sums do not depend on the order in which
+// blocks, warps and atomics add them, and each key's result (the integer sum
+// times 2^-S, rounded once to FP32) is the same bits in every run.  The
+// rounding to 2^-S is at most 2^-(63 - ceil(log2(n_hits + 1))) of the largest
+// |gradient| per cluster, far below the FP32 rounding of a sum.
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -224,6 +234,111 @@ cudaError_t launch_scan_exclusive(int* v, int n, int* tmp, cudaStream_t s) {
   scan_tiles<<<n_tiles, 1024, 0, s>>>(v, n, tmp);
   scan_totals<<<1, 1024, 0, s>>>(tmp, n_tiles);
   scan_add<<<n_tiles, 1024, 0, s>>>(v, n, tmp);
+  return cudaGetLastError();
+}
+
+namespace {
+
+// Largest finite |g| over the per-cluster gradients (non-negative floats order
+// like their bit patterns, so an unsigned max of the bits is the float max).
+__global__ void __launch_bounds__(256) fixed_absmax(const float* gm, int64_t n, unsigned* absmax) {
+  float m = 0.0f;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const float a = fabsf(gm[i]);
+    if (a <= 3.402823466e38f) m = fmaxf(m, a);  // finite values only
+  }
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, off));
+  if ((threadIdx.x & 31) == 0) atomicMax(absmax, __float_as_uint(m));
+}
+
+// Exponent S of the fixed-point unit 2^-S: |g| < 2^e for the largest |g|, and
+// n_hits terms of at most 2^(62 - cbits) each stay below 2^62.
+__device__ __forceinline__ int fixed_shift(unsigned absmax_bits, int cbits) {
+  int e = 0;
+  frexpf(__uint_as_float(absmax_bits), &e);
+  return 62 - cbits - e;
+}
+
+// Per block: a shared table of the 2 x 5472 fixed-point sums of the clusters
+// the block visits, added into the global table at the end.
+__global__ void __launch_bounds__(1024) fixed_accumulate(const float* gm, const uint16_t* rowsec, int n, int n_rows,
+                                                         const unsigned* absmax, int cbits,
+                                                         unsigned long long* table, unsigned* nonfinite) {
+  extern __shared__ unsigned long long sh[];  // [kKeys * 2]
+  for (int i = threadIdx.x; i < 2 * kKeys; i += blockDim.x) sh[i] = 0ull;
+  __syncthreads();
+  const int S = fixed_shift(*absmax, cbits);
+  for (int h = blockIdx.x * blockDim.x + threadIdx.x; h < n; h += gridDim.x * blockDim.x) {
+    const int k = cluster_key(rowsec, h, n_rows);
+    if (k == kKeyInvalid) continue;
+    const float2 g = reinterpret_cast<const float2*>(gm)[h];
+    if (!(fabsf(g.x) <= 3.402823466e38f) || !(fabsf(g.y) <= 3.402823466e38f)) {
+      atomicOr(nonfinite + k, 1u);
+      continue;
+    }
+    // g 2^S is exact in FP32 (|g 2^S| < 2^62) and rounds once to an integer
+    const long long qx = __float2ll_rn(ldexpf(g.x, S));
+    const long long qy = __float2ll_rn(ldexpf(g.y, S));
+    atomicAdd(sh + 2 * k, (unsigned long long)qx);
+    atomicAdd(sh + 2 * k + 1, (unsigned long long)qy);
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < 2 * kKeys; i += blockDim.x)
+    if (sh[i] != 0ull) atomicAdd(table + i, sh[i]);
+}
+
+// grad_align = -(sum) 2^-S, rounded once to FP32; NaN for a key with a
+// non-finite cluster gradient.
+__global__ void fixed_finish(const unsigned long long* table, const unsigned* nonfinite, const unsigned* absmax,
+                             int cbits, float* grad_align) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= 2 * kKeys) return;
+  const int S = fixed_shift(*absmax, cbits);
+  const double v = ldexp((double)(long long)table[i], -S);
+  grad_align[i] = nonfinite[i / 2] ? __int_as_float(0x7fc00000) : (float)(-v);
+}
+
+constexpr int kFixedThreads = 1024;
+constexpr size_t kFixedSmem = sizeof(unsigned long long) * 2 * kKeys;  // 87,552 B
+
+}  // namespace
+
+size_t key_fixed_scratch_bytes() {
+  return sizeof(unsigned long long) * 2 * kKeys + sizeof(unsigned) * (kKeys + 1);
+}
+
+cudaError_t launch_key_fixed_reduce(const float* grad_meas, const uint16_t* rowsec, int64_t n_hits, int n_rows,
+                                    void* scratch, float* grad_align, cudaStream_t s) {
+  static int blocks = 0;
+  if (blocks == 0) {
+    cudaError_t e = cudaFuncSetAttribute(fixed_accumulate, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kFixedSmem);
+    if (e != cudaSuccess) return e;
+    int dev = 0, sms = 0, per_sm = 0;
+    e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fixed_accumulate, kFixedThreads, kFixedSmem);
+    if (e != cudaSuccess) return e;
+    if (per_sm < 1) return cudaErrorInvalidConfiguration;
+    blocks = sms * per_sm;
+  }
+  unsigned long long* table = static_cast<unsigned long long*>(scratch);
+  unsigned* nonfinite = reinterpret_cast<unsigned*>(table + 2 * kKeys);
+  unsigned* absmax = nonfinite + kKeys;
+  cudaError_t e = cudaMemsetAsync(scratch, 0, key_fixed_scratch_bytes(), s);
+  if (e != cudaSuccess || n_hits == 0) {
+    if (e == cudaSuccess) e = cudaMemsetAsync(grad_align, 0, sizeof(float) * 2 * kKeys, s);
+    return e;
+  }
+  int cbits = 0;
+  while ((1ll << cbits) < n_hits + 1) ++cbits;
+  const int n = (int)n_hits;
+  const int nb = (int)(((int64_t)2 * n_hits + 255) / 256);
+  fixed_absmax<<<nb < blocks * 8 ? nb : blocks * 8, 256, 0, s>>>(grad_meas, 2 * n_hits, absmax);
+  const int na = (n + kFixedThreads - 1) / kFixedThreads;
+  fixed_accumulate<<<na < blocks ? na : blocks, kFixedThreads, kFixedSmem, s>>>(grad_meas, rowsec, n, n_rows, absmax,
+                                                                                   cbits, table, nonfinite);
+  fixed_finish<<<(2 * kKeys + 255) / 256, 256, 0, s>>>(table, nonfinite, absmax, cbits, grad_align);
   return cudaGetLastError();
 }
 

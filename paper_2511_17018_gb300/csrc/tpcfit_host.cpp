@@ -101,6 +101,7 @@ struct tpcfit_handle {
   int record = 0;
   int bwd_warps = 8;
   int bwd_form = 1;            // factor of the fast one-kernel backward: 1 U-D, 0 square root
+  int det_reduce = 0;          // deterministic alignment gradient: 0 fixed-point sums, 1 key sort + fixed-order sums
   int fit_form = 1;            // factor of the fast fit without material: 1 U-D, 0 square root
   int rtc = 0;                 // fit kernels compiled at run time (Sec. 5)
   std::string rtc_dir;         // their on-disk cache, or empty
@@ -442,6 +443,12 @@ tpcfit_status tpcfit_set_fit_form(tpcfit_handle* h, int form) {
   return TPCFIT_OK;
 }
 
+tpcfit_status tpcfit_set_det_reduction(tpcfit_handle* h, int method) {
+  if (!h || (method != 0 && method != 1)) return TPCFIT_EINVAL;
+  h->det_reduce = method;
+  return TPCFIT_OK;
+}
+
 tpcfit_status tpcfit_set_backward_form(tpcfit_handle* h, int form) {
   if (!h || (form != 0 && form != 1)) return TPCFIT_EINVAL;
   h->bwd_form = form;
@@ -581,7 +588,7 @@ tpcfit_status tpcfit_fit_backward(tpcfit_handle* h, const tpcfit_hits* hits, con
     if (st != TPCFIT_OK) return st;
     gm = h->d_gm;
   }
-  const size_t kb = key_sort_scratch_bytes(hits->n_hits);
+  const size_t kb = h->det_reduce == 1 ? key_sort_scratch_bytes(hits->n_hits) : key_fixed_scratch_bytes();
   if (kb > h->keys_cap) {
     if (h->d_keys) cudaFree(h->d_keys);
     h->d_keys = nullptr;
@@ -593,6 +600,11 @@ tpcfit_status tpcfit_fit_backward(tpcfit_handle* h, const tpcfit_hits* hits, con
   b.grad_meas = gm;
   b.grad_align_atomic = nullptr;
   e = launch_backward_det(b, h->bwd_warps, s);
+  if (h->det_reduce == 0) {
+    if (e == cudaSuccess)
+      e = launch_key_fixed_reduce(gm, hits->rowsec, hits->n_hits, h->geo.n_rows, h->d_keys, grad_align, s);
+    return from_cuda(e);
+  }
   int* sorted = nullptr;
   int* key_start = nullptr;
   if (e == cudaSuccess) e = launch_key_sort(hits->rowsec, hits->n_hits, h->geo.n_rows, h->d_keys, &sorted, &key_start, s);

@@ -61,6 +61,7 @@ def load():
         "tpcfit_set_record": (C.c_int, [vp, C.c_int]),
         "tpcfit_set_backward_config": (C.c_int, [vp, C.c_int]),
         "tpcfit_set_backward_form": (C.c_int, [vp, C.c_int]),
+        "tpcfit_set_det_reduction": (C.c_int, [vp, C.c_int]),
         "tpcfit_set_fit_form": (C.c_int, [vp, C.c_int]),
         "tpcfit_reject_outliers": (C.c_int, [vp, C.POINTER(_Hits), vp, C.c_int32, vp, C.c_float, vp, vp, vp, vp, vp]),
         "tpcfit_fit_frames": (C.c_int, [vp, C.POINTER(_Hits), vp, i32, vp, i32, vp, vp, i64, vp, vp, vp, vp, vp,
@@ -257,6 +258,10 @@ def tpcfit_fit_frames(h, y, z, rowsec, offsets, frame_base, seeds, params, cov, 
 
 def tpcfit_set_backward_config(h, warps_per_block: int = 8) -> None:
     _check(load().tpcfit_set_backward_config(h, int(warps_per_block)), "tpcfit_set_backward_config")
+
+
+def tpcfit_set_det_reduction(h, method: int = 0) -> None:
+    _check(load().tpcfit_set_det_reduction(h, int(method)), "tpcfit_set_det_reduction")
 
 
 def tpcfit_set_fit_form(h, form: int = 1) -> None:
@@ -505,6 +510,10 @@ class Fitter:
 
     def set_backward_config(self, warps_per_block: int = 8):
         tpcfit_set_backward_config(self.h, warps_per_block)
+
+    def set_det_reduction(self, method: int = 0):
+        """Deterministic alignment-gradient sums: 0 fixed-point (default), 1 key sort + fixed-order FP32."""
+        tpcfit_set_det_reduction(self.h, method)
 
     def set_fit_form(self, form: int = 1):
         """Factor of the fast fit without material: 1 U-D (default), 0 square root."""

@@ -77,6 +77,7 @@ def test_argument_errors_before_any_cuda_call(lib):
     assert lib.tpcfit_set_mode(None, 1) == tpcfit.EINVAL
     assert lib.tpcfit_set_config(None, 1, 4, 8, 1) == tpcfit.EINVAL
     assert lib.tpcfit_reserve(None, 10, 10) == tpcfit.EINVAL
+    assert lib.tpcfit_set_det_reduction(None, 0) == tpcfit.EINVAL
     assert lib.tpcfit_fit(None, None, None, 0, None, None, None, None, None, None) == tpcfit.EINVAL
     assert lib.tpcfit_get_status(None, None, None, None) == tpcfit.EINVAL
     assert lib.tpcfit_fit_host(None, None, None, None, 0, None, 1, None, None, None, None, None, None) == tpcfit.EINVAL

@@ -127,6 +127,96 @@ def test_deterministic_adjoint_is_bitwise_reproducible(case):
             assert np.array_equal(a.view(np.int32), b.view(np.int32)), (rps, warps, srt, bwd)
 
 
+def _det_reduce(fr, d_true, w, method, shapes=((4, 24, True, 8),)):
+    """Deterministic per-cluster and alignment gradients with the given
+    reduction, in each launch shape (rows per stage, warps, length order,
+    backward warps)."""
+    res = []
+    for rps, warps, srt, bwd in shapes:
+        dev = tf.frame_to_device(fr)
+        f = tf.Fitter(fr.geometry, fr.bz, deterministic=True, rows_per_stage=rps, warps_per_block=warps,
+                      sort_by_length=srt)
+        try:
+            f.set_backward_config(bwd)
+            f.set_det_reduction(method)
+            f.set_alignment(torch.from_numpy(d_true).cuda())
+            f.set_record(True)
+            out = f.fit(dev)
+            gm = torch.empty((fr.n_hits, 2), device="cuda")
+            ga, gs = f.backward(dev, out, torch.from_numpy(w).cuda(), gm)
+            torch.cuda.synchronize()
+            res.append((gm.cpu().numpy(), ga.cpu().numpy()))
+        finally:
+            f.close()
+    return res
+
+
+def _exact_key_sums(fr, gm):
+    """-(sum over each (sector, row) of the per-cluster gradients), in FP64 with
+    a compensated (math.fsum) sum per key."""
+    import math
+    rs = fr.rowsec.astype(np.int64)
+    key = (rs & 63) * 152 + (rs >> 6)
+    out = np.zeros((36 * 152, 2))
+    mag = np.zeros((36 * 152, 2))
+    order = np.argsort(key, kind="stable")
+    ks = key[order]
+    starts = np.flatnonzero(np.r_[True, ks[1:] != ks[:-1]])
+    ends = np.r_[starts[1:], ks.size]
+    g = gm.astype(np.float64)[order]
+    for b, e in zip(starts, ends):
+        out[ks[b], 0] = -math.fsum(g[b:e, 0])
+        out[ks[b], 1] = -math.fsum(g[b:e, 1])
+        mag[ks[b]] = np.abs(g[b:e]).sum(axis=0)
+    return out.reshape(36, 152, 2), mag.reshape(36, 152, 2)
+
+
+def test_deterministic_fixed_point_sums_are_exact_sums_rounded_once(case):
+    # the default reduction: each key's result is the exact sum of the FP32
+    # per-cluster gradients to within one FP32 rounding of the result plus
+    # the fixed-point unit per cluster (2^-S, S = 62 - ceil(log2(H+1)) -
+    # exponent of the largest |g|); the sorted FP32 sums are within the
+    # rounding of an FP32 summation of the same values
+    fr, d_true, w, _ = case
+    (gm, ga), = _det_reduce(fr, d_true, w, 0)
+    exact, mag = _exact_key_sums(fr, gm)
+    amax = np.abs(gm).max()
+    e = np.frexp(amax)[1]
+    cbits = int(np.ceil(np.log2(fr.n_hits + 1)))
+    unit = 2.0 ** (-(62 - cbits - int(e)))
+    n_key = np.bincount(((fr.rowsec.astype(np.int64) & 63) * 152 + (fr.rowsec.astype(np.int64) >> 6)),
+                        minlength=36 * 152).reshape(36, 152, 1)
+    bound = np.abs(exact) * 2.0 ** -23 + n_key * unit * 0.5 + 1e-45
+    assert np.all(np.abs(ga.astype(np.float64) - exact) <= bound)
+    (gm1, ga1), = _det_reduce(fr, d_true, w, 1)
+    assert np.array_equal(gm1.view(np.int32), gm.view(np.int32))  # the reduction does not touch the clusters
+    # an FP32 sum of n terms: within n 2^-24 of the sum of their magnitudes
+    err = np.abs(ga1.astype(np.float64) - exact)
+    assert np.all(err <= n_key * 2.0 ** -24 * mag + 1e-45), (err / np.maximum(mag, 1e-30)).max()
+
+
+def test_both_deterministic_reductions_are_bitwise_reproducible(case):
+    fr, d_true, w, _ = case
+    shapes = ((4, 24, True, 8), (8, 8, False, 4), (16, 8, True, 12))
+    for method in (0, 1):
+        res = _det_reduce(fr, d_true, w, method, shapes) + _det_reduce(fr, d_true, w, method, shapes[:1])
+        for gm, ga in res[1:]:
+            assert np.array_equal(ga.view(np.int32), res[0][1].view(np.int32)), method
+            assert np.array_equal(gm.view(np.int32), res[0][0].view(np.int32)), method
+
+
+def test_det_reduction_setter_rejects_other_values():
+    fr = synth.generate(20, 38)
+    f = tf.Fitter(fr.geometry, fr.bz)
+    try:
+        for bad in (-1, 2):
+            with pytest.raises(tf.TpcfitError) as e:
+                f.set_det_reduction(bad)
+            assert e.value.status == tf.EINVAL
+    finally:
+        f.close()
+
+
 def test_alignment_gradient_matches_fp64_finite_differences():
     # central differences of the FP64 oracle's weighted chi2 sum, step 1e-4 cm,
     # on a 200-track subset of the 100,000-track adjoint workload (its first
