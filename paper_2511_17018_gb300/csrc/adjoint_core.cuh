@@ -909,8 +909,10 @@ namespace tpcfit {
 namespace TPCFIT_NS {
 
 // Fire-and-forget global float add (no value returned, nothing to wait for).
+// No kernel reads the sums back, so the add carries no ordering constraint
+// (no memory clobber): the compiler may schedule other accesses around it.
 __device__ __forceinline__ void red_add(float* p, float v) {
-  asm volatile("red.global.add.f32 [%0], %1;\n" ::"l"(__cvta_generic_to_global(p)), "f"(v) : "memory");
+  asm volatile("red.global.add.f32 [%0], %1;\n" ::"l"(__cvta_generic_to_global(p)), "f"(v));
 }
 
 // prev: what the inward pass left at cluster h (read ahead by the caller; only
@@ -1108,16 +1110,22 @@ __global__ void __launch_bounds__(WARPS * 32, 1) backward_kernel(const __grid_co
             const float2 gcur = gnx;
             if (addg && i > 0) gnx = gmr[h - hd];
             float b_mc[2], b_mp[2];
-            if constexpr (FORM == 1)
+            if constexpr (FORM == 1) {
               step_rev_ud<FIELD>(G, T, &W.st[kk & 1][0][lane], mpy, mpz, T.row_x[prow], side_sector(psec), i == 0,
-                                 pass == 0, row, side_sector(sec), m0, m1, b_p, b_u, b_d, b_chi, b_mc, b_mp);
-            else if (MAT)
-              step_rev_mat<FIELD>(G, T, &W.st[kk & 1][0][lane], mpy, mpz, i == 0, pass == 0, row, side_sector(sec), m0, m1,
-                                  b_p, b_L, b_chi, b_mc, b_mp);
-            else
-              step_rev<FIELD>(G, T, &W.st[kk & 1][0][lane], mpy, mpz, i == 0, pass == 0, row, side_sector(sec), m0, m1,
-                              b_p, b_L, b_chi, b_mc, b_mp);
-            accumulate_meas_grad(a, pass, h, row, sec, b_mc[0] + pend0, b_mc[1] + pend1, gcur);
+                                 pass == 0, row, side_sector(sec), m0, m1, b_p, b_u, b_d, b_chi,
+                                 [&](float g0, float g1) {
+                                   accumulate_meas_grad(a, pass, h, row, sec, g0 + pend0, g1 + pend1, gcur);
+                                 },
+                                 b_mp);
+            } else {
+              if (MAT)
+                step_rev_mat<FIELD>(G, T, &W.st[kk & 1][0][lane], mpy, mpz, i == 0, pass == 0, row, side_sector(sec), m0,
+                                    m1, b_p, b_L, b_chi, b_mc, b_mp);
+              else
+                step_rev<FIELD>(G, T, &W.st[kk & 1][0][lane], mpy, mpz, i == 0, pass == 0, row, side_sector(sec), m0, m1,
+                                b_p, b_L, b_chi, b_mc, b_mp);
+              accumulate_meas_grad(a, pass, h, row, sec, b_mc[0] + pend0, b_mc[1] + pend1, gcur);
+            }
             pend0 = b_mp[0];
             pend1 = b_mp[1];
             m0 = mpy;

@@ -362,11 +362,14 @@ __device__ __forceinline__ void step_fwd_ud(const GeoRef& G, const SmemTables& T
 // Reverse of one step in U-D form; the arguments as for step_rev, with the
 // factor's adjoint (b_u, b_d) in place of b_L, and x_prev, sec_prev (the
 // previous cluster's row position and sector mod 18: the state's frame).
-template <int FIELD = 0>
+// The gradient of the current cluster's measurement is handed to acc(g0, g1)
+// as soon as the update reverses have produced it, so that it is not held
+// through the reverses of the transport and the prediction.
+template <int FIELD = 0, class Acc>
 __device__ __forceinline__ void step_rev_ud(const GeoRef& G, const SmemTables& T, const float4* src, float my_prev,
                                             float mz_prev, float x_prev, int sec_prev, bool first, bool conv, int row,
                                             int sec18, float m0, float m1, float b_p[5], float b_u[10], float b_d[5],
-                                            float b_chi, float b_mc[2], float b_mp[2]) {
+                                            float b_chi, Acc&& acc, float b_mp[2]) {
   UDState S0;
   read_state_ud<false>(src, S0);
   S0.x = x_prev;
@@ -412,19 +415,14 @@ __device__ __forceinline__ void step_rev_ud(const GeoRef& G, const SmemTables& T
   bierman_update<0>(p2, u2, d2, chi_dummy, G.v_meas);
   bierman_update_rev<1>(p2, u2, d2, G.v_meas, b_p, b_u, b_d, b_chi);
   bierman_update_rev<0>(p1, u1, d1, G.v_meas, b_p, b_u, b_d, b_chi);
-  // b_p is now the adjoint of the predicted (shifted) state p1
-  b_mc[0] = -b_p[0];
-  b_mc[1] = -b_p[1];
+  // b_p is now the adjoint of the predicted (shifted) state p1; the current
+  // measurement enters it as -m, except where the inward pass starts from
+  // residuals already and where the step did not move the state
+  const bool none = first ? !conv : !moved;
+  acc(none ? 0.0f : -b_p[0], none ? 0.0f : -b_p[1]);
   b_mp[0] = 0.0f;
   b_mp[1] = 0.0f;
-  if (first) {
-    if (!conv) b_mc[0] = b_mc[1] = 0.0f;  // the inward pass starts from residuals already
-    return;
-  }
-  if (!moved) {
-    b_mc[0] = b_mc[1] = 0.0f;
-    return;
-  }
+  if (first || !moved) return;
   read_state_ud<true>(src, S0);
   JacBar bJ;
   bJ.yy = bJ.ys = bJ.yq = bJ.zy = bJ.zs = bJ.zt = bJ.zq = bJ.sy = bJ.ss = bJ.sq = 0.0f;
