@@ -914,6 +914,12 @@ namespace TPCFIT_NS {
 __device__ __forceinline__ void red_add(float* p, float v) {
   asm volatile("red.global.add.f32 [%0], %1;\n" ::"l"(__cvta_generic_to_global(p)), "f"(v));
 }
+// The same for two adjacent floats at an 8-byte-aligned address (each element
+// added atomically): half the atomic operations at the alignment table, whose
+// keys several lanes hit at once.
+__device__ __forceinline__ void red_add2(float* p, float v0, float v1) {
+  asm volatile("red.global.add.v2.f32 [%0], {%1, %2};\n" ::"l"(__cvta_generic_to_global(p)), "f"(v0), "f"(v1));
+}
 
 // prev: what the inward pass left at cluster h (read ahead by the caller; only
 // the outward pass, pass 0, adds to it).
@@ -929,8 +935,12 @@ __device__ __forceinline__ void accumulate_meas_grad(const BwdArgs& a, int pass,
   }
   if (a.grad_align_atomic) {
     float* dst = a.grad_align_atomic + (sec * kMaxRows + row) * 2;
-    red_add(dst, -g0);
-    red_add(dst + 1, -g1);
+    if ((reinterpret_cast<uintptr_t>(dst) & 7u) == 0) {
+      red_add2(dst, -g0, -g1);  // one atomic for the key's (dy, dz) pair
+    } else {
+      red_add(dst, -g0);
+      red_add(dst + 1, -g1);
+    }
   }
 }
 
