@@ -390,6 +390,21 @@ def run_batched_frames(args, tf, torch, synth, flops, peak_tf):
                      "fitted_fraction": float((g.out["ndf"] > 0).float().mean().item())}
         del g
         f.close()
+    if not args.no_cpu_baseline:
+        # the oracle's FP64 fit on a slice of the pool the frames are drawn
+        # from, its per-track rate extrapolated to the batch
+        import oracle
+        threads = oracle.default_threads()
+        take = min(pool.n_tracks, 100_000)
+        sub = pool.subset(np.arange(take))
+        t0 = time.perf_counter()
+        oracle.fit(sub, "f64", nthreads=threads)
+        dt = time.perf_counter() - t0
+        res["cpu_baseline"] = {"value": take / dt, "unit": UNIT, "cores": threads, "kind": "oracle",
+                               "sample": f"first {take} tracks of the frames' pool: FP64 fit, {threads} threads, "
+                                         f"{dt:.2f} s",
+                               "extrapolated_batch_s": batch.n_tracks / (take / dt),
+                               "note": "the sample's per-track rate extrapolated to the batch's tracks"}
     del batch
     torch.cuda.empty_cache()
     return res
@@ -793,6 +808,16 @@ def main():
         torch.cuda.empty_cache()
         line["batched_frames"] = run_batched_frames(args, tf, torch, synth, flops, peak_tf)
         line["alignment_loop"] = run_alignment_loop(args, tf, torch, synth)
+        if "cpu_baseline" in line:
+            # one iteration = fit + gradient of every track: the oracle's rate on
+            # the time-frame sample, extrapolated to the loop's tracks
+            n_al = args.align_tracks
+            line["alignment_loop"]["cpu_baseline"] = {
+                "value": line["cpu_baseline"]["value"], "unit": UNIT, "kind": "oracle",
+                "cores": line["cpu_baseline"]["cores"],
+                "extrapolated_s_per_iteration": n_al / line["cpu_baseline"]["value"],
+                "note": "fit + forward-mode gradient rate of the time-frame sample (same track distributions), "
+                        "extrapolated to the loop's tracks"}
     print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()
